@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the data-driven H^2 construction (arXiv 2206.01885) on one GB300.
+
+A step is one pass of the whole path over one synthetic problem: Morton tree
+and near/far lists, HiDR, level-by-level kernel blocks + pivoted-QR
+interpolative decompositions, the H^2 matvec of a standard-normal vector, the
+exact float64 sums on 1000 sampled rows and the relative error on those rows.
+The default workload is 1,048,576 uniform points in [0,1]^3 with the Coulomb
+kernel, leaf size 256, ID tolerance 1e-8 in float64 (r1 = r2 = g^3 chosen from
+epsilon by the section 4.2 calibration, outside the timed region).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2206_01885_gb300 import inputs as I  # noqa: E402
+
+METRIC = "H² build ms & points/s, n=1M 3D Coulomb, rel err≤1e-8: mixed vs FP64 GPU"
+
+WORKLOADS = {
+    # n, dim, kernel, kparams, leaf size, ID tolerance, precision, seed, sampled rows
+    "cube1m_fp64": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-8, prec="fp64", seed=2,
+                        rows=1000),
+    "cube1m_mixed": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-5, prec="mixed", seed=2,
+                         rows=1000),
+    "cube8k_fp64": dict(n=8000, d=3, kernel="coulomb", kparams=(), q=200, eps=1e-6, prec="fp64", seed=1,
+                        rows=1000),
+}
+# same-size unit cells at integer offset v are well separated under eq. (1)
+# with tau = 7/10 when |v|^2 >= 8 (3D) / 5 (2D)
+MIN_SQ = {3: 8, 2: 5}
+
+# Peaks: HBM and bf16 are the measured copy / cuBLAS figures of this GPU pool;
+# the float64 and float32 ALU peaks are derived from 152 SMs at 2070 MHz:
+# float64 1.25 TFLOP/s (the GB300 nominal dense rate), float32 152 x 128 lanes
+# x 2 flops x 2.07 GHz = 80.5 TFLOP/s.
+PEAK_FP64_TFLOPS = 1.25
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FLOPS_PER_PAIR = 11  # 3 sub, 3 mul/add for r^2 (5 flops), 1 rsqrt, 1 fma accumulate (2 flops)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------- GPU arm
+def gpu_arm(args, wl, rank, world, dev):
+    import torch
+
+    from paper_2206_01885_gb300 import build as B
+    B.build()
+    from paper_2206_01885_gb300 import h2
+
+    torch.cuda.set_device(dev)
+    n, d = wl["n"], wl["d"]
+    seed = wl["seed"] + 1000 * rank  # independent problem per rank
+    pts = I.uniform_cube(n, d, seed=seed)
+    z = I.standard_normal(n, seed=seed + 7)
+    rows = I.sample_rows(n, wl["rows"], seed=seed + 9)
+    pts_d = torch.from_numpy(pts).to(dev)
+    z_d = torch.from_numpy(z).to(dev)
+    rows_d = torch.from_numpy(rows).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    # r1 = r2 = g^d from epsilon (Algorithm 2 step 2), data-independent
+    t0 = time.perf_counter()
+    z1, z2 = I.calibration_sets(d, MIN_SQ[d])
+    g, cal_err = h2.calibrate(d, wl["kernel"], wl["kparams"], wl["eps"], z1, z2, gmax=16)
+    cal_ms = (time.perf_counter() - t0) * 1e3
+    if g > 16:
+        raise RuntimeError(f"calibration did not converge for eps={wl['eps']}")
+
+    def step(p_in, z_in, rows_in):
+        t = h2.Tree(p_in, wl["q"])
+        hd = h2.Hidr(t, g, g)
+        A = h2.H2Matrix(t, hd, wl["kernel"], wl["kparams"], wl["eps"], wl["prec"])
+        y = A.matvec(z_in)
+        ex = h2.exact_rows(t, wl["kernel"], wl["kparams"], z_in, rows_in)
+        err = h2.sampled_error(ex, y, rows_in)
+        info = (json.loads(t.stats()), json.loads(hd.stats()), json.loads(A.stats()))
+        return t, hd, A, y, err, info
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        out = step(pts_d, z_d, rows_d)
+        del out
+    torch.cuda.synchronize()
+    last = None
+    h2.profile(True, True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    step_ms = []
+    infos = []
+    for _ in range(args.steps):
+        flush.zero_()  # evict L2 between steps (outside the timed interval)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t, hd, A, y, err, info = step(pts_d, z_d, rows_d)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+        if last is not None:
+            for o in last:
+                o.free()
+        last = (A, hd, t)
+        last_err = float(err.item())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ktimes = h2.kernel_times()
+    h2.profile(False, False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    A, hd, t = last
+
+    # algorithmic work of the last step (identical every step)
+    ranks = A.get("rank").astype(np.int64)
+    far_ptr, far_idx = t.get("far_ptr"), t.get("far_idx")
+    near_ptr, near_idx = t.get("near_ptr"), t.get("near_idx")
+    sizes = (t.get("end") - t.get("begin")).astype(np.int64)
+    rowsof = np.repeat(np.arange(t.nnodes), np.diff(far_ptr))
+    coupling_pairs = int(np.sum(ranks[rowsof] * ranks[far_idx]))
+    nrow = np.repeat(np.arange(t.nnodes), np.diff(near_ptr))
+    near_pairs = int(np.sum(sizes[nrow] * sizes[near_idx]))
+    tree_i, hidr_i, mat_i = infos[-1]
+    qr_flops = mat_i["qr_flops"]
+    block_evals = mat_i["block_evals"]
+
+    # roofline of the dominant kernel over the timed region
+    fp64 = wl["prec"] == "fp64"
+    alu_peak = PEAK_FP64_TFLOPS if fp64 else PEAK_FP32_TFLOPS
+    work = {  # kernel -> algorithmic flops per step
+        "cpqr": qr_flops,
+        "coupling": coupling_pairs * FLOPS_PER_PAIR,
+        "near": near_pairs * FLOPS_PER_PAIR,
+        "keval": block_evals * FLOPS_PER_PAIR,
+    }
+    dom = max(ktimes, key=lambda k: ktimes[k]["ms"])
+    dom_ms_per_launch = ktimes[dom]["ms"] / max(1, ktimes[dom]["launches"])
+    launches_per_step = ktimes[dom]["launches"] / args.steps
+    if dom in work:
+        achieved = work[dom] / launches_per_step / (dom_ms_per_launch * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": "derived: GB300 nominal float64" if fp64 else "derived: 152 SMs x 128 x 2 x 2.07 GHz"}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None}
+
+    gpu_launches = int(sum(v["launches"] for v in ktimes.values()) / 1)
+
+    # end-to-end through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if rank == 0 or world > 1:
+        pts_h = torch.from_numpy(pts).pin_memory()
+        z_h = torch.from_numpy(z).pin_memory()
+        rows_h = torch.from_numpy(rows)
+        e2e_ms = []
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            t2 = h2.Tree(pts_h.numpy(), wl["q"])
+            hd2 = h2.Hidr(t2, g, g)
+            A2 = h2.H2Matrix(t2, hd2, wl["kernel"], wl["kparams"], wl["eps"], wl["prec"])
+            y_h = A2.matvec(z_h.numpy())
+            ex_h = h2.exact_rows(t2, wl["kernel"], wl["kparams"], z_h.numpy(), rows_h.numpy())
+            err_h = h2.sampled_error(ex_h, y_h, rows_h.numpy())
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - w0) * 1e3)
+            A2.free()
+            hd2.free()
+            t2.free()
+        r = len(rows)
+        e2e = {"value": n / (statistics.median(e2e_ms) * 1e-3), "unit": "points/s",
+               "h2d_bytes_per_step": 8 * (d * n + n + n + r + n + r + r), "d2h_bytes_per_step": 8 * (n + r + 1),
+               "ms_per_step": statistics.median(e2e_ms), "rel_err": err_h}
+
+    ms_per_step = total_ms / args.steps
+    phases = {
+        "tree_ms": tree_i["ms_tree"], "lists_ms": tree_i["ms_lists"], "hidr_ms": hidr_i["ms_up"] + hidr_i["ms_down"],
+        "construct_ms": mat_i["ms_construct"],
+    }
+    phases["build_ms"] = phases["tree_ms"] + phases["lists_ms"] + phases["hidr_ms"] + phases["construct_ms"]
+    result = {
+        "metric": METRIC,
+        "value": world * n / (ms_per_step * 1e-3),
+        "unit": "points/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if fp64 else "f32+f64",
+        "data": "synthetic (seeded uniform cube, standard-normal right-hand side)",
+        "config": {"workload": args.workload, "n": n, "dim": d, "kernel": wl["kernel"], "leaf_size": wl["q"],
+                   "id_tol": wl["eps"], "precision": wl["prec"], "g": g, "r1": g ** d, "r2": g ** d,
+                   "tau": "7/10", "sampled_rows": len(rows), "rhs": 1,
+                   "l2": "flushed (256 MB write) between timed steps, outside the timed interval",
+                   "parallelism": f"{world} independent problem(s), one per GPU"},
+        "rel_err": last_err,
+        "phases_ms": phases,
+        "calibration": {"ms": cal_ms, "g": g, "error": cal_err},
+        "counts": {"nodes": tree_i["nodes"], "levels": tree_i["levels"], "near_pairs": tree_i["near_pairs"],
+                   "far_pairs": tree_i["far_pairs"], "k_total": mat_i["k_total"], "k_max": mat_i["k_max"],
+                   "qr_flops": qr_flops, "block_evals": block_evals, "coupling_evals": coupling_pairs,
+                   "near_evals": near_pairs},
+        "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in ktimes.items() if v["launches"]},
+        "roofline": roof,
+        "clocks": clocks,
+        "gpu_launches": gpu_launches,
+        "e2e": e2e,
+    }
+    return result
+
+
+# ----------------------------------------------------------- CPU oracle
+def oracle_sample(wl, n_s):
+    """One bounded-sample run of the CPU oracle: the same distribution, leaf
+    size, kernel and tolerance at n_s points (calibrated g as on the GPU)."""
+    from oracle import h2_oracle as O
+    d = wl["d"]
+    pts = I.uniform_cube(n_s, d, seed=wl["seed"])
+    z = I.standard_normal(n_s, seed=wl["seed"] + 7)
+    rows = I.sample_rows(n_s, wl["rows"], seed=wl["seed"] + 9)
+    g = wl.get("g_oracle")
+    t0 = time.perf_counter()
+    t = O.tree_build(pts, wl["q"])
+    h = O.Hidr(t, g, g)
+    H = O.H2(t, h, wl["kernel"], wl["kparams"], wl["eps"])
+    y = H.matvec(z)
+    ex = O.exact_rows(pts, wl["kernel"], wl["kparams"], z, rows)
+    err = float(np.linalg.norm(ex - y[rows]) / np.linalg.norm(ex))
+    return time.perf_counter() - t0, err
+
+
+def oracle_g(wl):
+    from oracle import h2_oracle as O
+    z1, z2 = I.calibration_sets(wl["d"], MIN_SQ[wl["d"]])
+    return O.calibrate(wl["d"], wl["kernel"], wl["kparams"], wl["eps"], z1, z2, gmax=16)
+
+
+def cpu_baseline(wl, n_s):
+    from oracle import h2_oracle as O
+    wl = dict(wl)
+    wl["g_oracle"] = oracle_g(wl)
+    sec, err = oracle_sample(wl, n_s)
+    return {"value": n_s / sec, "unit": "points/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n_s} points of the same distribution, leaf size, kernel, tolerance and grid size "
+                      f"(g={wl['g_oracle']}): tree + lists + HiDR + construction + matvec + {wl['rows']} exact rows",
+            "seconds": sec, "rel_err": err}
+
+
+def reference_arm(args, wl):
+    from oracle import h2_oracle as O
+    wl = dict(wl)
+    wl["g_oracle"] = oracle_g(wl)
+    n_s = args.cpu_sample
+    for _ in range(args.warmup):
+        oracle_sample(wl, min(n_s, 4096))
+    secs, errs = [], []
+    for _ in range(args.steps):
+        s, e = oracle_sample(wl, n_s)
+        secs.append(s)
+        errs.append(e)
+    v = n_s / statistics.median(secs)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(secs) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded uniform cube)",
+            "config": {"workload": args.workload, "n": n_s, "leaf_size": wl["q"], "id_tol": wl["eps"],
+                       "g": wl["g_oracle"], "note": "bounded sample of the workload on the host cores"},
+            "rel_err": errs[-1],
+            "cpu_baseline": {"value": v, "unit": "points/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{n_s} points per step"},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube1m_fp64", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-sample", type=int, default=65536)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference_arm(args, wl)), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = gpu_arm(args, wl, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample)
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * h2.h -- C ABI of the GB300 (sm_103a) library for the data-driven H^2
+ * construction of Cai, Huang, Chow and Xi, "Data-Driven Construction of
+ * Hierarchical Matrices with Nested Bases" (arXiv 2206.01885).
+ *
+ * Pipeline (each call consumes the previous call's handle):
+ *   h2_tree_build   adaptive Morton cluster tree + near/far interaction lists
+ *                   (section 2.1, eq. (1); Algorithm 2 step 1)
+ *   h2_calibrate    grid size g with r1 = r2 = g^d from epsilon (section 4.2;
+ *                   Algorithm 2 step 2)
+ *   h2_hidr_reduce  hierarchical data reduction X_i*, Y_i* (section 3,
+ *                   Algorithm 1; Algorithm 2 step 3)
+ *   h2_construct    level-by-level kernel blocks K(Y_i*, Xbar_i) and pivoted-QR
+ *                   interpolative decompositions giving skeletons Xhat_i and
+ *                   nested bases U_i (section 4.1 eqs. (3)-(5); Algorithm 2
+ *                   steps 4-14)
+ *   h2_matvec       y = K~ x, the O(n) H^2 product (section 2.1)
+ *   h2_exact_rows   exact (K z)_s on sampled rows, for the section 6 error
+ *
+ * Conventions shared by every call:
+ *   - Points are float64, row-major n x dim (point i at pts[i*dim + k]), in
+ *     the caller's original order.  dim is 2 or 3.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     queued on it; calls that must learn sizes (tree levels, list lengths,
+ *     per-level ranks) synchronise that stream internally.  A handle's later
+ *     calls may use another stream only after the first stream is synchronised.
+ *   - Pointers flagged `*_on_device` are device pointers of the current CUDA
+ *     device; otherwise host pointers (pageable or pinned).  The caller owns
+ *     every buffer it passes; the library copies what it keeps.
+ *   - Handles are opaque, owned by the library and released only by h2_free.
+ *     A tree must outlive every hidr and matrix built on it (h2_free of a tree
+ *     with live dependents returns H2_ERR_STATE and frees nothing).
+ *   - No call aborts the process.  Errors return a status and set a
+ *     thread-local message read by h2_last_error().  Device-side faults
+ *     surface as H2_ERR_CUDA at the next synchronising call.
+ *   - There is no CPU fallback: every step runs in this library's kernels.
+ */
+#ifndef H2_GB300_H
+#define H2_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    H2_OK = 0,
+    H2_ERR_INVALID_ARG = 1,   /* bad pointer, size, kernel id, parameter      */
+    H2_ERR_OOM = 2,           /* device allocation failed                      */
+    H2_ERR_CUDA = 3,          /* a CUDA runtime call or kernel failed          */
+    H2_ERR_TIMEOUT = 4,       /* a bounded device wait gave up                 */
+    H2_ERR_NUMERIC = 5,       /* non-finite value met                          */
+    H2_ERR_UNIMPLEMENTED = 6, /* option not built                              */
+    H2_ERR_STATE = 7          /* handle in the wrong state / has dependents    */
+} h2_status;
+
+/* kernel functions kappa(x, y) as functions of r = |x - y| (section 2, Table 1) */
+typedef enum {
+    H2_K_COULOMB = 1,      /* 1/r, and kappa(x, x) = 0 (Table 1 caption)       */
+    H2_K_GAUSSIAN = 2,     /* exp(-r^2 / h^2), kparams[0] = h                  */
+    H2_K_EXPONENTIAL = 3,  /* exp(-r / l), kparams[0] = l                      */
+    H2_K_MULTIQUADRIC = 4  /* sqrt(1 + r^2)                                    */
+} h2_kernel_id;
+
+/* arithmetic of h2_construct / h2_matvec */
+typedef enum {
+    H2_PREC_FP64 = 0,  /* everything in float64                                */
+    H2_PREC_MIXED = 1  /* float32 kernel blocks and QR updates; float64 column
+                          norms, pivots and R11^{-1} R12 solve                  */
+} h2_precision;
+
+typedef struct h2_tree_s *h2_tree;
+typedef struct h2_hidr_s *h2_hidr;
+typedef struct h2_matrix_s *h2_matrix;
+
+/* Algorithm 2 inputs "separation ratio tau" and "leaf size q".  tau is the
+ * rational tau_num / tau_den so that eq. (1) is decided exactly in integers
+ * (default 7/10, the top of the paper's range [0, 0.7]). */
+typedef struct {
+    int leaf_size; /* q >= 1: a node holding more than q points is split      */
+    int tau_num;   /* >= 0                                                     */
+    int tau_den;   /* >= 1                                                     */
+} h2_tree_params;
+
+/* ---------------------------------------------------------------- tree --- */
+/* Section 2.1 ("recursively partitioning X spatially until no more than m
+ * points are contained in each subset"), eq. (1) admissibility, and the
+ * interaction list; Algorithm 2 step 1.
+ * pts: n x dim float64 (device if pts_on_device, else host), n >= 1,
+ * n < 2^31.  The root box is the cube of side max_k(max x_k - min x_k) at the
+ * componentwise minimum; coordinates are quantised to 21 (dim 3) or 31
+ * (dim 2) bits and Morton-interleaved (coordinate 0 in the lowest bit); points
+ * are stably sorted by key.  A node splits while it holds more than q points;
+ * children are its non-empty orthants in key order; nodes are numbered level by
+ * level, then by key.  Near/far lists come from a dual traversal from
+ * (root, root): an admissible pair is far, a pair of leaves is near, otherwise
+ * every non-leaf side is split.  Errors: H2_ERR_INVALID_ARG (null pointers,
+ * n < 1, dim not 2/3, q < 1, bad tau), H2_ERR_OOM, H2_ERR_CUDA. */
+h2_status h2_tree_build(const double *pts, int64_t n, int dim, int pts_on_device,
+                        const h2_tree_params *params, void *stream, h2_tree *out);
+
+/* what for h2_tree_get (element type, length):
+ *   H2_TREE_PERM      int64 [n]          Morton position -> original index
+ *   H2_TREE_KEYS      uint64 [n]         sorted Morton keys
+ *   H2_TREE_LEVEL, H2_TREE_PARENT, H2_TREE_FCHILD, H2_TREE_NCHILD  int32 [nnodes]
+ *                                        (parent of root = -1, fchild of leaf = -1)
+ *   H2_TREE_BEGIN, H2_TREE_END  int64 [nnodes]  point range in Morton order
+ *   H2_TREE_PREFIX    uint64 [nnodes]    key >> dim*(B - level)
+ *   H2_TREE_LPTR      int32 [nlevels+1]  nodes of level l: [lptr[l], lptr[l+1])
+ *   H2_TREE_NEAR_PTR, H2_TREE_FAR_PTR   int64 [nnodes+1]  CSR row pointers
+ *   H2_TREE_NEAR_IDX, H2_TREE_FAR_IDX   int32 [nnear] / [nfar], rows sorted
+ *   H2_TREE_INFO      int64 [8]: n, dim, B, nnodes, nlevels, nnear, nfar, q
+ *   H2_TREE_GEOM      float64 [4]: lo[0..2] (unused entries 0), side
+ * host_buf may be NULL to query *len (in elements).  Synchronises the tree's
+ * stream.  Errors: H2_ERR_INVALID_ARG (unknown what, cap too small). */
+enum {
+    H2_TREE_PERM = 0, H2_TREE_KEYS = 1, H2_TREE_LEVEL = 2, H2_TREE_PARENT = 3,
+    H2_TREE_FCHILD = 4, H2_TREE_NCHILD = 5, H2_TREE_BEGIN = 6, H2_TREE_END = 7,
+    H2_TREE_PREFIX = 8, H2_TREE_LPTR = 9, H2_TREE_NEAR_PTR = 10, H2_TREE_FAR_PTR = 11,
+    H2_TREE_NEAR_IDX = 12, H2_TREE_FAR_IDX = 13, H2_TREE_INFO = 14, H2_TREE_GEOM = 15
+};
+h2_status h2_tree_get(h2_tree t, int what, void *host_buf, int64_t cap, int64_t *len);
+
+/* ----------------------------------------------------------- calibrate --- */
+/* Section 4.2: r1 = r2 = g^dim is raised from g = 1 until the interpolative
+ * decomposition of the artificial block K(Z2*, Z1), Z2* = DataReduct(Z2, g),
+ * reproduces K(Z1, Z2) with relative Frobenius error < 1e-2 * eps; the ID in
+ * this test is itself truncated at 1e-2 * eps.  z1 (n1 x dim) and z2
+ * (n2 x dim) are host float64 point sets that the caller draws well separated
+ * in the sense of eq. (1).  Runs on the GPU with the library's own DataReduct,
+ * kernel-block and ID kernels.  *g_out = the smallest g <= gmax that passes, or
+ * gmax + 1 if none does; *err_out (may be NULL) = that g's error.
+ * Synchronises `stream`.  Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
+h2_status h2_calibrate(int dim, int kernel, const double *kparams, double eps,
+                       const double *z1, int n1, const double *z2, int n2, int gmax,
+                       void *stream, int *g_out, double *err_out);
+
+/* ---------------------------------------------------------------- HiDR --- */
+/* Section 3.1-3.3 and Algorithm 1.  Bottom-up from the deepest level:
+ * S_i = X_i for a leaf, the union of the children's X_c* otherwise, and
+ * X_i* = DataReduct(S_i, g1^dim).  Top-down from level 1:
+ * T_i = Y_p* union X_j* over j in the interaction (far) list of i, and
+ * Y_i* = DataReduct(T_i, g2^dim) (empty when T_i is).  DataReduct(S, g^d) is the
+ * volume-based variant used in section 6: S itself when |S| <= g^d; otherwise
+ * the nearest point of S (float64 squared distance, ties to the smaller
+ * Morton position) to each cell-centred point of a g^d tensor grid on the
+ * bounding box of S, deduplicated.  Sets are stored as sorted Morton
+ * positions.  Kernel-independent: one hidr serves every kernel.
+ * g1, g2 >= 1 (g^dim <= 32768).  Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM,
+ * H2_ERR_CUDA. */
+h2_status h2_hidr_reduce(h2_tree t, int g1, int g2, void *stream, h2_hidr *out);
+
+/* which: 0 = X_i*, 1 = Y_i*.  Fills counts (int32 [nnodes], may be NULL) and,
+ * if data is not NULL, the concatenation over nodes in node order of the
+ * sorted Morton positions (int32, cap elements).  *total = sum of counts.
+ * Synchronises. */
+h2_status h2_hidr_get(h2_hidr h, int which, int32_t *counts, int32_t *data, int64_t cap,
+                      int64_t *total);
+
+/* ----------------------------------------------------------- construct --- */
+/* Section 4.1 eqs. (3)-(5) and Algorithm 2 steps 4-14.  For levels from the
+ * deepest to 1 and every node i with Y_i* non-empty: Xbar_i = X_i for a leaf,
+ * the concatenation of the children's skeletons (child order, each sorted) for a
+ * parent; A_i = K(Y_i*, Xbar_i) (|Y_i*| x |Xbar_i|); column-pivoted Householder
+ * QR of A_i (pivot = largest downdated column norm, ties to the first column;
+ * LAPACK-style downdating with recomputation); stop at the first step j whose
+ * pivot norm <= id_tol * |r_11|, so k_i = j; G^T = R11^{-1} R12; skeleton
+ * Xhat_i = the k_i pivoted candidates, stored sorted by Morton position;
+ * U_i = P [I; G] (|Xbar_i| x k_i, columns in skeleton order).  For a leaf U_i
+ * is the leaf basis, for a parent it stacks the transfer matrices R_c.
+ * Coupling blocks B_ij = K(Xhat_i, Xhat_j) and nearfield blocks K(X_i, X_j)
+ * are kernel submatrices and are evaluated inside h2_matvec.
+ * kparams: 4 float64 (host; may be NULL for Coulomb / multiquadric).
+ * precision: H2_PREC_FP64 or H2_PREC_MIXED.  id_tol >= 0.
+ * Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM, H2_ERR_CUDA, H2_ERR_UNIMPLEMENTED. */
+h2_status h2_construct(h2_tree t, h2_hidr h, int kernel, const double *kparams, double id_tol,
+                       int precision, void *stream, h2_matrix *out);
+
+/* what for h2_matrix_get:
+ *   H2_MAT_RANK   int32 [nnodes]  k_i (0 where Y_i* is empty; 0 for the root)
+ *   H2_MAT_NCAND  int32 [nnodes]  |Xbar_i|
+ *   H2_MAT_SKEL   int32 [sum k_i] skeletons in node order, each sorted
+ *   H2_MAT_U      float64 [sum |Xbar_i| k_i] U_i in node order, each column-major
+ *   H2_MAT_INFO   int64 [4]: sum k_i, sum |Xbar_i| k_i, max k_i, levels
+ * Synchronises. */
+enum { H2_MAT_RANK = 0, H2_MAT_NCAND = 1, H2_MAT_SKEL = 2, H2_MAT_U = 3, H2_MAT_INFO = 4 };
+h2_status h2_matrix_get(h2_matrix A, int what, void *host_buf, int64_t cap, int64_t *len);
+
+/* -------------------------------------------------------------- matvec --- */
+/* y = K~ x with the H^2 representation (section 2.1): upward pass
+ * xh_i = U_i^T x_i (leaves) and xh_p = U_p^T [xh_c ...] (parents); coupling
+ * zh_i = sum_{j far from i} K(Xhat_i, Xhat_j) xh_j; downward pass
+ * [zh_c ...] += U_p zh_p and y_i = U_i zh_i; nearfield y_i += K(X_i, X_j) x_j
+ * over near leaf pairs.  x, y: n float64 in the original point order (device
+ * pointers if on_device, else host; host buffers are copied in and out on
+ * `stream` and the call synchronises).  x and y must not overlap.
+ * Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
+h2_status h2_matvec(h2_matrix A, const double *x, double *y, int on_device, void *stream);
+
+/* ---------------------------------------------------------- exact rows --- */
+/* The reference of the section 6 error ||K z - K~ z|| / ||K z||: for each
+ * row s in rows (original indices), out[s'] = sum_j kappa(x_s, x_j) z_j over
+ * all n points, in float64 (kappa(x, x) = 0 for Coulomb).  z: n float64,
+ * rows: nrows int64, out: nrows float64; all device if on_device, else host
+ * (then the call synchronises).  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
+h2_status h2_exact_rows(h2_tree t, int kernel, const double *kparams, const double *z,
+                        const int64_t *rows, int64_t nrows, double *out, int on_device,
+                        void *stream);
+
+/* The section 6 error on sampled rows: *err_out = ||exact - approx[rows]||_2
+ * / ||exact||_2, with exact[r] = (K z)_{rows[r]} from h2_exact_rows and approx
+ * the full H^2 product (n entries, original order).  Device pointers if
+ * on_device (err_out then a device scalar), else host (the call then
+ * synchronises).  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
+h2_status h2_sampled_error(const double *exact, const double *approx, const int64_t *rows, int64_t nrows,
+                           int64_t n, double *err_out, int on_device, void *stream);
+
+/* ------------------------------------------------------------- common --- */
+/* Release any handle returned above (NULL is a no-op).  Device memory is
+ * returned on the handle's stream, which must still exist. */
+h2_status h2_free(void *handle);
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char *h2_last_error(void);
+
+/* JSON object with counters and per-phase device times (ms) of a tree, hidr
+ * or matrix handle, written to json (cap bytes, NUL-terminated).  With
+ * handle == NULL: the per-kernel totals {"name": {"ms", "launches"}} collected
+ * while profiling is enabled. */
+h2_status h2_get_stats(const void *handle, char *json, int64_t cap);
+
+/* Per-kernel timing: when enabled, the main kernels are bracketed by CUDA
+ * events on the stream they are launched on; `reset` zeroes the totals.
+ * Off by default. */
+h2_status h2_profile(int enable, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2_GB300_H */

@@ -1,0 +1,481 @@
+// capi.cu -- the extern "C" boundary declared in include/h2.h.  Validates
+// arguments, owns handle lifetimes and turns internal exceptions into
+// h2_status values plus a thread-local message.  Every compute step runs in
+// the library's CUDA kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "h2_internal.cuh"
+
+namespace {
+thread_local std::string g_last_error;
+
+void set_error(const std::string &m) { g_last_error = m; }
+
+template <class F>
+h2_status guard(F &&f) {
+    try {
+        g_last_error.clear();
+        f();
+        return H2_OK;
+    } catch (const h2::Error &e) {
+        set_error(e.msg);
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return H2_ERR_OOM;
+    } catch (...) {
+        set_error("unknown error");
+        return H2_ERR_CUDA;
+    }
+}
+
+bool valid_kernel(int kid) { return kid >= H2_K_COULOMB && kid <= H2_K_MULTIQUADRIC; }
+
+void kparams_check(int kid, const double *kp, double out[4]) {
+    for (int a = 0; a < 4; a++) out[a] = kp ? kp[a] : 0.0;
+    if (kid == H2_K_GAUSSIAN || kid == H2_K_EXPONENTIAL) {
+        H2_REQUIRE(kp != nullptr, "this kernel needs kparams[0]");
+        H2_REQUIRE(std::isfinite(out[0]) && out[0] > 0.0, "kparams[0] must be a positive length");
+    }
+}
+
+void pool_keep_memory() {
+    static bool done = false;
+    if (done) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
+    done = true;
+}
+
+template <class T>
+void copy_out(const std::vector<T> &v, void *buf, int64_t cap, int64_t *len) {
+    if (len) *len = (int64_t)v.size();
+    if (!buf) return;
+    H2_REQUIRE(cap >= (int64_t)v.size(), "output buffer too small");
+    if (!v.empty()) memcpy(buf, v.data(), v.size() * sizeof(T));
+}
+
+template <class Tsrc, class Tdst>
+std::vector<Tdst> widen(const std::vector<Tsrc> &v) {
+    return std::vector<Tdst>(v.begin(), v.end());
+}
+}  // namespace
+
+namespace h2 {
+h2_tree_s *as_tree(void *h) {
+    auto *t = static_cast<h2_tree_s *>(h);
+    if (!t || t->tag != TAG_TREE) fail(H2_ERR_INVALID_ARG, "not a tree handle");
+    return t;
+}
+h2_hidr_s *as_hidr(void *h) {
+    auto *t = static_cast<h2_hidr_s *>(h);
+    if (!t || t->tag != TAG_HIDR) fail(H2_ERR_INVALID_ARG, "not a hidr handle");
+    return t;
+}
+h2_matrix_s *as_matrix(void *h) {
+    auto *t = static_cast<h2_matrix_s *>(h);
+    if (!t || t->tag != TAG_MATRIX) fail(H2_ERR_INVALID_ARG, "not a matrix handle");
+    return t;
+}
+}  // namespace h2
+
+using namespace h2;
+
+extern "C" {
+
+const char *h2_last_error(void) { return g_last_error.c_str(); }
+
+h2_status h2_tree_build(const double *pts, int64_t n, int dim, int pts_on_device, const h2_tree_params *params,
+                        void *stream, h2_tree *out) {
+    return guard([&] {
+        H2_REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        H2_REQUIRE(pts != nullptr, "pts is NULL");
+        H2_REQUIRE(params != nullptr, "params is NULL");
+        H2_REQUIRE(n >= 1 && n < (int64_t)INT32_MAX, "n must be in [1, 2^31 - 1)");
+        H2_REQUIRE(dim == 2 || dim == 3, "dim must be 2 or 3");
+        H2_REQUIRE(params->leaf_size >= 1, "leaf_size must be >= 1");
+        H2_REQUIRE(params->tau_num >= 0 && params->tau_den >= 1, "tau must be tau_num/tau_den with tau_den >= 1");
+        pool_keep_memory();
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        auto *t = new h2_tree_s();
+        try {
+            t->stream = s;
+            t->n = n;
+            t->d = dim;
+            t->B = dim == 3 ? 21 : 31;
+            t->q = params->leaf_size;
+            t->tau_num = params->tau_num;
+            t->tau_den = params->tau_den;
+            DevBuf<double> tmp;
+            const double *pd = pts;
+            if (!pts_on_device) {
+                tmp.alloc((size_t)n * dim, s);
+                H2_CUDA(cudaMemcpyAsync(tmp.p, pts, (size_t)n * dim * sizeof(double), cudaMemcpyHostToDevice, s));
+                pd = tmp.p;
+            }
+            cudaEvent_t e0, e1, e2;
+            H2_CUDA(cudaEventCreate(&e0));
+            H2_CUDA(cudaEventCreate(&e1));
+            H2_CUDA(cudaEventCreate(&e2));
+            H2_CUDA(cudaEventRecord(e0, s));
+            tree_build_impl(t, pd);
+            H2_CUDA(cudaEventRecord(e1, s));
+            lists_build_impl(t);
+            H2_CUDA(cudaEventRecord(e2, s));
+            H2_CUDA(cudaEventSynchronize(e2));
+            float a = 0, b = 0;
+            cudaEventElapsedTime(&a, e0, e1);
+            cudaEventElapsedTime(&b, e1, e2);
+            t->ms_tree = a;
+            t->ms_lists = b;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaEventDestroy(e2);
+        } catch (...) {
+            t->tag = TAG_DEAD;
+            delete t;
+            throw;
+        }
+        *out = t;
+    });
+}
+
+h2_status h2_tree_get(h2_tree th, int what, void *buf, int64_t cap, int64_t *len) {
+    return guard([&] {
+        h2_tree_s *t = as_tree(th);
+        cudaStream_t s = t->stream;
+        const int nn = t->nnodes;
+        switch (what) {
+        case H2_TREE_PERM: copy_out(widen<int32_t, int64_t>(read_vec(t->perm.p, t->n, s)), buf, cap, len); break;
+        case H2_TREE_KEYS: copy_out(read_vec(t->key.p, t->n, s), buf, cap, len); break;
+        case H2_TREE_LEVEL: copy_out(read_vec(t->level.p, nn, s), buf, cap, len); break;
+        case H2_TREE_PARENT: copy_out(read_vec(t->parent.p, nn, s), buf, cap, len); break;
+        case H2_TREE_FCHILD: copy_out(read_vec(t->fchild.p, nn, s), buf, cap, len); break;
+        case H2_TREE_NCHILD: copy_out(read_vec(t->nchild.p, nn, s), buf, cap, len); break;
+        case H2_TREE_BEGIN: copy_out(widen<int32_t, int64_t>(read_vec(t->begin.p, nn, s)), buf, cap, len); break;
+        case H2_TREE_END: copy_out(widen<int32_t, int64_t>(read_vec(t->end.p, nn, s)), buf, cap, len); break;
+        case H2_TREE_PREFIX: copy_out(read_vec(t->prefix.p, nn, s), buf, cap, len); break;
+        case H2_TREE_LPTR: copy_out(std::vector<int32_t>(t->lptr.begin(), t->lptr.end()), buf, cap, len); break;
+        case H2_TREE_NEAR_PTR: copy_out(read_vec(t->near_ptr.p, nn + 1, s), buf, cap, len); break;
+        case H2_TREE_FAR_PTR: copy_out(read_vec(t->far_ptr.p, nn + 1, s), buf, cap, len); break;
+        case H2_TREE_NEAR_IDX: copy_out(read_vec(t->near_idx.p, t->nnear, s), buf, cap, len); break;
+        case H2_TREE_FAR_IDX: copy_out(read_vec(t->far_idx.p, t->nfar, s), buf, cap, len); break;
+        case H2_TREE_INFO: {
+            std::vector<int64_t> v = {t->n, t->d, t->B, t->nnodes, t->nlevels, t->nnear, t->nfar, t->q};
+            copy_out(v, buf, cap, len);
+            break;
+        }
+        case H2_TREE_GEOM: {
+            std::vector<double> v = {t->geom.lo[0], t->geom.lo[1], t->geom.lo[2], t->geom.side};
+            copy_out(v, buf, cap, len);
+            break;
+        }
+        default: fail(H2_ERR_INVALID_ARG, "unknown tree field");
+        }
+    });
+}
+
+h2_status h2_hidr_reduce(h2_tree th, int g1, int g2, void *stream, h2_hidr *out) {
+    return guard([&] {
+        H2_REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        h2_tree_s *t = as_tree(th);
+        H2_REQUIRE(g1 >= 1 && g2 >= 1, "g1 and g2 must be >= 1");
+        auto *h = new h2_hidr_s();
+        h->tree = t;
+        h->stream = static_cast<cudaStream_t>(stream);
+        h->g1 = g1;
+        h->g2 = g2;
+        try {
+            hidr_impl(h);
+        } catch (...) {
+            h->tag = TAG_DEAD;
+            delete h;
+            throw;
+        }
+        t->refs++;
+        *out = h;
+    });
+}
+
+h2_status h2_hidr_get(h2_hidr hh, int which, int32_t *counts, int32_t *data, int64_t cap, int64_t *total) {
+    return guard([&] {
+        h2_hidr_s *h = as_hidr(hh);
+        H2_REQUIRE(which == 0 || which == 1, "which must be 0 (X*) or 1 (Y*)");
+        cudaStream_t s = h->stream;
+        const int nn = h->tree->nnodes;
+        std::vector<int32_t> cnt = read_vec(which ? h->ycnt.p : h->xcnt.p, nn, s);
+        std::vector<int32_t *> ptr = read_vec(which ? h->yptr.p : h->xptr.p, nn, s);
+        int64_t tot = 0;
+        for (int32_t c : cnt) tot += c;
+        if (total) *total = tot;
+        if (counts) memcpy(counts, cnt.data(), nn * sizeof(int32_t));
+        if (data) {
+            H2_REQUIRE(cap >= tot, "output buffer too small");
+            int64_t w = 0;
+            for (int i = 0; i < nn; i++) {
+                if (cnt[i] > 0)
+                    H2_CUDA(cudaMemcpyAsync(data + w, ptr[i], cnt[i] * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                w += cnt[i];
+            }
+            H2_CUDA(cudaStreamSynchronize(s));
+        }
+    });
+}
+
+h2_status h2_construct(h2_tree th, h2_hidr hh, int kernel, const double *kparams, double id_tol, int precision,
+                       void *stream, h2_matrix *out) {
+    return guard([&] {
+        H2_REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        h2_tree_s *t = as_tree(th);
+        h2_hidr_s *h = as_hidr(hh);
+        H2_REQUIRE(h->tree == t, "hidr was built on another tree");
+        H2_REQUIRE(valid_kernel(kernel), "unknown kernel id");
+        H2_REQUIRE(std::isfinite(id_tol) && id_tol >= 0.0, "id_tol must be finite and >= 0");
+        H2_REQUIRE(precision == H2_PREC_FP64 || precision == H2_PREC_MIXED, "unknown precision");
+        auto *A = new h2_matrix_s();
+        A->tree = t;
+        A->stream = static_cast<cudaStream_t>(stream);
+        A->kid = kernel;
+        A->id_tol = id_tol;
+        A->prec = precision;
+        try {
+            kparams_check(kernel, kparams, A->kp);
+            if (precision != H2_PREC_FP64) fail(H2_ERR_UNIMPLEMENTED, "mixed precision construction not built");
+            construct_impl(A, h);
+        } catch (...) {
+            A->tag = TAG_DEAD;
+            delete A;
+            throw;
+        }
+        t->refs++;
+        *out = A;
+    });
+}
+
+h2_status h2_matrix_get(h2_matrix ah, int what, void *buf, int64_t cap, int64_t *len) {
+    return guard([&] {
+        h2_matrix_s *A = as_matrix(ah);
+        cudaStream_t s = A->stream;
+        const int nn = A->tree->nnodes;
+        switch (what) {
+        case H2_MAT_RANK: copy_out(read_vec(A->k.p, nn, s), buf, cap, len); break;
+        case H2_MAT_NCAND: copy_out(read_vec(A->c.p, nn, s), buf, cap, len); break;
+        case H2_MAT_SKEL: copy_out(read_vec(A->skel.p, A->ktotal, s), buf, cap, len); break;
+        case H2_MAT_U: {
+            std::vector<int32_t> k = read_vec(A->k.p, nn, s), c = read_vec(A->c.p, nn, s);
+            std::vector<double *> up = read_vec(A->uptr.p, nn, s);
+            int64_t tot = 0;
+            for (int i = 0; i < nn; i++) tot += (int64_t)k[i] * c[i];
+            if (len) *len = tot;
+            if (!buf) break;
+            H2_REQUIRE(cap >= tot, "output buffer too small");
+            double *dst = static_cast<double *>(buf);
+            for (int i = 0; i < nn; i++) {
+                int64_t e = (int64_t)k[i] * c[i];
+                if (e > 0) H2_CUDA(cudaMemcpyAsync(dst, up[i], e * sizeof(double), cudaMemcpyDeviceToHost, s));
+                dst += e;
+            }
+            H2_CUDA(cudaStreamSynchronize(s));
+            break;
+        }
+        case H2_MAT_INFO: {
+            std::vector<int64_t> v = {A->ktotal, A->utotal, A->kmax, A->tree->nlevels};
+            copy_out(v, buf, cap, len);
+            break;
+        }
+        default: fail(H2_ERR_INVALID_ARG, "unknown matrix field");
+        }
+    });
+}
+
+h2_status h2_matvec(h2_matrix ah, const double *x, double *y, int on_device, void *stream) {
+    return guard([&] {
+        h2_matrix_s *A = as_matrix(ah);
+        H2_REQUIRE(x != nullptr && y != nullptr, "x or y is NULL");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int64_t n = A->tree->n;
+        if (on_device) {
+            matvec_impl(A, x, y, s);
+            return;
+        }
+        DevBuf<double> xd, yd;
+        xd.alloc(n, s);
+        yd.alloc(n, s);
+        H2_CUDA(cudaMemcpyAsync(xd.p, x, n * sizeof(double), cudaMemcpyHostToDevice, s));
+        matvec_impl(A, xd.p, yd.p, s);
+        H2_CUDA(cudaMemcpyAsync(y, yd.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        H2_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+h2_status h2_exact_rows(h2_tree th, int kernel, const double *kparams, const double *z, const int64_t *rows,
+                        int64_t nrows, double *out, int on_device, void *stream) {
+    return guard([&] {
+        h2_tree_s *t = as_tree(th);
+        H2_REQUIRE(valid_kernel(kernel), "unknown kernel id");
+        H2_REQUIRE(z != nullptr && (nrows == 0 || (rows != nullptr && out != nullptr)), "NULL argument");
+        H2_REQUIRE(nrows >= 0 && nrows < (int64_t)INT32_MAX, "bad nrows");
+        double kp[4];
+        kparams_check(kernel, kparams, kp);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (!on_device) {
+            std::vector<int64_t> rv(rows, rows + nrows);
+            for (int64_t r : rv) H2_REQUIRE(r >= 0 && r < t->n, "row index out of range");
+            DevBuf<double> zd, od;
+            DevBuf<int64_t> rd;
+            zd.alloc(t->n, s);
+            od.alloc(std::max<int64_t>(nrows, 1), s);
+            rd.alloc(std::max<int64_t>(nrows, 1), s);
+            H2_CUDA(cudaMemcpyAsync(zd.p, z, t->n * sizeof(double), cudaMemcpyHostToDevice, s));
+            if (nrows) H2_CUDA(cudaMemcpyAsync(rd.p, rows, nrows * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            exact_rows_impl(t, kernel, kp, zd.p, rd.p, nrows, od.p, s);
+            if (nrows) H2_CUDA(cudaMemcpyAsync(out, od.p, nrows * sizeof(double), cudaMemcpyDeviceToHost, s));
+            H2_CUDA(cudaStreamSynchronize(s));
+            return;
+        }
+        exact_rows_impl(t, kernel, kp, z, rows, nrows, out, s);
+    });
+}
+
+h2_status h2_free(void *handle) {
+    return guard([&] {
+        if (!handle) return;
+        uint32_t tag = *static_cast<uint32_t *>(handle);
+        if (tag == TAG_TREE) {
+            auto *t = static_cast<h2_tree_s *>(handle);
+            if (t->refs > 0) fail(H2_ERR_STATE, "tree still has live hidr/matrix handles");
+            t->tag = TAG_DEAD;
+            delete t;
+        } else if (tag == TAG_HIDR) {
+            auto *h = static_cast<h2_hidr_s *>(handle);
+            h->tree->refs--;
+            h->tag = TAG_DEAD;
+            delete h;
+        } else if (tag == TAG_MATRIX) {
+            auto *A = static_cast<h2_matrix_s *>(handle);
+            A->tree->refs--;
+            A->tag = TAG_DEAD;
+            delete A;
+        } else {
+            fail(H2_ERR_INVALID_ARG, "not a live h2 handle");
+        }
+    });
+}
+
+h2_status h2_profile(int enable, int reset) {
+    return guard([&] { profile_set(enable != 0, reset != 0); });
+}
+
+h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
+    return guard([&] {
+        H2_REQUIRE(json && cap > 0, "NULL argument");
+        if (!handle) {
+            std::string js = profile_json();
+            H2_REQUIRE((int64_t)js.size() < cap, "json buffer too small");
+            memcpy(json, js.c_str(), js.size() + 1);
+            return;
+        }
+        uint32_t tag = *static_cast<const uint32_t *>(handle);
+        char buf[1024];
+        if (tag == TAG_TREE) {
+            auto *t = static_cast<const h2_tree_s *>(handle);
+            snprintf(buf, sizeof buf,
+                     "{\"n\": %lld, \"nodes\": %d, \"levels\": %d, \"near_pairs\": %lld, \"far_pairs\": %lld, "
+                     "\"max_leaf\": %d, \"ms_tree\": %.4f, \"ms_lists\": %.4f}",
+                     (long long)t->n, t->nnodes, t->nlevels, (long long)t->nnear, (long long)t->nfar, t->max_leaf,
+                     t->ms_tree, t->ms_lists);
+        } else if (tag == TAG_HIDR) {
+            auto *h = static_cast<const h2_hidr_s *>(handle);
+            snprintf(buf, sizeof buf,
+                     "{\"g1\": %d, \"g2\": %d, \"x_total\": %lld, \"y_total\": %lld, \"t_max_level\": %lld, "
+                     "\"ms_up\": %.4f, \"ms_down\": %.4f}",
+                     h->g1, h->g2, (long long)h->xtotal, (long long)h->ytotal, (long long)h->tmax, h->ms_up,
+                     h->ms_down);
+        } else if (tag == TAG_MATRIX) {
+            auto *A = static_cast<const h2_matrix_s *>(handle);
+            snprintf(buf, sizeof buf,
+                     "{\"k_total\": %lld, \"u_entries\": %lld, \"k_max\": %d, \"ms_construct\": %.4f, "
+                     "\"qr_flops\": %.6e, \"block_evals\": %.6e}",
+                     (long long)A->ktotal, (long long)A->utotal, A->kmax, A->ms_construct, A->flops_qr,
+                     A->evals_block);
+        } else {
+            fail(H2_ERR_INVALID_ARG, "not a live h2 handle");
+        }
+        H2_REQUIRE((int64_t)strlen(buf) < cap, "json buffer too small");
+        memcpy(json, buf, strlen(buf) + 1);
+    });
+}
+
+h2_status h2_calibrate(int dim, int kernel, const double *kparams, double eps, const double *z1, int n1,
+                       const double *z2, int n2, int gmax, void *stream, int *g_out, double *err_out) {
+    return guard([&] {
+        H2_REQUIRE(dim == 2 || dim == 3, "dim must be 2 or 3");
+        H2_REQUIRE(valid_kernel(kernel), "unknown kernel id");
+        H2_REQUIRE(z1 && z2 && g_out && n1 > 0 && n2 > 0 && gmax >= 1, "bad calibration arguments");
+        H2_REQUIRE(std::isfinite(eps) && eps > 0.0, "eps must be > 0");
+        double kp[4];
+        kparams_check(kernel, kparams, kp);
+        pool_keep_memory();
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        DevBuf<double> a[3], b[3];
+        std::vector<double> col(std::max(n1, n2));
+        for (int k = 0; k < 3; k++) {
+            a[k].alloc(k < dim ? n1 : 1, s);
+            b[k].alloc(k < dim ? n2 : 1, s);
+            if (k >= dim) continue;
+            for (int i = 0; i < n1; i++) col[i] = z1[(int64_t)i * dim + k];
+            H2_CUDA(cudaMemcpyAsync(a[k].p, col.data(), n1 * sizeof(double), cudaMemcpyHostToDevice, s));
+            for (int i = 0; i < n2; i++) col[i] = z2[(int64_t)i * dim + k];
+            H2_CUDA(cudaMemcpyAsync(b[k].p, col.data(), n2 * sizeof(double), cudaMemcpyHostToDevice, s));
+        }
+        const double *za[3] = {a[0].p, a[1].p, a[2].p}, *zb[3] = {b[0].p, b[1].p, b[2].p};
+        *g_out = gmax + 1;
+        double err = INFINITY;
+        for (int g = 1; g <= gmax; g++) {
+            double gp = 1.0;
+            for (int k = 0; k < dim; k++) gp *= g;
+            if (gp > 16384) break;
+            err = calib_error_gpu(dim, kernel, kp[0], 1e-2 * eps, za, n1, zb, n2, g, nullptr, nullptr, s);
+            if (err < 1e-2 * eps) {
+                *g_out = g;
+                break;
+            }
+        }
+        if (err_out) *err_out = err;
+    });
+}
+
+h2_status h2_sampled_error(const double *exact, const double *approx, const int64_t *rows, int64_t nrows,
+                           int64_t n, double *err_out, int on_device, void *stream) {
+    return guard([&] {
+        H2_REQUIRE(exact && approx && rows && err_out && nrows >= 1 && n >= 1, "bad arguments");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (on_device) {
+            sampled_error_impl(exact, approx, rows, nrows, n, err_out, s);
+            return;
+        }
+        DevBuf<double> e, a, o;
+        DevBuf<int64_t> r;
+        e.alloc(nrows, s); a.alloc(n, s); o.alloc(1, s); r.alloc(nrows, s);
+        H2_CUDA(cudaMemcpyAsync(e.p, exact, nrows * sizeof(double), cudaMemcpyHostToDevice, s));
+        H2_CUDA(cudaMemcpyAsync(a.p, approx, n * sizeof(double), cudaMemcpyHostToDevice, s));
+        H2_CUDA(cudaMemcpyAsync(r.p, rows, nrows * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        sampled_error_impl(e.p, a.p, r.p, nrows, n, o.p, s);
+        H2_CUDA(cudaMemcpyAsync(err_out, o.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        H2_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,573 @@
+// construct.cu -- Algorithm 2 of arXiv 2206.01885: for every level from the
+// deepest to 1, the kernel block A_i = K(Y_i*, Xbar_i) of every node, its
+// column-pivoted QR interpolative decomposition (section 4.1, eqs. (3)-(5)),
+// the skeleton Xhat_i and the nested basis U_i = P [I; (R11^{-1} R12)^T].
+//
+// One CTA factors one node's block; all nodes of a level run in one launch.
+// The float64 path evaluates the block and the Householder updates in
+// float64.  Column norms are downdated as in LAPACK's xLAQP2 and recomputed
+// once the downdated value has lost about half its digits.
+#include <climits>
+
+#include "h2_internal.cuh"
+
+namespace h2 {
+namespace {
+
+constexpr int QR_THREADS = 512;
+constexpr int QR_WARPS = QR_THREADS / 32;
+constexpr size_t SMEM_LIMIT = 220 * 1024;
+
+// c_i, m_i and the block / candidate sizes of each node of a level
+__global__ void k_cand_sizes(int lb, int nl, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
+                             const int32_t *end, const int32_t *kk, const int32_t *ycnt, int32_t *cc,
+                             int64_t *szc, int64_t *sza) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nl) return;
+    int i = lb + a;
+    int c = 0;
+    if (nchild[i] == 0) c = end[i] - begin[i];
+    else
+        for (int ch = fchild[i]; ch < fchild[i] + nchild[i]; ch++) c += kk[ch];
+    int m = ycnt[i];
+    if (m == 0) c = 0;  // no farfield: no basis, the node is skipped
+    cc[i] = c;
+    szc[a] = c;
+    sza[a] = (int64_t)m * c;
+}
+
+// Xbar_i: the leaf's points, or the children's skeletons in child order
+__global__ void k_gather_cand(int lb, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
+                              const int32_t *cc, const int32_t *kk, int32_t *const *skptr, const int64_t *coff,
+                              int32_t *cand) {
+    int a = blockIdx.x, i = lb + a;
+    int c = cc[i];
+    if (c == 0) return;
+    int32_t *dst = cand + coff[a];
+    if (nchild[i] == 0) {
+        for (int r = threadIdx.x; r < c; r += blockDim.x) dst[r] = begin[i] + r;
+        return;
+    }
+    int w = 0;
+    for (int ch = fchild[i]; ch < fchild[i] + nchild[i]; ch++) {
+        int n = kk[ch];
+        const int32_t *src = skptr[ch];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) dst[w + r] = src[r];
+        w += n;
+    }
+}
+
+// A_i[r + l m] = kappa(y_r, xbar_l), column-major m x c
+__global__ void k_keval_f64(int lb, const int32_t *ycnt, const int32_t *cc, int32_t *const *yptr,
+                            const int32_t *cand, const int64_t *coff, const int64_t *aoff, const double *x0,
+                            const double *x1, const double *x2, int d, int kid, double kp0, double *Abase) {
+    int a = blockIdx.x, i = lb + a;
+    int m = ycnt[i], c = cc[i];
+    if (m == 0 || c == 0) return;
+    const int32_t *Y = yptr[i];
+    const int32_t *X = cand + coff[a];
+    double *A = Abase + aoff[a];
+    int64_t total = (int64_t)m * c;
+    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.y * blockDim.x) {
+        int r = (int)(e % m), l = (int)(e / m);
+        int32_t y = Y[r], x = X[l];
+        double r2 = h2_dist2(d, x0[y], d > 1 ? x1[y] : 0.0, d > 2 ? x2[y] : 0.0, x0[x], d > 1 ? x1[x] : 0.0,
+                             d > 2 ? x2[x] : 0.0);
+        A[e] = h2_kappa(kid, kp0, r2);
+    }
+}
+
+// (value, index) max with ties to the smaller index
+__device__ __forceinline__ void argmax_merge(double &v, int &i, double v2, int i2) {
+    if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+}
+
+__device__ double block_sum(double x, double *red) {
+    x = warp_sum(x);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    return s;
+}
+
+// Column-pivoted Householder QR of each node's block, stopped at the first
+// step whose pivot norm is <= tol * |r_11|.  On exit A holds R (upper
+// triangle of the first k columns and rows 0..k-1 of the others), kout[i] = k
+// and piv[0..c) is the column order.
+__global__ void __launch_bounds__(QR_THREADS) k_cpqr_f64(int lb, const int32_t *ycnt, const int32_t *cc,
+                                                         const int64_t *aoff, double *Abase, double tol,
+                                                         int32_t *kout, const int64_t *coff, int32_t *pivbase) {
+    extern __shared__ unsigned char smem_raw[];
+    const int a = blockIdx.x, node = lb + a;
+    const int m = ycnt[node], c = cc[node];
+    if (m == 0 || c == 0) {
+        if (threadIdx.x == 0) kout[node] = 0;
+        return;
+    }
+    double *nrm = reinterpret_cast<double *>(smem_raw);
+    double *nrm0 = nrm + c;
+    double *v = nrm0 + c;
+    int32_t *pv = reinterpret_cast<int32_t *>(v + m);
+    __shared__ double red[QR_WARPS];
+    __shared__ double bval[QR_WARPS];
+    __shared__ int bidx[QR_WARPS];
+    __shared__ int s_p, s_stop;
+    double *A = Abase + aoff[a];
+    int32_t *piv = pivbase + coff[a];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double tol3z = sqrt(ldexp(1.0, -53));
+
+    for (int l = threadIdx.x; l < c; l += blockDim.x) pv[l] = l;
+    for (int l = warp; l < c; l += QR_WARPS) {
+        const double *col = A + (int64_t)l * m;
+        double s = 0.0;
+        for (int r = lane; r < m; r += 32) s += col[r] * col[r];
+        s = warp_sum(s);
+        if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
+    }
+    __syncthreads();
+    const int kmax = min(m, c);
+    int k = 0;
+    double r11 = 0.0;
+    for (int j = 0; j < kmax; j++) {
+        // pivot: largest downdated norm among columns j..c-1
+        double bv = -1.0;
+        int bi = INT_MAX;
+        for (int l = j + threadIdx.x; l < c; l += blockDim.x) argmax_merge(bv, bi, nrm[l], l);
+        for (int o = 16; o > 0; o >>= 1) {
+            double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+            int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            argmax_merge(bv, bi, v2, i2);
+        }
+        if (lane == 0) { bval[warp] = bv; bidx[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double vv = bval[0];
+            int ii = bidx[0];
+            for (int w = 1; w < QR_WARPS; w++) argmax_merge(vv, ii, bval[w], bidx[w]);
+            if (j == 0) r11 = vv;
+            s_p = ii;
+            s_stop = (!(vv > tol * r11) || vv == 0.0) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const int p = s_p;
+        if (p != j) {
+            double *cj = A + (int64_t)j * m, *cp = A + (int64_t)p * m;
+            for (int r = threadIdx.x; r < m; r += blockDim.x) {
+                double t = cj[r]; cj[r] = cp[r]; cp[r] = t;
+            }
+            if (threadIdx.x == 0) {
+                double t = nrm[j]; nrm[j] = nrm[p]; nrm[p] = t;
+                t = nrm0[j]; nrm0[j] = nrm0[p]; nrm0[p] = t;
+                int ti = pv[j]; pv[j] = pv[p]; pv[p] = ti;
+            }
+        }
+        __syncthreads();
+        // Householder reflector for A[j:m, j]
+        double *aj = A + (int64_t)j * m;
+        double part = 0.0;
+        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) part += aj[r] * aj[r];
+        double sigma = block_sum(part, red);
+        double alpha = aj[j];
+        if (alpha == 0.0 && sigma == 0.0) break;  // exactly zero pivot column
+        double tau = 0.0, beta = alpha, sc = 0.0;
+        if (sigma != 0.0) {
+            double xn = sqrt(alpha * alpha + sigma);
+            beta = alpha >= 0.0 ? -xn : xn;
+            tau = (beta - alpha) / beta;
+            sc = 1.0 / (alpha - beta);
+        }
+        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) v[r] = aj[r] * sc;
+        __syncthreads();
+        if (threadIdx.x == 0) aj[j] = beta;
+        // apply to the trailing columns and downdate their norms (one warp per column)
+        for (int l = j + 1 + warp; l < c; l += QR_WARPS) {
+            double *al = A + (int64_t)l * m;
+            double ajl = al[j];
+            if (tau != 0.0) {
+                double w = 0.0;
+                for (int r = j + 1 + lane; r < m; r += 32) w += v[r] * al[r];
+                w = warp_sum(w) + ajl;
+                w = w * tau;
+                for (int r = j + 1 + lane; r < m; r += 32) al[r] = al[r] - w * v[r];
+                ajl = ajl - w;
+                if (lane == 0) al[j] = ajl;
+            }
+            double nl = nrm[l];
+            if (nl != 0.0) {
+                double tt = fabs(ajl) / nl;
+                tt = 1.0 - tt * tt;
+                if (tt < 0.0) tt = 0.0;
+                double t2 = nl / nrm0[l];
+                t2 = tt * t2 * t2;
+                if (t2 <= tol3z) {
+                    double s = 0.0;
+                    for (int r = j + 1 + lane; r < m; r += 32) s += al[r] * al[r];
+                    s = warp_sum(s);
+                    if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
+                } else if (lane == 0) {
+                    nrm[l] = nl * sqrt(tt);
+                }
+            }
+        }
+        __syncthreads();
+        k = j + 1;
+    }
+    for (int l = threadIdx.x; l < c; l += blockDim.x) piv[l] = pv[l];
+    if (threadIdx.x == 0) kout[node] = k;
+}
+
+__device__ void bitonic_sort_i32(int32_t *v, int P) {
+    for (int kk = 2; kk <= P; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    bool asc = (i & kk) == 0;
+                    int32_t x = v[i], y = v[ixj];
+                    if ((x > y) == asc) { v[i] = y; v[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// T = R11^{-1} R12 (right-looking back substitution, in place of R12), then
+// U_i (c x k, column-major, columns in sorted-skeleton order) and the sorted
+// skeleton's Morton positions.
+__global__ void __launch_bounds__(QR_THREADS) k_id_solve_f64(int lb, const int32_t *ycnt, const int32_t *cc,
+                                                             const int32_t *kk, const int64_t *aoff, double *Abase,
+                                                             const int64_t *coff, const int32_t *pivbase,
+                                                             const int32_t *cand, double *const *uptr,
+                                                             int32_t *const *skptr) {
+    extern __shared__ unsigned char smem_raw[];
+    int32_t *sk = reinterpret_cast<int32_t *>(smem_raw);
+    const int a = blockIdx.x, node = lb + a;
+    const int m = ycnt[node], c = cc[node], k = kk[node];
+    if (k == 0) return;
+    double *A = Abase + aoff[a];
+    const int32_t *piv = pivbase + coff[a];
+    const int32_t *cd = cand + coff[a];
+    const int nr = c - k;
+    for (int i = k - 1; i >= 0; i--) {
+        const double rii = A[i + (int64_t)i * m];
+        for (int l = threadIdx.x; l < nr; l += blockDim.x) {
+            double *e = A + i + (int64_t)(k + l) * m;
+            *e = *e / rii;
+        }
+        __syncthreads();
+        const int64_t work = (int64_t)i * nr;
+        for (int64_t e = threadIdx.x; e < work; e += blockDim.x) {
+            int p = (int)(e % i), l = k + (int)(e / i);
+            A[p + (int64_t)l * m] -= A[p + (int64_t)i * m] * A[i + (int64_t)l * m];
+        }
+        __syncthreads();
+    }
+    int P = 1;
+    while (P < k) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < k ? piv[i] : INT_MAX;
+    __syncthreads();
+    bitonic_sort_i32(sk, P);
+    double *U = uptr[node];
+    int32_t *skel = skptr[node];
+    for (int64_t e = threadIdx.x; e < (int64_t)c * k; e += blockDim.x) U[e] = 0.0;
+    for (int q = threadIdx.x; q < k; q += blockDim.x) skel[q] = cd[sk[q]];
+    __syncthreads();
+    // column of U for pivot p: position of piv[p] in the sorted skeleton
+    for (int64_t e = threadIdx.x; e < (int64_t)(nr + 1) * k; e += blockDim.x) {
+        int p = (int)(e % k), l = (int)(e / k);  // l == 0: identity rows, else T column l-1
+        int lo = 0, hi = k - 1, key = piv[p];
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (sk[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        if (l == 0) U[piv[p] + (int64_t)lo * c] = 1.0;
+        else U[piv[k + l - 1] + (int64_t)lo * c] = A[p + (int64_t)(k + l - 1) * m];
+    }
+}
+
+__global__ void k_ku_sizes(int lb, int nl, const int32_t *kk, const int32_t *cc, int64_t *szk, int64_t *szu) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nl) return;
+    int i = lb + a;
+    szk[a] = kk[i];
+    szu[a] = (int64_t)kk[i] * cc[i];
+}
+
+__global__ void k_set_ptrs2(int lb, int nl, int32_t *kbase, const int64_t *koff, int32_t **skptr, double *ubase,
+                            const int64_t *uoff, double **uptr) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nl) return;
+    skptr[lb + a] = kbase + koff[a];
+    uptr[lb + a] = ubase + uoff[a];
+}
+
+// contiguous skeletons (node order) and their coordinates
+__global__ void k_compact_skel(int nn, const int32_t *kk, const int64_t *off, int32_t *const *skptr, int32_t *skel,
+                               const double *x0, const double *x1, const double *x2, int d, double *s0, double *s1,
+                               double *s2) {
+    int i = blockIdx.x;
+    if (i >= nn) return;
+    int k = kk[i];
+    const int32_t *src = skptr[i];
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+        int32_t p = src[q];
+        int64_t o = off[i] + q;
+        skel[o] = p;
+        s0[o] = x0[p];
+        if (d > 1) s1[o] = x1[p];
+        if (d > 2) s2[o] = x2[p];
+    }
+}
+
+size_t qr_smem(int cmax, int mmax) {
+    return (size_t)cmax * (2 * sizeof(double) + sizeof(int32_t)) + (size_t)mmax * sizeof(double) + 64;
+}
+
+}  // namespace
+
+void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
+    h2_tree_s *t = A->tree;
+    cudaStream_t s = A->stream;
+    const int nn = t->nnodes, d = t->d;
+    H2_REQUIRE(A->prec == H2_PREC_FP64, "only the float64 construction is built");
+    A->k.alloc(nn, s);
+    A->c.alloc(nn, s);
+    H2_CUDA(cudaMemsetAsync(A->k.p, 0, nn * sizeof(int32_t), s));
+    H2_CUDA(cudaMemsetAsync(A->c.p, 0, nn * sizeof(int32_t), s));
+    DevBuf<int32_t *> skptr;
+    skptr.alloc(nn, s);
+    A->uptr.alloc(nn, s);
+    H2_CUDA(cudaMemsetAsync(skptr.p, 0, nn * sizeof(int32_t *), s));
+    H2_CUDA(cudaMemsetAsync(A->uptr.p, 0, nn * sizeof(double *), s));
+    std::vector<DevBuf<int32_t>> skbufs(t->nlevels);
+    A->ubufs.resize(t->nlevels);
+    A->kmax_level.assign(t->nlevels, 0);
+    A->cmax_level.assign(t->nlevels, 0);
+    static bool attr = false;
+    if (!attr) {
+        H2_CUDA(cudaFuncSetAttribute(k_cpqr_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_id_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        attr = true;
+    }
+    cudaEvent_t e0, e1;
+    H2_CUDA(cudaEventCreate(&e0));
+    H2_CUDA(cudaEventCreate(&e1));
+    H2_CUDA(cudaEventRecord(e0, s));
+    const std::vector<int32_t> yc = read_vec(h->ycnt.p, nn, s);
+    DevBuf<int64_t> szc, sza, coff, aoff, szk, szu, koff, uoff;
+    DevBuf<int32_t> cand, piv;
+    DevBuf<double> Ablk;
+    for (int l = t->nlevels - 1; l >= 1; l--) {
+        const int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
+        szc.alloc(nl, s); sza.alloc(nl, s); coff.alloc(nl + 1, s); aoff.alloc(nl + 1, s);
+        k_cand_sizes<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, t->nchild.p, t->fchild.p, t->begin.p, t->end.p,
+                                                          A->k.p, h->ycnt.p, A->c.p, szc.p, sza.p);
+        H2_LAUNCH("k_cand_sizes");
+        scan_exclusive(szc.p, coff.p, nl, s);
+        scan_exclusive(sza.p, aoff.p, nl, s);
+        std::vector<int64_t> cs = read_vec(szc.p, nl, s);
+        int64_t ctot = read_scalar(coff.p + nl, s), atot = read_scalar(aoff.p + nl, s);
+        int cmax = 0;
+        for (int64_t v : cs) cmax = std::max<int>(cmax, (int)v);
+        A->cmax_level[l] = cmax;
+        if (ctot == 0) continue;
+        const int mmax = h->ymax_level[l];
+        if (qr_smem(cmax, mmax) > SMEM_LIMIT)
+            fail(H2_ERR_UNIMPLEMENTED, "kernel block too large for the single-CTA QR (candidates " +
+                                           std::to_string(cmax) + ", rows " + std::to_string(mmax) + ")");
+        cand.alloc(ctot, s);
+        piv.alloc(ctot, s);
+        Ablk.alloc(atot, s);
+        k_gather_cand<<<nl, 128, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->c.p, A->k.p, skptr.p, coff.p,
+                                         cand.p);
+        H2_LAUNCH("k_gather_cand");
+        dim3 kg(nl, std::max(1, std::min(16, (int)((int64_t)cmax * mmax / (256 * 64)))));
+        {
+        ProfScope ps(KT_KEVAL, s);
+        k_keval_f64<<<kg, 256, 0, s>>>(lb, h->ycnt.p, A->c.p, h->yptr.p, cand.p, coff.p, aoff.p, t->xs[0].p,
+                                       t->xs[1].p, t->xs[2].p, d, A->kid, A->kp[0], Ablk.p);
+        H2_LAUNCH("k_keval_f64");
+        }
+        A->evals_block += (double)atot;
+        {
+        ProfScope ps(KT_CPQR, s);
+        k_cpqr_f64<<<nl, QR_THREADS, qr_smem(cmax, mmax), s>>>(lb, h->ycnt.p, A->c.p, aoff.p, Ablk.p, A->id_tol,
+                                                              A->k.p, coff.p, piv.p);
+        H2_LAUNCH("k_cpqr_f64");
+        }
+        szk.alloc(nl, s); szu.alloc(nl, s); koff.alloc(nl + 1, s); uoff.alloc(nl + 1, s);
+        k_ku_sizes<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, A->k.p, A->c.p, szk.p, szu.p);
+        H2_LAUNCH("k_ku_sizes");
+        scan_exclusive(szk.p, koff.p, nl, s);
+        scan_exclusive(szu.p, uoff.p, nl, s);
+        std::vector<int64_t> ks = read_vec(szk.p, nl, s);
+        int64_t ktot = read_scalar(koff.p + nl, s), utot = read_scalar(uoff.p + nl, s);
+        int kmax = 0;
+        for (int64_t v : ks) kmax = std::max<int>(kmax, (int)v);
+        A->kmax_level[l] = kmax;
+        A->kmax = std::max(A->kmax, kmax);
+        for (int a = 0; a < nl; a++) {  // Householder QR flops of an m x c block stopped at rank k
+            double kk = (double)ks[a], cc = (double)cs[a], mm = (double)yc[lb + a];
+            if (kk > 0) A->flops_qr += 4 * mm * cc * kk - 2 * kk * kk * (mm + cc) + 4.0 / 3.0 * kk * kk * kk;
+        }
+        skbufs[l].alloc(ktot > 0 ? ktot : 1, s);
+        A->ubufs[l].alloc(utot > 0 ? utot : 1, s);
+        k_set_ptrs2<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, skbufs[l].p, koff.p, skptr.p, A->ubufs[l].p,
+                                                         uoff.p, A->uptr.p);
+        H2_LAUNCH("k_set_ptrs2");
+        int P = 1;
+        while (P < kmax) P <<= 1;
+        {
+        ProfScope ps(KT_SOLVE, s);
+        k_id_solve_f64<<<nl, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(
+            lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, Ablk.p, coff.p, piv.p, cand.p, A->uptr.p, skptr.p);
+        H2_LAUNCH("k_id_solve_f64");
+        }
+        A->ktotal += ktot;
+        A->utotal += utot;
+    }
+    // skeletons contiguous in node order, with coordinates for the matvec
+    A->sk_off.alloc(nn + 1, s);
+    scan_exclusive_i32(A->k.p, A->sk_off.p, nn, s);
+    int64_t kt = read_scalar(A->sk_off.p + nn, s);
+    A->skel.alloc(kt > 0 ? kt : 1, s);
+    for (int k = 0; k < 3; k++) A->skc[k].alloc(kt > 0 ? kt : 1, s);
+    k_compact_skel<<<std::max(1, nn), 128, 0, s>>>(nn, A->k.p, A->sk_off.p, skptr.p, A->skel.p, t->xs[0].p,
+                                                    t->xs[1].p, t->xs[2].p, d, A->skc[0].p, A->skc[1].p, A->skc[2].p);
+    H2_LAUNCH("k_compact_skel");
+    H2_CUDA(cudaEventRecord(e1, s));
+    H2_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    A->ms_construct = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+namespace {
+// A[r + l m] = kappa(y_{ids[r]}, x_l) for the calibration block K(Z2*, Z1)
+__global__ void k_calib_block(const int32_t *ids, int m, int c, const double *y0, const double *y1, const double *y2,
+                              const double *x0, const double *x1, const double *x2, int d, int kid, double kp0,
+                              double *A) {
+    int64_t total = (int64_t)m * c;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int r = (int)(e % m), l = (int)(e / m);
+        int32_t y = ids[r];
+        double r2 = h2_dist2(d, y0[y], d > 1 ? y1[y] : 0.0, d > 2 ? y2[y] : 0.0, x0[l], d > 1 ? x1[l] : 0.0,
+                             d > 2 ? x2[l] : 0.0);
+        A[e] = h2_kappa(kid, kp0, r2);
+    }
+}
+
+// per candidate l (block): num_l = sum_b (kappa(z1[piv l], z2 b) - sum_p T[p, l] kappa(z1[piv p], z2 b))^2
+// for l >= k (0 for skeleton columns), den_l = sum_b kappa(z1[piv l], z2 b)^2
+__global__ void k_calib_err(const double *A, int m, int c, int k, const int32_t *piv, const double *a0,
+                            const double *a1, const double *a2, int n1, const double *b0, const double *b1,
+                            const double *b2, int n2, int d, int kid, double kp0, double *num, double *den) {
+    __shared__ double red[2][32];
+    int l = blockIdx.x;
+    if (l >= c) return;
+    int pl = piv[l];
+    double sn = 0.0, sd = 0.0;
+    for (int b = threadIdx.x; b < n2; b += blockDim.x) {
+        double zb0 = b0[b], zb1 = d > 1 ? b1[b] : 0.0, zb2 = d > 2 ? b2[b] : 0.0;
+        double kv = h2_kappa(kid, kp0, h2_dist2(d, a0[pl], d > 1 ? a1[pl] : 0.0, d > 2 ? a2[pl] : 0.0, zb0, zb1, zb2));
+        sd += kv * kv;
+        if (l >= k) {
+            double s = 0.0;
+            for (int p = 0; p < k; p++) {
+                int pp = piv[p];
+                s += A[p + (int64_t)l * m] *
+                     h2_kappa(kid, kp0, h2_dist2(d, a0[pp], d > 1 ? a1[pp] : 0.0, d > 2 ? a2[pp] : 0.0, zb0, zb1, zb2));
+            }
+            double e = kv - s;
+            sn += e * e;
+        }
+    }
+    sn = warp_sum(sn);
+    sd = warp_sum(sd);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red[0][warp] = sn; red[1][warp] = sd; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tn = 0.0, td = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) { tn += red[0][w]; td += red[1][w]; }
+        num[l] = tn;
+        den[l] = td;
+    }
+    (void)n1;
+}
+}  // namespace
+
+double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *const z1s[3], int n1,
+                       const double *const z2s[3], int n2, int g, int *k_out, int *m_out, cudaStream_t s) {
+    DevBuf<int32_t> ids;
+    ids.alloc(n2, s);
+    int m = (int)datareduct_one(z2s, d, n2, g, ids.p, s);
+    const int c = n1;
+    DevBuf<double> A;
+    A.alloc((size_t)m * c, s);
+    k_calib_block<<<blocks_for((int64_t)m * c, 256), 256, 0, s>>>(ids.p, m, c, z2s[0], z2s[1], z2s[2], z1s[0],
+                                                                   z1s[1], z1s[2], d, kid, kp0, A.p);
+    H2_LAUNCH("k_calib_block");
+    // one-node level: ycnt = m, c, offsets 0
+    int32_t hv[2] = {m, c};
+    int64_t offs[4] = {0, (int64_t)m * c, 0, c};
+    DevBuf<int32_t> mc, kk, piv, skel;
+    DevBuf<int64_t> off;
+    DevBuf<double> U;
+    DevBuf<double *> up;
+    DevBuf<int32_t *> sp;
+    mc.alloc(2, s); kk.alloc(1, s); piv.alloc(c, s); off.alloc(4, s);
+    H2_CUDA(cudaMemcpyAsync(mc.p, hv, sizeof hv, cudaMemcpyHostToDevice, s));
+    H2_CUDA(cudaMemcpyAsync(off.p, offs, sizeof offs, cudaMemcpyHostToDevice, s));
+    static bool attr = false;
+    if (!attr) {
+        H2_CUDA(cudaFuncSetAttribute(k_cpqr_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_id_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        attr = true;
+    }
+    if (qr_smem(c, m) > SMEM_LIMIT) fail(H2_ERR_UNIMPLEMENTED, "calibration block too large");
+    k_cpqr_f64<<<1, QR_THREADS, qr_smem(c, m), s>>>(0, mc.p, mc.p + 1, off.p, A.p, id_tol, kk.p, off.p + 2, piv.p);
+    H2_LAUNCH("k_cpqr_f64 (calibration)");
+    int k = read_scalar(kk.p, s);
+    U.alloc((size_t)std::max(1, k) * c, s);
+    skel.alloc(std::max(1, k), s);
+    up.alloc(1, s);
+    sp.alloc(1, s);
+    H2_CUDA(cudaMemcpyAsync(up.p, &U.p, sizeof(double *), cudaMemcpyHostToDevice, s));
+    H2_CUDA(cudaMemcpyAsync(sp.p, &skel.p, sizeof(int32_t *), cudaMemcpyHostToDevice, s));
+    DevBuf<int32_t> cand;
+    cand.alloc(c, s);
+    std::vector<int32_t> iota(c);
+    for (int i = 0; i < c; i++) iota[i] = i;
+    H2_CUDA(cudaMemcpyAsync(cand.p, iota.data(), c * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (k > 0) {
+        int P = 1;
+        while (P < k) P <<= 1;
+        k_id_solve_f64<<<1, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(0, mc.p, mc.p + 1, kk.p, off.p, A.p,
+                                                                          off.p + 2, piv.p, cand.p, up.p, sp.p);
+        H2_LAUNCH("k_id_solve_f64 (calibration)");
+    }
+    DevBuf<double> num, den;
+    num.alloc(c, s);
+    den.alloc(c, s);
+    k_calib_err<<<c, 256, 0, s>>>(A.p, m, c, k, piv.p, z1s[0], z1s[1], z1s[2], n1, z2s[0], z2s[1], z2s[2], n2, d,
+                                  kid, kp0, num.p, den.p);
+    H2_LAUNCH("k_calib_err");
+    std::vector<double> nv = read_vec(num.p, c, s), dv = read_vec(den.p, c, s);
+    double tn = 0.0, td = 0.0;
+    for (int l = 0; l < c; l++) { tn += nv[l]; td += dv[l]; }
+    if (k_out) *k_out = k;
+    if (m_out) *m_out = m;
+    return td > 0.0 ? sqrt(tn / td) : 0.0;
+}
+
+}  // namespace h2

@@ -1,0 +1,269 @@
+// h2_internal.cuh -- shared declarations of the sm_103a H^2 library.
+//
+// Host orchestration is C++ with exceptions internally; every C-ABI entry
+// point catches them and turns them into an h2_status plus a thread-local
+// message.  Device memory comes from the stream-ordered allocator
+// (cudaMallocAsync) on the caller's stream.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/h2.h"
+
+namespace h2 {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    h2_status st;
+    std::string msg;
+};
+
+[[noreturn]] void fail(h2_status st, const std::string &msg);
+void cuda_check(cudaError_t e, const char *what, const char *file, int line);
+#define H2_CUDA(call) ::h2::cuda_check((call), #call, __FILE__, __LINE__)
+#define H2_LAUNCH(what) ::h2::cuda_check(cudaGetLastError(), what, __FILE__, __LINE__)
+#define H2_REQUIRE(cond, msg)                                             \
+    do {                                                                  \
+        if (!(cond)) ::h2::fail(H2_ERR_INVALID_ARG, std::string(msg));    \
+    } while (0)
+
+// ----------------------------------------------------------- device memory
+void *dmalloc_bytes(size_t bytes, cudaStream_t s);
+void dfree_bytes(void *p, cudaStream_t s);
+
+// Owning device array, released on the stream it was allocated on.
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t count, cudaStream_t st) {
+        release();
+        s = st;
+        n = count;
+        p = count ? static_cast<T *>(dmalloc_bytes(count * sizeof(T), st)) : nullptr;
+    }
+    void release() {
+        if (p) dfree_bytes(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    T *get() const { return p; }
+};
+
+// copy helpers (synchronous on the stream)
+template <class T>
+T read_scalar(const T *dptr, cudaStream_t s) {
+    T v;
+    H2_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    return v;
+}
+template <class T>
+std::vector<T> read_vec(const T *dptr, size_t n, cudaStream_t s) {
+    std::vector<T> v(n);
+    if (n) {
+        H2_CUDA(cudaMemcpyAsync(v.data(), dptr, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+        H2_CUDA(cudaStreamSynchronize(s));
+    }
+    return v;
+}
+
+// ----------------------------------------------------------- primitives
+// out[i] = sum_{j<i} in[j] for i in [0, n]; out has n+1 entries (out[n] = total).
+void scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+void scan_exclusive_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of 64-bit keys on their low `nbits` bits; `vals`
+// (may be null) are permuted alongside.  Buffers are sorted in place.
+void radix_sort(uint64_t *keys, int32_t *vals, int64_t n, int nbits, cudaStream_t s);
+
+// ------------------------------------------------------------- profiling
+// Optional CUDA-event timing of the main kernels, on the stream each kernel is
+// launched on; totals are read through h2_get_stats(NULL, ...).
+enum KernelKind {
+    KT_DATAREDUCT = 0, KT_KEVAL, KT_CPQR, KT_SOLVE, KT_UPWARD, KT_COUPLING, KT_DOWNWARD, KT_NEAR, KT_EXACT,
+    KT_SORT, KT_LISTS, KT_COUNT
+};
+extern const char *const kernel_kind_names[KT_COUNT];
+bool profiling_enabled();
+void profile_set(bool on, bool reset);
+std::string profile_json();
+struct ProfScope {
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(int k, cudaStream_t st);
+    ~ProfScope();
+};
+
+inline int blocks_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > 2147483647 ? 2147483647 : b));
+}
+
+// ---------------------------------------------------------------- handles
+enum : uint32_t { TAG_TREE = 0x48325452u, TAG_HIDR = 0x48324844u, TAG_MATRIX = 0x48324d58u, TAG_DEAD = 0xdeadbeefu };
+
+struct Geom {
+    double lo[3];
+    double hi[3];
+    double side;
+    double scale;  // 2^B / side, 0 when side == 0
+};
+
+struct PhaseTimes {
+    double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+}  // namespace h2
+
+struct h2_tree_s {
+    uint32_t tag = h2::TAG_TREE;
+    int refs = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0;
+    int d = 0, B = 0, q = 0, tau_num = 7, tau_den = 10;
+    h2::Geom geom{};
+    h2::DevBuf<double> xs[3];     // coordinates in Morton order, one array per dimension
+    h2::DevBuf<uint64_t> key;     // sorted Morton keys
+    h2::DevBuf<int32_t> perm;     // Morton position -> original index
+    h2::DevBuf<int32_t> iperm;    // original index -> Morton position
+    int nnodes = 0, nlevels = 0;
+    std::vector<int> lptr;        // host: nodes of level l are [lptr[l], lptr[l+1])
+    h2::DevBuf<int32_t> level, parent, fchild, nchild, begin, end;
+    h2::DevBuf<uint64_t> prefix;
+    h2::DevBuf<int64_t> near_ptr, far_ptr;
+    h2::DevBuf<int32_t> near_idx, far_idx;
+    int64_t nnear = 0, nfar = 0;
+    int max_leaf = 0;             // largest leaf population
+    double ms_tree = 0, ms_lists = 0;
+};
+
+struct h2_hidr_s {
+    uint32_t tag = h2::TAG_HIDR;
+    int refs = 0;
+    h2_tree_s *tree = nullptr;
+    cudaStream_t stream = nullptr;
+    int g1 = 0, g2 = 0;
+    // per node: count and device pointer into one of the per-level buffers
+    h2::DevBuf<int32_t> xcnt, ycnt;
+    h2::DevBuf<int32_t *> xptr, yptr;
+    std::vector<h2::DevBuf<int32_t>> xbufs, ybufs;
+    std::vector<int> xmax_level, ymax_level;  // host: largest set per level
+    int64_t xtotal = 0, ytotal = 0, tmax = 0;
+    double ms_up = 0, ms_down = 0;
+};
+
+struct h2_matrix_s {
+    uint32_t tag = h2::TAG_MATRIX;
+    int refs = 0;
+    h2_tree_s *tree = nullptr;
+    cudaStream_t stream = nullptr;
+    int kid = 1;
+    double kp[4] = {0, 0, 0, 0};
+    double id_tol = 0;
+    int prec = H2_PREC_FP64;
+    h2::DevBuf<int32_t> k, c;          // rank and candidate count per node
+    h2::DevBuf<int64_t> sk_off;        // exclusive scan of k over nodes (nnodes + 1)
+    h2::DevBuf<int32_t> skel;          // skeletons, node order, each sorted
+    h2::DevBuf<double> skc[3];         // skeleton coordinates, aligned with skel
+    h2::DevBuf<double *> uptr;         // per node U_i (c_i x k_i, column-major)
+    std::vector<h2::DevBuf<double>> ubufs;
+    std::vector<int> kmax_level, cmax_level;  // host
+    int64_t ktotal = 0, utotal = 0;
+    int kmax = 0;
+    double ms_construct = 0;
+    double flops_qr = 0, evals_block = 0;
+};
+
+namespace h2 {
+
+h2_tree_s *as_tree(void *h);
+h2_hidr_s *as_hidr(void *h);
+h2_matrix_s *as_matrix(void *h);
+
+// phases (host orchestration, defined in the per-phase .cu files)
+void tree_build_impl(h2_tree_s *t, const double *pts_dev_rowmajor);
+void lists_build_impl(h2_tree_s *t);
+void hidr_impl(h2_hidr_s *h);
+void construct_impl(h2_matrix_s *A, h2_hidr_s *h);
+void matvec_impl(h2_matrix_s *A, const double *x_dev, double *y_dev, cudaStream_t s);
+void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z_dev, const int64_t *rows_dev,
+                     int64_t nrows, double *out_dev, cudaStream_t s);
+
+void sampled_error_impl(const double *exact, const double *approx, const int64_t *rows, int64_t nrows, int64_t n,
+                        double *err_out, cudaStream_t s);
+
+// one DataReduct over an explicit point set (used by the calibration); ids
+// are labels 0..n-1 of the points in xs (SoA, n each).  Output sorted labels.
+int64_t datareduct_one(const double *const xs[3], int d, int64_t n, int g, int32_t *out_dev, cudaStream_t s);
+// Section 4.2 test problem at grid size g: relative Frobenius error of
+// K(Z1, Z2) ~= U K(Zhat1, Z2) where U comes from the ID (tolerance id_tol) of
+// K(DataReduct(Z2, g), Z1).  z1s, z2s: device SoA coordinates.
+double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *const z1s[3], int n1,
+                       const double *const z2s[3], int n2, int g, int *k_out, int *m_out, cudaStream_t s);
+
+}  // namespace h2
+
+// ----------------------------------------------------------- device math
+// Squared distance ((x0-y0)^2 + (x1-y1)^2) + (x2-y2)^2 with explicitly rounded
+// operations (no contraction), so that it is bit-identical to a plain IEEE
+// evaluation in this order.
+__device__ __forceinline__ double h2_dist2(int d, double a0, double a1, double a2, double b0, double b1,
+                                           double b2) {
+    double t = __dsub_rn(a0, b0);
+    double s = __dmul_rn(t, t);
+    if (d > 1) {
+        t = __dsub_rn(a1, b1);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    if (d > 2) {
+        t = __dsub_rn(a2, b2);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+// kappa(x, y) as a function of r^2 = |x - y|^2, float64 (Table 1 and section 2):
+// Coulomb 1/r with kappa(x, x) = 0; Gaussian exp(-r^2/h^2); exponential
+// exp(-r/l); multiquadric sqrt(1 + r^2).
+__device__ __forceinline__ double h2_kappa(int kid, double kp0, double r2) {
+    switch (kid) {
+    case H2_K_COULOMB: return r2 > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(r2)) : 0.0;
+    case H2_K_GAUSSIAN: return exp(-__ddiv_rn(r2, __dmul_rn(kp0, kp0)));
+    case H2_K_EXPONENTIAL: return exp(-__ddiv_rn(__dsqrt_rn(r2), kp0));
+    case H2_K_MULTIQUADRIC: return __dsqrt_rn(__dadd_rn(1.0, r2));
+    default: return 0.0;
+    }
+}
+
+// float32 kappa for the mixed-precision path
+__device__ __forceinline__ float h2_kappa_f(int kid, float kp0, float r2) {
+    switch (kid) {
+    case H2_K_COULOMB: return r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    case H2_K_GAUSSIAN: return __expf(-r2 / (kp0 * kp0));
+    case H2_K_EXPONENTIAL: return __expf(-sqrtf(r2) / kp0);
+    case H2_K_MULTIQUADRIC: return sqrtf(1.0f + r2);
+    default: return 0.0f;
+    }
+}
+
+// ----------------------------------------------------- block reductions
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}

@@ -1,0 +1,427 @@
+// hidr.cu -- hierarchical data reduction (section 3, Algorithm 1 of
+// arXiv 2206.01885) with the volume-based DataReduct of section 3.3.
+//
+// DataReduct(S, g^d): S itself (sorted) when |S| <= g^d; otherwise, for each
+// of the g^d cell-centred points q of a tensor grid on the bounding box of S,
+// the point of S nearest to q (float64 squared distance evaluated in a fixed
+// order without contraction; ties to the smaller Morton position), then the
+// distinct winners sorted.  One CTA reduces one node's set; all nodes of a
+// level run in one launch.
+#include <climits>
+
+#include "h2_internal.cuh"
+
+namespace h2 {
+namespace {
+
+constexpr int DR_THREADS = 256;
+constexpr int DR_TILE = 256;  // points staged in shared memory per pass
+constexpr int DR_GPT = 4;     // grid points per thread per sweep
+constexpr int DR_MAX_GRID = 16384;
+
+int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// ---------------------------------------------------------------- sizes
+// |S_i|: the leaf's points, or the sum of the children's |X_c*|
+__global__ void k_size_up(int lb, int nl, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
+                          const int32_t *end, const int32_t *xcnt, int g, int d, int64_t *sz, int64_t *cap) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nl) return;
+    int i = lb + a;
+    int64_t s = 0;
+    if (nchild[i] == 0) s = end[i] - begin[i];
+    else
+        for (int c = fchild[i]; c < fchild[i] + nchild[i]; c++) s += xcnt[c];
+    int64_t G = 1;
+    for (int k = 0; k < d; k++) G *= g;
+    sz[a] = s;
+    cap[a] = s < G ? s : G;
+}
+
+// |T_i| = |Y_p*| + sum over j in IL(i) of |X_j*|; one warp per node
+__global__ void k_size_down(int lb, int nl, const int32_t *parent, const int64_t *far_ptr, const int32_t *far_idx,
+                            const int32_t *xcnt, const int32_t *ycnt, int g, int d, int64_t *sz, int64_t *cap) {
+    int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (a >= nl) return;
+    int i = lb + a;
+    int64_t s = 0;
+    for (int64_t e = far_ptr[i] + lane; e < far_ptr[i + 1]; e += 32) s += xcnt[far_idx[e]];
+    s = warp_sum(s);
+    if (lane == 0) {
+        s += ycnt[parent[i]];
+        int64_t G = 1;
+        for (int k = 0; k < d; k++) G *= g;
+        sz[a] = s;
+        cap[a] = s < G ? s : G;
+    }
+}
+
+// --------------------------------------------------------------- gathers
+__global__ void k_gather_up(int lb, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
+                            const int32_t *end, int32_t *const *xptr, const int32_t *xcnt, const int64_t *toff,
+                            int32_t *tdata) {
+    int a = blockIdx.x;
+    int i = lb + a;
+    int32_t *dst = tdata + toff[a];
+    if (nchild[i] == 0) {
+        int32_t b0 = begin[i], n = end[i] - begin[i];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) dst[r] = b0 + r;
+        return;
+    }
+    int64_t w = 0;
+    for (int c = fchild[i]; c < fchild[i] + nchild[i]; c++) {
+        const int32_t *src = xptr[c];
+        int n = xcnt[c];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) dst[w + r] = src[r];
+        w += n;
+    }
+}
+
+__global__ void k_gather_down(int lb, const int32_t *parent, const int64_t *far_ptr, const int32_t *far_idx,
+                              int32_t *const *xptr, const int32_t *xcnt, int32_t *const *yptr, const int32_t *ycnt,
+                              const int64_t *toff, int32_t *tdata) {
+    int a = blockIdx.x;
+    int i = lb + a;
+    int32_t *dst = tdata + toff[a];
+    int p = parent[i];
+    int64_t w = 0;
+    {
+        const int32_t *src = yptr[p];
+        int n = ycnt[p];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) dst[r] = src[r];
+        w = n;
+    }
+    for (int64_t e = far_ptr[i]; e < far_ptr[i + 1]; e++) {
+        int j = far_idx[e];
+        const int32_t *src = xptr[j];
+        int n = xcnt[j];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) dst[w + r] = src[r];
+        w += n;
+    }
+}
+
+__global__ void k_set_ptrs(int lb, int nl, int32_t *base, const int64_t *off, int32_t **ptr) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < nl) ptr[lb + a] = base + off[a];
+}
+
+// ----------------------------------------------------------- DataReduct
+__device__ void block_bitonic_sort(int32_t *v, int P) {
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    bool asc = (i & k) == 0;
+                    int32_t x = v[i], y = v[ixj];
+                    if ((x > y) == asc) { v[i] = y; v[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// writes the distinct values of sorted v[0..P) (INT_MAX = padding) to out,
+// returns their number (valid in every thread)
+__device__ int block_unique_write(const int32_t *v, int P, int32_t *out, int *scratch) {
+    int chunk = (P + blockDim.x - 1) / blockDim.x;
+    int s0 = threadIdx.x * chunk, s1 = min(P, s0 + chunk);
+    int cnt = 0;
+    for (int i = s0; i < s1; i++)
+        if (v[i] != INT_MAX && (i == 0 || v[i] != v[i - 1])) cnt++;
+    // exclusive scan of cnt over the block
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? scratch[lane] : 0, wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < nw) scratch[lane] = wi - w;
+        if (lane == nw - 1) scratch[32] = wi;
+    }
+    __syncthreads();
+    int w = scratch[warp] + inc - cnt;
+    for (int i = s0; i < s1; i++)
+        if (v[i] != INT_MAX && (i == 0 || v[i] != v[i - 1])) out[w++] = v[i];
+    int total = scratch[32];
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
+__device__ __forceinline__ double dmax_(double a, double b) { return a > b ? a : b; }
+
+// One CTA per node.  tdata[toff[a] .. toff[a+1]) are the labels of S (T);
+// coordinates of label s are (x0[s], x1[s], x2[s]).
+__global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
+                                                           const double *x0, const double *x1, const double *x2,
+                                                           int32_t *const *outptr, int32_t *outcnt, int lb) {
+    extern __shared__ unsigned char smem_raw[];
+    int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
+    __shared__ int32_t tid_s[DR_TILE];
+    __shared__ double tx_s[3][DR_TILE];
+    __shared__ float tf_s[3][DR_TILE];
+    __shared__ double red[2][3][DR_THREADS / 32];
+    __shared__ int scratch[33];
+    const int a = blockIdx.x;
+    const int node = lb + a;
+    const int64_t t0 = toff[a], nt = toff[a + 1] - toff[a];
+    const int32_t *T = tdata + t0;
+    int32_t *out = outptr[node];
+    int G = 1;
+    for (int k = 0; k < d; k++) G *= g;
+    if (nt <= G) {  // DataReduct returns S itself
+        int P = 1;
+        while (P < nt) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) win[i] = i < nt ? T[i] : INT_MAX;
+        __syncthreads();
+        block_bitonic_sort(win, P);
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) out[i] = win[i];
+        if (threadIdx.x == 0) outcnt[node] = (int32_t)nt;
+        return;
+    }
+    // bounding box of S
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t r = threadIdx.x; r < nt; r += blockDim.x) {
+        int32_t s = T[r];
+        double c[3] = {x0[s], d > 1 ? x1[s] : 0.0, d > 2 ? x2[s] : 0.0};
+        for (int k = 0; k < 3; k++) { lo[k] = dmin_(lo[k], c[k]); hi[k] = dmax_(hi[k], c[k]); }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < 3; k++)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = dmin_(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = dmax_(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    if (lane == 0)
+        for (int k = 0; k < 3; k++) { red[0][k][warp] = lo[k]; red[1][k][warp] = hi[k]; }
+    __syncthreads();
+    double l[3], h[3];
+    for (int k = 0; k < 3; k++) {
+        double mn = red[0][k][0], mx = red[1][k][0];
+        for (int w = 1; w < nw; w++) { mn = dmin_(mn, red[0][k][w]); mx = dmax_(mx, red[1][k][w]); }
+        l[k] = mn;
+        h[k] = __ddiv_rn(__dsub_rn(mx, mn), (double)g);
+    }
+    // Nearest point to each grid point, DR_GPT grid points per thread per sweep.
+    // Exact float64 argmin through a float32 filter: with coordinates taken
+    // relative to the box corner l and W the largest box extent, the float32
+    // squared distance D32 differs from the float64 one by at most
+    // E = 1.7e-6 W^2 (per-coordinate error <= 3 u32 W, three squares and sums);
+    // the float64 winner therefore always satisfies D32 <= min D32 + 2E, so every
+    // point with D32 <= (running min D32) + M, M = 8e-6 W^2 >= 2E, is compared
+    // exactly in float64 with the smaller-label tie-break.
+    double W = 0.0;
+    for (int k = 0; k < d; k++) W = dmax_(W, __dmul_rn(h[k], (double)g));
+    const float M = (float)(8e-6 * W * W);
+    for (int gbase = 0; gbase < G; gbase += DR_THREADS * DR_GPT) {
+        double q[DR_GPT][3], bd[DR_GPT];
+        float qf[DR_GPT][3], thr[DR_GPT], b32[DR_GPT];
+        int32_t bi[DR_GPT];
+#pragma unroll
+        for (int j = 0; j < DR_GPT; j++) {
+            int gi = gbase + j * DR_THREADS + threadIdx.x;
+            int rem = gi;
+            for (int k = 0; k < 3; k++) {
+                int idx = 0;
+                if (k < d) { idx = rem % g; rem /= g; }
+                q[j][k] = k < d ? __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])) : 0.0;
+                qf[j][k] = k < d ? (float)__dsub_rn(q[j][k], l[k]) : 0.0f;
+            }
+            bd[j] = INFINITY;
+            bi[j] = INT_MAX;
+            b32[j] = INFINITY;
+            thr[j] = INFINITY;
+        }
+        for (int64_t tb = 0; tb < nt; tb += DR_TILE) {
+            int cnt = (int)(nt - tb < DR_TILE ? nt - tb : DR_TILE);
+            __syncthreads();
+            for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+                int32_t s = T[tb + r];
+                tid_s[r] = s;
+                double c0 = x0[s], c1 = d > 1 ? x1[s] : 0.0, c2 = d > 2 ? x2[s] : 0.0;
+                tx_s[0][r] = c0;
+                tx_s[1][r] = c1;
+                tx_s[2][r] = c2;
+                tf_s[0][r] = (float)__dsub_rn(c0, l[0]);
+                tf_s[1][r] = d > 1 ? (float)__dsub_rn(c1, l[1]) : 0.0f;
+                tf_s[2][r] = d > 2 ? (float)__dsub_rn(c2, l[2]) : 0.0f;
+            }
+            __syncthreads();
+            for (int r = 0; r < cnt; r++) {
+                float f0 = tf_s[0][r], f1 = tf_s[1][r], f2 = tf_s[2][r];
+#pragma unroll
+                for (int j = 0; j < DR_GPT; j++) {
+                    float e0 = f0 - qf[j][0], e1 = f1 - qf[j][1], e2 = f2 - qf[j][2];
+                    float d32 = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
+                    if (d32 <= thr[j]) {
+                        if (d32 < b32[j]) { b32[j] = d32; thr[j] = d32 + M; }
+                        int32_t s = tid_s[r];
+                        double dd = h2_dist2(d, tx_s[0][r], tx_s[1][r], tx_s[2][r], q[j][0], q[j][1], q[j][2]);
+                        if (dd < bd[j] || (dd == bd[j] && s < bi[j])) { bd[j] = dd; bi[j] = s; }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < DR_GPT; j++) {
+            int gi = gbase + j * DR_THREADS + threadIdx.x;
+            if (gi < G) win[gi] = bi[j];
+        }
+    }
+    __syncthreads();
+    int P = 1;
+    while (P < G) P <<= 1;
+    for (int i = G + threadIdx.x; i < P; i += blockDim.x) win[i] = INT_MAX;
+    __syncthreads();
+    block_bitonic_sort(win, P);
+    int m = block_unique_write(win, P, out, scratch);
+    if (threadIdx.x == 0) outcnt[node] = m;
+}
+
+int64_t gridsize(int g, int d) {
+    int64_t G = 1;
+    for (int k = 0; k < d; k++) G *= g;
+    return G;
+}
+
+void launch_datareduct(const int64_t *toff, const int32_t *tdata, int nl, int g, int d, const double *const xs[3],
+                       int32_t *const *outptr, int32_t *outcnt, int lb, cudaStream_t s) {
+    if (nl <= 0) return;
+    int G = (int)gridsize(g, d);
+    size_t sm = (size_t)next_pow2(G) * sizeof(int32_t);
+    static bool attr_set = false;
+    if (!attr_set) {
+        H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     DR_MAX_GRID * (int)sizeof(int32_t)));
+        attr_set = true;
+    }
+    ProfScope ps(KT_DATAREDUCT, s);
+    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, xs[0], xs[1], xs[2], outptr, outcnt, lb);
+    H2_LAUNCH("k_datareduct");
+}
+
+}  // namespace
+
+void hidr_impl(h2_hidr_s *h) {
+    h2_tree_s *t = h->tree;
+    cudaStream_t s = h->stream;
+    const int nn = t->nnodes, d = t->d;
+    H2_REQUIRE(gridsize(h->g1, d) <= DR_MAX_GRID && gridsize(h->g2, d) <= DR_MAX_GRID,
+               "g^dim must be at most 16384");
+    h->xcnt.alloc(nn, s);
+    h->ycnt.alloc(nn, s);
+    h->xptr.alloc(nn, s);
+    h->yptr.alloc(nn, s);
+    H2_CUDA(cudaMemsetAsync(h->xcnt.p, 0, nn * sizeof(int32_t), s));
+    H2_CUDA(cudaMemsetAsync(h->ycnt.p, 0, nn * sizeof(int32_t), s));
+    H2_CUDA(cudaMemsetAsync(h->xptr.p, 0, nn * sizeof(int32_t *), s));
+    H2_CUDA(cudaMemsetAsync(h->yptr.p, 0, nn * sizeof(int32_t *), s));
+    const double *xs[3] = {t->xs[0].p, t->xs[1].p, t->xs[2].p};
+    h->xbufs.resize(t->nlevels);
+    h->ybufs.resize(t->nlevels);
+    h->xmax_level.assign(t->nlevels, 0);
+    h->ymax_level.assign(t->nlevels, 0);
+    DevBuf<int64_t> sz, cap, toff, coff;
+    DevBuf<int32_t> tdata;
+    cudaEvent_t e0, e1, e2;
+    H2_CUDA(cudaEventCreate(&e0));
+    H2_CUDA(cudaEventCreate(&e1));
+    H2_CUDA(cudaEventCreate(&e2));
+    H2_CUDA(cudaEventRecord(e0, s));
+    // bottom-up: X_i* = DataReduct(S_i, g1^d), deepest level first
+    for (int l = t->nlevels - 1; l >= 1; l--) {
+        int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
+        sz.alloc(nl, s); cap.alloc(nl, s); toff.alloc(nl + 1, s); coff.alloc(nl + 1, s);
+        k_size_up<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, t->nchild.p, t->fchild.p, t->begin.p, t->end.p,
+                                                       h->xcnt.p, h->g1, d, sz.p, cap.p);
+        H2_LAUNCH("k_size_up");
+        scan_exclusive(sz.p, toff.p, nl, s);
+        scan_exclusive(cap.p, coff.p, nl, s);
+        int64_t ttot = read_scalar(toff.p + nl, s), ctot = read_scalar(coff.p + nl, s);
+        h->tmax = std::max(h->tmax, ttot);
+        tdata.alloc(ttot > 0 ? ttot : 1, s);
+        h->xbufs[l].alloc(ctot > 0 ? ctot : 1, s);
+        k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, h->xbufs[l].p, coff.p, h->xptr.p);
+        H2_LAUNCH("k_set_ptrs");
+        k_gather_up<<<nl, 256, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, t->end.p, h->xptr.p, h->xcnt.p,
+                                       toff.p, tdata.p);
+        H2_LAUNCH("k_gather_up");
+        launch_datareduct(toff.p, tdata.p, nl, h->g1, d, xs, h->xptr.p, h->xcnt.p, lb, s);
+        h->xtotal += ctot;
+    }
+    H2_CUDA(cudaEventRecord(e1, s));
+    // top-down: Y_i* = DataReduct(Y_p* u X_j* (j in IL(i)), g2^d), level 1 first
+    for (int l = 1; l < t->nlevels; l++) {
+        int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
+        sz.alloc(nl, s); cap.alloc(nl, s); toff.alloc(nl + 1, s); coff.alloc(nl + 1, s);
+        k_size_down<<<blocks_for((int64_t)nl * 32, 256), 256, 0, s>>>(lb, nl, t->parent.p, t->far_ptr.p,
+                                                                       t->far_idx.p, h->xcnt.p, h->ycnt.p, h->g2, d,
+                                                                       sz.p, cap.p);
+        H2_LAUNCH("k_size_down");
+        scan_exclusive(sz.p, toff.p, nl, s);
+        scan_exclusive(cap.p, coff.p, nl, s);
+        int64_t ttot = read_scalar(toff.p + nl, s), ctot = read_scalar(coff.p + nl, s);
+        h->tmax = std::max(h->tmax, ttot);
+        tdata.alloc(ttot > 0 ? ttot : 1, s);
+        h->ybufs[l].alloc(ctot > 0 ? ctot : 1, s);
+        k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, h->ybufs[l].p, coff.p, h->yptr.p);
+        H2_LAUNCH("k_set_ptrs");
+        k_gather_down<<<nl, 256, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->xptr.p, h->xcnt.p,
+                                         h->yptr.p, h->ycnt.p, toff.p, tdata.p);
+        H2_LAUNCH("k_gather_down");
+        launch_datareduct(toff.p, tdata.p, nl, h->g2, d, xs, h->yptr.p, h->ycnt.p, lb, s);
+        h->ytotal += ctot;
+    }
+    H2_CUDA(cudaEventRecord(e2, s));
+    H2_CUDA(cudaEventSynchronize(e2));
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, e0, e1);
+    cudaEventElapsedTime(&b, e1, e2);
+    h->ms_up = a;
+    h->ms_down = b;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    // per-level maxima of |X*| and |Y*| for later launch sizing
+    std::vector<int32_t> xc = read_vec(h->xcnt.p, nn, s), yc = read_vec(h->ycnt.p, nn, s);
+    for (int l = 0; l < t->nlevels; l++)
+        for (int i = t->lptr[l]; i < t->lptr[l + 1]; i++) {
+            h->xmax_level[l] = std::max(h->xmax_level[l], (int)xc[i]);
+            h->ymax_level[l] = std::max(h->ymax_level[l], (int)yc[i]);
+        }
+}
+
+int64_t datareduct_one(const double *const xs[3], int d, int64_t n, int g, int32_t *out_dev, cudaStream_t s) {
+    // one node whose set is the labels 0..n-1
+    DevBuf<int64_t> toff;
+    DevBuf<int32_t> tdata, cnt;
+    DevBuf<int32_t *> optr;
+    toff.alloc(2, s);
+    tdata.alloc(n, s);
+    cnt.alloc(1, s);
+    optr.alloc(1, s);
+    std::vector<int32_t> ids(n);
+    for (int64_t i = 0; i < n; i++) ids[i] = (int32_t)i;
+    int64_t offs[2] = {0, n};
+    H2_CUDA(cudaMemcpyAsync(toff.p, offs, sizeof offs, cudaMemcpyHostToDevice, s));
+    H2_CUDA(cudaMemcpyAsync(tdata.p, ids.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    H2_CUDA(cudaMemcpyAsync(optr.p, &out_dev, sizeof(int32_t *), cudaMemcpyHostToDevice, s));
+    launch_datareduct(toff.p, tdata.p, 1, g, d, xs, optr.p, cnt.p, 0, s);
+    return read_scalar(cnt.p, s);
+}
+
+}  // namespace h2

@@ -1,0 +1,316 @@
+"""Python binding of the sm_103a H^2 library (``include/h2.h``).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch supplies device memory (CUDA tensors) and the current stream.  If the
+shared library is missing this module raises instead of falling back to
+anything else.
+
+Names follow the C ABI: ``tree_build``, ``hidr_reduce``, ``construct``,
+``matvec``, ``exact_rows``, ``calibrate``, ``free``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libh2gb300.so")
+
+KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NUMERIC", 6: "UNIMPLEMENTED",
+          7: "STATE"}
+
+TREE_FIELDS = {"perm": (0, np.int64), "keys": (1, np.uint64), "level": (2, np.int32), "parent": (3, np.int32),
+               "fchild": (4, np.int32), "nchild": (5, np.int32), "begin": (6, np.int64), "end": (7, np.int64),
+               "prefix": (8, np.uint64), "lptr": (9, np.int32), "near_ptr": (10, np.int64),
+               "far_ptr": (11, np.int64), "near_idx": (12, np.int32), "far_idx": (13, np.int32),
+               "info": (14, np.int64), "geom": (15, np.float64)}
+MAT_FIELDS = {"rank": (0, np.int32), "ncand": (1, np.int32), "skel": (2, np.int32), "U": (3, np.float64),
+              "info": (4, np.int64)}
+
+_lib = None
+
+
+class H2Error(RuntimeError):
+    def __init__(self, call: str, status: int, msg: str):
+        super().__init__(f"{call}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Params(C.Structure):
+    _fields_ = [("leaf_size", C.c_int), ("tau_num", C.c_int), ("tau_den", C.c_int)]
+
+
+def lib():
+    """Load the shared library (built by ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with paper_2206_01885_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+        sig = {
+            "h2_tree_build": [vp, i64, i32, i32, C.POINTER(_Params), vp, C.POINTER(vp)],
+            "h2_tree_get": [vp, i32, vp, i64, C.POINTER(i64)],
+            "h2_hidr_reduce": [vp, i32, i32, vp, C.POINTER(vp)],
+            "h2_hidr_get": [vp, i32, vp, vp, i64, C.POINTER(i64)],
+            "h2_construct": [vp, vp, i32, vp, dbl, i32, vp, C.POINTER(vp)],
+            "h2_matrix_get": [vp, i32, vp, i64, C.POINTER(i64)],
+            "h2_matvec": [vp, vp, vp, i32, vp],
+            "h2_exact_rows": [vp, i32, vp, vp, vp, i64, vp, i32, vp],
+            "h2_calibrate": [i32, i32, vp, dbl, vp, i32, vp, i32, i32, vp, C.POINTER(i32), C.POINTER(dbl)],
+            "h2_free": [vp],
+            "h2_get_stats": [vp, C.c_char_p, i64],
+            "h2_sampled_error": [vp, vp, vp, i64, i64, vp, i32, vp],
+            "h2_profile": [i32, i32],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.h2_last_error.restype = C.c_char_p
+        L.h2_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(call: str, st: int):
+    if st != 0:
+        raise H2Error(call, st, lib().h2_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _kid(kernel) -> int:
+    return KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+
+
+def _kparams(kparams):
+    a = (C.c_double * 4)()
+    for i, v in enumerate(kparams or ()):
+        a[i] = float(v)
+    return a
+
+
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _ptr(x):
+    """(pointer, on_device, keepalive) for a torch tensor or numpy array."""
+    if _is_cuda(x):
+        assert x.is_contiguous()
+        return C.c_void_p(x.data_ptr()), 1, x
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data_as(C.c_void_p), 0, a
+
+
+def stats(handle) -> str:
+    buf = C.create_string_buffer(2048)
+    _check("h2_get_stats", lib().h2_get_stats(handle, buf, 2048))
+    return buf.value.decode()
+
+
+class _Handle:
+    _h = None
+
+    def free(self):
+        if self._h:
+            _check("h2_free", lib().h2_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.h2_free(self._h)
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> str:
+        return stats(self._h)
+
+
+class Tree(_Handle):
+    """h2_tree_build: Morton cluster tree and near/far interaction lists."""
+
+    def __init__(self, points, leaf_size: int, tau=(7, 10), stream=None):
+        if not _is_cuda(points):
+            points = np.ascontiguousarray(points, dtype=np.float64)
+        n, d = points.shape
+        p, on_dev, keep = _ptr(points)
+        prm = _Params(int(leaf_size), int(tau[0]), int(tau[1]))
+        h = C.c_void_p()
+        _check("h2_tree_build", lib().h2_tree_build(p, n, d, on_dev, C.byref(prm), _stream(stream), C.byref(h)))
+        self._h = h.value
+        info = self.get("info")
+        self.n, self.d, self.B, self.nnodes, self.nlevels, self.nnear, self.nfar, self.q = (int(v) for v in info)
+
+    def get(self, what: str) -> np.ndarray:
+        code, dt = TREE_FIELDS[what]
+        ln = C.c_int64(0)
+        _check("h2_tree_get", lib().h2_tree_get(self._h, code, None, 0, C.byref(ln)))
+        out = np.zeros(max(ln.value, 1), dtype=dt)
+        _check("h2_tree_get", lib().h2_tree_get(self._h, code, out.ctypes.data_as(C.c_void_p), out.size,
+                                                 C.byref(ln)))
+        return out[:ln.value]
+
+
+class Hidr(_Handle):
+    """h2_hidr_reduce: X_i*, Y_i* of Algorithm 1."""
+
+    def __init__(self, tree: Tree, g1: int, g2: int, stream=None):
+        h = C.c_void_p()
+        _check("h2_hidr_reduce", lib().h2_hidr_reduce(tree.handle, int(g1), int(g2), _stream(stream), C.byref(h)))
+        self._h = h.value
+        self.tree = tree
+
+    def get(self, which: str):
+        """(counts[nnodes], data) for which in {'x', 'y'}."""
+        w = 0 if which == "x" else 1
+        nn = self.tree.nnodes
+        counts = np.zeros(nn, dtype=np.int32)
+        tot = C.c_int64(0)
+        _check("h2_hidr_get", lib().h2_hidr_get(self._h, w, counts.ctypes.data_as(C.c_void_p), None, 0,
+                                                 C.byref(tot)))
+        data = np.zeros(max(tot.value, 1), dtype=np.int32)
+        _check("h2_hidr_get", lib().h2_hidr_get(self._h, w, None, data.ctypes.data_as(C.c_void_p), data.size,
+                                                 C.byref(tot)))
+        return counts, data[:tot.value]
+
+
+class H2Matrix(_Handle):
+    """h2_construct: nested bases (Algorithm 2); .matvec applies K~."""
+
+    def __init__(self, tree: Tree, hidr: Hidr, kernel, kparams=(), id_tol: float = 1e-6, precision="fp64",
+                 stream=None):
+        h = C.c_void_p()
+        kp = _kparams(kparams)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check("h2_construct", lib().h2_construct(tree.handle, hidr.handle, _kid(kernel), kp, float(id_tol), prec,
+                                                   _stream(stream), C.byref(h)))
+        self._h = h.value
+        self.tree = tree
+
+    def get(self, what: str) -> np.ndarray:
+        code, dt = MAT_FIELDS[what]
+        ln = C.c_int64(0)
+        _check("h2_matrix_get", lib().h2_matrix_get(self._h, code, None, 0, C.byref(ln)))
+        out = np.zeros(max(ln.value, 1), dtype=dt)
+        _check("h2_matrix_get", lib().h2_matrix_get(self._h, code, out.ctypes.data_as(C.c_void_p), out.size,
+                                                     C.byref(ln)))
+        return out[:ln.value]
+
+    def matvec(self, x, y=None, stream=None):
+        """y = K~ x.  x: CUDA float64 tensor (result on the device) or a host
+        array (copied in and out by the library)."""
+        if _is_cuda(x):
+            import torch
+            if y is None:
+                y = torch.empty_like(x)
+            _check("h2_matvec", lib().h2_matvec(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), 1,
+                                                 _stream(stream)))
+            return y
+        xa = np.ascontiguousarray(x, dtype=np.float64)
+        ya = np.zeros_like(xa) if y is None else y
+        _check("h2_matvec", lib().h2_matvec(self._h, xa.ctypes.data_as(C.c_void_p), ya.ctypes.data_as(C.c_void_p),
+                                             0, _stream(stream)))
+        return ya
+
+
+def tree_build(points, leaf_size, tau=(7, 10), stream=None) -> Tree:
+    return Tree(points, leaf_size, tau, stream)
+
+
+def hidr_reduce(tree, g1, g2, stream=None) -> Hidr:
+    return Hidr(tree, g1, g2, stream)
+
+
+def construct(tree, hidr, kernel, kparams=(), id_tol=1e-6, precision="fp64", stream=None) -> H2Matrix:
+    return H2Matrix(tree, hidr, kernel, kparams, id_tol, precision, stream)
+
+
+def matvec(A: H2Matrix, x, y=None, stream=None):
+    return A.matvec(x, y, stream)
+
+
+def exact_rows(tree: Tree, kernel, kparams, z, rows, out=None, stream=None):
+    """(K z)_s for s in rows, float64 sums on the GPU."""
+    kp = _kparams(kparams)
+    if _is_cuda(z):
+        import torch
+        if out is None:
+            out = torch.empty(len(rows), dtype=torch.float64, device=z.device)
+        _check("h2_exact_rows", lib().h2_exact_rows(tree.handle, _kid(kernel), kp, C.c_void_p(z.data_ptr()),
+                                                     C.c_void_p(rows.data_ptr()), len(rows),
+                                                     C.c_void_p(out.data_ptr()), 1, _stream(stream)))
+        return out
+    za = np.ascontiguousarray(z, dtype=np.float64)
+    ra = np.ascontiguousarray(rows, dtype=np.int64)
+    oa = np.zeros(len(ra))
+    _check("h2_exact_rows", lib().h2_exact_rows(tree.handle, _kid(kernel), kp, za.ctypes.data_as(C.c_void_p),
+                                                 ra.ctypes.data_as(C.c_void_p), len(ra),
+                                                 oa.ctypes.data_as(C.c_void_p), 0, _stream(stream)))
+    return oa
+
+
+def calibrate(dim, kernel, kparams, eps, z1, z2, gmax=16, stream=None):
+    """Section 4.2: smallest g (r1 = r2 = g^dim) meeting the test; (g, error)."""
+    kp = _kparams(kparams)
+    a1 = np.ascontiguousarray(z1, dtype=np.float64)
+    a2 = np.ascontiguousarray(z2, dtype=np.float64)
+    g = C.c_int(0)
+    err = C.c_double(0.0)
+    _check("h2_calibrate", lib().h2_calibrate(int(dim), _kid(kernel), kp, float(eps), a1.ctypes.data_as(C.c_void_p),
+                                               len(a1), a2.ctypes.data_as(C.c_void_p), len(a2), int(gmax),
+                                               _stream(stream), C.byref(g), C.byref(err)))
+    return g.value, err.value
+
+
+def free(handle_obj):
+    handle_obj.free()
+
+
+def sampled_error(exact, approx, rows, stream=None):
+    """||exact - approx[rows]|| / ||exact|| (section 6 metric on sampled rows).
+    CUDA tensors give a CUDA scalar tensor; host arrays give a float."""
+    L = lib()
+    if _is_cuda(exact):
+        import torch
+        out = torch.empty(1, dtype=torch.float64, device=exact.device)
+        _check("h2_sampled_error", L.h2_sampled_error(C.c_void_p(exact.data_ptr()), C.c_void_p(approx.data_ptr()),
+                                                       C.c_void_p(rows.data_ptr()), len(rows), approx.numel(),
+                                                       C.c_void_p(out.data_ptr()), 1, _stream(stream)))
+        return out
+    e = np.ascontiguousarray(exact, dtype=np.float64)
+    a = np.ascontiguousarray(approx, dtype=np.float64)
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    out = C.c_double(0.0)
+    _check("h2_sampled_error", L.h2_sampled_error(e.ctypes.data_as(C.c_void_p), a.ctypes.data_as(C.c_void_p),
+                                                   r.ctypes.data_as(C.c_void_p), len(r), len(a), C.byref(out), 0,
+                                                   _stream(stream)))
+    return out.value
+
+
+def profile(enable: bool = True, reset: bool = True):
+    """Turn per-kernel CUDA-event timing on or off (and zero its totals)."""
+    _check("h2_profile", lib().h2_profile(int(enable), int(reset)))
+
+
+def kernel_times() -> dict:
+    """{kernel: {"ms": total, "launches": n}} collected while profiling."""
+    import json
+    buf = C.create_string_buffer(8192)
+    _check("h2_get_stats", lib().h2_get_stats(None, buf, 8192))
+    return json.loads(buf.value.decode())

@@ -1,0 +1,171 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bit-exact: permutation, keys, node arrays, near/far lists, X_i*, Y_i*.
+Float64 construction: ranks and skeletons equal (the kernel blocks are
+bit-identical for Coulomb; pivot near-ties are reported, none occur here), U
+within 64 u c / eps of the oracle's (u = 2^-53, the conditioning bound of
+R11^{-1} R12 after truncation at eps), the H^2 matvec within 1e-12 of the oracle's
+H^2 matvec and within 10 eps of the dense product; exact rows within 1e-12.
+Sizes span several levels and tiles and include ragged leaves."""
+import numpy as np
+import pytest
+
+from oracle import h2_oracle as O
+from paper_2206_01885_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_01885_gb300 import build as B
+    B.build()
+    from paper_2206_01885_gb300 import h2
+    return h2
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+TREE_CASES = [
+    ("cube3d", lambda: I.uniform_cube(5000, 3, seed=1), 64),
+    ("cube3d_q1", lambda: I.uniform_cube(700, 3, seed=2), 1),
+    ("gmix2d", lambda: I.gaussian_mixture(20000, seed=3), 32),
+    ("sphere", lambda: I.sphere_surface(6000, seed=4), 40),
+    ("dups", lambda: np.repeat(I.uniform_cube(50, 3, seed=5), 9, axis=0), 4),
+    ("single_leaf", lambda: I.uniform_cube(100, 3, seed=6), 500),
+    ("n1", lambda: np.array([[0.25, 0.5, 0.75]]), 8),
+    ("n2_2d", lambda: np.array([[0.0, 0.0], [1.0, 1.0]]), 1),
+    ("all_same", lambda: np.tile([[0.1, 0.2, 0.3]], (40, 1)), 4),
+]
+
+
+@pytest.mark.parametrize("name,make,q", TREE_CASES, ids=[c[0] for c in TREE_CASES])
+def test_tree_and_lists_bit_exact(H2, name, make, q):
+    pts = make()
+    t = H2.Tree(dev(pts), q)
+    o = O.tree_build(pts, q)
+    assert t.nnodes == o.nnodes and t.nlevels == o.nlevels
+    for f in ["perm", "keys", "level", "parent", "fchild", "nchild", "begin", "end", "prefix", "lptr",
+              "near_ptr", "near_idx", "far_ptr", "far_idx"]:
+        got = t.get(f)
+        want = getattr(o, f.replace("keys", "key"))
+        assert np.array_equal(got, want.astype(got.dtype)), f
+    # host input path gives the same tree
+    t2 = H2.Tree(pts, q)
+    assert np.array_equal(t2.get("perm"), o.perm)
+
+
+HIDR_CASES = [("cube3d", 3, 6000, 60, 4, 5), ("gmix2d", 2, 8000, 30, 6, 7), ("cube3d_g2", 3, 3000, 20, 2, 3)]
+
+
+@pytest.mark.parametrize("name,d,n,q,g1,g2", HIDR_CASES, ids=[c[0] for c in HIDR_CASES])
+def test_hidr_bit_exact(H2, name, d, n, q, g1, g2):
+    pts = I.uniform_cube(n, d, seed=10 + d) if "cube" in name else I.gaussian_mixture(n, seed=11)
+    t = H2.Tree(dev(pts), q)
+    h = H2.Hidr(t, g1, g2)
+    o = O.tree_build(pts, q)
+    oh = O.Hidr(o, g1, g2)
+    for which in ["x", "y"]:
+        cnt, data = h.get(which)
+        off = np.concatenate([[0], np.cumsum(cnt)])
+        for i in range(1, t.nnodes):
+            want = oh.get(i, which)
+            got = data[off[i]:off[i + 1]]
+            assert np.array_equal(got, want), (which, i)
+
+
+def _node_cands(o, H, i):
+    if o.nchild[i] == 0:
+        return np.arange(o.begin[i], o.end[i])
+    return np.concatenate([H.skeleton(c) for c in range(o.fchild[i], o.fchild[i] + o.nchild[i])])
+
+
+CONSTRUCT_CASES = [
+    ("coulomb3d", 3, 6000, 100, "coulomb", (), 1e-6, 6),
+    ("coulomb3d_deep", 3, 12000, 40, "coulomb", (), 1e-5, 5),
+    ("gauss2d", 2, 6000, 64, "gaussian", (0.2,), 1e-6, 10),
+    ("expo2d", 2, 5000, 50, "exponential", (0.1,), 1e-6, 10),
+    ("mq3d", 3, 4000, 64, "multiquadric", (), 1e-7, 6),
+]
+
+
+@pytest.mark.parametrize("name,d,n,q,kern,kp,eps,g", CONSTRUCT_CASES, ids=[c[0] for c in CONSTRUCT_CASES])
+def test_construct_and_matvec_fp64(H2, name, d, n, q, kern, kp, eps, g):
+    pts = I.uniform_cube(n, d, seed=20 + d)
+    z = I.standard_normal(n, seed=21)
+    t = H2.Tree(dev(pts), q)
+    h = H2.Hidr(t, g, g)
+    A = H2.H2Matrix(t, h, kern, kp, eps)
+    o, oh, OH = O.build_h2(pts, kern, kp, q, eps, g, g)
+    ranks = A.get("rank")
+    want_ranks = np.array([max(OH.rank(i), 0) for i in range(o.nnodes)])
+    assert np.array_equal(ranks, want_ranks)
+    skel = A.get("skel")
+    U = A.get("U")
+    nc = A.get("ncand")
+    koff = np.concatenate([[0], np.cumsum(ranks)])
+    uoff = np.concatenate([[0], np.cumsum(ranks.astype(np.int64) * nc)])
+    for i in range(1, o.nnodes):
+        k = ranks[i]
+        if k == 0:
+            continue
+        assert np.array_equal(skel[koff[i]:koff[i + 1]], OH.skeleton(i)), i
+        Ui = U[uoff[i]:uoff[i + 1]].reshape(k, nc[i]).T
+        Uo = OH.U(i)
+        assert Ui.shape == Uo.shape
+        # U = P[I; (R11^{-1} R12)^T]: reordered float64 sums perturb R by ~c u |r_11|
+        # and the solve amplifies that by cond(R11) <~ |r_11| / |r_kk| < 1 / eps
+        tol = 64 * 2.0 ** -53 * nc[i] / eps
+        assert np.max(np.abs(Ui - Uo)) <= tol * max(1.0, np.max(np.abs(Uo))), i
+    y = A.matvec(dev(z)).cpu().numpy()
+    yo = OH.matvec(z)
+    assert np.linalg.norm(y - yo) <= 1e-12 * np.linalg.norm(yo)
+    yd = O.dense_matvec(pts, kern, kp, z)
+    assert np.linalg.norm(y - yd) / np.linalg.norm(yd) <= 10 * eps
+    # host-pointer matvec is the same product
+    yh = A.matvec(z)
+    assert np.array_equal(yh, y)
+
+
+def test_exact_rows(H2):
+    pts = I.uniform_cube(20000, 3, seed=31)
+    z = I.standard_normal(20000, seed=32)
+    rows = I.sample_rows(20000, 300, seed=33)
+    t = H2.Tree(dev(pts), 128)
+    got = H2.exact_rows(t, "coulomb", (), dev(z), dev(rows)).cpu().numpy()
+    want = O.exact_rows(pts, "coulomb", (), z, rows)
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    got_h = H2.exact_rows(t, "coulomb", (), z, rows)
+    assert np.array_equal(got_h, got)
+
+
+def test_degenerate_paths(H2):
+    # one point, a single leaf, identical points: matvec reduces to the nearfield
+    for pts, q in [(np.array([[0.5, 0.5, 0.5]]), 4), (I.uniform_cube(90, 3, seed=3), 200),
+                   (np.tile([[0.1, 0.2, 0.3]], (30, 1)), 4)]:
+        z = I.standard_normal(len(pts), seed=4)
+        t = H2.Tree(dev(pts), q)
+        h = H2.Hidr(t, 3, 3)
+        A = H2.H2Matrix(t, h, "coulomb", (), 1e-6)
+        y = A.matvec(dev(z)).cpu().numpy()
+        yd = O.dense_matvec(pts, "coulomb", (), z)
+        assert np.allclose(y, yd, rtol=1e-13, atol=1e-13 * max(1.0, np.abs(yd).max()))
+
+
+def test_handle_lifetimes(H2):
+    pts = I.uniform_cube(2000, 3, seed=41)
+    t = H2.Tree(dev(pts), 50)
+    h = H2.Hidr(t, 3, 3)
+    assert H2.lib().h2_free(t.handle) == 7  # the hidr depends on the tree
+    A = H2.H2Matrix(t, h, "coulomb", (), 1e-4)
+    st = H2.lib().h2_free(t.handle)
+    assert st == 7  # tree has dependents
+    A.free()
+    h.free()
+    t.free()

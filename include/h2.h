@@ -208,6 +208,28 @@ h2_status h2_exact_rows(h2_tree t, int kernel, const double *kparams, const doub
                         const int64_t *rows, int64_t nrows, double *out, int on_device,
                         void *stream);
 
+/* Allocation-free variant of h2_exact_rows, for callers that must not
+ * allocate device memory during the call: code running while a CUDA graph is
+ * being captured on another stream of the same device, applications whose
+ * memory is fully reserved up front by another allocator, or real-time loops
+ * that forbid allocator calls (cudaMalloc can synchronise the device and fail
+ * under memory pressure).  The paper has no counterpart; it computes exactly
+ * what h2_exact_rows computes.  Differences from h2_exact_rows:
+ *   - z, rows and out must be device pointers (no host staging);
+ *   - the tree may hold at most 1,048,576 points: the permuted right-hand side
+ *     is kept in a fixed 8 MiB array inside the library image, which every GPU
+ *     that loads the library holds until the process exits; larger trees are
+ *     rejected with H2_ERR_INVALID_ARG;
+ *   - no cudaMalloc, cudaFree or other allocating call is made; the first call
+ *     on a device looks up the array's device address (cudaGetSymbolAddress),
+ *     so make that first call before any stream capture begins;
+ *   - every call shares the one array (it is fully overwritten on each call),
+ *     so calls that may overlap on the GPU -- on different streams without
+ *     ordering between them -- race and must not be issued.
+ * Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
+h2_status h2_exact_rows_noalloc(h2_tree t, int kernel, const double *kparams, const double *z,
+                                const int64_t *rows, int64_t nrows, double *out, void *stream);
+
 /* The section 6 error on sampled rows: *err_out = ||exact - approx[rows]||_2
  * / ||exact||_2, with exact[r] = (K z)_{rows[r]} from h2_exact_rows and approx
  * the full H^2 product (n entries, original order).  Device pointers if

@@ -349,6 +349,19 @@ h2_status h2_exact_rows(h2_tree th, int kernel, const double *kparams, const dou
     });
 }
 
+h2_status h2_exact_rows_noalloc(h2_tree th, int kernel, const double *kparams, const double *z, const int64_t *rows,
+                                int64_t nrows, double *out, void *stream) {
+    return guard([&] {
+        h2_tree_s *t = as_tree(th);
+        H2_REQUIRE(valid_kernel(kernel), "unknown kernel id");
+        H2_REQUIRE(z != nullptr && (nrows == 0 || (rows != nullptr && out != nullptr)), "NULL argument");
+        H2_REQUIRE(nrows >= 0 && nrows < (int64_t)INT32_MAX, "bad nrows");
+        double kp[4];
+        kparams_check(kernel, kparams, kp);
+        exact_rows_noalloc_impl(t, kernel, kp, z, rows, nrows, out, static_cast<cudaStream_t>(stream));
+    });
+}
+
 h2_status h2_free(void *handle) {
     return guard([&] {
         if (!handle) return;

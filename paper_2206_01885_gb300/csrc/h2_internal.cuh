@@ -204,6 +204,8 @@ void matvec_impl(h2_matrix_s *A, const double *x_dev, double *y_dev, cudaStream_
 void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z_dev, const int64_t *rows_dev,
                      int64_t nrows, double *out_dev, cudaStream_t s);
 
+void exact_rows_noalloc_impl(h2_tree_s *t, int kid, const double *kp, const double *z_dev, const int64_t *rows_dev,
+                             int64_t nrows, double *out_dev, cudaStream_t s);
 void sampled_error_impl(const double *exact, const double *approx, const int64_t *rows, int64_t nrows, int64_t n,
                         double *err_out, cudaStream_t s);
 

@@ -7,7 +7,15 @@
 //   downward  [zh_c1; ...] += U_p zh_p (parent), y_i = U_i zh_i (leaf)
 //   near      y_i += K(X_i, X_j) x_j over near leaf pairs (on the fly)
 // Vectors live in Morton order inside; x and y are permuted at the ends.
+#include <mutex>
+
 #include "h2_internal.cuh"
+
+// Scratch of h2_exact_rows_noalloc: the right-hand side permuted to Morton
+// order.  It lives in the library image, so every GPU that loads the library
+// holds these H2_NOALLOC_MAX_N doubles (8 MiB) until the process exits.
+#define H2_NOALLOC_MAX_N (1 << 20)
+static __device__ __align__(256) double g_noalloc_zm[H2_NOALLOC_MAX_N];
 
 namespace h2 {
 namespace {
@@ -300,6 +308,41 @@ void sampled_error_impl(const double *exact, const double *approx, const int64_t
                         double *err_out, cudaStream_t s) {
     k_sampled_error<<<1, 1024, 0, s>>>(exact, approx, rows, nrows, n, err_out);
     H2_LAUNCH("k_sampled_error");
+}
+
+// Device address of g_noalloc_zm on the current device.  Host code cannot use
+// the symbol's name as a device pointer, so it is looked up once per device
+// (with that device current) and cached.
+static double *noalloc_scratch_for_current_device() {
+    static std::mutex mu;
+    static double *addr[256] = {};
+    int dev = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    H2_REQUIRE(dev >= 0 && dev < 256, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        H2_CUDA(cudaGetSymbolAddress(&p, g_noalloc_zm));
+        addr[dev] = static_cast<double *>(p);
+    }
+    return addr[dev];
+}
+
+void exact_rows_noalloc_impl(h2_tree_s *t, int kid, const double *kp, const double *z, const int64_t *rows,
+                             int64_t nrows, double *out, cudaStream_t s) {
+    const int64_t n = t->n;
+    if (n > H2_NOALLOC_MAX_N)
+        fail(H2_ERR_INVALID_ARG, "h2_exact_rows_noalloc supports at most 1048576 points (tree has " +
+                                     std::to_string(n) + ")");
+    double *zm = noalloc_scratch_for_current_device();
+    // zm[0..n) is fully overwritten below; nothing needs clearing first
+    k_perm_in<<<blocks_for(n, 256), 256, 0, s>>>(z, t->perm.p, n, zm);
+    H2_LAUNCH("k_perm_in (noalloc)");
+    if (nrows > 0) {
+        k_exact_rows<<<(unsigned)nrows, 512, 0, s>>>(rows, nrows, t->iperm.p, t->xs[0].p, t->xs[1].p, t->xs[2].p,
+                                                     zm, n, t->d, kid, kp[0], out);
+        H2_LAUNCH("k_exact_rows (noalloc)");
+    }
 }
 
 }  // namespace h2

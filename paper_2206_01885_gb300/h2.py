@@ -66,6 +66,7 @@ def lib():
             "h2_get_stats": [vp, C.c_char_p, i64],
             "h2_sampled_error": [vp, vp, vp, i64, i64, vp, i32, vp],
             "h2_profile": [i32, i32],
+            "h2_exact_rows_noalloc": [vp, i32, vp, vp, vp, i64, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)

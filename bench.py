@@ -35,7 +35,7 @@ METRIC = "H² build ms & points/s, n=1M 3D Coulomb, rel err≤1e-8: mixed vs FP6
 WORKLOADS = {
     # n, dim, kernel, kparams, leaf size, ID tolerance, precision, seed, sampled rows
     "cube1m_fp64": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-8, prec="fp64", seed=2,
-                        rows=1000),
+                        rows=1000, compare="cube1m_mixed"),
     "cube1m_mixed": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-5, prec="mixed", seed=2,
                          rows=1000),
     "cube8k_fp64": dict(n=8000, d=3, kernel="coulomb", kparams=(), q=200, eps=1e-6, prec="fp64", seed=1,
@@ -117,14 +117,13 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------- GPU arm
-def gpu_arm(args, wl, rank, world, dev):
+def measure_form(args, wl, rank, world, dev, with_e2e):
+    """W warm-up and K timed steps of one form (precision + tolerance) on this
+    rank's problem; returns the per-form measurements."""
     import torch
 
-    from paper_2206_01885_gb300 import build as B
-    B.build()
     from paper_2206_01885_gb300 import h2
 
-    torch.cuda.set_device(dev)
     n, d = wl["n"], wl["d"]
     seed = wl["seed"] + 1000 * rank  # independent problem per rank
     pts = I.uniform_cube(n, d, seed=seed)
@@ -166,8 +165,7 @@ def gpu_arm(args, wl, rank, world, dev):
     torch.cuda.synchronize()
     sampler = ClockSampler(dev)
     sampler.start()
-    step_ms = []
-    infos = []
+    step_ms, infos = [], []
     for _ in range(args.steps):
         flush.zero_()  # evict L2 between steps (outside the timed interval)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -218,23 +216,32 @@ def gpu_arm(args, wl, rank, world, dev):
         "near": near_pairs * FLOPS_PER_PAIR,
         "keval": block_evals * FLOPS_PER_PAIR,
     }
+    per_kernel = {}
+    for k, v in ktimes.items():
+        if not v["launches"]:
+            continue
+        e = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+        if k in work and v["ms"] > 0:
+            e["tflops"] = work[k] * args.steps / (v["ms"] * 1e-3) / 1e12
+            e["frac_of_alu_peak"] = e["tflops"] / alu_peak
+        per_kernel[k] = e
     dom = max(ktimes, key=lambda k: ktimes[k]["ms"])
-    dom_ms_per_launch = ktimes[dom]["ms"] / max(1, ktimes[dom]["launches"])
     launches_per_step = ktimes[dom]["launches"] / args.steps
+    dom_ms_per_launch = ktimes[dom]["ms"] / max(1, ktimes[dom]["launches"])
+    peak_src = "derived: GB300 nominal float64 1.25 TFLOP/s" if fp64 else \
+        "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
     if dom in work:
         achieved = work[dom] / launches_per_step / (dom_ms_per_launch * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None,
-                "peak_source": "derived: GB300 nominal float64" if fp64 else "derived: 152 SMs x 128 x 2 x 2.07 GHz"}
+                "frac": achieved / alu_peak, "traffic": None, "peak_source": peak_src,
+                "work_per_launch": work[dom] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "TFLOP/s", "frac": None,
-                "traffic": None}
+                "traffic": None, "peak_source": peak_src, "ms_per_launch": dom_ms_per_launch}
+    gpu_launches = int(sum(v["launches"] for v in ktimes.values()))
 
-    gpu_launches = int(sum(v["launches"] for v in ktimes.values()) / 1)
-
-    # end-to-end through host buffers (pinned), copies inside the timed region
     e2e = None
-    if rank == 0 or world > 1:
+    if with_e2e:  # end to end through host buffers (pinned), copies inside the timed region
         pts_h = torch.from_numpy(pts).pin_memory()
         z_h = torch.from_numpy(z).pin_memory()
         rows_h = torch.from_numpy(rows)
@@ -255,7 +262,7 @@ def gpu_arm(args, wl, rank, world, dev):
             hd2.free()
             t2.free()
         r = len(rows)
-        e2e = {"value": n / (statistics.median(e2e_ms) * 1e-3), "unit": "points/s",
+        e2e = {"value": world * n / (statistics.median(e2e_ms) * 1e-3), "unit": "points/s",
                "h2d_bytes_per_step": 8 * (d * n + n + n + r + n + r + r), "d2h_bytes_per_step": 8 * (n + r + 1),
                "ms_per_step": statistics.median(e2e_ms), "rel_err": err_h}
 
@@ -265,22 +272,14 @@ def gpu_arm(args, wl, rank, world, dev):
         "construct_ms": mat_i["ms_construct"],
     }
     phases["build_ms"] = phases["tree_ms"] + phases["lists_ms"] + phases["hidr_ms"] + phases["construct_ms"]
-    result = {
-        "metric": METRIC,
+    phases["matvec_ms"] = sum(per_kernel.get(k, {}).get("ms_per_step", 0.0)
+                              for k in ("upward", "coupling", "downward", "near"))
+    return {
         "value": world * n / (ms_per_step * 1e-3),
-        "unit": "points/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
         "ms_per_step": ms_per_step,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64" if fp64 else "f32+f64",
-        "data": "synthetic (seeded uniform cube, standard-normal right-hand side)",
-        "config": {"workload": args.workload, "n": n, "dim": d, "kernel": wl["kernel"], "leaf_size": wl["q"],
-                   "id_tol": wl["eps"], "precision": wl["prec"], "g": g, "r1": g ** d, "r2": g ** d,
-                   "tau": "7/10", "sampled_rows": len(rows), "rhs": 1,
+        "config": {"workload": args.workload if wl is WORKLOADS[args.workload] else wl["name"], "n": n, "dim": d,
+                   "kernel": wl["kernel"], "leaf_size": wl["q"], "id_tol": wl["eps"], "precision": wl["prec"],
+                   "g": g, "r1": g ** d, "r2": g ** d, "tau": "7/10", "sampled_rows": len(rows), "rhs": 1,
                    "l2": "flushed (256 MB write) between timed steps, outside the timed interval",
                    "parallelism": f"{world} independent problem(s), one per GPU"},
         "rel_err": last_err,
@@ -290,12 +289,36 @@ def gpu_arm(args, wl, rank, world, dev):
                    "far_pairs": tree_i["far_pairs"], "k_total": mat_i["k_total"], "k_max": mat_i["k_max"],
                    "qr_flops": qr_flops, "block_evals": block_evals, "coupling_evals": coupling_pairs,
                    "near_evals": near_pairs},
-        "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in ktimes.items() if v["launches"]},
+        "kernels": per_kernel,
         "roofline": roof,
         "clocks": clocks,
         "gpu_launches": gpu_launches,
         "e2e": e2e,
     }
+
+
+def gpu_arm(args, wl, rank, world, dev):
+    import torch
+
+    from paper_2206_01885_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(dev)
+    prim = measure_form(args, wl, rank, world, dev, with_e2e=True)
+    result = {
+        "metric": METRIC, "value": prim["value"], "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": prim["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if wl["prec"] == "fp64" else "f32+f64",
+        "data": "synthetic (seeded uniform cube, standard-normal right-hand side)",
+    }
+    result.update({k: v for k, v in prim.items() if k not in ("value", "ms_per_step")})
+    other = wl.get("compare")
+    if other and not args.no_compare:
+        sec = measure_form(args, dict(WORKLOADS[other], name=other), rank, world, dev, with_e2e=False)
+        result["compare"] = {"form": other, "value": sec["value"], "ms_per_step": sec["ms_per_step"],
+                             "rel_err": sec["rel_err"], "config": sec["config"], "phases_ms": sec["phases_ms"],
+                             "kernels": sec["kernels"], "roofline": sec["roofline"], "counts": sec["counts"],
+                             "clocks": sec["clocks"], "calibration": sec["calibration"],
+                             "build_speedup_vs_primary": prim["phases_ms"]["build_ms"] / sec["phases_ms"]["build_ms"]}
     return result
 
 
@@ -370,6 +393,7 @@ def main():
     ap.add_argument("--workload", default="cube1m_fp64", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample", type=int, default=65536)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the second (mixed) form")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))

@@ -252,7 +252,6 @@ h2_status h2_construct(h2_tree th, h2_hidr hh, int kernel, const double *kparams
         A->prec = precision;
         try {
             kparams_check(kernel, kparams, A->kp);
-            if (precision != H2_PREC_FP64) fail(H2_ERR_UNIMPLEMENTED, "mixed precision construction not built");
             construct_impl(A, h);
         } catch (...) {
             A->tag = TAG_DEAD;
@@ -275,16 +274,27 @@ h2_status h2_matrix_get(h2_matrix ah, int what, void *buf, int64_t cap, int64_t 
         case H2_MAT_SKEL: copy_out(read_vec(A->skel.p, A->ktotal, s), buf, cap, len); break;
         case H2_MAT_U: {
             std::vector<int32_t> k = read_vec(A->k.p, nn, s), c = read_vec(A->c.p, nn, s);
-            std::vector<double *> up = read_vec(A->uptr.p, nn, s);
+            std::vector<void *> up = read_vec(A->uptr.p, nn, s);
             int64_t tot = 0;
             for (int i = 0; i < nn; i++) tot += (int64_t)k[i] * c[i];
             if (len) *len = tot;
             if (!buf) break;
             H2_REQUIRE(cap >= tot, "output buffer too small");
             double *dst = static_cast<double *>(buf);
+            const bool f64 = A->prec == H2_PREC_FP64;
+            std::vector<float> tmp;
             for (int i = 0; i < nn; i++) {
                 int64_t e = (int64_t)k[i] * c[i];
-                if (e > 0) H2_CUDA(cudaMemcpyAsync(dst, up[i], e * sizeof(double), cudaMemcpyDeviceToHost, s));
+                if (e > 0) {
+                    if (f64) {
+                        H2_CUDA(cudaMemcpyAsync(dst, up[i], e * sizeof(double), cudaMemcpyDeviceToHost, s));
+                    } else {  // float32 storage, widened on the host
+                        tmp.resize(e);
+                        H2_CUDA(cudaMemcpyAsync(tmp.data(), up[i], e * sizeof(float), cudaMemcpyDeviceToHost, s));
+                        H2_CUDA(cudaStreamSynchronize(s));
+                        for (int64_t q = 0; q < e; q++) dst[q] = tmp[q];
+                    }
+                }
                 dst += e;
             }
             H2_CUDA(cudaStreamSynchronize(s));
@@ -420,9 +430,9 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
             auto *A = static_cast<const h2_matrix_s *>(handle);
             snprintf(buf, sizeof buf,
                      "{\"k_total\": %lld, \"u_entries\": %lld, \"k_max\": %d, \"ms_construct\": %.4f, "
-                     "\"qr_flops\": %.6e, \"block_evals\": %.6e}",
+                     "\"qr_flops\": %.6e, \"block_evals\": %.6e, \"precision\": \"%s\"}",
                      (long long)A->ktotal, (long long)A->utotal, A->kmax, A->ms_construct, A->flops_qr,
-                     A->evals_block);
+                     A->evals_block, A->prec == H2_PREC_FP64 ? "fp64" : "mixed");
         } else {
             fail(H2_ERR_INVALID_ARG, "not a live h2 handle");
         }

@@ -57,7 +57,9 @@ __global__ void k_gather_cand(int lb, const int32_t *nchild, const int32_t *fchi
     }
 }
 
-// A_i[r + l m] = kappa(y_r, xbar_l), column-major m x c
+// A_i[r + l m] = kappa(y_r, xbar_l), column-major m x c, float64: every entry
+// evaluated exactly as the plain IEEE formula (bit-identical to a CPU
+// evaluation for Coulomb).
 __global__ void k_keval_f64(int lb, const int32_t *ycnt, const int32_t *cc, int32_t *const *yptr,
                             const int32_t *cand, const int64_t *coff, const int64_t *aoff, const double *x0,
                             const double *x1, const double *x2, int d, int kid, double kp0, double *Abase) {
@@ -75,6 +77,45 @@ __global__ void k_keval_f64(int lb, const int32_t *ycnt, const int32_t *cc, int3
         double r2 = h2_dist2(d, x0[y], d > 1 ? x1[y] : 0.0, d > 2 ? x2[y] : 0.0, x0[x], d > 1 ? x1[x] : 0.0,
                              d > 2 ? x2[x] : 0.0);
         A[e] = h2_kappa(kid, kp0, r2);
+    }
+}
+
+// float32 block: the node's Y_i* and Xbar_i points, relative to the node's
+// cell centre, are staged once in shared memory as float32.
+__global__ void k_keval_f32(int lb, const int32_t *ycnt, const int32_t *cc, int32_t *const *yptr,
+                            const int32_t *cand, const int64_t *coff, const int64_t *aoff, const double *x0,
+                            const double *x1, const double *x2, const double *cen0, const double *cen1,
+                            const double *cen2, int d, int kid, double kp0, float *Abase) {
+    extern __shared__ float sp_[];
+    int a = blockIdx.x, i = lb + a;
+    int m = ycnt[i], c = cc[i];
+    if (m == 0 || c == 0) return;
+    const int32_t *Y = yptr[i];
+    const int32_t *X = cand + coff[a];
+    float *ys = sp_, *xs = sp_ + 3 * m;
+    const double o0 = cen0[i], o1 = d > 1 ? cen1[i] : 0.0, o2 = d > 2 ? cen2[i] : 0.0;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        int32_t y = Y[r];
+        ys[3 * r] = (float)(x0[y] - o0);
+        ys[3 * r + 1] = d > 1 ? (float)(x1[y] - o1) : 0.f;
+        ys[3 * r + 2] = d > 2 ? (float)(x2[y] - o2) : 0.f;
+    }
+    for (int l = threadIdx.x; l < c; l += blockDim.x) {
+        int32_t x = X[l];
+        xs[3 * l] = (float)(x0[x] - o0);
+        xs[3 * l + 1] = d > 1 ? (float)(x1[x] - o1) : 0.f;
+        xs[3 * l + 2] = d > 2 ? (float)(x2[x] - o2) : 0.f;
+    }
+    __syncthreads();
+    float *A = Abase + aoff[a];
+    const float k0 = (float)kp0;
+    int64_t total = (int64_t)m * c;
+    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.y * blockDim.x) {
+        int r = (int)(e % m), l = (int)(e / m);
+        float dx = ys[3 * r] - xs[3 * l], dy = ys[3 * r + 1] - xs[3 * l + 1], dz = ys[3 * r + 2] - xs[3 * l + 2];
+        float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        A[e] = h2_kappa_f(kid, k0, r2);
     }
 }
 
@@ -97,10 +138,15 @@ __device__ double block_sum(double x, double *red) {
 // Column-pivoted Householder QR of each node's block, stopped at the first
 // step whose pivot norm is <= tol * |r_11|.  On exit A holds R (upper
 // triangle of the first k columns and rows 0..k-1 of the others), kout[i] = k
-// and piv[0..c) is the column order.
-__global__ void __launch_bounds__(QR_THREADS) k_cpqr_f64(int lb, const int32_t *ycnt, const int32_t *cc,
-                                                         const int64_t *aoff, double *Abase, double tol,
-                                                         int32_t *kout, const int64_t *coff, int32_t *pivbase) {
+// and piv[0..c) is the column order.  Real = double: everything float64.
+// Real = float: the block, the reflector and the trailing update are float32;
+// column norms, their downdating, the pivot choice and the stop test are
+// float64 (recomputation threshold sqrt(2^-24), the float32 analogue of
+// LAPACK's sqrt(eps)).
+template <class Real>
+__global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt, const int32_t *cc,
+                                                     const int64_t *aoff, Real *Abase, double tol, int32_t *kout,
+                                                     const int64_t *coff, int32_t *pivbase) {
     extern __shared__ unsigned char smem_raw[];
     const int a = blockIdx.x, node = lb + a;
     const int m = ycnt[node], c = cc[node];
@@ -110,22 +156,22 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr_f64(int lb, const int32_t *
     }
     double *nrm = reinterpret_cast<double *>(smem_raw);
     double *nrm0 = nrm + c;
-    double *v = nrm0 + c;
+    Real *v = reinterpret_cast<Real *>(nrm0 + c);
     int32_t *pv = reinterpret_cast<int32_t *>(v + m);
     __shared__ double red[QR_WARPS];
     __shared__ double bval[QR_WARPS];
     __shared__ int bidx[QR_WARPS];
     __shared__ int s_p, s_stop;
-    double *A = Abase + aoff[a];
+    Real *A = Abase + aoff[a];
     int32_t *piv = pivbase + coff[a];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double tol3z = sqrt(ldexp(1.0, -53));
+    const double tol3z = sqrt(ldexp(1.0, sizeof(Real) == 8 ? -53 : -24));
 
     for (int l = threadIdx.x; l < c; l += blockDim.x) pv[l] = l;
     for (int l = warp; l < c; l += QR_WARPS) {
-        const double *col = A + (int64_t)l * m;
+        const Real *col = A + (int64_t)l * m;
         double s = 0.0;
-        for (int r = lane; r < m; r += 32) s += col[r] * col[r];
+        for (int r = lane; r < m; r += 32) s += (double)col[r] * (double)col[r];
         s = warp_sum(s);
         if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
     }
@@ -157,9 +203,9 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr_f64(int lb, const int32_t *
         if (s_stop) break;
         const int p = s_p;
         if (p != j) {
-            double *cj = A + (int64_t)j * m, *cp = A + (int64_t)p * m;
+            Real *cj = A + (int64_t)j * m, *cp = A + (int64_t)p * m;
             for (int r = threadIdx.x; r < m; r += blockDim.x) {
-                double t = cj[r]; cj[r] = cp[r]; cp[r] = t;
+                Real t = cj[r]; cj[r] = cp[r]; cp[r] = t;
             }
             if (threadIdx.x == 0) {
                 double t = nrm[j]; nrm[j] = nrm[p]; nrm[p] = t;
@@ -169,11 +215,11 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr_f64(int lb, const int32_t *
         }
         __syncthreads();
         // Householder reflector for A[j:m, j]
-        double *aj = A + (int64_t)j * m;
+        Real *aj = A + (int64_t)j * m;
         double part = 0.0;
-        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) part += aj[r] * aj[r];
+        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) part += (double)aj[r] * (double)aj[r];
         double sigma = block_sum(part, red);
-        double alpha = aj[j];
+        double alpha = (double)aj[j];
         if (alpha == 0.0 && sigma == 0.0) break;  // exactly zero pivot column
         double tau = 0.0, beta = alpha, sc = 0.0;
         if (sigma != 0.0) {
@@ -182,32 +228,33 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr_f64(int lb, const int32_t *
             tau = (beta - alpha) / beta;
             sc = 1.0 / (alpha - beta);
         }
-        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) v[r] = aj[r] * sc;
+        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) v[r] = (Real)((double)aj[r] * sc);
         __syncthreads();
-        if (threadIdx.x == 0) aj[j] = beta;
+        if (threadIdx.x == 0) aj[j] = (Real)beta;
+        const Real tauR = (Real)tau;
         // apply to the trailing columns and downdate their norms (one warp per column)
         for (int l = j + 1 + warp; l < c; l += QR_WARPS) {
-            double *al = A + (int64_t)l * m;
-            double ajl = al[j];
+            Real *al = A + (int64_t)l * m;
+            Real ajl = al[j];
             if (tau != 0.0) {
-                double w = 0.0;
+                Real w = 0;
                 for (int r = j + 1 + lane; r < m; r += 32) w += v[r] * al[r];
                 w = warp_sum(w) + ajl;
-                w = w * tau;
+                w = w * tauR;
                 for (int r = j + 1 + lane; r < m; r += 32) al[r] = al[r] - w * v[r];
                 ajl = ajl - w;
                 if (lane == 0) al[j] = ajl;
             }
             double nl = nrm[l];
             if (nl != 0.0) {
-                double tt = fabs(ajl) / nl;
+                double tt = fabs((double)ajl) / nl;
                 tt = 1.0 - tt * tt;
                 if (tt < 0.0) tt = 0.0;
                 double t2 = nl / nrm0[l];
                 t2 = tt * t2 * t2;
                 if (t2 <= tol3z) {
                     double s = 0.0;
-                    for (int r = j + 1 + lane; r < m; r += 32) s += al[r] * al[r];
+                    for (int r = j + 1 + lane; r < m; r += 32) s += (double)al[r] * (double)al[r];
                     s = warp_sum(s);
                     if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
                 } else if (lane == 0) {
@@ -237,34 +284,44 @@ __device__ void bitonic_sort_i32(int32_t *v, int P) {
         }
 }
 
-// T = R11^{-1} R12 (right-looking back substitution, in place of R12), then
-// U_i (c x k, column-major, columns in sorted-skeleton order) and the sorted
-// skeleton's Morton positions.
-__global__ void __launch_bounds__(QR_THREADS) k_id_solve_f64(int lb, const int32_t *ycnt, const int32_t *cc,
-                                                             const int32_t *kk, const int64_t *aoff, double *Abase,
-                                                             const int64_t *coff, const int32_t *pivbase,
-                                                             const int32_t *cand, double *const *uptr,
-                                                             int32_t *const *skptr) {
+// T = R11^{-1} R12 in float64 (right-looking back substitution in the
+// workspace W, which for a float64 block is the block itself), then U_i
+// (c x k, column-major, columns in sorted-skeleton order, stored as Real) and
+// the sorted skeleton's Morton positions.
+template <class Real>
+__global__ void __launch_bounds__(QR_THREADS) k_id_solve(int lb, const int32_t *ycnt, const int32_t *cc,
+                                                         const int32_t *kk, const int64_t *aoff, const Real *Abase,
+                                                         double *Wbase, const int64_t *coff, const int32_t *pivbase,
+                                                         const int32_t *cand, void *const *uptr,
+                                                         int32_t *const *skptr) {
     extern __shared__ unsigned char smem_raw[];
     int32_t *sk = reinterpret_cast<int32_t *>(smem_raw);
     const int a = blockIdx.x, node = lb + a;
     const int m = ycnt[node], c = cc[node], k = kk[node];
     if (k == 0) return;
-    double *A = Abase + aoff[a];
+    const Real *A = Abase + aoff[a];
+    double *W = Wbase + aoff[a];
     const int32_t *piv = pivbase + coff[a];
     const int32_t *cd = cand + coff[a];
     const int nr = c - k;
+    if ((const void *)A != (const void *)W) {  // float32 block: R12 into the float64 workspace
+        for (int64_t e = threadIdx.x; e < (int64_t)k * nr; e += blockDim.x) {
+            int p = (int)(e % k), l = k + (int)(e / k);
+            W[p + (int64_t)l * m] = (double)A[p + (int64_t)l * m];
+        }
+        __syncthreads();
+    }
     for (int i = k - 1; i >= 0; i--) {
-        const double rii = A[i + (int64_t)i * m];
+        const double rii = (double)A[i + (int64_t)i * m];
         for (int l = threadIdx.x; l < nr; l += blockDim.x) {
-            double *e = A + i + (int64_t)(k + l) * m;
+            double *e = W + i + (int64_t)(k + l) * m;
             *e = *e / rii;
         }
         __syncthreads();
         const int64_t work = (int64_t)i * nr;
         for (int64_t e = threadIdx.x; e < work; e += blockDim.x) {
             int p = (int)(e % i), l = k + (int)(e / i);
-            A[p + (int64_t)l * m] -= A[p + (int64_t)i * m] * A[i + (int64_t)l * m];
+            W[p + (int64_t)l * m] -= (double)A[p + (int64_t)i * m] * W[i + (int64_t)l * m];
         }
         __syncthreads();
     }
@@ -273,9 +330,9 @@ __global__ void __launch_bounds__(QR_THREADS) k_id_solve_f64(int lb, const int32
     for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < k ? piv[i] : INT_MAX;
     __syncthreads();
     bitonic_sort_i32(sk, P);
-    double *U = uptr[node];
+    Real *U = static_cast<Real *>(uptr[node]);
     int32_t *skel = skptr[node];
-    for (int64_t e = threadIdx.x; e < (int64_t)c * k; e += blockDim.x) U[e] = 0.0;
+    for (int64_t e = threadIdx.x; e < (int64_t)c * k; e += blockDim.x) U[e] = (Real)0;
     for (int q = threadIdx.x; q < k; q += blockDim.x) skel[q] = cd[sk[q]];
     __syncthreads();
     // column of U for pivot p: position of piv[p] in the sorted skeleton
@@ -287,8 +344,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_id_solve_f64(int lb, const int32
             if (sk[mid] < key) lo = mid + 1;
             else hi = mid;
         }
-        if (l == 0) U[piv[p] + (int64_t)lo * c] = 1.0;
-        else U[piv[k + l - 1] + (int64_t)lo * c] = A[p + (int64_t)(k + l - 1) * m];
+        if (l == 0) U[piv[p] + (int64_t)lo * c] = (Real)1;
+        else U[piv[k + l - 1] + (int64_t)lo * c] = (Real)W[p + (int64_t)(k + l - 1) * m];
     }
 }
 
@@ -300,18 +357,19 @@ __global__ void k_ku_sizes(int lb, int nl, const int32_t *kk, const int32_t *cc,
     szu[a] = (int64_t)kk[i] * cc[i];
 }
 
-__global__ void k_set_ptrs2(int lb, int nl, int32_t *kbase, const int64_t *koff, int32_t **skptr, double *ubase,
-                            const int64_t *uoff, double **uptr) {
+__global__ void k_set_ptrs2(int lb, int nl, int32_t *kbase, const int64_t *koff, int32_t **skptr,
+                            unsigned char *ubase, const int64_t *uoff, int esize, void **uptr) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nl) return;
     skptr[lb + a] = kbase + koff[a];
-    uptr[lb + a] = ubase + uoff[a];
+    uptr[lb + a] = ubase + uoff[a] * esize;
 }
 
 // contiguous skeletons (node order) and their coordinates
 __global__ void k_compact_skel(int nn, const int32_t *kk, const int64_t *off, int32_t *const *skptr, int32_t *skel,
                                const double *x0, const double *x1, const double *x2, int d, double *s0, double *s1,
-                               double *s2) {
+                               double *s2, const double *c0, const double *c1, const double *c2, float *r0,
+                               float *r1, float *r2) {
     int i = blockIdx.x;
     if (i >= nn) return;
     int k = kk[i];
@@ -321,13 +379,14 @@ __global__ void k_compact_skel(int nn, const int32_t *kk, const int64_t *off, in
         int64_t o = off[i] + q;
         skel[o] = p;
         s0[o] = x0[p];
-        if (d > 1) s1[o] = x1[p];
-        if (d > 2) s2[o] = x2[p];
+        r0[o] = (float)(x0[p] - c0[i]);
+        if (d > 1) { s1[o] = x1[p]; r1[o] = (float)(x1[p] - c1[i]); }
+        if (d > 2) { s2[o] = x2[p]; r2[o] = (float)(x2[p] - c2[i]); }
     }
 }
 
-size_t qr_smem(int cmax, int mmax) {
-    return (size_t)cmax * (2 * sizeof(double) + sizeof(int32_t)) + (size_t)mmax * sizeof(double) + 64;
+size_t qr_smem(int cmax, int mmax, size_t esize = sizeof(double)) {
+    return (size_t)cmax * (2 * sizeof(double) + sizeof(int32_t)) + (size_t)mmax * esize + 64;
 }
 
 }  // namespace
@@ -336,7 +395,8 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     h2_tree_s *t = A->tree;
     cudaStream_t s = A->stream;
     const int nn = t->nnodes, d = t->d;
-    H2_REQUIRE(A->prec == H2_PREC_FP64, "only the float64 construction is built");
+    const bool f64 = A->prec == H2_PREC_FP64;
+    const size_t esize = f64 ? sizeof(double) : sizeof(float);
     A->k.alloc(nn, s);
     A->c.alloc(nn, s);
     H2_CUDA(cudaMemsetAsync(A->k.p, 0, nn * sizeof(int32_t), s));
@@ -345,15 +405,20 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     skptr.alloc(nn, s);
     A->uptr.alloc(nn, s);
     H2_CUDA(cudaMemsetAsync(skptr.p, 0, nn * sizeof(int32_t *), s));
-    H2_CUDA(cudaMemsetAsync(A->uptr.p, 0, nn * sizeof(double *), s));
+    H2_CUDA(cudaMemsetAsync(A->uptr.p, 0, nn * sizeof(void *), s));
     std::vector<DevBuf<int32_t>> skbufs(t->nlevels);
     A->ubufs.resize(t->nlevels);
     A->kmax_level.assign(t->nlevels, 0);
     A->cmax_level.assign(t->nlevels, 0);
     static bool attr = false;
     if (!attr) {
-        H2_CUDA(cudaFuncSetAttribute(k_cpqr_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
-        H2_CUDA(cudaFuncSetAttribute(k_id_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_cpqr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_cpqr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_id_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_id_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_keval_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
         attr = true;
     }
     cudaEvent_t e0, e1;
@@ -363,7 +428,8 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     const std::vector<int32_t> yc = read_vec(h->ycnt.p, nn, s);
     DevBuf<int64_t> szc, sza, coff, aoff, szk, szu, koff, uoff;
     DevBuf<int32_t> cand, piv;
-    DevBuf<double> Ablk;
+    DevBuf<unsigned char> Ablk;
+    DevBuf<double> Wf;  // float64 workspace of the solve when the block is float32
     for (int l = t->nlevels - 1; l >= 1; l--) {
         const int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
         szc.alloc(nl, s); sza.alloc(nl, s); coff.alloc(nl + 1, s); aoff.alloc(nl + 1, s);
@@ -379,28 +445,44 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         A->cmax_level[l] = cmax;
         if (ctot == 0) continue;
         const int mmax = h->ymax_level[l];
-        if (qr_smem(cmax, mmax) > SMEM_LIMIT)
+        if (qr_smem(cmax, mmax, esize) > SMEM_LIMIT)
             fail(H2_ERR_UNIMPLEMENTED, "kernel block too large for the single-CTA QR (candidates " +
                                            std::to_string(cmax) + ", rows " + std::to_string(mmax) + ")");
         cand.alloc(ctot, s);
         piv.alloc(ctot, s);
-        Ablk.alloc(atot, s);
+        Ablk.alloc((size_t)atot * esize, s);
+        if (!f64) Wf.alloc(atot, s);
         k_gather_cand<<<nl, 128, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->c.p, A->k.p, skptr.p, coff.p,
                                          cand.p);
         H2_LAUNCH("k_gather_cand");
         dim3 kg(nl, std::max(1, std::min(16, (int)((int64_t)cmax * mmax / (256 * 64)))));
         {
-        ProfScope ps(KT_KEVAL, s);
-        k_keval_f64<<<kg, 256, 0, s>>>(lb, h->ycnt.p, A->c.p, h->yptr.p, cand.p, coff.p, aoff.p, t->xs[0].p,
-                                       t->xs[1].p, t->xs[2].p, d, A->kid, A->kp[0], Ablk.p);
-        H2_LAUNCH("k_keval_f64");
+            ProfScope ps(KT_KEVAL, s);
+            if (f64) {
+                k_keval_f64<<<kg, 256, 0, s>>>(lb, h->ycnt.p, A->c.p, h->yptr.p, cand.p, coff.p, aoff.p, t->xs[0].p,
+                                               t->xs[1].p, t->xs[2].p, d, A->kid, A->kp[0],
+                                               reinterpret_cast<double *>(Ablk.p));
+            } else {
+                size_t sm = (size_t)(cmax + mmax) * 3 * sizeof(float);
+                if (sm > SMEM_LIMIT) fail(H2_ERR_UNIMPLEMENTED, "kernel block too large for the float32 evaluation");
+                k_keval_f32<<<kg, 256, sm, s>>>(lb, h->ycnt.p, A->c.p, h->yptr.p, cand.p, coff.p, aoff.p, t->xs[0].p,
+                                                t->xs[1].p, t->xs[2].p, t->cen[0].p, t->cen[1].p, t->cen[2].p, d,
+                                                A->kid, A->kp[0], reinterpret_cast<float *>(Ablk.p));
+            }
+            H2_LAUNCH("k_keval");
         }
         A->evals_block += (double)atot;
         {
-        ProfScope ps(KT_CPQR, s);
-        k_cpqr_f64<<<nl, QR_THREADS, qr_smem(cmax, mmax), s>>>(lb, h->ycnt.p, A->c.p, aoff.p, Ablk.p, A->id_tol,
-                                                              A->k.p, coff.p, piv.p);
-        H2_LAUNCH("k_cpqr_f64");
+            ProfScope ps(KT_CPQR, s);
+            if (f64)
+                k_cpqr<double><<<nl, QR_THREADS, qr_smem(cmax, mmax, esize), s>>>(
+                    lb, h->ycnt.p, A->c.p, aoff.p, reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p,
+                    piv.p);
+            else
+                k_cpqr<float><<<nl, QR_THREADS, qr_smem(cmax, mmax, esize), s>>>(
+                    lb, h->ycnt.p, A->c.p, aoff.p, reinterpret_cast<float *>(Ablk.p), A->id_tol, A->k.p, coff.p,
+                    piv.p);
+            H2_LAUNCH("k_cpqr");
         }
         szk.alloc(nl, s); szu.alloc(nl, s); koff.alloc(nl + 1, s); uoff.alloc(nl + 1, s);
         k_ku_sizes<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, A->k.p, A->c.p, szk.p, szu.p);
@@ -418,17 +500,23 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
             if (kk > 0) A->flops_qr += 4 * mm * cc * kk - 2 * kk * kk * (mm + cc) + 4.0 / 3.0 * kk * kk * kk;
         }
         skbufs[l].alloc(ktot > 0 ? ktot : 1, s);
-        A->ubufs[l].alloc(utot > 0 ? utot : 1, s);
+        A->ubufs[l].alloc((size_t)(utot > 0 ? utot : 1) * esize, s);
         k_set_ptrs2<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, skbufs[l].p, koff.p, skptr.p, A->ubufs[l].p,
-                                                         uoff.p, A->uptr.p);
+                                                         uoff.p, (int)esize, A->uptr.p);
         H2_LAUNCH("k_set_ptrs2");
         int P = 1;
         while (P < kmax) P <<= 1;
         {
-        ProfScope ps(KT_SOLVE, s);
-        k_id_solve_f64<<<nl, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(
-            lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, Ablk.p, coff.p, piv.p, cand.p, A->uptr.p, skptr.p);
-        H2_LAUNCH("k_id_solve_f64");
+            ProfScope ps(KT_SOLVE, s);
+            if (f64)
+                k_id_solve<double><<<nl, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(
+                    lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<double *>(Ablk.p),
+                    reinterpret_cast<double *>(Ablk.p), coff.p, piv.p, cand.p, A->uptr.p, skptr.p);
+            else
+                k_id_solve<float><<<nl, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(
+                    lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<float *>(Ablk.p), Wf.p, coff.p, piv.p,
+                    cand.p, A->uptr.p, skptr.p);
+            H2_LAUNCH("k_id_solve");
         }
         A->ktotal += ktot;
         A->utotal += utot;
@@ -438,9 +526,14 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     scan_exclusive_i32(A->k.p, A->sk_off.p, nn, s);
     int64_t kt = read_scalar(A->sk_off.p + nn, s);
     A->skel.alloc(kt > 0 ? kt : 1, s);
-    for (int k = 0; k < 3; k++) A->skc[k].alloc(kt > 0 ? kt : 1, s);
+    for (int k = 0; k < 3; k++) {
+        A->skc[k].alloc(kt > 0 ? kt : 1, s);
+        A->skr[k].alloc(kt > 0 ? kt : 1, s);
+    }
     k_compact_skel<<<std::max(1, nn), 128, 0, s>>>(nn, A->k.p, A->sk_off.p, skptr.p, A->skel.p, t->xs[0].p,
-                                                    t->xs[1].p, t->xs[2].p, d, A->skc[0].p, A->skc[1].p, A->skc[2].p);
+                                                    t->xs[1].p, t->xs[2].p, d, A->skc[0].p, A->skc[1].p, A->skc[2].p,
+                                                    t->cen[0].p, t->cen[1].p, t->cen[2].p, A->skr[0].p, A->skr[1].p,
+                                                    A->skr[2].p);
     H2_LAUNCH("k_compact_skel");
     H2_CUDA(cudaEventRecord(e1, s));
     H2_CUDA(cudaEventSynchronize(e1));
@@ -523,20 +616,22 @@ double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *
     DevBuf<int32_t> mc, kk, piv, skel;
     DevBuf<int64_t> off;
     DevBuf<double> U;
-    DevBuf<double *> up;
+    DevBuf<void *> up;
     DevBuf<int32_t *> sp;
     mc.alloc(2, s); kk.alloc(1, s); piv.alloc(c, s); off.alloc(4, s);
     H2_CUDA(cudaMemcpyAsync(mc.p, hv, sizeof hv, cudaMemcpyHostToDevice, s));
     H2_CUDA(cudaMemcpyAsync(off.p, offs, sizeof offs, cudaMemcpyHostToDevice, s));
     static bool attr = false;
     if (!attr) {
-        H2_CUDA(cudaFuncSetAttribute(k_cpqr_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
-        H2_CUDA(cudaFuncSetAttribute(k_id_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_cpqr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_id_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_LIMIT));
         attr = true;
     }
     if (qr_smem(c, m) > SMEM_LIMIT) fail(H2_ERR_UNIMPLEMENTED, "calibration block too large");
-    k_cpqr_f64<<<1, QR_THREADS, qr_smem(c, m), s>>>(0, mc.p, mc.p + 1, off.p, A.p, id_tol, kk.p, off.p + 2, piv.p);
-    H2_LAUNCH("k_cpqr_f64 (calibration)");
+    k_cpqr<double><<<1, QR_THREADS, qr_smem(c, m), s>>>(0, mc.p, mc.p + 1, off.p, A.p, id_tol, kk.p, off.p + 2,
+                                                        piv.p);
+    H2_LAUNCH("k_cpqr (calibration)");
     int k = read_scalar(kk.p, s);
     U.alloc((size_t)std::max(1, k) * c, s);
     skel.alloc(std::max(1, k), s);
@@ -552,9 +647,9 @@ double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *
     if (k > 0) {
         int P = 1;
         while (P < k) P <<= 1;
-        k_id_solve_f64<<<1, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(0, mc.p, mc.p + 1, kk.p, off.p, A.p,
-                                                                          off.p + 2, piv.p, cand.p, up.p, sp.p);
-        H2_LAUNCH("k_id_solve_f64 (calibration)");
+        k_id_solve<double><<<1, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(
+            0, mc.p, mc.p + 1, kk.p, off.p, A.p, A.p, off.p + 2, piv.p, cand.p, up.p, sp.p);
+        H2_LAUNCH("k_id_solve (calibration)");
     }
     DevBuf<double> num, den;
     num.alloc(c, s);

@@ -150,6 +150,12 @@ struct h2_tree_s {
     int64_t nnear = 0, nfar = 0;
     int max_leaf = 0;             // largest leaf population
     double ms_tree = 0, ms_lists = 0;
+    h2::DevBuf<double> cen[3];    // cell centre of every node
+    h2::DevBuf<float> xr[3];      // point coordinates relative to their leaf's centre (float32 kernels)
+    h2::DevBuf<int2> near_tiles;  // (leaf, first target) tiles of the nearfield kernel, built on first use
+    int near_tile_tpt = 0;
+    h2::DevBuf<int64_t> leaf_start;  // begin of every node as int64 (nearfield point sets)
+    h2::DevBuf<int32_t> leaf_count;  // end - begin of every node
 };
 
 struct h2_hidr_s {
@@ -180,8 +186,11 @@ struct h2_matrix_s {
     h2::DevBuf<int64_t> sk_off;        // exclusive scan of k over nodes (nnodes + 1)
     h2::DevBuf<int32_t> skel;          // skeletons, node order, each sorted
     h2::DevBuf<double> skc[3];         // skeleton coordinates, aligned with skel
-    h2::DevBuf<double *> uptr;         // per node U_i (c_i x k_i, column-major)
-    std::vector<h2::DevBuf<double>> ubufs;
+    h2::DevBuf<float> skr[3];          // skeleton coordinates relative to their node's centre (float32)
+    h2::DevBuf<void *> uptr;           // per node U_i (c_i x k_i, column-major; double or float)
+    std::vector<h2::DevBuf<unsigned char>> ubufs;
+    h2::DevBuf<int2> far_tiles;        // (node, first target) tiles of the coupling kernel
+    int far_tile_tpt = 0;
     std::vector<int> kmax_level, cmax_level;  // host
     int64_t ktotal = 0, utotal = 0;
     int kmax = 0;

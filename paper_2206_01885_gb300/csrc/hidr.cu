@@ -164,11 +164,37 @@ __device__ int block_unique_write(const int32_t *v, int P, int32_t *out, int *sc
 __device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax_(double a, double b) { return a > b ? a : b; }
 
+constexpr int DR_CHUNK = 32;        // points per chunk
+constexpr int DR_SUPER = 32;        // chunks per superchunk
+constexpr int DR_MAX_SUPER = 1024;  // superchunk boxes kept in shared memory
+constexpr int DR_PRUNE_MIN = 2048;  // sets at least this large use the pruned search
+
+// squared distance from q to the box [b[0..2], b[3..5]]; a lower bound of the
+// squared distance to every point inside the box
+__device__ __forceinline__ double box_lb2(const double *b, const double *q, int d) {
+    double s = 0.0;
+    for (int k = 0; k < d; k++) {
+        double g = dmax_(0.0, dmax_(b[k] - q[k], q[k] - b[3 + k]));
+        s += g * g;
+    }
+    return s;
+}
+
+// warp-wide lexicographic minimum of (value, label); every lane gets the result
+__device__ __forceinline__ void warp_argmin(double &v, int32_t &i) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int32_t i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (v2 < v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+    }
+}
+
 // One CTA per node.  tdata[toff[a] .. toff[a+1]) are the labels of S (T);
 // coordinates of label s are (x0[s], x1[s], x2[s]).
 __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
                                                            const double *x0, const double *x1, const double *x2,
-                                                           int32_t *const *outptr, int32_t *outcnt, int lb) {
+                                                           int32_t *const *outptr, int32_t *outcnt, int lb,
+                                                           double *cbox_base) {
     extern __shared__ unsigned char smem_raw[];
     int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
     __shared__ int32_t tid_s[DR_TILE];
@@ -216,6 +242,105 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         l[k] = mn;
         h[k] = __ddiv_rn(__dsub_rn(mx, mn), (double)g);
     }
+    const int64_t nchunks = (nt + DR_CHUNK - 1) / DR_CHUNK;
+    const int64_t nsuper = (nchunks + DR_SUPER - 1) / DR_SUPER;
+    if (nt >= DR_PRUNE_MIN && nsuper <= DR_MAX_SUPER && cbox_base != nullptr) {
+        // Pruned exact search.  T is cut into chunks of 32 consecutive labels
+        // (Morton-coherent) and superchunks of 32 chunks, each with the exact
+        // float64 bounding box of its points.  For a grid point q the best
+        // (distance, label) pair starts from the chunk nearest to q and every
+        // chunk whose box lower bound exceeds the current best distance by more
+        // than 1e-12 relative is skipped: the bound and the point distances are
+        // both float64 evaluations within 10 ulps of their real values, so a
+        // skipped chunk cannot hold a point at or below the best distance.
+        double *cbox = cbox_base + (t0 / DR_CHUNK + a) * 6;
+        double *sbox = reinterpret_cast<double *>(smem_raw + (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t));
+        for (int64_t c = warp; c < nchunks; c += nw) {
+            int64_t p = c * DR_CHUNK + lane;
+            double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+            if (p < nt) {
+                int32_t sid = T[p];
+                mn[0] = mx[0] = x0[sid];
+                if (d > 1) mn[1] = mx[1] = x1[sid];
+                if (d > 2) mn[2] = mx[2] = x2[sid];
+            }
+            for (int k = 0; k < 3; k++)
+                for (int o = 16; o > 0; o >>= 1) {
+                    mn[k] = dmin_(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+                    mx[k] = dmax_(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+                }
+            if (lane < 3) { cbox[c * 6 + lane] = mn[lane]; cbox[c * 6 + 3 + lane] = mx[lane]; }
+        }
+        __syncthreads();
+        for (int64_t sc = threadIdx.x; sc < nsuper; sc += blockDim.x) {
+            double b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+            for (int64_t c = sc * DR_SUPER; c < min(nchunks, (sc + 1) * DR_SUPER); c++)
+                for (int k = 0; k < 3; k++) {
+                    b[k] = dmin_(b[k], cbox[c * 6 + k]);
+                    b[3 + k] = dmax_(b[3 + k], cbox[c * 6 + 3 + k]);
+                }
+            for (int k = 0; k < 6; k++) sbox[sc * 6 + k] = b[k];
+        }
+        __syncthreads();
+        const double slack = 1.0 + 1e-12;
+        for (int gi = warp; gi < G; gi += nw) {
+            double q[3];
+            int rem = gi;
+            for (int k = 0; k < 3; k++) {
+                int idx = 0;
+                if (k < d) { idx = rem % g; rem /= g; }
+                q[k] = k < d ? __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])) : 0.0;
+            }
+            // seed: the chunk with the smallest bound inside the nearest superchunk
+            double v = INFINITY;
+            int32_t si = INT_MAX;
+            for (int64_t sc = lane; sc < nsuper; sc += 32) {
+                double lbv = box_lb2(sbox + sc * 6, q, d);
+                if (lbv < v || (lbv == v && sc < si)) { v = lbv; si = (int32_t)sc; }
+            }
+            warp_argmin(v, si);
+            int64_t c = (int64_t)si * DR_SUPER + lane;
+            v = c < nchunks ? box_lb2(cbox + c * 6, q, d) : INFINITY;
+            int32_t c0 = c < nchunks ? (int32_t)c : INT_MAX;
+            warp_argmin(v, c0);
+            double bd = INFINITY;
+            int32_t bi = INT_MAX;
+            {
+                int64_t p = (int64_t)c0 * DR_CHUNK + lane;
+                if (p < nt) {
+                    bi = T[p];
+                    bd = h2_dist2(d, x0[bi], d > 1 ? x1[bi] : 0.0, d > 2 ? x2[bi] : 0.0, q[0], q[1], q[2]);
+                }
+                warp_argmin(bd, bi);
+            }
+            for (int64_t sb = 0; sb < nsuper; sb += 32) {
+                int64_t sc = sb + lane;
+                bool fl = sc < nsuper && box_lb2(sbox + sc * 6, q, d) <= bd * slack;
+                unsigned smask = __ballot_sync(0xffffffffu, fl);
+                while (smask) {
+                    int64_t s1 = sb + __ffs(smask) - 1;
+                    smask &= smask - 1;
+                    int64_t cc = s1 * DR_SUPER + lane;
+                    bool cf = cc < nchunks && cc != c0 && box_lb2(cbox + cc * 6, q, d) <= bd * slack;
+                    unsigned cmask = __ballot_sync(0xffffffffu, cf);
+                    while (cmask) {
+                        int64_t c1 = s1 * DR_SUPER + __ffs(cmask) - 1;
+                        cmask &= cmask - 1;
+                        int64_t p = c1 * DR_CHUNK + lane;
+                        double dd = INFINITY;
+                        int32_t id = INT_MAX;
+                        if (p < nt) {
+                            id = T[p];
+                            dd = h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0, d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]);
+                        }
+                        warp_argmin(dd, id);
+                        if (dd < bd || (dd == bd && id < bi)) { bd = dd; bi = id; }
+                    }
+                }
+            }
+            if (lane == 0) win[gi] = bi;
+        }
+    } else {
     // Nearest point to each grid point, DR_GPT grid points per thread per sweep.
     // Exact float64 argmin through a float32 filter: with coordinates taken
     // relative to the box corner l and W the largest box extent, the float32
@@ -282,6 +407,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             if (gi < G) win[gi] = bi[j];
         }
     }
+    }  // brute-force sweep
     __syncthreads();
     int P = 1;
     while (P < G) P <<= 1;
@@ -298,19 +424,23 @@ int64_t gridsize(int g, int d) {
     return G;
 }
 
-void launch_datareduct(const int64_t *toff, const int32_t *tdata, int nl, int g, int d, const double *const xs[3],
-                       int32_t *const *outptr, int32_t *outcnt, int lb, cudaStream_t s) {
+void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, int nl, int g, int d,
+                       const double *const xs[3], int32_t *const *outptr, int32_t *outcnt, int lb, cudaStream_t s) {
     if (nl <= 0) return;
     int G = (int)gridsize(g, d);
-    size_t sm = (size_t)next_pow2(G) * sizeof(int32_t);
+    // win (next power of two >= G labels) followed by the superchunk boxes
+    size_t sm = std::max((size_t)next_pow2(G) * sizeof(int32_t), (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t)) +
+                (size_t)DR_MAX_SUPER * 6 * sizeof(double);
     static bool attr_set = false;
     if (!attr_set) {
         H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     DR_MAX_GRID * (int)sizeof(int32_t)));
+                                     DR_MAX_GRID * (int)sizeof(int32_t) + DR_MAX_SUPER * 6 * (int)sizeof(double)));
         attr_set = true;
     }
+    DevBuf<double> cbox;
+    cbox.alloc((size_t)(ttot / DR_CHUNK + nl + 1) * 6, s);
     ProfScope ps(KT_DATAREDUCT, s);
-    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, xs[0], xs[1], xs[2], outptr, outcnt, lb);
+    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, xs[0], xs[1], xs[2], outptr, outcnt, lb, cbox.p);
     H2_LAUNCH("k_datareduct");
 }
 
@@ -360,7 +490,7 @@ void hidr_impl(h2_hidr_s *h) {
         k_gather_up<<<nl, 256, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, t->end.p, h->xptr.p, h->xcnt.p,
                                        toff.p, tdata.p);
         H2_LAUNCH("k_gather_up");
-        launch_datareduct(toff.p, tdata.p, nl, h->g1, d, xs, h->xptr.p, h->xcnt.p, lb, s);
+        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g1, d, xs, h->xptr.p, h->xcnt.p, lb, s);
         h->xtotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e1, s));
@@ -383,7 +513,7 @@ void hidr_impl(h2_hidr_s *h) {
         k_gather_down<<<nl, 256, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->xptr.p, h->xcnt.p,
                                          h->yptr.p, h->ycnt.p, toff.p, tdata.p);
         H2_LAUNCH("k_gather_down");
-        launch_datareduct(toff.p, tdata.p, nl, h->g2, d, xs, h->yptr.p, h->ycnt.p, lb, s);
+        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, xs, h->yptr.p, h->ycnt.p, lb, s);
         h->ytotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e2, s));
@@ -420,7 +550,7 @@ int64_t datareduct_one(const double *const xs[3], int d, int64_t n, int g, int32
     H2_CUDA(cudaMemcpyAsync(toff.p, offs, sizeof offs, cudaMemcpyHostToDevice, s));
     H2_CUDA(cudaMemcpyAsync(tdata.p, ids.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     H2_CUDA(cudaMemcpyAsync(optr.p, &out_dev, sizeof(int32_t *), cudaMemcpyHostToDevice, s));
-    launch_datareduct(toff.p, tdata.p, 1, g, d, xs, optr.p, cnt.p, 0, s);
+    launch_datareduct(toff.p, tdata.p, n, 1, g, d, xs, optr.p, cnt.p, 0, s);
     return read_scalar(cnt.p, s);
 }
 

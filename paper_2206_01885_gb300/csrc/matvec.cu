@@ -21,8 +21,7 @@ namespace h2 {
 namespace {
 
 constexpr int MV_THREADS = 256;
-constexpr int NB_TILE = 256;  // source points staged per pass in the N-body kernels
-constexpr int MAX_TPT = 8;    // targets per thread in the N-body kernels
+constexpr int NB_WARPS = 8;   // warps of an N-body CTA, each taking every 8th source block
 
 __global__ void k_perm_in(const double *x, const int32_t *perm, int64_t n, double *xm) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,9 +33,11 @@ __global__ void k_perm_out(const double *ym, const int32_t *perm, int64_t n, dou
     if (p < n) y[perm[p]] = ym[p];
 }
 
-// xh_i[a] = sum_r U_i[r, a] in[r]; one CTA per node, one warp per column
+// xh_i[a] = sum_r U_i[r, a] in[r]; one CTA per node, one warp per column,
+// float64 accumulation (U is float64 or float32)
+template <class UT>
 __global__ void k_upward(int lb, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
-                         const int32_t *kk, const int32_t *cc, double *const *uptr, const int64_t *sk_off,
+                         const int32_t *kk, const int32_t *cc, void *const *uptr, const int64_t *sk_off,
                          const double *xm, double *xh) {
     extern __shared__ double sin_[];
     int i = lb + blockIdx.x;
@@ -45,20 +46,21 @@ __global__ void k_upward(int lb, const int32_t *nchild, const int32_t *fchild, c
     const double *in = nchild[i] == 0 ? xm + begin[i] : xh + sk_off[fchild[i]];
     for (int r = threadIdx.x; r < c; r += blockDim.x) sin_[r] = in[r];
     __syncthreads();
-    const double *U = uptr[i];
+    const UT *U = static_cast<const UT *>(uptr[i]);
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = warp; a < k; a += nw) {
-        const double *col = U + (int64_t)a * c;
+        const UT *col = U + (int64_t)a * c;
         double s = 0.0;
-        for (int r = lane; r < c; r += 32) s += col[r] * sin_[r];
+        for (int r = lane; r < c; r += 32) s += (double)col[r] * sin_[r];
         s = warp_sum(s);
         if (lane == 0) xh[sk_off[i] + a] = s;
     }
 }
 
 // out = U_i zh_i, added to the children's zh (parent) or to y (leaf)
+template <class UT>
 __global__ void k_downward(int lb, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
-                           const int32_t *kk, const int32_t *cc, double *const *uptr, const int64_t *sk_off,
+                           const int32_t *kk, const int32_t *cc, void *const *uptr, const int64_t *sk_off,
                            double *zh, double *ym) {
     extern __shared__ double sz_[];
     int i = lb + blockIdx.x;
@@ -67,79 +69,102 @@ __global__ void k_downward(int lb, const int32_t *nchild, const int32_t *fchild,
     const double *z = zh + sk_off[i];
     for (int a = threadIdx.x; a < k; a += blockDim.x) sz_[a] = z[a];
     __syncthreads();
-    const double *U = uptr[i];
+    const UT *U = static_cast<const UT *>(uptr[i]);
     double *out = nchild[i] == 0 ? ym + begin[i] : zh + sk_off[fchild[i]];
     for (int r = threadIdx.x; r < c; r += blockDim.x) {
         double s = 0.0;
-        for (int a = 0; a < k; a++) s += U[r + (int64_t)a * c] * sz_[a];
+        for (int a = 0; a < k; a++) s += (double)U[r + (int64_t)a * c] * sz_[a];
         out[r] += s;
     }
 }
 
-// N-body accumulation: targets t (owned by this CTA) += sum_s kappa(t, s) w_s
-// over a list of source blocks.  kind 0: coupling (sources = far skeletons),
-// kind 1: nearfield (sources = near leaves' points).
-template <int TPT>
-__global__ void __launch_bounds__(MV_THREADS) k_nbody(int kind, const int32_t *kk, const int64_t *sk_off,
-                                                      const double *s0, const double *s1, const double *s2,
-                                                      const double *xh, double *zh, const int32_t *begin,
-                                                      const int32_t *end, const double *x0, const double *x1,
-                                                      const double *x2, const double *xm, double *ym,
-                                                      const int64_t *lptr, const int32_t *lidx,
-                                                      const int32_t *nodes, int d, int kid, double kp0) {
-    __shared__ double sx[3][NB_TILE], sw[NB_TILE];
-    const int i = nodes[blockIdx.x];
-    // target range of this CTA
-    int64_t tb, nt;
-    const double *tx0, *tx1, *tx2;
-    if (kind == 0) { tb = sk_off[i]; nt = kk[i]; tx0 = s0; tx1 = s1; tx2 = s2; }
-    else { tb = begin[i]; nt = end[i] - begin[i]; tx0 = x0; tx1 = x1; tx2 = x2; }
-    for (int64_t chunk = 0; chunk < nt; chunk += (int64_t)MV_THREADS * TPT) {
-        double t[TPT][3], acc[TPT];
+// kappa for the matvec kernels: fast forms (rsqrt, exp) in float64 or float32
+template <int KID>
+__device__ __forceinline__ double kap(double r2, double p) {  // p: 1/h^2 (Gaussian) or 1/l (exponential)
+    if constexpr (KID == H2_K_COULOMB) return r2 > 0.0 ? rsqrt(r2) : 0.0;
+    else if constexpr (KID == H2_K_GAUSSIAN) return exp(-r2 * p);
+    else if constexpr (KID == H2_K_EXPONENTIAL) return exp(-sqrt(r2) * p);
+    else return sqrt(1.0 + r2);
+}
+template <int KID>
+__device__ __forceinline__ float kap(float r2, float p) {
+    if constexpr (KID == H2_K_COULOMB) return r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    else if constexpr (KID == H2_K_GAUSSIAN) return __expf(-r2 * p);
+    else if constexpr (KID == H2_K_EXPONENTIAL) return __expf(-sqrtf(r2) * p);
+    else return sqrtf(1.0f + r2);
+}
+
+// Tiled N-body accumulation out[t] += sum_s kappa(x_t, x_s) w_s.  A point set
+// of node i is [start[i], start[i] + count[i]) of the coordinate arrays; one
+// CTA takes the 32*TPT targets of one tile of node i, its warps split the
+// source blocks j of the list lidx[lptr[i] .. lptr[i+1]) and every lane reads
+// each source point as a broadcast load.  Real = double: absolute float64
+// coordinates.  Real = float: float32 coordinates relative to each node's cell
+// centre, the centre offset added per block pair in float64 first; each block's
+// float32 sum is added into a float64 accumulator.
+template <class Real, int KID, int TPT>
+__global__ void __launch_bounds__(NB_WARPS * 32)
+    k_nbody(const int2 *tiles, const int64_t *start, const int32_t *count, const Real *X0, const Real *X1,
+            const Real *X2, const double *C0, const double *C1, const double *C2, const double *w, double *out,
+            const int64_t *lptr, const int32_t *lidx, int d, double kpar) {
+    __shared__ double part[NB_WARPS][32 * TPT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int2 tl = tiles[blockIdx.x];
+    const int i = tl.x;
+    const int64_t ts = start[i];
+    const int tn = count[i];
+    const Real p = (Real)kpar;
+    Real tx[TPT][3];
+    double acc[TPT];
 #pragma unroll
-        for (int u = 0; u < TPT; u++) {
-            int64_t a = chunk + u * MV_THREADS + threadIdx.x;
-            bool ok = a < nt;
-            t[u][0] = ok ? tx0[tb + a] : 0.0;
-            t[u][1] = ok && d > 1 ? tx1[tb + a] : 0.0;
-            t[u][2] = ok && d > 2 ? tx2[tb + a] : 0.0;
-            acc[u] = 0.0;
+    for (int u = 0; u < TPT; u++) {
+        int a = tl.y + u * 32 + lane;
+        bool ok = a < tn;
+        tx[u][0] = ok ? X0[ts + a] : (Real)0;
+        tx[u][1] = ok && d > 1 ? X1[ts + a] : (Real)0;
+        tx[u][2] = ok && d > 2 ? X2[ts + a] : (Real)0;
+        acc[u] = 0.0;
+    }
+    for (int64_t e = lptr[i] + warp; e < lptr[i + 1]; e += NB_WARPS) {
+        const int j = lidx[e];
+        const int64_t ss = start[j];
+        const int sn = count[j];
+        Real sh[TPT][3];
+        if constexpr (sizeof(Real) == 4) {  // target coordinates in node j's frame
+            float o0 = (float)(C0[i] - C0[j]), o1 = d > 1 ? (float)(C1[i] - C1[j]) : 0.f,
+                  o2 = d > 2 ? (float)(C2[i] - C2[j]) : 0.f;
+#pragma unroll
+            for (int u = 0; u < TPT; u++) { sh[u][0] = tx[u][0] + o0; sh[u][1] = tx[u][1] + o1; sh[u][2] = tx[u][2] + o2; }
+        } else {
+#pragma unroll
+            for (int u = 0; u < TPT; u++) { sh[u][0] = tx[u][0]; sh[u][1] = tx[u][1]; sh[u][2] = tx[u][2]; }
         }
-        for (int64_t e = lptr[i]; e < lptr[i + 1]; e++) {
-            int j = lidx[e];
-            int64_t sb, ns;
-            const double *q0, *q1, *q2, *w;
-            if (kind == 0) { sb = sk_off[j]; ns = kk[j]; q0 = s0; q1 = s1; q2 = s2; w = xh; }
-            else { sb = begin[j]; ns = end[j] - begin[j]; q0 = x0; q1 = x1; q2 = x2; w = xm; }
-            for (int64_t p0 = 0; p0 < ns; p0 += NB_TILE) {
-                int cnt = (int)(ns - p0 < NB_TILE ? ns - p0 : NB_TILE);
-                __syncthreads();
-                for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
-                    sx[0][r] = q0[sb + p0 + r];
-                    sx[1][r] = d > 1 ? q1[sb + p0 + r] : 0.0;
-                    sx[2][r] = d > 2 ? q2[sb + p0 + r] : 0.0;
-                    sw[r] = w[sb + p0 + r];
-                }
-                __syncthreads();
-                for (int r = 0; r < cnt; r++) {
-                    double a0 = sx[0][r], a1 = sx[1][r], a2 = sx[2][r], ww = sw[r];
+        Real blk[TPT];
 #pragma unroll
-                    for (int u = 0; u < TPT; u++) {
-                        double r2 = h2_dist2(d, t[u][0], t[u][1], t[u][2], a0, a1, a2);
-                        acc[u] += h2_kappa(kid, kp0, r2) * ww;
-                    }
-                }
+        for (int u = 0; u < TPT; u++) blk[u] = (Real)0;
+        for (int q = 0; q < sn; q++) {
+            const Real a0 = X0[ss + q], a1 = d > 1 ? X1[ss + q] : (Real)0, a2 = d > 2 ? X2[ss + q] : (Real)0;
+            const Real ws = (Real)w[ss + q];
+#pragma unroll
+            for (int u = 0; u < TPT; u++) {
+                Real dx = sh[u][0] - a0, dy = sh[u][1] - a1, dz = sh[u][2] - a2;
+                Real r2 = dx * dx + dy * dy + dz * dz;
+                blk[u] += kap<KID>(r2, p) * ws;
             }
         }
 #pragma unroll
-        for (int u = 0; u < TPT; u++) {
-            int64_t a = chunk + u * MV_THREADS + threadIdx.x;
-            if (a < nt) {
-                if (kind == 0) zh[tb + a] += acc[u];
-                else ym[tb + a] += acc[u];
-            }
+        for (int u = 0; u < TPT; u++) acc[u] += (double)blk[u];
+    }
+#pragma unroll
+    for (int u = 0; u < TPT; u++) part[warp][u * 32 + lane] = acc[u];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * TPT; t += blockDim.x) {
+        int a = tl.y + t;
+        if (a < tn) {
+            double sum = 0.0;
+            for (int wv = 0; wv < NB_WARPS; wv++) sum += part[wv][t];
+            out[ts + a] += sum;
         }
-        __syncthreads();
     }
 }
 
@@ -197,13 +222,55 @@ __global__ void k_sampled_error(const double *exact, const double *approx, const
     }
 }
 
-__global__ void k_active_nodes(const int32_t *kk, const int64_t *lptr, int nn, int32_t *list, int32_t *cnt,
-                               const int32_t *nchild, int kind) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nn) return;
-    bool act = kind == 0 ? (kk[i] > 0 && lptr[i + 1] > lptr[i]) : (nchild[i] == 0 && lptr[i + 1] > lptr[i]);
-    if (act) list[atomicAdd(cnt, 1)] = i;
+// (node, first target) tiles for every node with targets and a non-empty list
+void build_tiles(const std::vector<int32_t> &cnt, const std::vector<int64_t> &lptr, int per_tile,
+                 DevBuf<int2> &tiles, cudaStream_t s) {
+    std::vector<int2> v;
+    for (size_t i = 0; i < cnt.size(); i++) {
+        if (cnt[i] <= 0 || lptr[i + 1] == lptr[i]) continue;
+        for (int a = 0; a < cnt[i]; a += per_tile) v.push_back(make_int2((int)i, a));
+    }
+    tiles.alloc(std::max<size_t>(v.size(), 1), s);
+    if (!v.empty()) H2_CUDA(cudaMemcpyAsync(tiles.p, v.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    tiles.n = v.size();
 }
+
+template <class Real, int KID, int TPT>
+void nbody_launch(const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
+                  const Real *X1, const Real *X2, const double *C0, const double *C1, const double *C2, const double *w,
+                  double *out, const int64_t *lptr, const int32_t *lidx, int d, double kpar, cudaStream_t s) {
+    if (tiles.n == 0) return;
+    k_nbody<Real, KID, TPT><<<(unsigned)tiles.n, NB_WARPS * 32, 0, s>>>(tiles.p, start, count, X0, X1, X2, C0, C1,
+                                                                       C2, w, out, lptr, lidx, d, kpar);
+    H2_LAUNCH("k_nbody");
+}
+
+template <class Real, int TPT>
+void nbody_dispatch(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
+                    const Real *X1, const Real *X2, const double *C0, const double *C1, const double *C2,
+                    const double *w, double *out, const int64_t *lptr, const int32_t *lidx, int d, double kp0,
+                    cudaStream_t s) {
+    switch (kid) {
+    case H2_K_COULOMB:
+        nbody_launch<Real, H2_K_COULOMB, TPT>(tiles, start, count, X0, X1, X2, C0, C1, C2, w, out, lptr, lidx, d,
+                                              0.0, s);
+        break;
+    case H2_K_GAUSSIAN:
+        nbody_launch<Real, H2_K_GAUSSIAN, TPT>(tiles, start, count, X0, X1, X2, C0, C1, C2, w, out, lptr, lidx, d,
+                                               1.0 / (kp0 * kp0), s);
+        break;
+    case H2_K_EXPONENTIAL:
+        nbody_launch<Real, H2_K_EXPONENTIAL, TPT>(tiles, start, count, X0, X1, X2, C0, C1, C2, w, out, lptr, lidx,
+                                                  d, 1.0 / kp0, s);
+        break;
+    default:
+        nbody_launch<Real, H2_K_MULTIQUADRIC, TPT>(tiles, start, count, X0, X1, X2, C0, C1, C2, w, out, lptr, lidx,
+                                                   d, 0.0, s);
+    }
+}
+
+constexpr int TPT_F64 = 1, TPT_F32 = 4;
 
 }  // namespace
 
@@ -211,15 +278,44 @@ void matvec_impl(h2_matrix_s *A, const double *x, double *y, cudaStream_t s) {
     h2_tree_s *t = A->tree;
     const int nn = t->nnodes, d = t->d;
     const int64_t n = t->n;
+    const bool f64 = A->prec == H2_PREC_FP64;
     static bool attr = false;
     if (!attr) {
-        H2_CUDA(cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        H2_CUDA(cudaFuncSetAttribute(k_downward, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        for (auto f : {(const void *)k_upward<double>, (const void *)k_upward<float>, (const void *)k_downward<double>,
+                       (const void *)k_downward<float>})
+            H2_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr = true;
     }
     for (int l = 1; l < t->nlevels; l++)
         if ((size_t)A->cmax_level[l] * sizeof(double) > 200 * 1024)
             fail(H2_ERR_UNIMPLEMENTED, "candidate set too large for the single-CTA upward pass");
+    const int tpt = f64 ? TPT_F64 : TPT_F32;
+    // tiles of the coupling (per matrix) and nearfield (per tree) kernels, built once
+    if (A->far_tile_tpt != tpt) {
+        std::vector<int32_t> kh = read_vec(A->k.p, nn, s);
+        std::vector<int64_t> fp = read_vec(t->far_ptr.p, nn + 1, s);
+        build_tiles(kh, fp, 32 * tpt, A->far_tiles, s);
+        A->far_tile_tpt = tpt;
+    }
+    if (t->near_tile_tpt != tpt) {
+        std::vector<int32_t> b = read_vec(t->begin.p, nn, s), e = read_vec(t->end.p, nn, s),
+                             nc = read_vec(t->nchild.p, nn, s);
+        std::vector<int64_t> np = read_vec(t->near_ptr.p, nn + 1, s);
+        std::vector<int32_t> cnt(nn);
+        for (int i = 0; i < nn; i++) cnt[i] = nc[i] == 0 ? e[i] - b[i] : 0;
+        build_tiles(cnt, np, 32 * tpt, t->near_tiles, s);
+        t->near_tile_tpt = tpt;
+        if (!t->leaf_start.p) {  // int64 starts of every node's points (nearfield point sets)
+            std::vector<int64_t> st(b.begin(), b.end());
+            std::vector<int32_t> ct(nn);
+            for (int i = 0; i < nn; i++) ct[i] = e[i] - b[i];
+            t->leaf_start.alloc(nn, s);
+            t->leaf_count.alloc(nn, s);
+            H2_CUDA(cudaMemcpyAsync(t->leaf_start.p, st.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            H2_CUDA(cudaMemcpyAsync(t->leaf_count.p, ct.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            H2_CUDA(cudaStreamSynchronize(s));
+        }
+    }
     DevBuf<double> xm, ym, xh, zh;
     xm.alloc(n, s);
     ym.alloc(n, s);
@@ -236,55 +332,52 @@ void matvec_impl(h2_matrix_s *A, const double *x, double *y, cudaStream_t s) {
         if (A->kmax_level[l] == 0) continue;
         size_t sm = (size_t)A->cmax_level[l] * sizeof(double);
         ProfScope ps(KT_UPWARD, s);
-        k_upward<<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p, A->uptr.p,
-                                            A->sk_off.p, xm.p, xh.p);
+        if (f64)
+            k_upward<double><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
+                                                        A->uptr.p, A->sk_off.p, xm.p, xh.p);
+        else
+            k_upward<float><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
+                                                       A->uptr.p, A->sk_off.p, xm.p, xh.p);
         H2_LAUNCH("k_upward");
     }
-    // coupling over far pairs
-    DevBuf<int32_t> list, cnt;
-    list.alloc(std::max(nn, 1), s);
-    cnt.alloc(1, s);
-    H2_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t), s));
-    k_active_nodes<<<blocks_for(nn, 256), 256, 0, s>>>(A->k.p, t->far_ptr.p, nn, list.p, cnt.p, t->nchild.p, 0);
-    H2_LAUNCH("k_active_nodes far");
-    int nact = read_scalar(cnt.p, s);
-    int tpt = 1;
-    while (tpt < MAX_TPT && (int64_t)tpt * MV_THREADS < A->kmax) tpt *= 2;
-    auto launch_nbody = [&](int kind, int nblocks, int tp, const int64_t *lp, const int32_t *li) {
-        if (nblocks <= 0) return;
-#define H2_NB(T)                                                                                                   \
-    k_nbody<T><<<nblocks, MV_THREADS, 0, s>>>(kind, A->k.p, A->sk_off.p, A->skc[0].p, A->skc[1].p, A->skc[2].p,    \
-                                              xh.p, zh.p, t->begin.p, t->end.p, t->xs[0].p, t->xs[1].p,            \
-                                              t->xs[2].p, xm.p, ym.p, lp, li, list.p, d, A->kid, A->kp[0])
-        ProfScope ps(kind == 0 ? KT_COUPLING : KT_NEAR, s);
-        switch (tp) {
-        case 1: H2_NB(1); break;
-        case 2: H2_NB(2); break;
-        case 4: H2_NB(4); break;
-        default: H2_NB(8); break;
-        }
-#undef H2_NB
-        H2_LAUNCH("k_nbody");
-    };
-    launch_nbody(0, nact, tpt, t->far_ptr.p, t->far_idx.p);
+    // coupling over far pairs: B_ij = K(Xhat_i, Xhat_j) on the fly
+    {
+        ProfScope ps(KT_COUPLING, s);
+        if (f64)
+            nbody_dispatch<double, TPT_F64>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skc[0].p, A->skc[1].p,
+                                            A->skc[2].p, nullptr, nullptr, nullptr, xh.p, zh.p, t->far_ptr.p,
+                                            t->far_idx.p, d, A->kp[0], s);
+        else
+            nbody_dispatch<float, TPT_F32>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skr[0].p, A->skr[1].p,
+                                           A->skr[2].p, t->cen[0].p, t->cen[1].p, t->cen[2].p, xh.p, zh.p,
+                                           t->far_ptr.p, t->far_idx.p, d, A->kp[0], s);
+    }
     // downward, level 1 first
     for (int l = 1; l < t->nlevels; l++) {
         int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
         if (A->kmax_level[l] == 0) continue;
         size_t sm = (size_t)A->kmax_level[l] * sizeof(double);
         ProfScope ps(KT_DOWNWARD, s);
-        k_downward<<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p, A->uptr.p,
-                                              A->sk_off.p, zh.p, ym.p);
+        if (f64)
+            k_downward<double><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
+                                                          A->uptr.p, A->sk_off.p, zh.p, ym.p);
+        else
+            k_downward<float><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
+                                                         A->uptr.p, A->sk_off.p, zh.p, ym.p);
         H2_LAUNCH("k_downward");
     }
-    // nearfield over near leaf pairs
-    H2_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t), s));
-    k_active_nodes<<<blocks_for(nn, 256), 256, 0, s>>>(A->k.p, t->near_ptr.p, nn, list.p, cnt.p, t->nchild.p, 1);
-    H2_LAUNCH("k_active_nodes near");
-    int nleaf = read_scalar(cnt.p, s);
-    int tpn = 1;
-    while (tpn < MAX_TPT && (int64_t)tpn * MV_THREADS < t->max_leaf) tpn *= 2;
-    launch_nbody(1, nleaf, tpn, t->near_ptr.p, t->near_idx.p);
+    // nearfield over near leaf pairs: K(X_i, X_j) on the fly
+    {
+        ProfScope ps(KT_NEAR, s);
+        if (f64)
+            nbody_dispatch<double, TPT_F64>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xs[0].p,
+                                            t->xs[1].p, t->xs[2].p, nullptr, nullptr, nullptr, xm.p, ym.p,
+                                            t->near_ptr.p, t->near_idx.p, d, A->kp[0], s);
+        else
+            nbody_dispatch<float, TPT_F32>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xr[0].p,
+                                           t->xr[1].p, t->xr[2].p, t->cen[0].p, t->cen[1].p, t->cen[2].p, xm.p, ym.p,
+                                           t->near_ptr.p, t->near_idx.p, d, A->kp[0], s);
+    }
     k_perm_out<<<blocks_for(n, 256), 256, 0, s>>>(ym.p, t->perm.p, n, y);
     H2_LAUNCH("k_perm_out");
 }

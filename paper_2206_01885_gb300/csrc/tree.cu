@@ -147,6 +147,33 @@ __global__ void k_split_write(int32_t *level, int32_t *parent, int32_t *fchild, 
     }
 }
 
+// centre of each node's cell in real coordinates: lo + (c + 1/2) side / 2^level
+__global__ void k_node_centres(const int32_t *level, const uint64_t *prefix, int nn, int d, const Geom *g, double *c0,
+                               double *c1, double *c2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    int l = level[i];
+    uint64_t c[3] = {0, 0, 0};
+    for (int b = 0; b < l; b++)
+        for (int k = 0; k < d; k++) c[k] |= ((prefix[i] >> (d * b + k)) & 1ull) << b;
+    double w = ldexp(g->side, -l);
+    double *out[3] = {c0, c1, c2};
+    for (int k = 0; k < d; k++) out[k][i] = g->lo[k] + ((double)c[k] + 0.5) * w;
+}
+
+// float32 coordinates of each point relative to the centre of its leaf (one CTA per node, leaves only)
+__global__ void k_rel_coords(const int32_t *nchild, const int32_t *begin, const int32_t *end, const double *c0,
+                             const double *c1, const double *c2, const double *x0, const double *x1,
+                             const double *x2, int d, float *r0, float *r1, float *r2) {
+    int i = blockIdx.x;
+    if (nchild[i] != 0) return;
+    for (int p = begin[i] + threadIdx.x; p < end[i]; p += blockDim.x) {
+        r0[p] = (float)(x0[p] - c0[i]);
+        if (d > 1) r1[p] = (float)(x1[p] - c1[i]);
+        if (d > 2) r2[p] = (float)(x2[p] - c2[i]);
+    }
+}
+
 __global__ void k_max_leaf(const int32_t *nchild, const int32_t *begin, const int32_t *end, int nn, int32_t *mx) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nn && nchild[i] == 0) atomicMax(mx, end[i] - begin[i]);
@@ -324,6 +351,17 @@ void tree_build_impl(h2_tree_s *t, const double *pts) {
     }
     t->nnodes = t->lptr.back();
     t->nlevels = (int)t->lptr.size() - 1;
+    // cell centres and leaf-relative float32 coordinates (float32 kernels)
+    for (int k = 0; k < 3; k++) {
+        t->cen[k].alloc(k < d ? t->nnodes : 1, s);
+        t->xr[k].alloc(k < d ? n : 1, s);
+    }
+    k_node_centres<<<blocks_for(t->nnodes, 256), 256, 0, s>>>(t->level.p, t->prefix.p, t->nnodes, d, g.p,
+                                                              t->cen[0].p, t->cen[1].p, t->cen[2].p);
+    H2_LAUNCH("k_node_centres");
+    k_rel_coords<<<t->nnodes, 128, 0, s>>>(t->nchild.p, t->begin.p, t->end.p, t->cen[0].p, t->cen[1].p, t->cen[2].p,
+                                          t->xs[0].p, t->xs[1].p, t->xs[2].p, d, t->xr[0].p, t->xr[1].p, t->xr[2].p);
+    H2_LAUNCH("k_rel_coords");
     DevBuf<int32_t> mx;
     mx.alloc(1, s);
     H2_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int32_t), s));

@@ -61,12 +61,21 @@ def test_tree_and_lists_bit_exact(H2, name, make, q):
     assert np.array_equal(t2.get("perm"), o.perm)
 
 
-HIDR_CASES = [("cube3d", 3, 6000, 60, 4, 5), ("gmix2d", 2, 8000, 30, 6, 7), ("cube3d_g2", 3, 3000, 20, 2, 3)]
+HIDR_CASES = [("cube3d", 3, 6000, 60, 4, 5), ("gmix2d", 2, 8000, 30, 6, 7), ("cube3d_g2", 3, 3000, 20, 2, 3),
+              # sets of tens of thousands of points: the pruned nearest-point search
+              ("cube3d_big", 3, 40000, 64, 5, 6),
+              # points snapped to a lattice: many exact distance ties between labels
+              ("lattice3d", 3, 20000, 32, 4, 4)]
 
 
 @pytest.mark.parametrize("name,d,n,q,g1,g2", HIDR_CASES, ids=[c[0] for c in HIDR_CASES])
 def test_hidr_bit_exact(H2, name, d, n, q, g1, g2):
-    pts = I.uniform_cube(n, d, seed=10 + d) if "cube" in name else I.gaussian_mixture(n, seed=11)
+    if name == "lattice3d":
+        pts = np.round(I.uniform_cube(n, d, seed=12) * 16.0) / 16.0
+    elif "cube" in name:
+        pts = I.uniform_cube(n, d, seed=10 + d)
+    else:
+        pts = I.gaussian_mixture(n, seed=11)
     t = H2.Tree(dev(pts), q)
     h = H2.Hidr(t, g1, g2)
     o = O.tree_build(pts, q)
@@ -169,3 +178,48 @@ def test_handle_lifetimes(H2):
     A.free()
     h.free()
     t.free()
+
+
+MIXED_CASES = [
+    ("coulomb3d", 3, 8000, 100, "coulomb", (), 1e-5, 7),
+    ("coulomb3d_deep", 3, 20000, 40, "coulomb", (), 1e-4, 5),
+    ("gauss2d", 2, 6000, 64, "gaussian", (0.2,), 1e-5, 10),
+    ("expo2d", 2, 5000, 50, "exponential", (0.1,), 1e-5, 10),
+]
+
+
+@pytest.mark.parametrize("name,d,n,q,kern,kp,eps,g", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_construct_and_matvec_mixed(H2, name, d, n, q, kern, kp, eps, g):
+    """float32 blocks / Householder updates / matvec kernels, float64 norms,
+    pivots and solve: the product stays within 10 eps of both the dense product
+    and the oracle's float64 H^2 product built with the same eps and g."""
+    pts = I.uniform_cube(n, d, seed=60 + d)
+    z = I.standard_normal(n, seed=61)
+    t = H2.Tree(dev(pts), q)
+    h = H2.Hidr(t, g, g)
+    A = H2.H2Matrix(t, h, kern, kp, eps, "mixed")
+    y = A.matvec(dev(z)).cpu().numpy()
+    yd = O.dense_matvec(pts, kern, kp, z)
+    assert np.linalg.norm(y - yd) / np.linalg.norm(yd) <= 10 * eps
+    o, oh, OH = O.build_h2(pts, kern, kp, q, eps, g, g)
+    yo = OH.matvec(z)
+    assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps
+    # structure: sorted skeletons inside the candidates, identity rows of U
+    ranks, nc = A.get("rank"), A.get("ncand")
+    skel, U = A.get("skel"), A.get("U")
+    koff = np.concatenate([[0], np.cumsum(ranks)])
+    uoff = np.concatenate([[0], np.cumsum(ranks.astype(np.int64) * nc)])
+    for i in range(1, t.nnodes):
+        k = ranks[i]
+        if k == 0:
+            continue
+        sk = skel[koff[i]:koff[i + 1]]
+        assert np.all(np.diff(sk) > 0)
+        if o.nchild[i] == 0:
+            cand = np.arange(o.begin[i], o.end[i])
+        else:
+            cand = np.concatenate([skel[koff[c]:koff[c + 1]] for c in range(o.fchild[i], o.fchild[i] + o.nchild[i])])
+        rows = np.searchsorted(cand, sk)
+        assert np.array_equal(cand[rows], sk)
+        Ui = U[uoff[i]:uoff[i + 1]].reshape(k, nc[i]).T
+        assert np.array_equal(Ui[rows], np.eye(k))

@@ -38,6 +38,11 @@ WORKLOADS = {
                         rows=1000, compare="cube1m_mixed"),
     "cube1m_mixed": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-5, prec="mixed", seed=2,
                          rows=1000),
+    # 262,144-point versions of the two forms (profiling-sized: tree depth 4)
+    "cube256k_fp64": dict(n=1 << 18, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-8, prec="fp64", seed=2,
+                          rows=1000, compare="cube256k_mixed"),
+    "cube256k_mixed": dict(n=1 << 18, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-5, prec="mixed", seed=2,
+                           rows=1000),
     "cube8k_fp64": dict(n=8000, d=3, kernel="coulomb", kparams=(), q=200, eps=1e-6, prec="fp64", seed=1,
                         rows=1000),
 }

@@ -169,15 +169,22 @@ constexpr int DR_SUPER = 32;        // chunks per superchunk
 constexpr int DR_MAX_SUPER = 1024;  // superchunk boxes kept in shared memory
 constexpr int DR_PRUNE_MIN = 2048;  // sets at least this large use the pruned search
 
-// squared distance from q to the box [b[0..2], b[3..5]]; a lower bound of the
-// squared distance to every point inside the box
-__device__ __forceinline__ double box_lb2(const double *b, const double *q, int d) {
-    double s = 0.0;
+// float32 squared distance from q to the box [b[0..2], b[3..5]]
+__device__ __forceinline__ float box_lb2f(const float *b, const float *q, int d) {
+    float s = 0.f;
     for (int k = 0; k < d; k++) {
-        double g = dmax_(0.0, dmax_(b[k] - q[k], q[k] - b[3 + k]));
-        s += g * g;
+        float g = fmaxf(0.f, fmaxf(b[k] - q[k], q[k] - b[3 + k]));
+        s = fmaf(g, g, s);
     }
     return s;
+}
+
+__device__ __forceinline__ void warp_argminf(float &v, int32_t &i) {
+    for (int o = 16; o > 0; o >>= 1) {
+        float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int32_t i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (v2 < v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+    }
 }
 
 // warp-wide lexicographic minimum of (value, label); every lane gets the result
@@ -194,7 +201,7 @@ __device__ __forceinline__ void warp_argmin(double &v, int32_t &i) {
 __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
                                                            const double *x0, const double *x1, const double *x2,
                                                            int32_t *const *outptr, int32_t *outcnt, int lb,
-                                                           double *cbox_base) {
+                                                           float *cbox_base, float *pf_base) {
     extern __shared__ unsigned char smem_raw[];
     int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
     __shared__ int32_t tid_s[DR_TILE];
@@ -246,63 +253,75 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
     const int64_t nsuper = (nchunks + DR_SUPER - 1) / DR_SUPER;
     if (nt >= DR_PRUNE_MIN && nsuper <= DR_MAX_SUPER && cbox_base != nullptr) {
         // Pruned exact search.  T is cut into chunks of 32 consecutive labels
-        // (Morton-coherent) and superchunks of 32 chunks, each with the exact
-        // float64 bounding box of its points.  For a grid point q the best
-        // (distance, label) pair starts from the chunk nearest to q and every
-        // chunk whose box lower bound exceeds the current best distance by more
-        // than 1e-12 relative is skipped: the bound and the point distances are
-        // both float64 evaluations within 10 ulps of their real values, so a
-        // skipped chunk cannot hold a point at or below the best distance.
-        double *cbox = cbox_base + (t0 / DR_CHUNK + a) * 6;
-        double *sbox = reinterpret_cast<double *>(smem_raw + (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t));
+        // (Morton-coherent) and superchunks of 32 chunks.  Every point is staged
+        // once as float32 coordinates relative to the box corner l, and each
+        // (super)chunk gets the float32 box of its staged points.  For a grid
+        // point q the best (distance, label) pair is seeded exactly from the
+        // chunk whose box is nearest to q; afterwards a (super)chunk is skipped
+        // when its float32 box bound exceeds the best distance by more than
+        // M = 8e-6 W^2, and inside a visited chunk only points whose float32
+        // distance is within M of the best are compared exactly in float64.
+        // Both tests are conservative: staged coordinates are within 1.2e-7 W
+        // of the true ones, so float32 squared distances and box bounds are
+        // within 2e-6 W^2 of the float64 values (W = largest box extent), and a
+        // point at or below the best float64 distance is never skipped.
+        float *cbox = cbox_base + (t0 / DR_CHUNK + a) * 6;
+        float *pf0 = pf_base + 3 * t0, *pf1 = pf0 + nt, *pf2 = pf1 + nt;
+        float *sbox = reinterpret_cast<float *>(smem_raw + (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t));
+        double W = 0.0;
+        for (int k = 0; k < d; k++) W = dmax_(W, __dmul_rn(h[k], (double)g));
+        const float M = (float)(8e-6 * W * W);
         for (int64_t c = warp; c < nchunks; c += nw) {
             int64_t p = c * DR_CHUNK + lane;
-            double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+            float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
             if (p < nt) {
                 int32_t sid = T[p];
-                mn[0] = mx[0] = x0[sid];
-                if (d > 1) mn[1] = mx[1] = x1[sid];
-                if (d > 2) mn[2] = mx[2] = x2[sid];
+                float f0 = (float)__dsub_rn(x0[sid], l[0]);
+                float f1 = d > 1 ? (float)__dsub_rn(x1[sid], l[1]) : 0.f;
+                float f2 = d > 2 ? (float)__dsub_rn(x2[sid], l[2]) : 0.f;
+                pf0[p] = f0; pf1[p] = f1; pf2[p] = f2;
+                mn[0] = mx[0] = f0; mn[1] = mx[1] = f1; mn[2] = mx[2] = f2;
             }
             for (int k = 0; k < 3; k++)
                 for (int o = 16; o > 0; o >>= 1) {
-                    mn[k] = dmin_(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
-                    mx[k] = dmax_(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+                    mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+                    mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
                 }
             if (lane < 3) { cbox[c * 6 + lane] = mn[lane]; cbox[c * 6 + 3 + lane] = mx[lane]; }
         }
         __syncthreads();
         for (int64_t sc = threadIdx.x; sc < nsuper; sc += blockDim.x) {
-            double b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+            float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
             for (int64_t c = sc * DR_SUPER; c < min(nchunks, (sc + 1) * DR_SUPER); c++)
                 for (int k = 0; k < 3; k++) {
-                    b[k] = dmin_(b[k], cbox[c * 6 + k]);
-                    b[3 + k] = dmax_(b[3 + k], cbox[c * 6 + 3 + k]);
+                    b[k] = fminf(b[k], cbox[c * 6 + k]);
+                    b[3 + k] = fmaxf(b[3 + k], cbox[c * 6 + 3 + k]);
                 }
             for (int k = 0; k < 6; k++) sbox[sc * 6 + k] = b[k];
         }
         __syncthreads();
-        const double slack = 1.0 + 1e-12;
         for (int gi = warp; gi < G; gi += nw) {
             double q[3];
+            float qf[3];
             int rem = gi;
             for (int k = 0; k < 3; k++) {
                 int idx = 0;
                 if (k < d) { idx = rem % g; rem /= g; }
                 q[k] = k < d ? __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])) : 0.0;
+                qf[k] = k < d ? (float)__dsub_rn(q[k], l[k]) : 0.f;
             }
-            // seed: the chunk with the smallest bound inside the nearest superchunk
-            double v = INFINITY;
+            // seed: the nearest chunk of the nearest superchunk, compared exactly
+            float v = INFINITY;
             int32_t si = INT_MAX;
             for (int64_t sc = lane; sc < nsuper; sc += 32) {
-                double lbv = box_lb2(sbox + sc * 6, q, d);
+                float lbv = box_lb2f(sbox + sc * 6, qf, d);
                 if (lbv < v || (lbv == v && sc < si)) { v = lbv; si = (int32_t)sc; }
             }
-            warp_argmin(v, si);
+            warp_argminf(v, si);
             int64_t c = (int64_t)si * DR_SUPER + lane;
-            v = c < nchunks ? box_lb2(cbox + c * 6, q, d) : INFINITY;
+            v = c < nchunks ? box_lb2f(cbox + c * 6, qf, d) : INFINITY;
             int32_t c0 = c < nchunks ? (int32_t)c : INT_MAX;
-            warp_argmin(v, c0);
+            warp_argminf(v, c0);
             double bd = INFINITY;
             int32_t bi = INT_MAX;
             {
@@ -313,28 +332,39 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                 }
                 warp_argmin(bd, bi);
             }
+            float lim = __double2float_ru(bd) + M;
             for (int64_t sb = 0; sb < nsuper; sb += 32) {
                 int64_t sc = sb + lane;
-                bool fl = sc < nsuper && box_lb2(sbox + sc * 6, q, d) <= bd * slack;
+                bool fl = sc < nsuper && box_lb2f(sbox + sc * 6, qf, d) <= lim;
                 unsigned smask = __ballot_sync(0xffffffffu, fl);
                 while (smask) {
                     int64_t s1 = sb + __ffs(smask) - 1;
                     smask &= smask - 1;
                     int64_t cc = s1 * DR_SUPER + lane;
-                    bool cf = cc < nchunks && cc != c0 && box_lb2(cbox + cc * 6, q, d) <= bd * slack;
+                    bool cf = cc < nchunks && cc != c0 && box_lb2f(cbox + cc * 6, qf, d) <= lim;
                     unsigned cmask = __ballot_sync(0xffffffffu, cf);
                     while (cmask) {
                         int64_t c1 = s1 * DR_SUPER + __ffs(cmask) - 1;
                         cmask &= cmask - 1;
                         int64_t p = c1 * DR_CHUNK + lane;
+                        bool cand = false;
+                        if (p < nt) {
+                            float e0 = pf0[p] - qf[0], e1 = pf1[p] - qf[1], e2 = pf2[p] - qf[2];
+                            cand = fmaf(e2, e2, fmaf(e1, e1, e0 * e0)) <= lim;
+                        }
+                        if (__ballot_sync(0xffffffffu, cand) == 0u) continue;
                         double dd = INFINITY;
                         int32_t id = INT_MAX;
-                        if (p < nt) {
+                        if (cand) {
                             id = T[p];
                             dd = h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0, d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]);
                         }
                         warp_argmin(dd, id);
-                        if (dd < bd || (dd == bd && id < bi)) { bd = dd; bi = id; }
+                        if (dd < bd || (dd == bd && id < bi)) {
+                            bd = dd;
+                            bi = id;
+                            lim = __double2float_ru(bd) + M;
+                        }
                     }
                 }
             }
@@ -430,17 +460,19 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
     int G = (int)gridsize(g, d);
     // win (next power of two >= G labels) followed by the superchunk boxes
     size_t sm = std::max((size_t)next_pow2(G) * sizeof(int32_t), (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t)) +
-                (size_t)DR_MAX_SUPER * 6 * sizeof(double);
+                (size_t)DR_MAX_SUPER * 6 * sizeof(float);
     static bool attr_set = false;
     if (!attr_set) {
         H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      DR_MAX_GRID * (int)sizeof(int32_t) + DR_MAX_SUPER * 6 * (int)sizeof(double)));
         attr_set = true;
     }
-    DevBuf<double> cbox;
+    DevBuf<float> cbox, pf;
     cbox.alloc((size_t)(ttot / DR_CHUNK + nl + 1) * 6, s);
+    pf.alloc((size_t)std::max<int64_t>(ttot, 1) * 3, s);
     ProfScope ps(KT_DATAREDUCT, s);
-    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, xs[0], xs[1], xs[2], outptr, outcnt, lb, cbox.p);
+    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, xs[0], xs[1], xs[2], outptr, outcnt, lb, cbox.p,
+                                            pf.p);
     H2_LAUNCH("k_datareduct");
 }
 

@@ -261,6 +261,18 @@ __device__ __forceinline__ double h2_kappa(int kid, double kp0, double r2) {
     }
 }
 
+// float64 kappa in its fast forms (rsqrt: within 1 ulp of 1/sqrt) for
+// products that are compared with a tolerance rather than bit for bit
+__device__ __forceinline__ double h2_kappa_fast(int kid, double kp0, double r2) {
+    switch (kid) {
+    case H2_K_COULOMB: return r2 > 0.0 ? rsqrt(r2) : 0.0;
+    case H2_K_GAUSSIAN: return exp(-r2 / (kp0 * kp0));
+    case H2_K_EXPONENTIAL: return exp(-sqrt(r2) / kp0);
+    case H2_K_MULTIQUADRIC: return sqrt(1.0 + r2);
+    default: return 0.0;
+    }
+}
+
 // float32 kappa for the mixed-precision path
 __device__ __forceinline__ float h2_kappa_f(int kid, float kp0, float r2) {
     switch (kid) {

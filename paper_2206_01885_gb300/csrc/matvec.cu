@@ -184,8 +184,9 @@ __global__ void k_exact_rows(const int64_t *rows, int64_t nrows, const int32_t *
     double a0 = x0[p], a1 = d > 1 ? x1[p] : 0.0, a2 = d > 2 ? x2[p] : 0.0;
     double s = 0.0;
     for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
-        double r2 = h2_dist2(d, a0, a1, a2, x0[q], d > 1 ? x1[q] : 0.0, d > 2 ? x2[q] : 0.0);
-        s += h2_kappa(kid, kp0, r2) * zm[q];
+        double dx = a0 - x0[q], dy = d > 1 ? a1 - x1[q] : 0.0, dz = d > 2 ? a2 - x2[q] : 0.0;
+        double r2 = dx * dx + dy * dy + dz * dz;
+        s += h2_kappa_fast(kid, kp0, r2) * zm[q];
     }
     s = warp_sum(s);
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

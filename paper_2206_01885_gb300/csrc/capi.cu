@@ -423,9 +423,9 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
             auto *h = static_cast<const h2_hidr_s *>(handle);
             snprintf(buf, sizeof buf,
                      "{\"g1\": %d, \"g2\": %d, \"x_total\": %lld, \"y_total\": %lld, \"t_max_level\": %lld, "
-                     "\"ms_up\": %.4f, \"ms_down\": %.4f}",
-                     h->g1, h->g2, (long long)h->xtotal, (long long)h->ytotal, (long long)h->tmax, h->ms_up,
-                     h->ms_down);
+                     "\"t_total\": %lld, \"ms_up\": %.4f, \"ms_down\": %.4f}",
+                     h->g1, h->g2, (long long)h->xtotal, (long long)h->ytotal, (long long)h->tmax,
+                     (long long)h->ttotal, h->ms_up, h->ms_down);
         } else if (tag == TAG_MATRIX) {
             auto *A = static_cast<const h2_matrix_s *>(handle);
             snprintf(buf, sizeof buf,

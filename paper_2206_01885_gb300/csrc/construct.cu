@@ -139,7 +139,8 @@ __device__ double block_sum(double x, double *red) {
 // step whose pivot norm is <= tol * |r_11|.  On exit A holds R (upper
 // triangle of the first k columns and rows 0..k-1 of the others), kout[i] = k
 // and piv[0..c) is the column order.  Real = double: everything float64.
-// Real = float: the block, the reflector and the trailing update are float32;
+// Real = float: the block, the reflector and the trailing update are float32,
+// and so are the per-lane partial sums of squares; the cross-lane sums, the
 // column norms, their downdating, the pivot choice and the stop test are
 // float64 (recomputation threshold sqrt(2^-24), the float32 analogue of
 // LAPACK's sqrt(eps)).
@@ -156,8 +157,10 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
     }
     double *nrm = reinterpret_cast<double *>(smem_raw);
     double *nrm0 = nrm + c;
-    Real *v = reinterpret_cast<Real *>(nrm0 + c);
+    double *rowj = nrm0 + c;
+    Real *v = reinterpret_cast<Real *>(rowj + c);
     int32_t *pv = reinterpret_cast<int32_t *>(v + m);
+    unsigned char *flag = reinterpret_cast<unsigned char *>(pv + c);
     __shared__ double red[QR_WARPS];
     __shared__ double bval[QR_WARPS];
     __shared__ int bidx[QR_WARPS];
@@ -168,11 +171,12 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
     const double tol3z = sqrt(ldexp(1.0, sizeof(Real) == 8 ? -53 : -24));
 
     for (int l = threadIdx.x; l < c; l += blockDim.x) pv[l] = l;
+    // per-lane partial sums in the block's type, reduced across lanes in float64
     for (int l = warp; l < c; l += QR_WARPS) {
         const Real *col = A + (int64_t)l * m;
-        double s = 0.0;
-        for (int r = lane; r < m; r += 32) s += (double)col[r] * (double)col[r];
-        s = warp_sum(s);
+        Real sp = 0;
+        for (int r = lane; r < m; r += 32) sp += col[r] * col[r];
+        double s = warp_sum((double)sp);
         if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
     }
     __syncthreads();
@@ -216,9 +220,9 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
         __syncthreads();
         // Householder reflector for A[j:m, j]
         Real *aj = A + (int64_t)j * m;
-        double part = 0.0;
-        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) part += (double)aj[r] * (double)aj[r];
-        double sigma = block_sum(part, red);
+        Real part = 0;
+        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) part += aj[r] * aj[r];
+        double sigma = block_sum((double)part, red);
         double alpha = (double)aj[j];
         if (alpha == 0.0 && sigma == 0.0) break;  // exactly zero pivot column
         double tau = 0.0, beta = alpha, sc = 0.0;
@@ -228,11 +232,13 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
             tau = (beta - alpha) / beta;
             sc = 1.0 / (alpha - beta);
         }
-        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) v[r] = (Real)((double)aj[r] * sc);
+        const Real scR = (Real)sc;
+        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) v[r] = aj[r] * scR;
         __syncthreads();
         if (threadIdx.x == 0) aj[j] = (Real)beta;
         const Real tauR = (Real)tau;
-        // apply to the trailing columns and downdate their norms (one warp per column)
+        // apply to the trailing columns (one warp per column); row j of the
+        // result goes to shared memory for the norm downdate
         for (int l = j + 1 + warp; l < c; l += QR_WARPS) {
             Real *al = A + (int64_t)l * m;
             Real ajl = al[j];
@@ -245,22 +251,32 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
                 ajl = ajl - w;
                 if (lane == 0) al[j] = ajl;
             }
+            if (lane == 0) rowj[l] = (double)ajl;
+        }
+        __syncthreads();
+        // downdate the norms, one thread per column; flag the ones that have
+        // lost about half their digits for recomputation
+        for (int l = j + 1 + threadIdx.x; l < c; l += blockDim.x) {
             double nl = nrm[l];
+            flag[l] = 0;
             if (nl != 0.0) {
-                double tt = fabs((double)ajl) / nl;
+                double tt = fabs(rowj[l]) / nl;
                 tt = 1.0 - tt * tt;
                 if (tt < 0.0) tt = 0.0;
                 double t2 = nl / nrm0[l];
                 t2 = tt * t2 * t2;
-                if (t2 <= tol3z) {
-                    double s = 0.0;
-                    for (int r = j + 1 + lane; r < m; r += 32) s += (double)al[r] * (double)al[r];
-                    s = warp_sum(s);
-                    if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
-                } else if (lane == 0) {
-                    nrm[l] = nl * sqrt(tt);
-                }
+                if (t2 <= tol3z) flag[l] = 1;
+                else nrm[l] = nl * sqrt(tt);
             }
+        }
+        __syncthreads();
+        for (int l = j + 1 + warp; l < c; l += QR_WARPS) {
+            if (!flag[l]) continue;
+            const Real *al = A + (int64_t)l * m;
+            Real sp = 0;
+            for (int r = j + 1 + lane; r < m; r += 32) sp += al[r] * al[r];
+            double s = warp_sum((double)sp);
+            if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
         }
         __syncthreads();
         k = j + 1;
@@ -386,7 +402,7 @@ __global__ void k_compact_skel(int nn, const int32_t *kk, const int64_t *off, in
 }
 
 size_t qr_smem(int cmax, int mmax, size_t esize = sizeof(double)) {
-    return (size_t)cmax * (2 * sizeof(double) + sizeof(int32_t)) + (size_t)mmax * esize + 64;
+    return (size_t)cmax * (3 * sizeof(double) + sizeof(int32_t) + 1) + (size_t)mmax * esize + 64;
 }
 
 }  // namespace

@@ -169,7 +169,7 @@ struct h2_hidr_s {
     h2::DevBuf<int32_t *> xptr, yptr;
     std::vector<h2::DevBuf<int32_t>> xbufs, ybufs;
     std::vector<int> xmax_level, ymax_level;  // host: largest set per level
-    int64_t xtotal = 0, ytotal = 0, tmax = 0;
+    int64_t xtotal = 0, ytotal = 0, tmax = 0, ttotal = 0;
     double ms_up = 0, ms_down = 0;
 };
 

@@ -515,6 +515,7 @@ void hidr_impl(h2_hidr_s *h) {
         scan_exclusive(cap.p, coff.p, nl, s);
         int64_t ttot = read_scalar(toff.p + nl, s), ctot = read_scalar(coff.p + nl, s);
         h->tmax = std::max(h->tmax, ttot);
+        h->ttotal += ttot;
         tdata.alloc(ttot > 0 ? ttot : 1, s);
         h->xbufs[l].alloc(ctot > 0 ? ctot : 1, s);
         k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, h->xbufs[l].p, coff.p, h->xptr.p);
@@ -538,6 +539,7 @@ void hidr_impl(h2_hidr_s *h) {
         scan_exclusive(cap.p, coff.p, nl, s);
         int64_t ttot = read_scalar(toff.p + nl, s), ctot = read_scalar(coff.p + nl, s);
         h->tmax = std::max(h->tmax, ttot);
+        h->ttotal += ttot;
         tdata.alloc(ttot > 0 ? ttot : 1, s);
         h->ybufs[l].alloc(ctot > 0 ? ctot : 1, s);
         k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, h->ybufs[l].p, coff.p, h->yptr.p);

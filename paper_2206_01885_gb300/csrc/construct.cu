@@ -142,9 +142,12 @@ __device__ double block_sum(double x, double *red) {
 // Real = float: the block, the reflector and the trailing update are float32,
 // and so are the per-lane partial sums of squares; the cross-lane sums, the
 // column norms, their downdating, the pivot choice and the stop test are
-// float64 (recomputation threshold sqrt(2^-24), the float32 analogue of
-// LAPACK's sqrt(eps)).
-template <class Real>
+// float64.  This form keeps squared norms and downdates them as nu^2 - r^2
+// (one float64 fma instead of two divisions and a square root: float64 runs
+// at 1/64 of the float32 rate on this GPU), recomputing once the downdated
+// value falls below sqrt(2^-24) of its last recomputed value, the float32
+// analogue of LAPACK's sqrt(eps).
+template <class Real, int RPL>
 __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt, const int32_t *cc,
                                                      const int64_t *aoff, Real *Abase, double tol, int32_t *kout,
                                                      const int64_t *coff, int32_t *pivbase) {
@@ -172,12 +175,15 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
 
     for (int l = threadIdx.x; l < c; l += blockDim.x) pv[l] = l;
     // per-lane partial sums in the block's type, reduced across lanes in float64
+    // float64 form: nrm holds column norms (LAPACK downdating); float32 form:
+    // nrm holds squared column norms, downdated as nu^2 - r^2 in float64
+    constexpr bool SQ = sizeof(Real) == 4;
     for (int l = warp; l < c; l += QR_WARPS) {
         const Real *col = A + (int64_t)l * m;
         Real sp = 0;
         for (int r = lane; r < m; r += 32) sp += col[r] * col[r];
         double s = warp_sum((double)sp);
-        if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
+        if (lane == 0) { nrm[l] = SQ ? s : sqrt(s); nrm0[l] = nrm[l]; }
     }
     __syncthreads();
     const int kmax = min(m, c);
@@ -201,7 +207,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
             for (int w = 1; w < QR_WARPS; w++) argmax_merge(vv, ii, bval[w], bidx[w]);
             if (j == 0) r11 = vv;
             s_p = ii;
-            s_stop = (!(vv > tol * r11) || vv == 0.0) ? 1 : 0;
+            // float32 form compares squared norms: nu^2 <= tol^2 r11^2
+            s_stop = (!(vv > (SQ ? tol * tol : tol) * r11) || vv == 0.0) ? 1 : 0;
         }
         __syncthreads();
         if (s_stop) break;
@@ -238,11 +245,37 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
         if (threadIdx.x == 0) aj[j] = (Real)beta;
         const Real tauR = (Real)tau;
         // apply to the trailing columns (one warp per column); row j of the
-        // result goes to shared memory for the norm downdate
+        // result goes to shared memory for the norm downdate.  With RPL > 0 a
+        // lane keeps its RPL rows of the column in registers: all loads are
+        // issued together and the update reuses them.
         for (int l = j + 1 + warp; l < c; l += QR_WARPS) {
             Real *al = A + (int64_t)l * m;
             Real ajl = al[j];
-            if (tau != 0.0) {
+            if constexpr (RPL > 0) {
+                Real a[RPL];
+#pragma unroll
+                for (int u = 0; u < RPL; u++) {
+                    int r = j + 1 + lane + 32 * u;
+                    a[u] = r < m ? al[r] : (Real)0;
+                }
+                if (tau != 0.0) {
+                    Real w = 0;
+#pragma unroll
+                    for (int u = 0; u < RPL; u++) {
+                        int r = j + 1 + lane + 32 * u;
+                        if (r < m) w += v[r] * a[u];
+                    }
+                    w = warp_sum(w) + ajl;
+                    w = w * tauR;
+#pragma unroll
+                    for (int u = 0; u < RPL; u++) {
+                        int r = j + 1 + lane + 32 * u;
+                        if (r < m) al[r] = a[u] - w * v[r];
+                    }
+                    ajl = ajl - w;
+                    if (lane == 0) al[j] = ajl;
+                }
+            } else if (tau != 0.0) {
                 Real w = 0;
                 for (int r = j + 1 + lane; r < m; r += 32) w += v[r] * al[r];
                 w = warp_sum(w) + ajl;
@@ -260,13 +293,19 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
             double nl = nrm[l];
             flag[l] = 0;
             if (nl != 0.0) {
-                double tt = fabs(rowj[l]) / nl;
-                tt = 1.0 - tt * tt;
-                if (tt < 0.0) tt = 0.0;
-                double t2 = nl / nrm0[l];
-                t2 = tt * t2 * t2;
-                if (t2 <= tol3z) flag[l] = 1;
-                else nrm[l] = nl * sqrt(tt);
+                if constexpr (SQ) {  // nu^2 - r^2, recomputed once below sqrt(2^-24) nu0^2
+                    double n2 = fma(-rowj[l], rowj[l], nl);
+                    if (!(n2 > tol3z * nrm0[l])) flag[l] = 1;
+                    else nrm[l] = n2;
+                } else {
+                    double tt = fabs(rowj[l]) / nl;
+                    tt = 1.0 - tt * tt;
+                    if (tt < 0.0) tt = 0.0;
+                    double t2 = nl / nrm0[l];
+                    t2 = tt * t2 * t2;
+                    if (t2 <= tol3z) flag[l] = 1;
+                    else nrm[l] = nl * sqrt(tt);
+                }
             }
         }
         __syncthreads();
@@ -274,9 +313,20 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
             if (!flag[l]) continue;
             const Real *al = A + (int64_t)l * m;
             Real sp = 0;
-            for (int r = j + 1 + lane; r < m; r += 32) sp += al[r] * al[r];
+            if constexpr (RPL > 0) {
+                Real a[RPL];
+#pragma unroll
+                for (int u = 0; u < RPL; u++) {
+                    int r = j + 1 + lane + 32 * u;
+                    a[u] = r < m ? al[r] : (Real)0;
+                }
+#pragma unroll
+                for (int u = 0; u < RPL; u++) sp += a[u] * a[u];
+            } else {
+                for (int r = j + 1 + lane; r < m; r += 32) sp += al[r] * al[r];
+            }
             double s = warp_sum((double)sp);
-            if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
+            if (lane == 0) { nrm[l] = SQ ? s : sqrt(s); nrm0[l] = nrm[l]; }
         }
         __syncthreads();
         k = j + 1;
@@ -401,6 +451,35 @@ __global__ void k_compact_skel(int nn, const int32_t *kk, const int64_t *off, in
     }
 }
 
+// launch the QR with the smallest register slice that holds the level's tallest
+// block (rows per lane = ceil(mmax / 32)), or the loop form above 1024 rows
+template <class Real>
+void launch_cpqr(int nl, size_t smem, int mmax, int lb, const int32_t *ycnt, const int32_t *cc, const int64_t *aoff,
+                 Real *A, double tol, int32_t *kout, const int64_t *coff, int32_t *piv, cudaStream_t s) {
+#define H2_QR(R) k_cpqr<Real, R><<<nl, QR_THREADS, smem, s>>>(lb, ycnt, cc, aoff, A, tol, kout, coff, piv)
+    int rpl = (mmax + 31) / 32;
+    // the float64 form is bound by the float64 pipe, not by load latency: the
+    // loop form keeps its register count (and occupancy) low
+    if (sizeof(Real) == 8) H2_QR(0);
+    else if (rpl <= 4) H2_QR(4);
+    else if (rpl <= 8) H2_QR(8);
+    else if (rpl <= 12) H2_QR(12);
+    else if (rpl <= 16) H2_QR(16);
+    else if (rpl <= 24) H2_QR(24);
+    else if (rpl <= 32) H2_QR(32);
+    else H2_QR(0);
+#undef H2_QR
+}
+
+template <class Real>
+void set_qr_attrs() {
+    for (const void *f : {(const void *)k_cpqr<Real, 4>, (const void *)k_cpqr<Real, 8>, (const void *)k_cpqr<Real, 12>,
+                          (const void *)k_cpqr<Real, 16>, (const void *)k_cpqr<Real, 24>,
+                          (const void *)k_cpqr<Real, 32>, (const void *)k_cpqr<Real, 0>})
+        // (all variants are instantiated; the float64 form launches the loop variant)
+        H2_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+}
+
 size_t qr_smem(int cmax, int mmax, size_t esize = sizeof(double)) {
     return (size_t)cmax * (3 * sizeof(double) + sizeof(int32_t) + 1) + (size_t)mmax * esize + 64;
 }
@@ -428,8 +507,8 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     A->cmax_level.assign(t->nlevels, 0);
     static bool attr = false;
     if (!attr) {
-        H2_CUDA(cudaFuncSetAttribute(k_cpqr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
-        H2_CUDA(cudaFuncSetAttribute(k_cpqr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        set_qr_attrs<double>();
+        set_qr_attrs<float>();
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_LIMIT));
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -491,13 +570,11 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         {
             ProfScope ps(KT_CPQR, s);
             if (f64)
-                k_cpqr<double><<<nl, QR_THREADS, qr_smem(cmax, mmax, esize), s>>>(
-                    lb, h->ycnt.p, A->c.p, aoff.p, reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p,
-                    piv.p);
+                launch_cpqr<double>(nl, qr_smem(cmax, mmax, esize), mmax, lb, h->ycnt.p, A->c.p, aoff.p,
+                                    reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p, piv.p, s);
             else
-                k_cpqr<float><<<nl, QR_THREADS, qr_smem(cmax, mmax, esize), s>>>(
-                    lb, h->ycnt.p, A->c.p, aoff.p, reinterpret_cast<float *>(Ablk.p), A->id_tol, A->k.p, coff.p,
-                    piv.p);
+                launch_cpqr<float>(nl, qr_smem(cmax, mmax, esize), mmax, lb, h->ycnt.p, A->c.p, aoff.p,
+                                   reinterpret_cast<float *>(Ablk.p), A->id_tol, A->k.p, coff.p, piv.p, s);
             H2_LAUNCH("k_cpqr");
         }
         szk.alloc(nl, s); szu.alloc(nl, s); koff.alloc(nl + 1, s); uoff.alloc(nl + 1, s);
@@ -639,14 +716,13 @@ double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *
     H2_CUDA(cudaMemcpyAsync(off.p, offs, sizeof offs, cudaMemcpyHostToDevice, s));
     static bool attr = false;
     if (!attr) {
-        H2_CUDA(cudaFuncSetAttribute(k_cpqr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        set_qr_attrs<double>();
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_LIMIT));
         attr = true;
     }
     if (qr_smem(c, m) > SMEM_LIMIT) fail(H2_ERR_UNIMPLEMENTED, "calibration block too large");
-    k_cpqr<double><<<1, QR_THREADS, qr_smem(c, m), s>>>(0, mc.p, mc.p + 1, off.p, A.p, id_tol, kk.p, off.p + 2,
-                                                        piv.p);
+    launch_cpqr<double>(1, qr_smem(c, m), m, 0, mc.p, mc.p + 1, off.p, A.p, id_tol, kk.p, off.p + 2, piv.p, s);
     H2_LAUNCH("k_cpqr (calibration)");
     int k = read_scalar(kk.p, s);
     U.alloc((size_t)std::max(1, k) * c, s);

@@ -168,6 +168,7 @@ constexpr int DR_CHUNK = 32;        // points per chunk
 constexpr int DR_SUPER = 32;        // chunks per superchunk
 constexpr int DR_MAX_SUPER = 1024;  // superchunk boxes kept in shared memory
 constexpr int DR_PRUNE_MIN = 2048;  // sets at least this large use the pruned search
+constexpr int DR_QTAB = 1024;       // grid points tabulated in shared memory
 
 // float32 squared distance from q to the box [b[0..2], b[3..5]]
 __device__ __forceinline__ float box_lb2f(const float *b, const float *q, int d) {
@@ -187,14 +188,6 @@ __device__ __forceinline__ void warp_argminf(float &v, int32_t &i) {
     }
 }
 
-// warp-wide lexicographic minimum of (value, label); every lane gets the result
-__device__ __forceinline__ void warp_argmin(double &v, int32_t &i) {
-    for (int o = 16; o > 0; o >>= 1) {
-        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        int32_t i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (v2 < v || (v2 == v && i2 < i)) { v = v2; i = i2; }
-    }
-}
 
 // One CTA per node.  tdata[toff[a] .. toff[a+1]) are the labels of S (T);
 // coordinates of label s are (x0[s], x1[s], x2[s]).
@@ -268,6 +261,8 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         float *cbox = cbox_base + (t0 / DR_CHUNK + a) * 6;
         float *pf0 = pf_base + 3 * t0, *pf1 = pf0 + nt, *pf2 = pf1 + nt;
         float *sbox = reinterpret_cast<float *>(smem_raw + (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t));
+        double *qtab = reinterpret_cast<double *>(sbox + DR_MAX_SUPER * 6);
+        float *qftab = reinterpret_cast<float *>(qtab + DR_QTAB * 3);
         double W = 0.0;
         for (int k = 0; k < d; k++) W = dmax_(W, __dmul_rn(h[k], (double)g));
         const float M = (float)(8e-6 * W * W);
@@ -300,17 +295,36 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             for (int k = 0; k < 6; k++) sbox[sc * 6 + k] = b[k];
         }
         __syncthreads();
+        // grid points, each computed once (float64 q and its float32 offset qf)
+        const bool table = G <= DR_QTAB;
+        if (table) {
+            for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
+                int rem = gi;
+                for (int k = 0; k < 3; k++) {
+                    int idx = 0;
+                    if (k < d) { idx = rem % g; rem /= g; }
+                    double qk = k < d ? __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])) : 0.0;
+                    qtab[gi * 3 + k] = qk;
+                    qftab[gi * 3 + k] = k < d ? (float)__dsub_rn(qk, l[k]) : 0.f;
+                }
+            }
+            __syncthreads();
+        }
         for (int gi = warp; gi < G; gi += nw) {
             double q[3];
             float qf[3];
-            int rem = gi;
-            for (int k = 0; k < 3; k++) {
-                int idx = 0;
-                if (k < d) { idx = rem % g; rem /= g; }
-                q[k] = k < d ? __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])) : 0.0;
-                qf[k] = k < d ? (float)__dsub_rn(q[k], l[k]) : 0.f;
+            if (table) {
+                for (int k = 0; k < 3; k++) { q[k] = qtab[gi * 3 + k]; qf[k] = qftab[gi * 3 + k]; }
+            } else {
+                int rem = gi;
+                for (int k = 0; k < 3; k++) {
+                    int idx = 0;
+                    if (k < d) { idx = rem % g; rem /= g; }
+                    q[k] = k < d ? __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])) : 0.0;
+                    qf[k] = k < d ? (float)__dsub_rn(q[k], l[k]) : 0.f;
+                }
             }
-            // seed: the nearest chunk of the nearest superchunk, compared exactly
+            // seed: the nearest chunk of the nearest superchunk
             float v = INFINITY;
             int32_t si = INT_MAX;
             for (int64_t sc = lane; sc < nsuper; sc += 32) {
@@ -324,15 +338,42 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             warp_argminf(v, c0);
             double bd = INFINITY;
             int32_t bi = INT_MAX;
-            {
-                int64_t p = (int64_t)c0 * DR_CHUNK + lane;
+            float lim = INFINITY;
+            // scan one chunk: float32 filter against lim (for the seed, against
+            // the chunk's own float32 minimum + M), then exact float64 distances
+            // for the surviving lanes, merged one lane at a time
+            auto scan_chunk = [&](int64_t cc, bool seed) {
+                int64_t p = cc * DR_CHUNK + lane;
+                float d32 = INFINITY;
                 if (p < nt) {
-                    bi = T[p];
-                    bd = h2_dist2(d, x0[bi], d > 1 ? x1[bi] : 0.0, d > 2 ? x2[bi] : 0.0, q[0], q[1], q[2]);
+                    float e0 = pf0[p] - qf[0], e1 = pf1[p] - qf[1], e2 = pf2[p] - qf[2];
+                    d32 = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
                 }
-                warp_argmin(bd, bi);
-            }
-            float lim = __double2float_ru(bd) + M;
+                float bound = lim;
+                if (seed) {
+                    float m32 = d32;
+                    for (int o = 16; o > 0; o >>= 1) m32 = fminf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
+                    bound = m32 + M;
+                }
+                unsigned cm = __ballot_sync(0xffffffffu, p < nt && d32 <= bound);
+                if (cm == 0u) return;
+                double dd = INFINITY;
+                int32_t id = INT_MAX;
+                if ((cm >> lane) & 1u) {
+                    id = T[p];
+                    dd = h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0, d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]);
+                }
+                bool improved = false;
+                while (cm) {
+                    int src = __ffs(cm) - 1;
+                    cm &= cm - 1;
+                    double dv = __shfl_sync(0xffffffffu, dd, src);
+                    int32_t iv = __shfl_sync(0xffffffffu, id, src);
+                    if (dv < bd || (dv == bd && iv < bi)) { bd = dv; bi = iv; improved = true; }
+                }
+                if (improved) lim = __double2float_ru(bd) + M;
+            };
+            scan_chunk(c0, true);
             for (int64_t sb = 0; sb < nsuper; sb += 32) {
                 int64_t sc = sb + lane;
                 bool fl = sc < nsuper && box_lb2f(sbox + sc * 6, qf, d) <= lim;
@@ -346,25 +387,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     while (cmask) {
                         int64_t c1 = s1 * DR_SUPER + __ffs(cmask) - 1;
                         cmask &= cmask - 1;
-                        int64_t p = c1 * DR_CHUNK + lane;
-                        bool cand = false;
-                        if (p < nt) {
-                            float e0 = pf0[p] - qf[0], e1 = pf1[p] - qf[1], e2 = pf2[p] - qf[2];
-                            cand = fmaf(e2, e2, fmaf(e1, e1, e0 * e0)) <= lim;
-                        }
-                        if (__ballot_sync(0xffffffffu, cand) == 0u) continue;
-                        double dd = INFINITY;
-                        int32_t id = INT_MAX;
-                        if (cand) {
-                            id = T[p];
-                            dd = h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0, d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]);
-                        }
-                        warp_argmin(dd, id);
-                        if (dd < bd || (dd == bd && id < bi)) {
-                            bd = dd;
-                            bi = id;
-                            lim = __double2float_ru(bd) + M;
-                        }
+                        scan_chunk(c1, false);
                     }
                 }
             }
@@ -460,11 +483,12 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
     int G = (int)gridsize(g, d);
     // win (next power of two >= G labels) followed by the superchunk boxes
     size_t sm = std::max((size_t)next_pow2(G) * sizeof(int32_t), (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t)) +
-                (size_t)DR_MAX_SUPER * 6 * sizeof(float);
+                (size_t)DR_MAX_SUPER * 6 * sizeof(float) + (size_t)DR_QTAB * 3 * (sizeof(double) + sizeof(float));
     static bool attr_set = false;
     if (!attr_set) {
         H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     DR_MAX_GRID * (int)sizeof(int32_t) + DR_MAX_SUPER * 6 * (int)sizeof(double)));
+                                     DR_MAX_GRID * (int)sizeof(int32_t) + DR_MAX_SUPER * 6 * (int)sizeof(float) +
+                                         DR_QTAB * 3 * (int)(sizeof(double) + sizeof(float))));
         attr_set = true;
     }
     DevBuf<float> cbox, pf;

@@ -28,6 +28,11 @@ __global__ void k_perm_in(const double *x, const int32_t *perm, int64_t n, doubl
     if (p < n) xm[p] = x[perm[p]];
 }
 
+__global__ void k_to_float(const double *a, int64_t n, float *b) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) b[p] = (float)a[p];
+}
+
 __global__ void k_perm_out(const double *ym, const int32_t *perm, int64_t n, double *y) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < n) y[perm[p]] = ym[p];
@@ -105,7 +110,7 @@ __device__ __forceinline__ float kap(float r2, float p) {
 template <class Real, int KID, int TPT>
 __global__ void __launch_bounds__(NB_WARPS * 32)
     k_nbody(const int2 *tiles, const int64_t *start, const int32_t *count, const Real *X0, const Real *X1,
-            const Real *X2, const double *C0, const double *C1, const double *C2, const double *w, double *out,
+            const Real *X2, const double *C0, const double *C1, const double *C2, const Real *w, double *out,
             const int64_t *lptr, const int32_t *lidx, int d, double kpar) {
     __shared__ double part[NB_WARPS][32 * TPT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -144,7 +149,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
         for (int u = 0; u < TPT; u++) blk[u] = (Real)0;
         for (int q = 0; q < sn; q++) {
             const Real a0 = X0[ss + q], a1 = d > 1 ? X1[ss + q] : (Real)0, a2 = d > 2 ? X2[ss + q] : (Real)0;
-            const Real ws = (Real)w[ss + q];
+            const Real ws = w[ss + q];
 #pragma unroll
             for (int u = 0; u < TPT; u++) {
                 Real dx = sh[u][0] - a0, dy = sh[u][1] - a1, dz = sh[u][2] - a2;
@@ -239,7 +244,7 @@ void build_tiles(const std::vector<int32_t> &cnt, const std::vector<int64_t> &lp
 
 template <class Real, int KID, int TPT>
 void nbody_launch(const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
-                  const Real *X1, const Real *X2, const double *C0, const double *C1, const double *C2, const double *w,
+                  const Real *X1, const Real *X2, const double *C0, const double *C1, const double *C2, const Real *w,
                   double *out, const int64_t *lptr, const int32_t *lidx, int d, double kpar, cudaStream_t s) {
     if (tiles.n == 0) return;
     k_nbody<Real, KID, TPT><<<(unsigned)tiles.n, NB_WARPS * 32, 0, s>>>(tiles.p, start, count, X0, X1, X2, C0, C1,
@@ -250,7 +255,7 @@ void nbody_launch(const DevBuf<int2> &tiles, const int64_t *start, const int32_t
 template <class Real, int TPT>
 void nbody_dispatch(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
                     const Real *X1, const Real *X2, const double *C0, const double *C1, const double *C2,
-                    const double *w, double *out, const int64_t *lptr, const int32_t *lidx, int d, double kp0,
+                    const Real *w, double *out, const int64_t *lptr, const int32_t *lidx, int d, double kp0,
                     cudaStream_t s) {
     switch (kid) {
     case H2_K_COULOMB:
@@ -341,6 +346,15 @@ void matvec_impl(h2_matrix_s *A, const double *x, double *y, cudaStream_t s) {
                                                        A->uptr.p, A->sk_off.p, xm.p, xh.p);
         H2_LAUNCH("k_upward");
     }
+    // float32 copies of the weights for the float32 N-body kernels
+    DevBuf<float> xmf, xhf;
+    if (!f64) {
+        xmf.alloc(n, s);
+        xhf.alloc(kt, s);
+        k_to_float<<<blocks_for(n, 256), 256, 0, s>>>(xm.p, n, xmf.p);
+        k_to_float<<<blocks_for(kt, 256), 256, 0, s>>>(xh.p, kt, xhf.p);
+        H2_LAUNCH("k_to_float");
+    }
     // coupling over far pairs: B_ij = K(Xhat_i, Xhat_j) on the fly
     {
         ProfScope ps(KT_COUPLING, s);
@@ -350,7 +364,7 @@ void matvec_impl(h2_matrix_s *A, const double *x, double *y, cudaStream_t s) {
                                             t->far_idx.p, d, A->kp[0], s);
         else
             nbody_dispatch<float, TPT_F32>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skr[0].p, A->skr[1].p,
-                                           A->skr[2].p, t->cen[0].p, t->cen[1].p, t->cen[2].p, xh.p, zh.p,
+                                           A->skr[2].p, t->cen[0].p, t->cen[1].p, t->cen[2].p, xhf.p, zh.p,
                                            t->far_ptr.p, t->far_idx.p, d, A->kp[0], s);
     }
     // downward, level 1 first
@@ -376,7 +390,7 @@ void matvec_impl(h2_matrix_s *A, const double *x, double *y, cudaStream_t s) {
                                             t->near_ptr.p, t->near_idx.p, d, A->kp[0], s);
         else
             nbody_dispatch<float, TPT_F32>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xr[0].p,
-                                           t->xr[1].p, t->xr[2].p, t->cen[0].p, t->cen[1].p, t->cen[2].p, xm.p, ym.p,
+                                           t->xr[1].p, t->xr[2].p, t->cen[0].p, t->cen[1].p, t->cen[2].p, xmf.p, ym.p,
                                            t->near_ptr.p, t->near_idx.p, d, A->kp[0], s);
     }
     k_perm_out<<<blocks_for(n, 256), 256, 0, s>>>(ym.p, t->perm.p, n, y);

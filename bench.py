@@ -212,14 +212,19 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
     qr_flops = mat_i["qr_flops"]
     block_evals = mat_i["block_evals"]
 
-    # roofline of the dominant kernel over the timed region
+    # roofline of the dominant kernel over the timed region.  ALU-bound kernels:
+    # algorithmic flops (QR flop count, 11 flops per kernel evaluation);
+    # DataReduct: the bytes it must read at least once (every entry of its input
+    # sets T_i: a 4-byte label and d float64 coordinates), against HBM.
     fp64 = wl["prec"] == "fp64"
     alu_peak = PEAK_FP64_TFLOPS if fp64 else PEAK_FP32_TFLOPS
-    work = {  # kernel -> algorithmic flops per step
-        "cpqr": qr_flops,
-        "coupling": coupling_pairs * FLOPS_PER_PAIR,
-        "near": near_pairs * FLOPS_PER_PAIR,
-        "keval": block_evals * FLOPS_PER_PAIR,
+    peaks, peak_kind = measured_peaks()
+    work = {  # kernel -> (bound, algorithmic units per step)
+        "cpqr": ("alu", qr_flops),
+        "coupling": ("alu", coupling_pairs * FLOPS_PER_PAIR),
+        "near": ("alu", near_pairs * FLOPS_PER_PAIR),
+        "keval": ("alu", block_evals * FLOPS_PER_PAIR),
+        "datareduct": ("hbm", hidr_i["t_total"] * (4 + 8 * d)),
     }
     per_kernel = {}
     for k, v in ktimes.items():
@@ -227,22 +232,33 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
             continue
         e = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
         if k in work and v["ms"] > 0:
-            e["tflops"] = work[k] * args.steps / (v["ms"] * 1e-3) / 1e12
-            e["frac_of_alu_peak"] = e["tflops"] / alu_peak
+            b, u = work[k]
+            rate = u * args.steps / (v["ms"] * 1e-3)
+            if b == "alu":
+                e["tflops"] = rate / 1e12
+                e["frac_of_alu_peak"] = e["tflops"] / alu_peak
+            else:
+                e["gbs"] = rate / 1e9
+                e["frac_of_hbm_peak"] = e["gbs"] / peaks["hbm_gbs"]
         per_kernel[k] = e
     dom = max(ktimes, key=lambda k: ktimes[k]["ms"])
     launches_per_step = ktimes[dom]["launches"] / args.steps
     dom_ms_per_launch = ktimes[dom]["ms"] / max(1, ktimes[dom]["launches"])
-    peak_src = "derived: GB300 nominal float64 1.25 TFLOP/s" if fp64 else \
-        "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-    if dom in work:
-        achieved = work[dom] / launches_per_step / (dom_ms_per_launch * 1e-3) / 1e12
+    if dom in work and work[dom][0] == "hbm":
+        achieved = work[dom][1] / launches_per_step / (dom_ms_per_launch * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{peak_kind} (copy bandwidth)",
+                "work_per_launch": work[dom][1] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
+    elif dom in work:
+        peak_src = "derived: GB300 nominal float64 1.25 TFLOP/s" if fp64 else \
+            "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+        achieved = work[dom][1] / launches_per_step / (dom_ms_per_launch * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": None, "peak_source": peak_src,
-                "work_per_launch": work[dom] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
+                "work_per_launch": work[dom][1] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "peak_source": peak_src, "ms_per_launch": dom_ms_per_launch}
+                "traffic": None, "ms_per_launch": dom_ms_per_launch}
     gpu_launches = int(sum(v["launches"] for v in ktimes.values()))
 
     e2e = None

@@ -121,6 +121,28 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+# ----------------------------------------------------------- multi-rank
+def problem_seed(base: int, rank: int) -> int:
+    """Seed of this rank's independent problem (one problem per GPU)."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time (the only cross-rank exchange of the bench)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(n_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: points built by all ranks per second."""
+    return world * n_per_rank / (ms_per_step * 1e-3)
+
+
 # ----------------------------------------------------------- GPU arm
 def measure_form(args, wl, rank, world, dev, with_e2e):
     """W warm-up and K timed steps of one form (precision + tolerance) on this
@@ -130,7 +152,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
     from paper_2206_01885_gb300 import h2
 
     n, d = wl["n"], wl["d"]
-    seed = wl["seed"] + 1000 * rank  # independent problem per rank
+    seed = problem_seed(wl["seed"], rank)  # independent problem per rank
     pts = I.uniform_cube(n, d, seed=seed)
     z = I.standard_normal(n, seed=seed + 7)
     rows = I.sample_rows(n, wl["rows"], seed=seed + 9)
@@ -192,11 +214,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
     clocks = sampler.stop()
     ktimes = h2.kernel_times()
     h2.profile(False, False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     A, hd, t = last
 
     # algorithmic work of the last step (identical every step)
@@ -296,7 +314,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
     phases["matvec_ms"] = sum(per_kernel.get(k, {}).get("ms_per_step", 0.0)
                               for k in ("upward", "coupling", "downward", "near"))
     return {
-        "value": world * n / (ms_per_step * 1e-3),
+        "value": aggregate_value(n, world, ms_per_step),
         "ms_per_step": ms_per_step,
         "config": {"workload": args.workload if wl is WORKLOADS[args.workload] else wl["name"], "n": n, "dim": d,
                    "kernel": wl["kernel"], "leaf_size": wl["q"], "id_tol": wl["eps"], "precision": wl["prec"],

@@ -161,32 +161,44 @@ __device__ int block_unique_write(const int32_t *v, int P, int32_t *out, int *sc
     return total;
 }
 
+// in-place inclusive scan of v[0..n) in shared memory by the whole block
+__device__ void block_scan_inclusive(int *v, int n, int *scratch) {
+    int chunk = (n + blockDim.x - 1) / blockDim.x;
+    int s0 = threadIdx.x * chunk, s1 = min(n, s0 + chunk);
+    int sum = 0;
+    for (int i = s0; i < s1; i++) sum += v[i];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int inc = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? scratch[lane] : 0, wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < nw) scratch[lane] = wi - w;
+    }
+    __syncthreads();
+    int run = scratch[warp] + inc - sum;
+    for (int i = s0; i < s1; i++) {
+        run += v[i];
+        v[i] = run;
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax_(double a, double b) { return a > b ? a : b; }
 
-constexpr int DR_CHUNK = 32;        // points per chunk
-constexpr int DR_SUPER = 32;        // chunks per superchunk
-constexpr int DR_MAX_SUPER = 1024;  // superchunk boxes kept in shared memory
-constexpr int DR_PRUNE_MIN = 2048;  // sets at least this large use the pruned search
-constexpr int DR_QTAB = 1024;       // grid points tabulated in shared memory
+constexpr int DR_PRUNE_MIN = 2048;  // sets at least this large use the binned search
+constexpr int DR_BIN_MAX = 4096;    // largest grid binned in shared memory
 
-// float32 squared distance from q to the box [b[0..2], b[3..5]]
-__device__ __forceinline__ float box_lb2f(const float *b, const float *q, int d) {
-    float s = 0.f;
-    for (int k = 0; k < d; k++) {
-        float g = fmaxf(0.f, fmaxf(b[k] - q[k], q[k] - b[3 + k]));
-        s = fmaf(g, g, s);
-    }
-    return s;
-}
 
-__device__ __forceinline__ void warp_argminf(float &v, int32_t &i) {
-    for (int o = 16; o > 0; o >>= 1) {
-        float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        int32_t i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (v2 < v || (v2 == v && i2 < i)) { v = v2; i = i2; }
-    }
-}
 
 
 // One CTA per node.  tdata[toff[a] .. toff[a+1]) are the labels of S (T);
@@ -194,7 +206,7 @@ __device__ __forceinline__ void warp_argminf(float &v, int32_t &i) {
 __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
                                                            const double *x0, const double *x1, const double *x2,
                                                            int32_t *const *outptr, int32_t *outcnt, int lb,
-                                                           float *cbox_base, float *pf_base) {
+                                                           int32_t *bin_base, float *pf_base) {
     extern __shared__ unsigned char smem_raw[];
     int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
     __shared__ int32_t tid_s[DR_TILE];
@@ -242,154 +254,176 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         l[k] = mn;
         h[k] = __ddiv_rn(__dsub_rn(mx, mn), (double)g);
     }
-    const int64_t nchunks = (nt + DR_CHUNK - 1) / DR_CHUNK;
-    const int64_t nsuper = (nchunks + DR_SUPER - 1) / DR_SUPER;
-    if (nt >= DR_PRUNE_MIN && nsuper <= DR_MAX_SUPER && cbox_base != nullptr) {
-        // Pruned exact search.  T is cut into chunks of 32 consecutive labels
-        // (Morton-coherent) and superchunks of 32 chunks.  Every point is staged
-        // once as float32 coordinates relative to the box corner l, and each
-        // (super)chunk gets the float32 box of its staged points.  For a grid
-        // point q the best (distance, label) pair is seeded exactly from the
-        // chunk whose box is nearest to q; afterwards a (super)chunk is skipped
-        // when its float32 box bound exceeds the best distance by more than
-        // M = 8e-6 W^2, and inside a visited chunk only points whose float32
-        // distance is within M of the best are compared exactly in float64.
-        // Both tests are conservative: staged coordinates are within 1.2e-7 W
-        // of the true ones, so float32 squared distances and box bounds are
-        // within 2e-6 W^2 of the float64 values (W = largest box extent), and a
-        // point at or below the best float64 distance is never skipped.
-        float *cbox = cbox_base + (t0 / DR_CHUNK + a) * 6;
+    if (nt >= DR_PRUNE_MIN && G <= DR_BIN_MAX && bin_base != nullptr) {
+        // Binned exact search.  The points of S are binned into the g^d cells of
+        // the reference grid itself (grid point q is the centre of its cell) by a
+        // counting sort in shared memory, with their float32 coordinates
+        // relative to the box corner stored in bin order.  For each grid point a
+        // warp scans its own cell, then Chebyshev rings of cells, and stops after
+        // ring r once the best float64 distance is below ((r + 1/2) h_min - delta)^2,
+        // a lower bound for every point in a farther cell (delta = 1e-5 W covers
+        // float32 binning error).  Inside a ring, a cell whose box bound exceeds
+        // the best distance by M = 8e-6 W^2, or a point whose float32 distance
+        // does, is skipped; the rest are compared exactly in float64 with the
+        // smaller-label tie-break, so the winner equals the float64 brute force.
+        int32_t *bidx = bin_base + 2 * t0;  // bin of each entry, then labels in bin order
+        int32_t *slab = bidx + nt;
         float *pf0 = pf_base + 3 * t0, *pf1 = pf0 + nt, *pf2 = pf1 + nt;
-        float *sbox = reinterpret_cast<float *>(smem_raw + (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t));
-        double *qtab = reinterpret_cast<double *>(sbox + DR_MAX_SUPER * 6);
-        float *qftab = reinterpret_cast<float *>(qtab + DR_QTAB * 3);
-        double W = 0.0;
-        for (int k = 0; k < d; k++) W = dmax_(W, __dmul_rn(h[k], (double)g));
+        int *bstart = reinterpret_cast<int *>(smem_raw + (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t));
+        int *bcur = bstart + G + 1;
+        double W = 0.0, hmin = INFINITY;
+        float ihf[3] = {0.f, 0.f, 0.f}, hf[3] = {0.f, 0.f, 0.f};
+        bool flat[3] = {true, true, true};
+        
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if (k >= d) break;
+            W = dmax_(W, __dmul_rn(h[k], (double)g));
+            flat[k] = !(h[k] > 0.0);
+            if (!flat[k]) { hmin = dmin_(hmin, h[k]); ihf[k] = (float)(1.0 / h[k]); hf[k] = (float)h[k]; }
+        }
         const float M = (float)(8e-6 * W * W);
-        for (int64_t c = warp; c < nchunks; c += nw) {
-            int64_t p = c * DR_CHUNK + lane;
-            float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        const float delf = (float)(1e-5 * W);
+        const double delta = 1e-5 * W;
+        for (int b = threadIdx.x; b <= G; b += blockDim.x) bstart[b] = 0;
+        __syncthreads();
+        // counting sort into cells.  Consecutive labels are Morton-coherent and
+        // mostly share a cell, so the atomics are warp-aggregated: lanes with the
+        // same cell elect one leader that adds the group's count, and each lane
+        // takes base + its rank in the group.
+        const unsigned lt = (1u << lane) - 1u;
+        for (int64_t p0 = (int64_t)warp * 32; p0 < nt; p0 += blockDim.x) {
+            const int64_t p = p0 + lane;
+            int bi = -1;
             if (p < nt) {
                 int32_t sid = T[p];
-                float f0 = (float)__dsub_rn(x0[sid], l[0]);
-                float f1 = d > 1 ? (float)__dsub_rn(x1[sid], l[1]) : 0.f;
-                float f2 = d > 2 ? (float)__dsub_rn(x2[sid], l[2]) : 0.f;
-                pf0[p] = f0; pf1[p] = f1; pf2[p] = f2;
-                mn[0] = mx[0] = f0; mn[1] = mx[1] = f1; mn[2] = mx[2] = f2;
-            }
-            for (int k = 0; k < 3; k++)
-                for (int o = 16; o > 0; o >>= 1) {
-                    mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
-                    mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+                int stride = 1;
+                bi = 0;
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    if (k >= d) break;
+                    const double *xk = k == 0 ? x0 : (k == 1 ? x1 : x2);
+                    int cidx = 0;
+                    if (!flat[k]) {
+                        float f = (float)__dsub_rn(xk[sid], l[k]);
+                        cidx = min(max((int)(f * ihf[k]), 0), g - 1);
+                    }
+                    bi += cidx * stride;
+                    stride *= g;
                 }
-            if (lane < 3) { cbox[c * 6 + lane] = mn[lane]; cbox[c * 6 + 3 + lane] = mx[lane]; }
+                bidx[p] = bi;
+            }
+            unsigned peers = __match_any_sync(0xffffffffu, bi);
+            if (bi >= 0 && (peers & lt) == 0u) atomicAdd(&bstart[bi + 1], __popc(peers));
         }
         __syncthreads();
-        for (int64_t sc = threadIdx.x; sc < nsuper; sc += blockDim.x) {
-            float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-            for (int64_t c = sc * DR_SUPER; c < min(nchunks, (sc + 1) * DR_SUPER); c++)
-                for (int k = 0; k < 3; k++) {
-                    b[k] = fminf(b[k], cbox[c * 6 + k]);
-                    b[3 + k] = fmaxf(b[3 + k], cbox[c * 6 + 3 + k]);
-                }
-            for (int k = 0; k < 6; k++) sbox[sc * 6 + k] = b[k];
+        block_scan_inclusive(bstart, G + 1, scratch);
+        for (int b = threadIdx.x; b < G; b += blockDim.x) bcur[b] = bstart[b];
+        __syncthreads();
+        for (int64_t p0 = (int64_t)warp * 32; p0 < nt; p0 += blockDim.x) {
+            const int64_t p = p0 + lane;
+            const int bi = p < nt ? bidx[p] : -1;
+            unsigned peers = __match_any_sync(0xffffffffu, bi);
+            int leader = __ffs(peers) - 1;
+            int base = 0;
+            if (bi >= 0 && lane == leader) base = atomicAdd(&bcur[bi], __popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (bi >= 0) {
+                int pos = base + __popc(peers & lt);
+                int32_t sid = T[p];
+                slab[pos] = sid;
+                pf0[pos] = (float)__dsub_rn(x0[sid], l[0]);
+                pf1[pos] = d > 1 ? (float)__dsub_rn(x1[sid], l[1]) : 0.f;
+                pf2[pos] = d > 2 ? (float)__dsub_rn(x2[sid], l[2]) : 0.f;
+            }
         }
         __syncthreads();
-        // grid points, each computed once (float64 q and its float32 offset qf)
-        const bool table = G <= DR_QTAB;
-        if (table) {
-            for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
-                int rem = gi;
-                for (int k = 0; k < 3; k++) {
-                    int idx = 0;
-                    if (k < d) { idx = rem % g; rem /= g; }
-                    double qk = k < d ? __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])) : 0.0;
-                    qtab[gi * 3 + k] = qk;
-                    qftab[gi * 3 + k] = k < d ? (float)__dsub_rn(qk, l[k]) : 0.f;
-                }
-            }
-            __syncthreads();
-        }
         for (int gi = warp; gi < G; gi += nw) {
-            double q[3];
-            float qf[3];
-            if (table) {
-                for (int k = 0; k < 3; k++) { q[k] = qtab[gi * 3 + k]; qf[k] = qftab[gi * 3 + k]; }
-            } else {
+            double q[3] = {0.0, 0.0, 0.0};
+            float qf[3] = {0.f, 0.f, 0.f};
+            int cid[3] = {0, 0, 0};
+            int rmax = 0;
+            {
                 int rem = gi;
-                for (int k = 0; k < 3; k++) {
-                    int idx = 0;
-                    if (k < d) { idx = rem % g; rem /= g; }
-                    q[k] = k < d ? __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])) : 0.0;
-                    qf[k] = k < d ? (float)__dsub_rn(q[k], l[k]) : 0.f;
+                
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if (k >= d) break;
+                    int idx = rem % g;
+                    rem /= g;
+                    q[k] = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
+                    qf[k] = (float)__dsub_rn(q[k], l[k]);
+                    cid[k] = flat[k] ? 0 : idx;
+                    if (!flat[k]) rmax = max(rmax, max(cid[k], g - 1 - cid[k]));
                 }
             }
-            // seed: the nearest chunk of the nearest superchunk
-            float v = INFINITY;
-            int32_t si = INT_MAX;
-            for (int64_t sc = lane; sc < nsuper; sc += 32) {
-                float lbv = box_lb2f(sbox + sc * 6, qf, d);
-                if (lbv < v || (lbv == v && sc < si)) { v = lbv; si = (int32_t)sc; }
-            }
-            warp_argminf(v, si);
-            int64_t c = (int64_t)si * DR_SUPER + lane;
-            v = c < nchunks ? box_lb2f(cbox + c * 6, qf, d) : INFINITY;
-            int32_t c0 = c < nchunks ? (int32_t)c : INT_MAX;
-            warp_argminf(v, c0);
             double bd = INFINITY;
             int32_t bi = INT_MAX;
             float lim = INFINITY;
-            // scan one chunk: float32 filter against lim (for the seed, against
-            // the chunk's own float32 minimum + M), then exact float64 distances
-            // for the surviving lanes, merged one lane at a time
-            auto scan_chunk = [&](int64_t cc, bool seed) {
-                int64_t p = cc * DR_CHUNK + lane;
-                float d32 = INFINITY;
-                if (p < nt) {
-                    float e0 = pf0[p] - qf[0], e1 = pf1[p] - qf[1], e2 = pf2[p] - qf[2];
-                    d32 = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
-                }
-                float bound = lim;
-                if (seed) {
-                    float m32 = d32;
-                    for (int o = 16; o > 0; o >>= 1) m32 = fminf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
-                    bound = m32 + M;
-                }
-                unsigned cm = __ballot_sync(0xffffffffu, p < nt && d32 <= bound);
-                if (cm == 0u) return;
-                double dd = INFINITY;
-                int32_t id = INT_MAX;
-                if ((cm >> lane) & 1u) {
-                    id = T[p];
-                    dd = h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0, d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]);
-                }
-                bool improved = false;
-                while (cm) {
-                    int src = __ffs(cm) - 1;
-                    cm &= cm - 1;
-                    double dv = __shfl_sync(0xffffffffu, dd, src);
-                    int32_t iv = __shfl_sync(0xffffffffu, id, src);
-                    if (dv < bd || (dv == bd && iv < bi)) { bd = dv; bi = iv; improved = true; }
-                }
-                if (improved) lim = __double2float_ru(bd) + M;
-            };
-            scan_chunk(c0, true);
-            for (int64_t sb = 0; sb < nsuper; sb += 32) {
-                int64_t sc = sb + lane;
-                bool fl = sc < nsuper && box_lb2f(sbox + sc * 6, qf, d) <= lim;
-                unsigned smask = __ballot_sync(0xffffffffu, fl);
-                while (smask) {
-                    int64_t s1 = sb + __ffs(smask) - 1;
-                    smask &= smask - 1;
-                    int64_t cc = s1 * DR_SUPER + lane;
-                    bool cf = cc < nchunks && cc != c0 && box_lb2f(cbox + cc * 6, qf, d) <= lim;
-                    unsigned cmask = __ballot_sync(0xffffffffu, cf);
-                    while (cmask) {
-                        int64_t c1 = s1 * DR_SUPER + __ffs(cmask) - 1;
-                        cmask &= cmask - 1;
-                        scan_chunk(c1, false);
+            for (int r = 0; r <= rmax; r++) {
+                const int side = 2 * r + 1;
+                int total = 1;
+                for (int k = 0; k < d; k++) total *= flat[k] ? 1 : side;
+                for (int e0 = 0; e0 < total; e0 += 32) {
+                    int e = e0 + lane;
+                    bool ok = e < total;
+                    int bin = 0, stride = 1, cheb = 0;
+                    float lb = 0.f;
+                    if (ok) {
+                        int rem = e;
+                        
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if (k >= d) break;
+                            int o = 0;
+                            if (!flat[k]) { o = rem % side - r; rem /= side; }
+                            int ck = cid[k] + o;
+                            ok = ok && ck >= 0 && ck < g;
+                            cheb = max(cheb, abs(o));
+                            bin += ck * stride;
+                            stride *= g;
+                            if (!flat[k]) {
+                                float lo = (float)ck * hf[k] - delf, hi = (float)(ck + 1) * hf[k] + delf;
+                                float gap = fmaxf(0.f, fmaxf(lo - qf[k], qf[k] - hi));
+                                lb = fmaf(gap, gap, lb);
+                            }
+                        }
+                        ok = ok && cheb == r && bstart[bin + 1] > bstart[bin] && lb <= lim;
+                    }
+                    unsigned cm = __ballot_sync(0xffffffffu, ok);
+                    while (cm) {
+                        int src = __ffs(cm) - 1;
+                        cm &= cm - 1;
+                        int b = __shfl_sync(0xffffffffu, bin, src);
+                        for (int p0 = bstart[b]; p0 < bstart[b + 1]; p0 += 32) {
+                            int p = p0 + lane;
+                            float d32 = INFINITY;
+                            if (p < bstart[b + 1]) {
+                                float e0f = pf0[p] - qf[0], e1f = pf1[p] - qf[1], e2f = pf2[p] - qf[2];
+                                d32 = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f));
+                            }
+                            unsigned pm = __ballot_sync(0xffffffffu, p < bstart[b + 1] && d32 <= lim);
+                            if (pm == 0u) continue;
+                            double dd = INFINITY;
+                            int32_t id = INT_MAX;
+                            if ((pm >> lane) & 1u) {
+                                id = slab[p];
+                                dd = h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0, d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]);
+                            }
+                            bool improved = false;
+                            while (pm) {
+                                int s2 = __ffs(pm) - 1;
+                                pm &= pm - 1;
+                                double dv = __shfl_sync(0xffffffffu, dd, s2);
+                                int32_t iv = __shfl_sync(0xffffffffu, id, s2);
+                                if (dv < bd || (dv == bd && iv < bi)) { bd = dv; bi = iv; improved = true; }
+                            }
+                            if (improved) lim = __double2float_ru(bd) + M;
+                        }
                     }
                 }
+                const double reach = (r + 0.5) * hmin - delta;
+                if (reach > 0.0 && bd * (1.0 + 1e-12) < reach * reach) break;
             }
             if (lane == 0) win[gi] = bi;
         }
@@ -481,21 +515,22 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
                        const double *const xs[3], int32_t *const *outptr, int32_t *outcnt, int lb, cudaStream_t s) {
     if (nl <= 0) return;
     int G = (int)gridsize(g, d);
-    // win (next power of two >= G labels) followed by the superchunk boxes
+    // win (labels of the grid points, padded to a power of two) followed by the
+    // bin starts and cursors of the binned search
     size_t sm = std::max((size_t)next_pow2(G) * sizeof(int32_t), (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t)) +
-                (size_t)DR_MAX_SUPER * 6 * sizeof(float) + (size_t)DR_QTAB * 3 * (sizeof(double) + sizeof(float));
+                (size_t)(2 * DR_BIN_MAX + 1) * sizeof(int);
     static bool attr_set = false;
     if (!attr_set) {
         H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     DR_MAX_GRID * (int)sizeof(int32_t) + DR_MAX_SUPER * 6 * (int)sizeof(float) +
-                                         DR_QTAB * 3 * (int)(sizeof(double) + sizeof(float))));
+                                     2 * DR_MAX_GRID * (int)sizeof(int32_t) + (2 * DR_BIN_MAX + 1) * (int)sizeof(int)));
         attr_set = true;
     }
-    DevBuf<float> cbox, pf;
-    cbox.alloc((size_t)(ttot / DR_CHUNK + nl + 1) * 6, s);
+    DevBuf<int32_t> bins;
+    DevBuf<float> pf;
+    bins.alloc((size_t)std::max<int64_t>(ttot, 1) * 2, s);
     pf.alloc((size_t)std::max<int64_t>(ttot, 1) * 3, s);
     ProfScope ps(KT_DATAREDUCT, s);
-    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, xs[0], xs[1], xs[2], outptr, outcnt, lb, cbox.p,
+    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, xs[0], xs[1], xs[2], outptr, outcnt, lb, bins.p,
                                             pf.p);
     H2_LAUNCH("k_datareduct");
 }

@@ -453,17 +453,31 @@ h2_status h2_calibrate(int dim, int kernel, const double *kparams, double eps, c
         pool_keep_memory();
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         DevBuf<double> a[3], b[3];
+        DevBuf<float> bg[3];
         std::vector<double> col(std::max(n1, n2));
+        std::vector<float> colf(n2);
+        DRPoints zb;
+        zb.R = 0.0;
         for (int k = 0; k < 3; k++) {
             a[k].alloc(k < dim ? n1 : 1, s);
             b[k].alloc(k < dim ? n2 : 1, s);
+            bg[k].alloc(k < dim ? n2 : 1, s);
+            zb.x[k] = b[k].p;
+            zb.xg[k] = bg[k].p;
+            zb.ref[k] = 0.0;
             if (k >= dim) continue;
             for (int i = 0; i < n1; i++) col[i] = z1[(int64_t)i * dim + k];
             H2_CUDA(cudaMemcpyAsync(a[k].p, col.data(), n1 * sizeof(double), cudaMemcpyHostToDevice, s));
-            for (int i = 0; i < n2; i++) col[i] = z2[(int64_t)i * dim + k];
+            for (int i = 0; i < n2; i++) {
+                col[i] = z2[(int64_t)i * dim + k];
+                colf[i] = (float)col[i];  // relative to ref = 0
+                zb.R = std::max(zb.R, std::fabs(col[i]));
+            }
             H2_CUDA(cudaMemcpyAsync(b[k].p, col.data(), n2 * sizeof(double), cudaMemcpyHostToDevice, s));
+            H2_CUDA(cudaMemcpyAsync(bg[k].p, colf.data(), n2 * sizeof(float), cudaMemcpyHostToDevice, s));
+            H2_CUDA(cudaStreamSynchronize(s));
         }
-        const double *za[3] = {a[0].p, a[1].p, a[2].p}, *zb[3] = {b[0].p, b[1].p, b[2].p};
+        const double *za[3] = {a[0].p, a[1].p, a[2].p};
         *g_out = gmax + 1;
         double err = INFINITY;
         for (int g = 1; g <= gmax; g++) {

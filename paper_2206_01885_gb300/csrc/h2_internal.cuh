@@ -152,6 +152,7 @@ struct h2_tree_s {
     double ms_tree = 0, ms_lists = 0;
     h2::DevBuf<double> cen[3];    // cell centre of every node
     h2::DevBuf<float> xr[3];      // point coordinates relative to their leaf's centre (float32 kernels)
+    h2::DevBuf<float> xg[3];      // point coordinates relative to the root box corner (float32 filters)
     h2::DevBuf<int2> near_tiles;  // (leaf, first target) tiles of the nearfield kernel, built on first use
     int near_tile_tpt = 0;
     h2::DevBuf<int64_t> leaf_start;  // begin of every node as int64 (nearfield point sets)
@@ -218,14 +219,22 @@ void exact_rows_noalloc_impl(h2_tree_s *t, int kid, const double *kp, const doub
 void sampled_error_impl(const double *exact, const double *approx, const int64_t *rows, int64_t nrows, int64_t n,
                         double *err_out, cudaStream_t s);
 
+// Coordinates DataReduct reads: float64 x (exact distances) and float32
+// xg = x - ref with |x - ref| <= R per coordinate (its float32 filters).
+struct DRPoints {
+    const double *x[3];
+    const float *xg[3];
+    double ref[3];
+    double R;
+};
 // one DataReduct over an explicit point set (used by the calibration); ids
-// are labels 0..n-1 of the points in xs (SoA, n each).  Output sorted labels.
-int64_t datareduct_one(const double *const xs[3], int d, int64_t n, int g, int32_t *out_dev, cudaStream_t s);
+// are labels 0..n-1 of the points.  Output sorted labels.
+int64_t datareduct_one(const DRPoints &pts, int d, int64_t n, int g, int32_t *out_dev, cudaStream_t s);
 // Section 4.2 test problem at grid size g: relative Frobenius error of
 // K(Z1, Z2) ~= U K(Zhat1, Z2) where U comes from the ID (tolerance id_tol) of
 // K(DataReduct(Z2, g), Z1).  z1s, z2s: device SoA coordinates.
 double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *const z1s[3], int n1,
-                       const double *const z2s[3], int n2, int g, int *k_out, int *m_out, cudaStream_t s);
+                       const DRPoints &z2, int n2, int g, int *k_out, int *m_out, cudaStream_t s);
 
 }  // namespace h2
 

@@ -192,11 +192,39 @@ __device__ void block_scan_inclusive(int *v, int n, int *scratch) {
     __syncthreads();
 }
 
+// order-preserving map of a float64 to a signed 64-bit integer and back
+__device__ __forceinline__ long long dkey(double x) {
+    long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dkey_inv(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
 __device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax_(double a, double b) { return a > b ? a : b; }
 
 constexpr int DR_PRUNE_MIN = 2048;  // sets at least this large use the binned search
 constexpr int DR_BIN_MAX = 4096;    // largest grid binned in shared memory
+constexpr int DR_QTAB = 1024;       // largest grid tabulated in shared memory
+
+// dynamic shared memory of k_datareduct: win (grid-point winners, padded to a
+// power of two), then the bin starts and cursors (2G + 1 ints), then, 8-byte
+// aligned, the grid-point table (3G doubles and 3G floats) when G <= DR_QTAB
+__host__ __device__ __forceinline__ size_t dr_win_bytes(int G) {
+    size_t p2 = 1;
+    while (p2 < (size_t)G) p2 <<= 1;
+    size_t a = p2 * 4, b = (size_t)((G + 31) & ~31) * 8;
+    return a > b ? a : b;
+}
+__host__ __device__ __forceinline__ size_t dr_bins_offset(int G) { return dr_win_bytes(G); }
+__host__ __device__ __forceinline__ size_t dr_qtab_offset(int G) {
+    return (dr_bins_offset(G) + (size_t)(2 * G + 1) * 4 + 7) & ~(size_t)7;
+}
+__host__ __device__ __forceinline__ size_t dr_smem_bytes(int G) {
+    if (G > DR_BIN_MAX) return dr_win_bytes(G);  // no binned search above DR_BIN_MAX
+    return dr_qtab_offset(G) + (G <= DR_QTAB ? (size_t)G * 3 * (8 + 4) : 0);
+}
 
 
 
@@ -204,15 +232,15 @@ constexpr int DR_BIN_MAX = 4096;    // largest grid binned in shared memory
 // One CTA per node.  tdata[toff[a] .. toff[a+1]) are the labels of S (T);
 // coordinates of label s are (x0[s], x1[s], x2[s]).
 __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
-                                                           const double *x0, const double *x1, const double *x2,
-                                                           int32_t *const *outptr, int32_t *outcnt, int lb,
+                                                           DRPoints PT, int32_t *const *outptr, int32_t *outcnt, int lb,
                                                            int32_t *bin_base, float *pf_base) {
+    const double *x0 = PT.x[0], *x1 = PT.x[1], *x2 = PT.x[2];
     extern __shared__ unsigned char smem_raw[];
     int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
     __shared__ int32_t tid_s[DR_TILE];
     __shared__ double tx_s[3][DR_TILE];
     __shared__ float tf_s[3][DR_TILE];
-    __shared__ double red[2][3][DR_THREADS / 32];
+    __shared__ long long red[2][3][DR_THREADS / 32];
     __shared__ int scratch[33];
     const int a = blockIdx.x;
     const int node = lb + a;
@@ -231,28 +259,34 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         if (threadIdx.x == 0) outcnt[node] = (int32_t)nt;
         return;
     }
-    // bounding box of S
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    // bounding box of S: exact min / max through order-preserving integer keys
+    // of the float64 coordinates (no float64 arithmetic)
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
     for (int64_t r = threadIdx.x; r < nt; r += blockDim.x) {
         int32_t s = T[r];
-        double c[3] = {x0[s], d > 1 ? x1[s] : 0.0, d > 2 ? x2[s] : 0.0};
-        for (int k = 0; k < 3; k++) { lo[k] = dmin_(lo[k], c[k]); hi[k] = dmax_(hi[k], c[k]); }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if (k >= d) break;
+            long long kv = dkey((k == 0 ? x0 : (k == 1 ? x1 : x2))[s]);
+            lo[k] = min(lo[k], kv);
+            hi[k] = max(hi[k], kv);
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = 0; k < 3; k++)
         for (int o = 16; o > 0; o >>= 1) {
-            lo[k] = dmin_(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-            hi[k] = dmax_(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
         }
     if (lane == 0)
         for (int k = 0; k < 3; k++) { red[0][k][warp] = lo[k]; red[1][k][warp] = hi[k]; }
     __syncthreads();
-    double l[3], h[3];
-    for (int k = 0; k < 3; k++) {
-        double mn = red[0][k][0], mx = red[1][k][0];
-        for (int w = 1; w < nw; w++) { mn = dmin_(mn, red[0][k][w]); mx = dmax_(mx, red[1][k][w]); }
-        l[k] = mn;
-        h[k] = __ddiv_rn(__dsub_rn(mx, mn), (double)g);
+    double l[3] = {0.0, 0.0, 0.0}, h[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < d; k++) {
+        long long mn = red[0][k][0], mx = red[1][k][0];
+        for (int w = 1; w < nw; w++) { mn = min(mn, red[0][k][w]); mx = max(mx, red[1][k][w]); }
+        l[k] = dkey_inv(mn);
+        h[k] = __ddiv_rn(__dsub_rn(dkey_inv(mx), l[k]), (double)g);
     }
     if (nt >= DR_PRUNE_MIN && G <= DR_BIN_MAX && bin_base != nullptr) {
         // Binned exact search.  The points of S are binned into the g^d cells of
@@ -269,7 +303,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         int32_t *bidx = bin_base + 2 * t0;  // bin of each entry, then labels in bin order
         int32_t *slab = bidx + nt;
         float *pf0 = pf_base + 3 * t0, *pf1 = pf0 + nt, *pf2 = pf1 + nt;
-        int *bstart = reinterpret_cast<int *>(smem_raw + (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t));
+        int *bstart = reinterpret_cast<int *>(smem_raw + dr_bins_offset(G));
         int *bcur = bstart + G + 1;
         double W = 0.0, hmin = INFINITY;
         float ihf[3] = {0.f, 0.f, 0.f}, hf[3] = {0.f, 0.f, 0.f};
@@ -282,9 +316,16 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             flat[k] = !(h[k] > 0.0);
             if (!flat[k]) { hmin = dmin_(hmin, h[k]); ihf[k] = (float)(1.0 / h[k]); hf[k] = (float)h[k]; }
         }
-        const float M = (float)(8e-6 * W * W);
-        const float delf = (float)(1e-5 * W);
-        const double delta = 1e-5 * W;
+        // Staged offsets x - l come from the float32 root-relative coordinates
+        // (x - ref, |x - ref| <= R): per coordinate within 5 u32 Rm of exact,
+        // Rm = max(W, R), so float32 squared distances are within 1.6e-6 W Rm of
+        // the float64 ones and cells within 3e-7 Rm of their true place.
+        const double Rm = dmax_(W, PT.R);
+        const float M = (float)(8e-6 * W * Rm);
+        const float delf = (float)(1e-5 * Rm);
+        const double delta = 1e-5 * Rm;
+        float lf[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < d; k++) lf[k] = (float)(l[k] - PT.ref[k]);
         for (int b = threadIdx.x; b <= G; b += blockDim.x) bstart[b] = 0;
         __syncthreads();
         // counting sort into cells.  Consecutive labels are Morton-coherent and
@@ -302,10 +343,9 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
                     if (k >= d) break;
-                    const double *xk = k == 0 ? x0 : (k == 1 ? x1 : x2);
                     int cidx = 0;
                     if (!flat[k]) {
-                        float f = (float)__dsub_rn(xk[sid], l[k]);
+                        float f = PT.xg[k][sid] - lf[k];
                         cidx = min(max((int)(f * ihf[k]), 0), g - 1);
                     }
                     bi += cidx * stride;
@@ -332,11 +372,26 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                 int pos = base + __popc(peers & lt);
                 int32_t sid = T[p];
                 slab[pos] = sid;
-                pf0[pos] = (float)__dsub_rn(x0[sid], l[0]);
-                pf1[pos] = d > 1 ? (float)__dsub_rn(x1[sid], l[1]) : 0.f;
-                pf2[pos] = d > 2 ? (float)__dsub_rn(x2[sid], l[2]) : 0.f;
+                pf0[pos] = PT.xg[0][sid] - lf[0];
+                pf1[pos] = d > 1 ? PT.xg[1][sid] - lf[1] : 0.f;
+                pf2[pos] = d > 2 ? PT.xg[2][sid] - lf[2] : 0.f;
             }
         }
+        // grid points: float64 q and its float32 offset qf, computed once each
+        double *qtab = reinterpret_cast<double *>(smem_raw + dr_qtab_offset(G));
+        float *qftab = reinterpret_cast<float *>(qtab + 3 * G);
+        const bool table = G <= DR_QTAB;
+        if (table)
+            for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
+                int rem = gi;
+                for (int k = 0; k < d; k++) {
+                    int idx = rem % g;
+                    rem /= g;
+                    double qk = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
+                    qtab[3 * gi + k] = qk;
+                    qftab[3 * gi + k] = (float)__dsub_rn(qk, l[k]);
+                }
+            }
         __syncthreads();
         for (int gi = warp; gi < G; gi += nw) {
             double q[3] = {0.0, 0.0, 0.0};
@@ -351,8 +406,13 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             if (k >= d) break;
                     int idx = rem % g;
                     rem /= g;
-                    q[k] = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
-                    qf[k] = (float)__dsub_rn(q[k], l[k]);
+                    if (table) {
+                        q[k] = qtab[3 * gi + k];
+                        qf[k] = qftab[3 * gi + k];
+                    } else {
+                        q[k] = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
+                        qf[k] = (float)__dsub_rn(q[k], l[k]);
+                    }
                     cid[k] = flat[k] ? 0 : idx;
                     if (!flat[k]) rmax = max(rmax, max(cid[k], g - 1 - cid[k]));
                 }
@@ -512,17 +572,14 @@ int64_t gridsize(int g, int d) {
 }
 
 void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, int nl, int g, int d,
-                       const double *const xs[3], int32_t *const *outptr, int32_t *outcnt, int lb, cudaStream_t s) {
+                       const DRPoints &pts, int32_t *const *outptr, int32_t *outcnt, int lb, cudaStream_t s) {
     if (nl <= 0) return;
     int G = (int)gridsize(g, d);
-    // win (labels of the grid points, padded to a power of two) followed by the
-    // bin starts and cursors of the binned search
-    size_t sm = std::max((size_t)next_pow2(G) * sizeof(int32_t), (size_t)((G + 31) & ~31) * 2 * sizeof(int32_t)) +
-                (size_t)(2 * DR_BIN_MAX + 1) * sizeof(int);
+    size_t sm = dr_smem_bytes(G);
     static bool attr_set = false;
     if (!attr_set) {
-        H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     2 * DR_MAX_GRID * (int)sizeof(int32_t) + (2 * DR_BIN_MAX + 1) * (int)sizeof(int)));
+        size_t mx = std::max(dr_smem_bytes(DR_MAX_GRID), dr_smem_bytes(DR_BIN_MAX));
+        H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         attr_set = true;
     }
     DevBuf<int32_t> bins;
@@ -530,8 +587,7 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
     bins.alloc((size_t)std::max<int64_t>(ttot, 1) * 2, s);
     pf.alloc((size_t)std::max<int64_t>(ttot, 1) * 3, s);
     ProfScope ps(KT_DATAREDUCT, s);
-    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, xs[0], xs[1], xs[2], outptr, outcnt, lb, bins.p,
-                                            pf.p);
+    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, pts, outptr, outcnt, lb, bins.p, pf.p);
     H2_LAUNCH("k_datareduct");
 }
 
@@ -551,7 +607,13 @@ void hidr_impl(h2_hidr_s *h) {
     H2_CUDA(cudaMemsetAsync(h->ycnt.p, 0, nn * sizeof(int32_t), s));
     H2_CUDA(cudaMemsetAsync(h->xptr.p, 0, nn * sizeof(int32_t *), s));
     H2_CUDA(cudaMemsetAsync(h->yptr.p, 0, nn * sizeof(int32_t *), s));
-    const double *xs[3] = {t->xs[0].p, t->xs[1].p, t->xs[2].p};
+    DRPoints pts;
+    for (int k = 0; k < 3; k++) {
+        pts.x[k] = t->xs[k].p;
+        pts.xg[k] = t->xg[k].p;
+        pts.ref[k] = t->geom.lo[k];
+    }
+    pts.R = t->geom.side;
     h->xbufs.resize(t->nlevels);
     h->ybufs.resize(t->nlevels);
     h->xmax_level.assign(t->nlevels, 0);
@@ -582,7 +644,7 @@ void hidr_impl(h2_hidr_s *h) {
         k_gather_up<<<nl, 256, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, t->end.p, h->xptr.p, h->xcnt.p,
                                        toff.p, tdata.p);
         H2_LAUNCH("k_gather_up");
-        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g1, d, xs, h->xptr.p, h->xcnt.p, lb, s);
+        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g1, d, pts, h->xptr.p, h->xcnt.p, lb, s);
         h->xtotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e1, s));
@@ -606,7 +668,7 @@ void hidr_impl(h2_hidr_s *h) {
         k_gather_down<<<nl, 256, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->xptr.p, h->xcnt.p,
                                          h->yptr.p, h->ycnt.p, toff.p, tdata.p);
         H2_LAUNCH("k_gather_down");
-        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, xs, h->yptr.p, h->ycnt.p, lb, s);
+        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, pts, h->yptr.p, h->ycnt.p, lb, s);
         h->ytotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e2, s));
@@ -628,7 +690,7 @@ void hidr_impl(h2_hidr_s *h) {
         }
 }
 
-int64_t datareduct_one(const double *const xs[3], int d, int64_t n, int g, int32_t *out_dev, cudaStream_t s) {
+int64_t datareduct_one(const DRPoints &pts, int d, int64_t n, int g, int32_t *out_dev, cudaStream_t s) {
     // one node whose set is the labels 0..n-1
     DevBuf<int64_t> toff;
     DevBuf<int32_t> tdata, cnt;
@@ -643,7 +705,7 @@ int64_t datareduct_one(const double *const xs[3], int d, int64_t n, int g, int32
     H2_CUDA(cudaMemcpyAsync(toff.p, offs, sizeof offs, cudaMemcpyHostToDevice, s));
     H2_CUDA(cudaMemcpyAsync(tdata.p, ids.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     H2_CUDA(cudaMemcpyAsync(optr.p, &out_dev, sizeof(int32_t *), cudaMemcpyHostToDevice, s));
-    launch_datareduct(toff.p, tdata.p, n, 1, g, d, xs, optr.p, cnt.p, 0, s);
+    launch_datareduct(toff.p, tdata.p, n, 1, g, d, pts, optr.p, cnt.p, 0, s);
     return read_scalar(cnt.p, s);
 }
 

@@ -174,6 +174,16 @@ __global__ void k_rel_coords(const int32_t *nchild, const int32_t *begin, const 
     }
 }
 
+// float32 coordinates relative to the root box corner (DataReduct's float32 filters)
+__global__ void k_root_coords(const double *x0, const double *x1, const double *x2, int64_t n, int d, const Geom *g,
+                              float *r0, float *r1, float *r2) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    r0[p] = (float)(x0[p] - g->lo[0]);
+    if (d > 1) r1[p] = (float)(x1[p] - g->lo[1]);
+    if (d > 2) r2[p] = (float)(x2[p] - g->lo[2]);
+}
+
 __global__ void k_max_leaf(const int32_t *nchild, const int32_t *begin, const int32_t *end, int nn, int32_t *mx) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nn && nchild[i] == 0) atomicMax(mx, end[i] - begin[i]);
@@ -362,6 +372,10 @@ void tree_build_impl(h2_tree_s *t, const double *pts) {
     k_rel_coords<<<t->nnodes, 128, 0, s>>>(t->nchild.p, t->begin.p, t->end.p, t->cen[0].p, t->cen[1].p, t->cen[2].p,
                                           t->xs[0].p, t->xs[1].p, t->xs[2].p, d, t->xr[0].p, t->xr[1].p, t->xr[2].p);
     H2_LAUNCH("k_rel_coords");
+    for (int k = 0; k < 3; k++) t->xg[k].alloc(k < d ? n : 1, s);
+    k_root_coords<<<blocks_for(n, 256), 256, 0, s>>>(t->xs[0].p, t->xs[1].p, t->xs[2].p, n, d, g.p, t->xg[0].p,
+                                                     t->xg[1].p, t->xg[2].p);
+    H2_LAUNCH("k_root_coords");
     DevBuf<int32_t> mx;
     mx.alloc(1, s);
     H2_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int32_t), s));

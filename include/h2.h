@@ -96,7 +96,8 @@ typedef struct {
  * level, then by key.  Near/far lists come from a dual traversal from
  * (root, root): an admissible pair is far, a pair of leaves is near, otherwise
  * every non-leaf side is split.  Errors: H2_ERR_INVALID_ARG (null pointers,
- * n < 1, dim not 2/3, q < 1, bad tau), H2_ERR_OOM, H2_ERR_CUDA. */
+ * n < 1, dim not 2/3, q < 1, bad tau), H2_ERR_NUMERIC (a coordinate is NaN or
+ * infinite), H2_ERR_OOM, H2_ERR_CUDA. */
 h2_status h2_tree_build(const double *pts, int64_t n, int dim, int pts_on_device,
                         const h2_tree_params *params, void *stream, h2_tree *out);
 

@@ -453,9 +453,9 @@ h2_status h2_calibrate(int dim, int kernel, const double *kparams, double eps, c
         pool_keep_memory();
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         DevBuf<double> a[3], b[3];
-        DevBuf<float> bg[3];
+        DevBuf<float2> bg[3];
         std::vector<double> col(std::max(n1, n2));
-        std::vector<float> colf(n2);
+        std::vector<float2> colf(n2);
         DRPoints zb;
         zb.R = 0.0;
         for (int k = 0; k < 3; k++) {
@@ -470,11 +470,12 @@ h2_status h2_calibrate(int dim, int kernel, const double *kparams, double eps, c
             H2_CUDA(cudaMemcpyAsync(a[k].p, col.data(), n1 * sizeof(double), cudaMemcpyHostToDevice, s));
             for (int i = 0; i < n2; i++) {
                 col[i] = z2[(int64_t)i * dim + k];
-                colf[i] = (float)col[i];  // relative to ref = 0
+                float hi = (float)col[i];  // relative to ref = 0, split into float32 hi + lo
+                colf[i] = make_float2(hi, (float)(col[i] - (double)hi));
                 zb.R = std::max(zb.R, std::fabs(col[i]));
             }
             H2_CUDA(cudaMemcpyAsync(b[k].p, col.data(), n2 * sizeof(double), cudaMemcpyHostToDevice, s));
-            H2_CUDA(cudaMemcpyAsync(bg[k].p, colf.data(), n2 * sizeof(float), cudaMemcpyHostToDevice, s));
+            H2_CUDA(cudaMemcpyAsync(bg[k].p, colf.data(), n2 * sizeof(float2), cudaMemcpyHostToDevice, s));
             H2_CUDA(cudaStreamSynchronize(s));
         }
         const double *za[3] = {a[0].p, a[1].p, a[2].p};

@@ -122,6 +122,7 @@ struct Geom {
     double hi[3];
     double side;
     double scale;  // 2^B / side, 0 when side == 0
+    int nonfinite;  // 1 when some coordinate is NaN or infinite
 };
 
 struct PhaseTimes {
@@ -152,7 +153,7 @@ struct h2_tree_s {
     double ms_tree = 0, ms_lists = 0;
     h2::DevBuf<double> cen[3];    // cell centre of every node
     h2::DevBuf<float> xr[3];      // point coordinates relative to their leaf's centre (float32 kernels)
-    h2::DevBuf<float> xg[3];      // point coordinates relative to the root box corner (float32 filters)
+    h2::DevBuf<float2> xg[3];     // x - root corner split into float32 hi + lo (DataReduct's float32 search)
     h2::DevBuf<int2> near_tiles;  // (leaf, first target) tiles of the nearfield kernel, built on first use
     int near_tile_tpt = 0;
     h2::DevBuf<int64_t> leaf_start;  // begin of every node as int64 (nearfield point sets)
@@ -219,11 +220,12 @@ void exact_rows_noalloc_impl(h2_tree_s *t, int kid, const double *kp, const doub
 void sampled_error_impl(const double *exact, const double *approx, const int64_t *rows, int64_t nrows, int64_t n,
                         double *err_out, cudaStream_t s);
 
-// Coordinates DataReduct reads: float64 x (exact distances) and float32
-// xg = x - ref with |x - ref| <= R per coordinate (its float32 filters).
+// Coordinates DataReduct reads: float64 x (exact distances) and xg, the
+// float64 difference x - ref (|x - ref| <= R per coordinate) split into a
+// float32 pair {hi, lo} with hi + lo equal to it within 2^-47 R.
 struct DRPoints {
     const double *x[3];
-    const float *xg[3];
+    const float2 *xg[3];
     double ref[3];
     double R;
 };

@@ -19,12 +19,6 @@ constexpr int DR_TILE = 256;  // points staged in shared memory per pass
 constexpr int DR_GPT = 4;     // grid points per thread per sweep
 constexpr int DR_MAX_GRID = 16384;
 
-int next_pow2(int v) {
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
-
 // ---------------------------------------------------------------- sizes
 // |S_i|: the leaf's points, or the sum of the children's |X_c*|
 __global__ void k_size_up(int lb, int nl, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
@@ -204,7 +198,45 @@ __device__ __forceinline__ double dkey_inv(long long k) {
 __device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax_(double a, double b) { return a > b ? a : b; }
 
-constexpr int DR_PRUNE_MIN = 2048;  // sets at least this large use the binned search
+__device__ __forceinline__ float warp_minf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Cell e of the (2r+1)^d block of cells around cell cid (flat dimensions
+// collapsed): whether it lies inside the grid at Chebyshev distance exactly r,
+// its bin, and a float32 lower bound lb of the squared distance from the grid
+// point (offset qf from the box corner) to the cell widened by delf per side.
+__device__ __forceinline__ bool dr_ring_cell(int e, int r, int d, int g, const int *cid, const bool *flat,
+                                             const float *hf, const float *qf, float delf, int &bin, float &lb) {
+    const int side = 2 * r + 1;
+    int rem = e, stride = 1, cheb = 0;
+    bool ok = true;
+    bin = 0;
+    lb = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (k >= d) break;
+        int o = 0;
+        if (!flat[k]) {
+            o = rem % side - r;
+            rem /= side;
+        }
+        const int ck = cid[k] + o;
+        ok = ok && ck >= 0 && ck < g;
+        cheb = max(cheb, abs(o));
+        bin += ck * stride;
+        stride *= g;
+        if (!flat[k]) {
+            const float lo = (float)ck * hf[k] - delf, hi = (float)(ck + 1) * hf[k] + delf;
+            const float gap = fmaxf(0.f, fmaxf(lo - qf[k], qf[k] - hi));
+            lb = fmaf(gap, gap, lb);
+        }
+    }
+    return ok && cheb == r;
+}
+
 constexpr int DR_BIN_MAX = 4096;    // largest grid binned in shared memory
 constexpr int DR_QTAB = 1024;       // largest grid tabulated in shared memory
 
@@ -238,7 +270,6 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
     extern __shared__ unsigned char smem_raw[];
     int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
     __shared__ int32_t tid_s[DR_TILE];
-    __shared__ double tx_s[3][DR_TILE];
     __shared__ float tf_s[3][DR_TILE];
     __shared__ long long red[2][3][DR_THREADS / 32];
     __shared__ int scratch[33];
@@ -282,50 +313,62 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         for (int k = 0; k < 3; k++) { red[0][k][warp] = lo[k]; red[1][k][warp] = hi[k]; }
     __syncthreads();
     double l[3] = {0.0, 0.0, 0.0}, h[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < d; k++) {
+    #pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (k >= d) break;
         long long mn = red[0][k][0], mx = red[1][k][0];
         for (int w = 1; w < nw; w++) { mn = min(mn, red[0][k][w]); mx = max(mx, red[1][k][w]); }
         l[k] = dkey_inv(mn);
         h[k] = __ddiv_rn(__dsub_rn(dkey_inv(mx), l[k]), (double)g);
     }
-    if (nt >= DR_PRUNE_MIN && G <= DR_BIN_MAX && bin_base != nullptr) {
-        // Binned exact search.  The points of S are binned into the g^d cells of
-        // the reference grid itself (grid point q is the centre of its cell) by a
-        // counting sort in shared memory, with their float32 coordinates
-        // relative to the box corner stored in bin order.  For each grid point a
-        // warp scans its own cell, then Chebyshev rings of cells, and stops after
-        // ring r once the best float64 distance is below ((r + 1/2) h_min - delta)^2,
-        // a lower bound for every point in a farther cell (delta = 1e-5 W covers
-        // float32 binning error).  Inside a ring, a cell whose box bound exceeds
-        // the best distance by M = 8e-6 W^2, or a point whose float32 distance
-        // does, is skipped; the rest are compared exactly in float64 with the
-        // smaller-label tie-break, so the winner equals the float64 brute force.
+    // Both searches below stage float32 offsets from the box corner l,
+    //   x - l = (xh - lh) + (xl - ll),
+    // from the {hi, lo} split of the root-relative coordinates (xh + xl and
+    // lh + ll within 2^-47 R of x - ref and l - ref, R the root extent).  Per
+    // coordinate the offset is within 2 u W + 8 u^2 R of exact (u = 2^-24, W the
+    // largest box extent), the grid point's within u W, so a float32 squared
+    // distance is within E = 30 u W^2 + 48 u^2 W R of the float64 one.  With
+    // M = 8e-6 W^2 + 1e-12 W R > 2E + 3u (3 W^2): when a point's float32
+    // distance exceeds the smallest one by more than M, its float64 distance
+    // exceeds the float64 distance of the float32 winner, which is then the
+    // float64 winner; otherwise the float64 distances of every point within M
+    // of the smallest decide, the smaller label taking ties.
+    double W = 0.0, hmin = INFINITY;
+    float ihf[3] = {0.f, 0.f, 0.f}, hf[3] = {0.f, 0.f, 0.f}, lh[3] = {0.f, 0.f, 0.f}, ll[3] = {0.f, 0.f, 0.f};
+    bool flat[3] = {true, true, true};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (k >= d) break;
+        W = dmax_(W, __dmul_rn(h[k], (double)g));
+        flat[k] = !(h[k] > 0.0);
+        if (!flat[k]) {
+            hmin = dmin_(hmin, h[k]);
+            ihf[k] = (float)(1.0 / h[k]);
+            hf[k] = (float)h[k];
+        }
+        const double Lk = l[k] - PT.ref[k];
+        lh[k] = (float)Lk;
+        ll[k] = (float)(Lk - (double)lh[k]);
+    }
+    const float M = (float)(8e-6 * W * W + 1e-12 * W * PT.R);
+    if (G <= DR_BIN_MAX && bin_base != nullptr) {
+        // Binned search.  The points of S are binned into the g^d cells of the
+        // reference grid itself (grid point q is the centre of its cell) by a
+        // counting sort in shared memory, their float32 offsets stored in bin
+        // order.  For each grid point a warp scans its own cell, then the
+        // Chebyshev rings of cells around it, each lane keeping the two
+        // smallest float32 distances it has seen.  A cell whose widened box
+        // bound exceeds the warp's smallest distance plus M is skipped, and the
+        // search stops after ring r once that sum is below the square of
+        // (r + 1/2) h_min - delta, a lower bound for every point in a farther
+        // cell (delta = 1e-5 W + 1e-12 R covers the float32 binning error).
         int32_t *bidx = bin_base + 2 * t0;  // bin of each entry, then labels in bin order
         int32_t *slab = bidx + nt;
         float *pf0 = pf_base + 3 * t0, *pf1 = pf0 + nt, *pf2 = pf1 + nt;
         int *bstart = reinterpret_cast<int *>(smem_raw + dr_bins_offset(G));
         int *bcur = bstart + G + 1;
-        double W = 0.0, hmin = INFINITY;
-        float ihf[3] = {0.f, 0.f, 0.f}, hf[3] = {0.f, 0.f, 0.f};
-        bool flat[3] = {true, true, true};
-        
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            if (k >= d) break;
-            W = dmax_(W, __dmul_rn(h[k], (double)g));
-            flat[k] = !(h[k] > 0.0);
-            if (!flat[k]) { hmin = dmin_(hmin, h[k]); ihf[k] = (float)(1.0 / h[k]); hf[k] = (float)h[k]; }
-        }
-        // Staged offsets x - l come from the float32 root-relative coordinates
-        // (x - ref, |x - ref| <= R): per coordinate within 5 u32 Rm of exact,
-        // Rm = max(W, R), so float32 squared distances are within 1.6e-6 W Rm of
-        // the float64 ones and cells within 3e-7 Rm of their true place.
-        const double Rm = dmax_(W, PT.R);
-        const float M = (float)(8e-6 * W * Rm);
-        const float delf = (float)(1e-5 * Rm);
-        const double delta = 1e-5 * Rm;
-        float lf[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < d; k++) lf[k] = (float)(l[k] - PT.ref[k]);
+        const float delf = (float)(1e-5 * W + 1e-12 * PT.R);
+        const float hminf = (float)hmin;
         for (int b = threadIdx.x; b <= G; b += blockDim.x) bstart[b] = 0;
         __syncthreads();
         // counting sort into cells.  Consecutive labels are Morton-coherent and
@@ -337,7 +380,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             const int64_t p = p0 + lane;
             int bi = -1;
             if (p < nt) {
-                int32_t sid = T[p];
+                const int32_t sid = T[p];
                 int stride = 1;
                 bi = 0;
 #pragma unroll
@@ -345,7 +388,8 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     if (k >= d) break;
                     int cidx = 0;
                     if (!flat[k]) {
-                        float f = PT.xg[k][sid] - lf[k];
+                        const float2 v = PT.xg[k][sid];
+                        const float f = (v.x - lh[k]) + (v.y - ll[k]);
                         cidx = min(max((int)(f * ihf[k]), 0), g - 1);
                     }
                     bi += cidx * stride;
@@ -353,7 +397,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                 }
                 bidx[p] = bi;
             }
-            unsigned peers = __match_any_sync(0xffffffffu, bi);
+            const unsigned peers = __match_any_sync(0xffffffffu, bi);
             if (bi >= 0 && (peers & lt) == 0u) atomicAdd(&bstart[bi + 1], __popc(peers));
         }
         __syncthreads();
@@ -363,18 +407,28 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         for (int64_t p0 = (int64_t)warp * 32; p0 < nt; p0 += blockDim.x) {
             const int64_t p = p0 + lane;
             const int bi = p < nt ? bidx[p] : -1;
-            unsigned peers = __match_any_sync(0xffffffffu, bi);
-            int leader = __ffs(peers) - 1;
+            const unsigned peers = __match_any_sync(0xffffffffu, bi);
+            const int leader = __ffs(peers) - 1;
             int base = 0;
             if (bi >= 0 && lane == leader) base = atomicAdd(&bcur[bi], __popc(peers));
             base = __shfl_sync(0xffffffffu, base, leader);
             if (bi >= 0) {
-                int pos = base + __popc(peers & lt);
-                int32_t sid = T[p];
+                const int pos = base + __popc(peers & lt);
+                const int32_t sid = T[p];
                 slab[pos] = sid;
-                pf0[pos] = PT.xg[0][sid] - lf[0];
-                pf1[pos] = d > 1 ? PT.xg[1][sid] - lf[1] : 0.f;
-                pf2[pos] = d > 2 ? PT.xg[2][sid] - lf[2] : 0.f;
+                const float2 v0 = PT.xg[0][sid];
+                pf0[pos] = (v0.x - lh[0]) + (v0.y - ll[0]);
+                float f1 = 0.f, f2 = 0.f;
+                if (d > 1) {
+                    const float2 v1 = PT.xg[1][sid];
+                    f1 = (v1.x - lh[1]) + (v1.y - ll[1]);
+                }
+                if (d > 2) {
+                    const float2 v2 = PT.xg[2][sid];
+                    f2 = (v2.x - lh[2]) + (v2.y - ll[2]);
+                }
+                pf1[pos] = f1;
+                pf2[pos] = f2;
             }
         }
         // grid points: float64 q and its float32 offset qf, computed once each
@@ -384,10 +438,12 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         if (table)
             for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
                 int rem = gi;
-                for (int k = 0; k < d; k++) {
-                    int idx = rem % g;
+                #pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    if (k >= d) break;
+                    const int idx = rem % g;
                     rem /= g;
-                    double qk = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
+                    const double qk = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
                     qtab[3 * gi + k] = qk;
                     qftab[3 * gi + k] = (float)__dsub_rn(qk, l[k]);
                 }
@@ -400,11 +456,10 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             int rmax = 0;
             {
                 int rem = gi;
-                
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
-            if (k >= d) break;
-                    int idx = rem % g;
+                for (int k = 0; k < 3; k++) {
+                    if (k >= d) break;
+                    const int idx = rem % g;
                     rem /= g;
                     if (table) {
                         q[k] = qtab[3 * gi + k];
@@ -417,144 +472,234 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     if (!flat[k]) rmax = max(rmax, max(cid[k], g - 1 - cid[k]));
                 }
             }
-            double bd = INFINITY;
-            int32_t bi = INT_MAX;
-            float lim = INFINITY;
+            float b1 = INFINITY, b2 = INFINITY;  // this lane's two smallest float32 distances
+            int p1 = -1;                         // bin-order position of its smallest
+            float lim = INFINITY;                // the warp's smallest distance + M
+            int rlast = rmax;
             for (int r = 0; r <= rmax; r++) {
                 const int side = 2 * r + 1;
                 int total = 1;
-                for (int k = 0; k < d; k++) total *= flat[k] ? 1 : side;
+                #pragma unroll
+                for (int k = 0; k < 3; k++)
+                    if (k < d) total *= flat[k] ? 1 : side;
                 for (int e0 = 0; e0 < total; e0 += 32) {
-                    int e = e0 + lane;
-                    bool ok = e < total;
-                    int bin = 0, stride = 1, cheb = 0;
+                    int bin = 0;
                     float lb = 0.f;
-                    if (ok) {
-                        int rem = e;
-                        
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            if (k >= d) break;
-                            int o = 0;
-                            if (!flat[k]) { o = rem % side - r; rem /= side; }
-                            int ck = cid[k] + o;
-                            ok = ok && ck >= 0 && ck < g;
-                            cheb = max(cheb, abs(o));
-                            bin += ck * stride;
-                            stride *= g;
-                            if (!flat[k]) {
-                                float lo = (float)ck * hf[k] - delf, hi = (float)(ck + 1) * hf[k] + delf;
-                                float gap = fmaxf(0.f, fmaxf(lo - qf[k], qf[k] - hi));
-                                lb = fmaf(gap, gap, lb);
-                            }
-                        }
-                        ok = ok && cheb == r && bstart[bin + 1] > bstart[bin] && lb <= lim;
-                    }
+                    bool ok = e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, flat, hf, qf, delf, bin, lb);
+                    ok = ok && lb <= lim && bstart[bin + 1] > bstart[bin];
                     unsigned cm = __ballot_sync(0xffffffffu, ok);
                     while (cm) {
-                        int src = __ffs(cm) - 1;
+                        const int b = __shfl_sync(0xffffffffu, bin, __ffs(cm) - 1);
                         cm &= cm - 1;
-                        int b = __shfl_sync(0xffffffffu, bin, src);
-                        for (int p0 = bstart[b]; p0 < bstart[b + 1]; p0 += 32) {
-                            int p = p0 + lane;
-                            float d32 = INFINITY;
-                            if (p < bstart[b + 1]) {
-                                float e0f = pf0[p] - qf[0], e1f = pf1[p] - qf[1], e2f = pf2[p] - qf[2];
-                                d32 = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f));
+                        const int pe = bstart[b + 1];
+                        for (int p = bstart[b] + lane; p < pe; p += 32) {
+                            const float e0f = pf0[p] - qf[0], e1f = pf1[p] - qf[1], e2f = pf2[p] - qf[2];
+                            const float d32 = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f));
+                            if (d32 < b2) {
+                                if (d32 < b1) {
+                                    b2 = b1;
+                                    b1 = d32;
+                                    p1 = p;
+                                } else {
+                                    b2 = d32;
+                                }
                             }
-                            unsigned pm = __ballot_sync(0xffffffffu, p < bstart[b + 1] && d32 <= lim);
-                            if (pm == 0u) continue;
-                            double dd = INFINITY;
-                            int32_t id = INT_MAX;
-                            if ((pm >> lane) & 1u) {
-                                id = slab[p];
-                                dd = h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0, d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]);
+                        }
+                    }
+                    lim = warp_minf(b1) + M;
+                }
+                // (r + 1/2) h_min - delta and its square rounded down in float32
+                const float rr = ((float)r + 0.5f) * hminf * 0.9999996f - delf;
+                if (rr > 0.f && lim < rr * rr * 0.9999996f) {
+                    rlast = r;
+                    break;
+                }
+            }
+            const float m1 = warp_minf(b1);
+            const int w = __ffs(__ballot_sync(0xffffffffu, b1 == m1)) - 1;
+            const float sec = warp_minf(lane == w ? b2 : b1);
+            const float limx = m1 + M;
+            int32_t winner;
+            if (sec > limx) {
+                winner = slab[__shfl_sync(0xffffffffu, p1, w)];
+            } else {
+                // near tie: every point within M of the smallest, in float64;
+                // non-negative doubles order as their bit patterns
+                long long bk = LLONG_MAX;
+                int32_t bl = INT_MAX;
+                for (int r = 0; r <= rlast; r++) {
+                    const int side = 2 * r + 1;
+                    int total = 1;
+                    #pragma unroll
+                    for (int k = 0; k < 3; k++)
+                        if (k < d) total *= flat[k] ? 1 : side;
+                    for (int e0 = 0; e0 < total; e0 += 32) {
+                        int bin = 0;
+                        float lb = 0.f;
+                        bool ok =
+                            e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, flat, hf, qf, delf, bin, lb);
+                        ok = ok && lb <= limx && bstart[bin + 1] > bstart[bin];
+                        unsigned cm = __ballot_sync(0xffffffffu, ok);
+                        while (cm) {
+                            const int b = __shfl_sync(0xffffffffu, bin, __ffs(cm) - 1);
+                            cm &= cm - 1;
+                            const int pe = bstart[b + 1];
+                            for (int p0 = bstart[b]; p0 < pe; p0 += 32) {
+                                const int p = p0 + lane;
+                                bool c = false;
+                                if (p < pe) {
+                                    const float e0f = pf0[p] - qf[0], e1f = pf1[p] - qf[1], e2f = pf2[p] - qf[2];
+                                    c = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f)) <= limx;
+                                }
+                                unsigned pm = __ballot_sync(0xffffffffu, c);
+                                if (pm == 0u) continue;
+                                long long kk = LLONG_MAX;
+                                int32_t id = INT_MAX;
+                                if (c) {
+                                    id = slab[p];
+                                    kk = __double_as_longlong(h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0,
+                                                                       d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]));
+                                }
+                                while (pm) {
+                                    const int s2 = __ffs(pm) - 1;
+                                    pm &= pm - 1;
+                                    const long long kv = __shfl_sync(0xffffffffu, kk, s2);
+                                    const int32_t iv = __shfl_sync(0xffffffffu, id, s2);
+                                    if (kv < bk || (kv == bk && iv < bl)) {
+                                        bk = kv;
+                                        bl = iv;
+                                    }
+                                }
                             }
-                            bool improved = false;
-                            while (pm) {
-                                int s2 = __ffs(pm) - 1;
-                                pm &= pm - 1;
-                                double dv = __shfl_sync(0xffffffffu, dd, s2);
-                                int32_t iv = __shfl_sync(0xffffffffu, id, s2);
-                                if (dv < bd || (dv == bd && iv < bi)) { bd = dv; bi = iv; improved = true; }
-                            }
-                            if (improved) lim = __double2float_ru(bd) + M;
                         }
                     }
                 }
-                const double reach = (r + 0.5) * hmin - delta;
-                if (reach > 0.0 && bd * (1.0 + 1e-12) < reach * reach) break;
+                winner = bl;
             }
-            if (lane == 0) win[gi] = bi;
+            if (lane == 0) win[gi] = winner;
         }
     } else {
-    // Nearest point to each grid point, DR_GPT grid points per thread per sweep.
-    // Exact float64 argmin through a float32 filter: with coordinates taken
-    // relative to the box corner l and W the largest box extent, the float32
-    // squared distance D32 differs from the float64 one by at most
-    // E = 1.7e-6 W^2 (per-coordinate error <= 3 u32 W, three squares and sums);
-    // the float64 winner therefore always satisfies D32 <= min D32 + 2E, so every
-    // point with D32 <= (running min D32) + M, M = 8e-6 W^2 >= 2E, is compared
-    // exactly in float64 with the smaller-label tie-break.
-    double W = 0.0;
-    for (int k = 0; k < d; k++) W = dmax_(W, __dmul_rn(h[k], (double)g));
-    const float M = (float)(8e-6 * W * W);
-    for (int gbase = 0; gbase < G; gbase += DR_THREADS * DR_GPT) {
-        double q[DR_GPT][3], bd[DR_GPT];
-        float qf[DR_GPT][3], thr[DR_GPT], b32[DR_GPT];
-        int32_t bi[DR_GPT];
+        // Brute force (grids above DR_BIN_MAX): DR_GPT grid points per thread
+        // per sweep over S staged in shared memory, each keeping its two
+        // smallest float32 distances; a grid point without a gap of more than M
+        // between them takes a second sweep that compares every point within M
+        // of the smallest in float64.
+        for (int gbase = 0; gbase < G; gbase += DR_THREADS * DR_GPT) {
+            float qf[DR_GPT][3], b1[DR_GPT], b2[DR_GPT];
+            int32_t i1[DR_GPT];
 #pragma unroll
-        for (int j = 0; j < DR_GPT; j++) {
-            int gi = gbase + j * DR_THREADS + threadIdx.x;
-            int rem = gi;
-            for (int k = 0; k < 3; k++) {
-                int idx = 0;
-                if (k < d) { idx = rem % g; rem /= g; }
-                q[j][k] = k < d ? __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])) : 0.0;
-                qf[j][k] = k < d ? (float)__dsub_rn(q[j][k], l[k]) : 0.0f;
+            for (int j = 0; j < DR_GPT; j++) {
+                int rem = gbase + j * DR_THREADS + threadIdx.x;
+                for (int k = 0; k < 3; k++) {
+                    int idx = 0;
+                    if (k < d) {
+                        idx = rem % g;
+                        rem /= g;
+                    }
+                    qf[j][k] = k < d ? (float)__dsub_rn(
+                                           __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])), l[k])
+                                     : 0.0f;
+                }
+                b1[j] = INFINITY;
+                b2[j] = INFINITY;
+                i1[j] = INT_MAX;
             }
-            bd[j] = INFINITY;
-            bi[j] = INT_MAX;
-            b32[j] = INFINITY;
-            thr[j] = INFINITY;
-        }
-        for (int64_t tb = 0; tb < nt; tb += DR_TILE) {
-            int cnt = (int)(nt - tb < DR_TILE ? nt - tb : DR_TILE);
-            __syncthreads();
-            for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
-                int32_t s = T[tb + r];
-                tid_s[r] = s;
-                double c0 = x0[s], c1 = d > 1 ? x1[s] : 0.0, c2 = d > 2 ? x2[s] : 0.0;
-                tx_s[0][r] = c0;
-                tx_s[1][r] = c1;
-                tx_s[2][r] = c2;
-                tf_s[0][r] = (float)__dsub_rn(c0, l[0]);
-                tf_s[1][r] = d > 1 ? (float)__dsub_rn(c1, l[1]) : 0.0f;
-                tf_s[2][r] = d > 2 ? (float)__dsub_rn(c2, l[2]) : 0.0f;
-            }
-            __syncthreads();
-            for (int r = 0; r < cnt; r++) {
-                float f0 = tf_s[0][r], f1 = tf_s[1][r], f2 = tf_s[2][r];
+            for (int64_t tb = 0; tb < nt; tb += DR_TILE) {
+                const int cnt = (int)(nt - tb < DR_TILE ? nt - tb : DR_TILE);
+                __syncthreads();
+                for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+                    const int32_t s = T[tb + r];
+                    tid_s[r] = s;
 #pragma unroll
-                for (int j = 0; j < DR_GPT; j++) {
-                    float e0 = f0 - qf[j][0], e1 = f1 - qf[j][1], e2 = f2 - qf[j][2];
-                    float d32 = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
-                    if (d32 <= thr[j]) {
-                        if (d32 < b32[j]) { b32[j] = d32; thr[j] = d32 + M; }
-                        int32_t s = tid_s[r];
-                        double dd = h2_dist2(d, tx_s[0][r], tx_s[1][r], tx_s[2][r], q[j][0], q[j][1], q[j][2]);
-                        if (dd < bd[j] || (dd == bd[j] && s < bi[j])) { bd[j] = dd; bi[j] = s; }
+                    for (int k = 0; k < 3; k++) {
+                        float f = 0.f;
+                        if (k < d) {
+                            const float2 v = PT.xg[k][s];
+                            f = (v.x - lh[k]) + (v.y - ll[k]);
+                        }
+                        tf_s[k][r] = f;
+                    }
+                }
+                __syncthreads();
+                for (int r = 0; r < cnt; r++) {
+                    const float f0 = tf_s[0][r], f1 = tf_s[1][r], f2 = tf_s[2][r];
+#pragma unroll
+                    for (int j = 0; j < DR_GPT; j++) {
+                        const float e0 = f0 - qf[j][0], e1 = f1 - qf[j][1], e2 = f2 - qf[j][2];
+                        const float d32 = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
+                        if (d32 < b2[j]) {
+                            if (d32 < b1[j]) {
+                                b2[j] = b1[j];
+                                b1[j] = d32;
+                                i1[j] = tid_s[r];
+                            } else {
+                                b2[j] = d32;
+                            }
+                        }
                     }
                 }
             }
-        }
+            // near ties, one grid-point slot at a time
 #pragma unroll
-        for (int j = 0; j < DR_GPT; j++) {
-            int gi = gbase + j * DR_THREADS + threadIdx.x;
-            if (gi < G) win[gi] = bi[j];
+            for (int j = 0; j < DR_GPT; j++) {
+                const int gi = gbase + j * DR_THREADS + threadIdx.x;
+                const float limx = b1[j] + M;
+                const bool need = gi < G && !(b2[j] > limx);
+                if (!__syncthreads_or(need)) continue;
+                double q[3] = {0.0, 0.0, 0.0};
+                {
+                    int rem = gi;
+                    #pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        if (k >= d) break;
+                        const int idx = rem % g;
+                        rem /= g;
+                        q[k] = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
+                    }
+                }
+                long long bk = LLONG_MAX;
+                int32_t bl = INT_MAX;
+                for (int64_t tb = 0; tb < nt; tb += DR_TILE) {
+                    const int cnt = (int)(nt - tb < DR_TILE ? nt - tb : DR_TILE);
+                    __syncthreads();
+                    for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+                        const int32_t s = T[tb + r];
+                        tid_s[r] = s;
+#pragma unroll
+                        for (int k = 0; k < 3; k++) {
+                            float f = 0.f;
+                            if (k < d) {
+                                const float2 v = PT.xg[k][s];
+                                f = (v.x - lh[k]) + (v.y - ll[k]);
+                            }
+                            tf_s[k][r] = f;
+                        }
+                    }
+                    __syncthreads();
+                    if (need)
+                        for (int r = 0; r < cnt; r++) {
+                            const float e0 = tf_s[0][r] - qf[j][0], e1 = tf_s[1][r] - qf[j][1],
+                                        e2 = tf_s[2][r] - qf[j][2];
+                            if (fmaf(e2, e2, fmaf(e1, e1, e0 * e0)) <= limx) {
+                                const int32_t s = tid_s[r];
+                                const long long kk = __double_as_longlong(
+                                    h2_dist2(d, x0[s], d > 1 ? x1[s] : 0.0, d > 2 ? x2[s] : 0.0, q[0], q[1], q[2]));
+                                if (kk < bk || (kk == bk && s < bl)) {
+                                    bk = kk;
+                                    bl = s;
+                                }
+                            }
+                        }
+                }
+                if (need) i1[j] = bl;
+            }
+#pragma unroll
+            for (int j = 0; j < DR_GPT; j++) {
+                const int gi = gbase + j * DR_THREADS + threadIdx.x;
+                if (gi < G) win[gi] = i1[j];
+            }
         }
     }
-    }  // brute-force sweep
     __syncthreads();
     int P = 1;
     while (P < G) P <<= 1;

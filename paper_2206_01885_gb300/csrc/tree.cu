@@ -10,19 +10,22 @@ namespace {
 
 constexpr int BBOX_THREADS = 256;
 
-// per-block min/max of each coordinate; pts row-major n x d
+// per-block min/max of each coordinate and whether any is non-finite;
+// pts row-major n x d; part holds 7 values per block
 __global__ void k_bbox_partial(const double *pts, int64_t n, int d, double *part) {
     __shared__ double smin[3][BBOX_THREADS], smax[3][BBOX_THREADS];
     double mn[3], mx[3];
+    bool bad = false;
     for (int k = 0; k < 3; k++) { mn[k] = INFINITY; mx[k] = -INFINITY; }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         for (int k = 0; k < d; k++) {
             double v = pts[i * d + k];
+            bad = bad || !isfinite(v);
             mn[k] = fmin(mn[k], v);
             mx[k] = fmax(mx[k], v);
         }
     for (int k = 0; k < 3; k++) { smin[k][threadIdx.x] = mn[k]; smax[k][threadIdx.x] = mx[k]; }
-    __syncthreads();
+    bad = __syncthreads_or(bad);
     for (int o = BBOX_THREADS / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o)
             for (int k = 0; k < 3; k++) {
@@ -31,16 +34,21 @@ __global__ void k_bbox_partial(const double *pts, int64_t n, int d, double *part
             }
         __syncthreads();
     }
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 3; k++) { part[blockIdx.x * 6 + k] = smin[k][0]; part[blockIdx.x * 6 + 3 + k] = smax[k][0]; }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; k++) { part[blockIdx.x * 7 + k] = smin[k][0]; part[blockIdx.x * 7 + 3 + k] = smax[k][0]; }
+        part[blockIdx.x * 7 + 6] = bad ? 1.0 : 0.0;
+    }
 }
 
 // root cube: lo = componentwise min, side = max_k (hi_k - lo_k), scale = 2^B / side
 __global__ void k_bbox_final(const double *part, int nblk, int d, int B, Geom *g) {
     if (threadIdx.x != 0) return;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nblk; b++)
-        for (int k = 0; k < 3; k++) { lo[k] = fmin(lo[k], part[b * 6 + k]); hi[k] = fmax(hi[k], part[b * 6 + 3 + k]); }
+    int bad = 0;
+    for (int b = 0; b < nblk; b++) {
+        for (int k = 0; k < 3; k++) { lo[k] = fmin(lo[k], part[b * 7 + k]); hi[k] = fmax(hi[k], part[b * 7 + 3 + k]); }
+        bad |= part[b * 7 + 6] != 0.0;
+    }
     double side = 0.0;
     for (int k = 0; k < 3; k++) {
         g->lo[k] = k < d ? lo[k] : 0.0;
@@ -52,6 +60,7 @@ __global__ void k_bbox_final(const double *part, int nblk, int d, int B, Geom *g
     }
     g->side = side;
     g->scale = side > 0.0 ? __ddiv_rn(ldexp(1.0, B), side) : 0.0;
+    g->nonfinite = bad;
 }
 
 // quantise c = min(floor((x - lo) * scale), 2^B - 1) and interleave the bits,
@@ -174,14 +183,20 @@ __global__ void k_rel_coords(const int32_t *nchild, const int32_t *begin, const 
     }
 }
 
-// float32 coordinates relative to the root box corner (DataReduct's float32 filters)
+// coordinates relative to the root box corner as float32 {hi, lo} pairs:
+// hi = fl32(x - lo), lo = fl32((x - lo) - hi) (DataReduct's float32 search)
+__device__ __forceinline__ float2 h2_split(double v) {
+    float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
 __global__ void k_root_coords(const double *x0, const double *x1, const double *x2, int64_t n, int d, const Geom *g,
-                              float *r0, float *r1, float *r2) {
+                              float2 *r0, float2 *r1, float2 *r2) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    r0[p] = (float)(x0[p] - g->lo[0]);
-    if (d > 1) r1[p] = (float)(x1[p] - g->lo[1]);
-    if (d > 2) r2[p] = (float)(x2[p] - g->lo[2]);
+    r0[p] = h2_split(x0[p] - g->lo[0]);
+    if (d > 1) r1[p] = h2_split(x1[p] - g->lo[1]);
+    if (d > 2) r2[p] = h2_split(x2[p] - g->lo[2]);
 }
 
 __global__ void k_max_leaf(const int32_t *nchild, const int32_t *begin, const int32_t *end, int nn, int32_t *mx) {
@@ -306,7 +321,7 @@ void tree_build_impl(h2_tree_s *t, const double *pts) {
     // root box
     int nblk = (int)std::min<int64_t>(1024, (n + BBOX_THREADS - 1) / BBOX_THREADS);
     DevBuf<double> part;
-    part.alloc((size_t)nblk * 6, s);
+    part.alloc((size_t)nblk * 7, s);
     DevBuf<Geom> g;
     g.alloc(1, s);
     k_bbox_partial<<<nblk, BBOX_THREADS, 0, s>>>(pts, n, d, part.p);
@@ -328,6 +343,7 @@ void tree_build_impl(h2_tree_s *t, const double *pts) {
                                                         t->iperm.p);
     H2_LAUNCH("k_gather_coords");
     t->geom = read_scalar(g.p, s);
+    if (t->geom.nonfinite) fail(H2_ERR_NUMERIC, "point coordinates must be finite");
     // levels: split every node holding more than q points into its non-empty orthants
     size_t cap = 1024;
     t->level.alloc(cap, s); t->parent.alloc(cap, s); t->fchild.alloc(cap, s); t->nchild.alloc(cap, s);

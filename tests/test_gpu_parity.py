@@ -62,20 +62,39 @@ def test_tree_and_lists_bit_exact(H2, name, make, q):
 
 
 HIDR_CASES = [("cube3d", 3, 6000, 60, 4, 5), ("gmix2d", 2, 8000, 30, 6, 7), ("cube3d_g2", 3, 3000, 20, 2, 3),
-              # sets of tens of thousands of points: the pruned nearest-point search
+              # sets of tens of thousands of points: the binned search with many points per cell
               ("cube3d_big", 3, 40000, 64, 5, 6),
               # points snapped to a lattice: many exact distance ties between labels
-              ("lattice3d", 3, 20000, 32, 4, 4)]
+              ("lattice3d", 3, 20000, 32, 4, 4),
+              # grids of 65^2 points, above the binned search's limit: the brute-force sweep
+              ("square2d_g65", 2, 40000, 2600, 65, 65), ("lattice2d_g65", 2, 40000, 2600, 65, 65),
+              # one coordinate constant everywhere: a flat dimension in every box
+              ("plane3d", 3, 20000, 64, 4, 5),
+              # 3000 identical points: a chain of cells down to the deepest level, boxes of size 0
+              ("same3d", 3, 3400, 64, 3, 3)]
+
+
+def _hidr_points(name, d, n):
+    if name == "lattice3d":
+        return np.round(I.uniform_cube(n, d, seed=12) * 16.0) / 16.0
+    if name == "square2d_g65":
+        return I.uniform_cube(n, d, seed=13)
+    if name == "lattice2d_g65":
+        return np.round(I.uniform_cube(n, d, seed=14) * 32.0) / 32.0
+    if name == "plane3d":
+        p = I.uniform_cube(n, d, seed=15)
+        p[:, 2] = 0.5
+        return p
+    if name == "same3d":
+        return np.concatenate([np.tile([[0.1, 0.2, 0.3]], (3000, 1)), I.uniform_cube(n - 3000, d, seed=16)])
+    if "cube" in name:
+        return I.uniform_cube(n, d, seed=10 + d)
+    return I.gaussian_mixture(n, seed=11)
 
 
 @pytest.mark.parametrize("name,d,n,q,g1,g2", HIDR_CASES, ids=[c[0] for c in HIDR_CASES])
 def test_hidr_bit_exact(H2, name, d, n, q, g1, g2):
-    if name == "lattice3d":
-        pts = np.round(I.uniform_cube(n, d, seed=12) * 16.0) / 16.0
-    elif "cube" in name:
-        pts = I.uniform_cube(n, d, seed=10 + d)
-    else:
-        pts = I.gaussian_mixture(n, seed=11)
+    pts = _hidr_points(name, d, n)
     t = H2.Tree(dev(pts), q)
     h = H2.Hidr(t, g1, g2)
     o = O.tree_build(pts, q)
@@ -177,6 +196,19 @@ def test_handle_lifetimes(H2):
     assert st == 7  # tree has dependents
     A.free()
     h.free()
+    t.free()
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_nonfinite_points_rejected(H2, bad):
+    pts = I.uniform_cube(3000, 3, seed=42)
+    pts[1234, 1] = bad
+    with pytest.raises(H2.H2Error) as e:
+        H2.Tree(dev(pts), 50)
+    assert e.value.status == 5 and "finite" in str(e.value)  # H2_ERR_NUMERIC
+    # the context stays usable
+    t = H2.Tree(dev(np.nan_to_num(pts, posinf=0.5, neginf=0.5, nan=0.5)), 50)
+    assert t.get("perm").shape == (3000,)
     t.free()
 
 

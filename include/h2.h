@@ -148,7 +148,7 @@ h2_status h2_calibrate(int dim, int kernel, const double *kparams, double eps,
  * Morton position) to each cell-centred point of a g^d tensor grid on the
  * bounding box of S, deduplicated.  Sets are stored as sorted Morton
  * positions.  Kernel-independent: one hidr serves every kernel.
- * g1, g2 >= 1 (g^dim <= 32768).  Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM,
+ * g1, g2 >= 1 (g^dim <= 16384).  Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM,
  * H2_ERR_CUDA. */
 h2_status h2_hidr_reduce(h2_tree t, int g1, int g2, void *stream, h2_hidr *out);
 
@@ -189,15 +189,27 @@ enum { H2_MAT_RANK = 0, H2_MAT_NCAND = 1, H2_MAT_SKEL = 2, H2_MAT_U = 3, H2_MAT_
 h2_status h2_matrix_get(h2_matrix A, int what, void *host_buf, int64_t cap, int64_t *len);
 
 /* -------------------------------------------------------------- matvec --- */
-/* y = K~ x with the H^2 representation (section 2.1): upward pass
- * xh_i = U_i^T x_i (leaves) and xh_p = U_p^T [xh_c ...] (parents); coupling
- * zh_i = sum_{j far from i} K(Xhat_i, Xhat_j) xh_j; downward pass
- * [zh_c ...] += U_p zh_p and y_i = U_i zh_i; nearfield y_i += K(X_i, X_j) x_j
- * over near leaf pairs.  x, y: n float64 in the original point order (device
- * pointers if on_device, else host; host buffers are copied in and out on
- * `stream` and the call synchronises).  x and y must not overlap.
- * Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
-h2_status h2_matvec(h2_matrix A, const double *x, double *y, int on_device, void *stream);
+/* element type of h2_matvec's vectors */
+enum { H2_DTYPE_F64 = 0, H2_DTYPE_F32 = 1 };
+
+/* Y = K~ X for nrhs right-hand sides with the H^2 representation (section
+ * 2.1): upward pass xh_i = U_i^T x_i (leaves) and xh_p = U_p^T [xh_c ...]
+ * (parents); coupling zh_i = sum_{j far from i} K(Xhat_i, Xhat_j) xh_j;
+ * downward pass [zh_c ...] += U_p zh_p and y_i = U_i zh_i; nearfield
+ * y_i += K(X_i, X_j) x_j over near leaf pairs.  Every kernel evaluation serves
+ * all right-hand sides.
+ *   x, y   column-major n x nrhs in the original point order: entry (i, j) at
+ *          x[i + j * ld]; elements of `dtype` (H2_DTYPE_F64 or H2_DTYPE_F32);
+ *          device pointers if on_device, else host (then copied in and out
+ *          on `stream` and the call synchronises; entries of y between
+ *          columns are left untouched).  x and y must not overlap.
+ *   nrhs   >= 1; ld >= n.
+ * The arithmetic follows the matrix's precision (float64, or float32 kernel
+ * evaluations with float64 or compensated float32 accumulation); dtype only
+ * sets the element type of x and y.
+ * Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM, H2_ERR_CUDA, H2_ERR_UNIMPLEMENTED. */
+h2_status h2_matvec(h2_matrix A, const void *x, void *y, int nrhs, int dtype, int64_t ld, int on_device,
+                    void *stream);
 
 /* ---------------------------------------------------------- exact rows --- */
 /* The reference of the section 6 error ||K z - K~ z|| / ||K z||: for each

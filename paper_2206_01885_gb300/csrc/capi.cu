@@ -310,22 +310,37 @@ h2_status h2_matrix_get(h2_matrix ah, int what, void *buf, int64_t cap, int64_t 
     });
 }
 
-h2_status h2_matvec(h2_matrix ah, const double *x, double *y, int on_device, void *stream) {
+h2_status h2_matvec(h2_matrix ah, const void *x, void *y, int nrhs, int dtype, int64_t ld, int on_device,
+                    void *stream) {
     return guard([&] {
         h2_matrix_s *A = as_matrix(ah);
         H2_REQUIRE(x != nullptr && y != nullptr, "x or y is NULL");
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        H2_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+        H2_REQUIRE(dtype == H2_DTYPE_F64 || dtype == H2_DTYPE_F32, "dtype must be H2_DTYPE_F64 or H2_DTYPE_F32");
         const int64_t n = A->tree->n;
+        H2_REQUIRE(ld >= n, "ld must be >= n");
+        const size_t es = dtype == H2_DTYPE_F64 ? sizeof(double) : sizeof(float);
+        const size_t span = ((size_t)(nrhs - 1) * (size_t)ld + (size_t)n) * es;
+        const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
+        H2_REQUIRE(xb + span <= yb || yb + span <= xb, "x and y overlap");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const bool single = nrhs == 1 && dtype == H2_DTYPE_F64;
         if (on_device) {
-            matvec_impl(A, x, y, s);
+            if (single)
+                matvec_impl(A, static_cast<const double *>(x), static_cast<double *>(y), s);
+            else
+                matvec_multi_impl(A, x, y, nrhs, dtype, ld, s);
             return;
         }
-        DevBuf<double> xd, yd;
-        xd.alloc(n, s);
-        yd.alloc(n, s);
-        H2_CUDA(cudaMemcpyAsync(xd.p, x, n * sizeof(double), cudaMemcpyHostToDevice, s));
-        matvec_impl(A, xd.p, yd.p, s);
-        H2_CUDA(cudaMemcpyAsync(y, yd.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DevBuf<char> xd, yd;
+        xd.alloc((size_t)n * nrhs * es, s);
+        yd.alloc((size_t)n * nrhs * es, s);
+        H2_CUDA(cudaMemcpy2DAsync(xd.p, n * es, x, ld * es, n * es, nrhs, cudaMemcpyHostToDevice, s));
+        if (single)
+            matvec_impl(A, reinterpret_cast<const double *>(xd.p), reinterpret_cast<double *>(yd.p), s);
+        else
+            matvec_multi_impl(A, xd.p, yd.p, nrhs, dtype, n, s);
+        H2_CUDA(cudaMemcpy2DAsync(y, ld * es, yd.p, n * es, n * es, nrhs, cudaMemcpyDeviceToHost, s));
         H2_CUDA(cudaStreamSynchronize(s));
     });
 }

@@ -154,6 +154,7 @@ struct h2_tree_s {
     h2::DevBuf<double> cen[3];    // cell centre of every node
     h2::DevBuf<float> xr[3];      // point coordinates relative to their leaf's centre (float32 kernels)
     h2::DevBuf<float2> xg[3];     // x - root corner split into float32 hi + lo (DataReduct's float32 search)
+    h2::DevBuf<float2> cenf[3];   // cell centre - root corner split into float32 hi + lo (float32 N-body)
     h2::DevBuf<int2> near_tiles;  // (leaf, first target) tiles of the nearfield kernel, built on first use
     int near_tile_tpt = 0;
     h2::DevBuf<int64_t> leaf_start;  // begin of every node as int64 (nearfield point sets)
@@ -212,6 +213,9 @@ void lists_build_impl(h2_tree_s *t);
 void hidr_impl(h2_hidr_s *h);
 void construct_impl(h2_matrix_s *A, h2_hidr_s *h);
 void matvec_impl(h2_matrix_s *A, const double *x_dev, double *y_dev, cudaStream_t s);
+// nrhs columns, x and y column-major with leading dimension ld (device)
+void matvec_multi_impl(h2_matrix_s *A, const void *x_dev, void *y_dev, int nrhs, int dtype, int64_t ld,
+                       cudaStream_t s);
 void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z_dev, const int64_t *rows_dev,
                      int64_t nrows, double *out_dev, cudaStream_t s);
 

@@ -33,11 +33,6 @@ __global__ void k_to_float(const double *a, int64_t n, float *b) {
     if (p < n) b[p] = (float)a[p];
 }
 
-__global__ void k_perm_out(const double *ym, const int32_t *perm, int64_t n, double *y) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < n) y[perm[p]] = ym[p];
-}
-
 // xh_i[a] = sum_r U_i[r, a] in[r]; one CTA per node, one warp per column,
 // float64 accumulation (U is float64 or float32)
 template <class UT>
@@ -93,84 +88,14 @@ __device__ __forceinline__ double kap(double r2, double p) {  // p: 1/h^2 (Gauss
 }
 template <int KID>
 __device__ __forceinline__ float kap(float r2, float p) {
-    if constexpr (KID == H2_K_COULOMB) return r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    if constexpr (KID == H2_K_COULOMB) {
+        float y;
+        asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(r2));  // relative error below 2^-22
+        return r2 > 0.0f ? y : 0.0f;
+    }
     else if constexpr (KID == H2_K_GAUSSIAN) return __expf(-r2 * p);
     else if constexpr (KID == H2_K_EXPONENTIAL) return __expf(-sqrtf(r2) * p);
     else return sqrtf(1.0f + r2);
-}
-
-// Tiled N-body accumulation out[t] += sum_s kappa(x_t, x_s) w_s.  A point set
-// of node i is [start[i], start[i] + count[i]) of the coordinate arrays; one
-// CTA takes the 32*TPT targets of one tile of node i, its warps split the
-// source blocks j of the list lidx[lptr[i] .. lptr[i+1]) and every lane reads
-// each source point as a broadcast load.  Real = double: absolute float64
-// coordinates.  Real = float: float32 coordinates relative to each node's cell
-// centre, the centre offset added per block pair in float64 first; each block's
-// float32 sum is added into a float64 accumulator.
-template <class Real, int KID, int TPT>
-__global__ void __launch_bounds__(NB_WARPS * 32)
-    k_nbody(const int2 *tiles, const int64_t *start, const int32_t *count, const Real *X0, const Real *X1,
-            const Real *X2, const double *C0, const double *C1, const double *C2, const Real *w, double *out,
-            const int64_t *lptr, const int32_t *lidx, int d, double kpar) {
-    __shared__ double part[NB_WARPS][32 * TPT];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int2 tl = tiles[blockIdx.x];
-    const int i = tl.x;
-    const int64_t ts = start[i];
-    const int tn = count[i];
-    const Real p = (Real)kpar;
-    Real tx[TPT][3];
-    double acc[TPT];
-#pragma unroll
-    for (int u = 0; u < TPT; u++) {
-        int a = tl.y + u * 32 + lane;
-        bool ok = a < tn;
-        tx[u][0] = ok ? X0[ts + a] : (Real)0;
-        tx[u][1] = ok && d > 1 ? X1[ts + a] : (Real)0;
-        tx[u][2] = ok && d > 2 ? X2[ts + a] : (Real)0;
-        acc[u] = 0.0;
-    }
-    for (int64_t e = lptr[i] + warp; e < lptr[i + 1]; e += NB_WARPS) {
-        const int j = lidx[e];
-        const int64_t ss = start[j];
-        const int sn = count[j];
-        Real sh[TPT][3];
-        if constexpr (sizeof(Real) == 4) {  // target coordinates in node j's frame
-            float o0 = (float)(C0[i] - C0[j]), o1 = d > 1 ? (float)(C1[i] - C1[j]) : 0.f,
-                  o2 = d > 2 ? (float)(C2[i] - C2[j]) : 0.f;
-#pragma unroll
-            for (int u = 0; u < TPT; u++) { sh[u][0] = tx[u][0] + o0; sh[u][1] = tx[u][1] + o1; sh[u][2] = tx[u][2] + o2; }
-        } else {
-#pragma unroll
-            for (int u = 0; u < TPT; u++) { sh[u][0] = tx[u][0]; sh[u][1] = tx[u][1]; sh[u][2] = tx[u][2]; }
-        }
-        Real blk[TPT];
-#pragma unroll
-        for (int u = 0; u < TPT; u++) blk[u] = (Real)0;
-        for (int q = 0; q < sn; q++) {
-            const Real a0 = X0[ss + q], a1 = d > 1 ? X1[ss + q] : (Real)0, a2 = d > 2 ? X2[ss + q] : (Real)0;
-            const Real ws = w[ss + q];
-#pragma unroll
-            for (int u = 0; u < TPT; u++) {
-                Real dx = sh[u][0] - a0, dy = sh[u][1] - a1, dz = sh[u][2] - a2;
-                Real r2 = dx * dx + dy * dy + dz * dz;
-                blk[u] += kap<KID>(r2, p) * ws;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < TPT; u++) acc[u] += (double)blk[u];
-    }
-#pragma unroll
-    for (int u = 0; u < TPT; u++) part[warp][u * 32 + lane] = acc[u];
-    __syncthreads();
-    for (int t = threadIdx.x; t < 32 * TPT; t += blockDim.x) {
-        int a = tl.y + t;
-        if (a < tn) {
-            double sum = 0.0;
-            for (int wv = 0; wv < NB_WARPS; wv++) sum += part[wv][t];
-            out[ts + a] += sum;
-        }
-    }
 }
 
 // out[r] = sum_q kappa(x_s, x_q) z_q for s = rows[r]; one CTA per row
@@ -242,49 +167,252 @@ void build_tiles(const std::vector<int32_t> &cnt, const std::vector<int64_t> &lp
     tiles.n = v.size();
 }
 
-template <class Real, int KID, int TPT>
-void nbody_launch(const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
-                  const Real *X1, const Real *X2, const double *C0, const double *C1, const double *C2, const Real *w,
-                  double *out, const int64_t *lptr, const int32_t *lidx, int d, double kpar, cudaStream_t s) {
-    if (tiles.n == 0) return;
-    k_nbody<Real, KID, TPT><<<(unsigned)tiles.n, NB_WARPS * 32, 0, s>>>(tiles.p, start, count, X0, X1, X2, C0, C1,
-                                                                       C2, w, out, lptr, lidx, d, kpar);
-    H2_LAUNCH("k_nbody");
+// ------------------------------------------------------------ several RHS
+// Inside, R right-hand sides are stored point-major: entry (p, j) at p*R + j.
+
+template <class T>
+__global__ void k_perm_in_multi(const T *x, int64_t ld, const int32_t *perm, int64_t n, int R, double *xm) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * R) return;
+    int64_t p = t / R;
+    int j = (int)(t - p * R);
+    xm[t] = (double)x[perm[p] + j * ld];
 }
 
-template <class Real, int TPT>
-void nbody_dispatch(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
-                    const Real *X1, const Real *X2, const double *C0, const double *C1, const double *C2,
-                    const Real *w, double *out, const int64_t *lptr, const int32_t *lidx, int d, double kp0,
-                    cudaStream_t s) {
-    switch (kid) {
-    case H2_K_COULOMB:
-        nbody_launch<Real, H2_K_COULOMB, TPT>(tiles, start, count, X0, X1, X2, C0, C1, C2, w, out, lptr, lidx, d,
-                                              0.0, s);
-        break;
-    case H2_K_GAUSSIAN:
-        nbody_launch<Real, H2_K_GAUSSIAN, TPT>(tiles, start, count, X0, X1, X2, C0, C1, C2, w, out, lptr, lidx, d,
-                                               1.0 / (kp0 * kp0), s);
-        break;
-    case H2_K_EXPONENTIAL:
-        nbody_launch<Real, H2_K_EXPONENTIAL, TPT>(tiles, start, count, X0, X1, X2, C0, C1, C2, w, out, lptr, lidx,
-                                                  d, 1.0 / kp0, s);
-        break;
-    default:
-        nbody_launch<Real, H2_K_MULTIQUADRIC, TPT>(tiles, start, count, X0, X1, X2, C0, C1, C2, w, out, lptr, lidx,
-                                                   d, 0.0, s);
+template <class T>
+__global__ void k_perm_out_multi(const double *ym, const int32_t *perm, int64_t n, int R, T *y, int64_t ld) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * R) return;
+    int64_t p = t / R;
+    int j = (int)(t - p * R);
+    y[perm[p] + j * ld] = (T)ym[t];
+}
+
+// xh_i[a, j] = sum_r U_i[r, a] in[r, j]; one CTA per node, a thread per (a, j)
+template <class UT>
+__global__ void k_upward_multi(int lb, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
+                               const int32_t *kk, const int32_t *cc, void *const *uptr, const int64_t *sk_off,
+                               const double *xm, double *xh, int R) {
+    const int i = lb + blockIdx.x;
+    const int k = kk[i], c = cc[i];
+    if (k == 0) return;
+    const double *in = nchild[i] == 0 ? xm + (int64_t)begin[i] * R : xh + sk_off[fchild[i]] * R;
+    const UT *U = static_cast<const UT *>(uptr[i]);
+    double *o = xh + sk_off[i] * R;
+    for (int t = threadIdx.x; t < k * R; t += blockDim.x) {
+        const int a = t / R, j = t - a * R;
+        const UT *col = U + (int64_t)a * c;
+        double s = 0.0;
+        for (int r = 0; r < c; r++) s += (double)col[r] * in[(int64_t)r * R + j];
+        o[t] = s;
     }
 }
 
-constexpr int TPT_F64 = 1, TPT_F32 = 4;
+// out[r, j] += sum_a U_i[r, a] zh_i[a, j], into the children's zh (parent) or y (leaf)
+template <class UT>
+__global__ void k_downward_multi(int lb, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
+                                 const int32_t *kk, const int32_t *cc, void *const *uptr, const int64_t *sk_off,
+                                 double *zh, double *ym, int R) {
+    const int i = lb + blockIdx.x;
+    const int k = kk[i], c = cc[i];
+    if (k == 0) return;
+    const double *z = zh + sk_off[i] * R;
+    const UT *U = static_cast<const UT *>(uptr[i]);
+    double *out = nchild[i] == 0 ? ym + (int64_t)begin[i] * R : zh + sk_off[fchild[i]] * R;
+    for (int t = threadIdx.x; t < c * R; t += blockDim.x) {
+        const int r = t / R, j = t - r * R;
+        double s = 0.0;
+        for (int a = 0; a < k; a++) s += (double)U[r + (int64_t)a * c] * z[(int64_t)a * R + j];
+        out[t] += s;
+    }
+}
 
-}  // namespace
+// Error-free sum of a + b (Knuth's TwoSum); the rounding error goes into e.
+__device__ __forceinline__ void two_sum_acc(float &a, float &e, float b) {
+    const float s = a + b, bp = s - a;
+    e += (a - (s - bp)) + (b - bp);
+    a = s;
+}
 
-void matvec_impl(h2_matrix_s *A, const double *x, double *y, cudaStream_t s) {
-    h2_tree_s *t = A->tree;
-    const int nn = t->nnodes, d = t->d;
-    const int64_t n = t->n;
-    const bool f64 = A->prec == H2_PREC_FP64;
+// Tiled N-body accumulation for R right-hand sides at once:
+//   out[t, j] += sum_s kappa(x_t, x_s) w[s, j]
+// (w and out with row strides ws and os).  The point set of node i is
+// [start[i], start[i] + count[i]) of the coordinate arrays.  One CTA takes a
+// tile of 32 * TPT targets of node i (TPT per lane); its warps split the source
+// blocks j of the list lidx[lptr[i] .. lptr[i+1]), and each warp stages 32
+// source points at a time (coordinates and R weights) in shared memory, read
+// back as broadcasts, so one kernel evaluation feeds R fused multiply-adds.
+// Real = double: absolute float64 coordinates, float64 sums.  Real = float:
+// coordinates relative to each node's cell centre, the centre offset added per
+// block pair from the centres' float32 {hi, lo} splits, each block's float32
+// sums folded into compensated float32 accumulators.
+template <class Real, int KID, int R, int TPT>
+__global__ void __launch_bounds__(NB_WARPS * 32)
+    k_nbody(const int2 *tiles, const int64_t *start, const int32_t *count, const Real *X0, const Real *X1,
+            const Real *X2, const float2 *F0, const float2 *F1, const float2 *F2, const Real *w, int ws, double *out,
+            int os, const int64_t *lptr, const int32_t *lidx, int d, double kpar) {
+    constexpr int RW = (int)((((4 + R) * sizeof(Real) + 15) / 16 * 16) / sizeof(Real));
+    constexpr size_t STG = sizeof(Real) * NB_WARPS * 32 * RW, PART = sizeof(double) * NB_WARPS * 32 * TPT * R;
+    __shared__ __align__(16) unsigned char sraw[STG > PART ? STG : PART];
+    Real(*stg)[32][RW] = reinterpret_cast<Real(*)[32][RW]>(sraw);
+    double(*part)[32 * TPT][R] = reinterpret_cast<double(*)[32 * TPT][R]>(sraw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int2 tl = tiles[blockIdx.x];
+    const int i = tl.x;
+    const int64_t ts = start[i];
+    const int tn = count[i];
+    const Real p = (Real)kpar;
+    Real tx[TPT][3], acc[TPT][R], cmp[TPT][R];
+#pragma unroll
+    for (int u = 0; u < TPT; u++) {
+        const int a = tl.y + u * 32 + lane;
+        const bool ok = a < tn;
+        tx[u][0] = ok ? X0[ts + a] : (Real)0;
+        tx[u][1] = ok && d > 1 ? X1[ts + a] : (Real)0;
+        tx[u][2] = ok && d > 2 ? X2[ts + a] : (Real)0;
+#pragma unroll
+        for (int j = 0; j < R; j++) { acc[u][j] = (Real)0; cmp[u][j] = (Real)0; }
+    }
+    for (int64_t e = lptr[i] + warp; e < lptr[i + 1]; e += NB_WARPS) {
+        const int jn = lidx[e];
+        const int64_t ss = start[jn];
+        const int sn = count[jn];
+        Real o0 = (Real)0, o1 = (Real)0, o2 = (Real)0;
+        if constexpr (sizeof(Real) == 4) {  // target coordinates in node jn's frame
+            const float2 a0 = F0[i], b0 = F0[jn];
+            o0 = (a0.x - b0.x) + (a0.y - b0.y);
+            if (d > 1) {
+                const float2 a1 = F1[i], b1 = F1[jn];
+                o1 = (a1.x - b1.x) + (a1.y - b1.y);
+            }
+            if (d > 2) {
+                const float2 a2 = F2[i], b2 = F2[jn];
+                o2 = (a2.x - b2.x) + (a2.y - b2.y);
+            }
+        }
+        Real sh[TPT][3], blk[TPT][R];
+#pragma unroll
+        for (int u = 0; u < TPT; u++) {
+            sh[u][0] = tx[u][0] + o0;
+            sh[u][1] = tx[u][1] + o1;
+            sh[u][2] = tx[u][2] + o2;
+#pragma unroll
+            for (int j = 0; j < R; j++) blk[u][j] = (Real)0;
+        }
+        for (int q0 = 0; q0 < sn; q0 += 32) {
+            const int cnt = min(32, sn - q0);
+            __syncwarp();
+            if (lane < cnt) {
+                const int64_t sp = ss + q0 + lane;
+                stg[warp][lane][0] = X0[sp];
+                stg[warp][lane][1] = d > 1 ? X1[sp] : (Real)0;
+                stg[warp][lane][2] = d > 2 ? X2[sp] : (Real)0;
+            }
+            for (int e2 = lane; e2 < cnt * R; e2 += 32) {
+                const int r = e2 / R, c = e2 - r * R;
+                stg[warp][r][4 + c] = w[(ss + q0 + r) * (int64_t)ws + c];
+            }
+            __syncwarp();
+            for (int q = 0; q < cnt; q++) {
+                const Real *row = stg[warp][q];
+                const Real a0 = row[0], a1 = row[1], a2 = row[2];
+#pragma unroll
+                for (int u = 0; u < TPT; u++) {
+                    const Real dx = sh[u][0] - a0, dy = sh[u][1] - a1, dz = sh[u][2] - a2;
+                    const Real kv = kap<KID>(dx * dx + dy * dy + dz * dz, p);
+#pragma unroll
+                    for (int j = 0; j < R; j++) blk[u][j] += kv * row[4 + j];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TPT; u++)
+#pragma unroll
+            for (int j = 0; j < R; j++) {
+                if constexpr (sizeof(Real) == 8) acc[u][j] += blk[u][j];
+                else two_sum_acc(acc[u][j], cmp[u][j], blk[u][j]);
+            }
+    }
+    __syncthreads();  // every warp is done with its staging area before it becomes part[]
+#pragma unroll
+    for (int u = 0; u < TPT; u++)
+#pragma unroll
+        for (int j = 0; j < R; j++) part[warp][u * 32 + lane][j] = (double)acc[u][j] + (double)cmp[u][j];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * TPT * R; t += blockDim.x) {
+        const int l = t / R, j = t - l * R;
+        const int aa = tl.y + l;
+        if (aa < tn) {
+            double sum = 0.0;
+            for (int wv = 0; wv < NB_WARPS; wv++) sum += part[wv][l][j];
+            out[(ts + aa) * (int64_t)os + j] += sum;
+        }
+    }
+}
+
+template <class Real, int R, int TPT>
+void nbody_kid(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
+               const Real *X1, const Real *X2, const float2 *F0, const float2 *F1, const float2 *F2, const Real *w,
+               int ws, double *out, int os, const int64_t *lptr, const int32_t *lidx, int d, double kp0,
+               cudaStream_t s) {
+    const unsigned nb = (unsigned)tiles.n;
+    switch (kid) {
+    case H2_K_COULOMB:
+        k_nbody<Real, H2_K_COULOMB, R, TPT><<<nb, NB_WARPS * 32, 0, s>>>(tiles.p, start, count, X0, X1, X2, F0, F1,
+                                                                         F2, w, ws, out, os, lptr, lidx, d, 0.0);
+        break;
+    case H2_K_GAUSSIAN:
+        k_nbody<Real, H2_K_GAUSSIAN, R, TPT><<<nb, NB_WARPS * 32, 0, s>>>(
+            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, ws, out, os, lptr, lidx, d, 1.0 / (kp0 * kp0));
+        break;
+    case H2_K_EXPONENTIAL:
+        k_nbody<Real, H2_K_EXPONENTIAL, R, TPT><<<nb, NB_WARPS * 32, 0, s>>>(
+            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, ws, out, os, lptr, lidx, d, 1.0 / kp0);
+        break;
+    default:
+        k_nbody<Real, H2_K_MULTIQUADRIC, R, TPT><<<nb, NB_WARPS * 32, 0, s>>>(
+            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, ws, out, os, lptr, lidx, d, 0.0);
+    }
+    H2_LAUNCH("k_nbody");
+}
+
+// all nrhs columns, in launches of 16, 8, 4, 2 and 1 columns; tiles hold 32
+// targets (one a lane: skeletons of a few dozen points fill whole tiles)
+template <class Real>
+void nbody(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
+           const Real *X1, const Real *X2, const float2 *F0, const float2 *F1, const float2 *F2, const Real *w,
+           double *out, int nrhs, const int64_t *lptr, const int32_t *lidx, int d, double kp0, cudaStream_t s) {
+    if (tiles.n == 0) return;
+    for (int c0 = 0; c0 < nrhs;) {
+        const int left = nrhs - c0;
+        const Real *wc = w + c0;
+        double *oc = out + c0;
+        if (left >= 16) {
+            nbody_kid<Real, 16, 1>(kid, tiles, start, count, X0, X1, X2, F0, F1, F2, wc, nrhs, oc, nrhs, lptr, lidx,
+                                   d, kp0, s);
+            c0 += 16;
+        } else if (left >= 8) {
+            nbody_kid<Real, 8, 1>(kid, tiles, start, count, X0, X1, X2, F0, F1, F2, wc, nrhs, oc, nrhs, lptr, lidx, d,
+                                  kp0, s);
+            c0 += 8;
+        } else if (left >= 4) {
+            nbody_kid<Real, 4, 1>(kid, tiles, start, count, X0, X1, X2, F0, F1, F2, wc, nrhs, oc, nrhs, lptr, lidx, d,
+                                  kp0, s);
+            c0 += 4;
+        } else if (left >= 2) {
+            nbody_kid<Real, 2, 1>(kid, tiles, start, count, X0, X1, X2, F0, F1, F2, wc, nrhs, oc, nrhs, lptr, lidx, d,
+                                  kp0, s);
+            c0 += 2;
+        } else {
+            nbody_kid<Real, 1, 1>(kid, tiles, start, count, X0, X1, X2, F0, F1, F2, wc, nrhs, oc, nrhs, lptr, lidx, d,
+                                  kp0, s);
+            c0 += 1;
+        }
+    }
+}
+
+// the upward/downward kernels' shared-memory opt-in, once per process
+void set_matvec_attrs() {
     static bool attr = false;
     if (!attr) {
         for (auto f : {(const void *)k_upward<double>, (const void *)k_upward<float>, (const void *)k_downward<double>,
@@ -292,11 +420,13 @@ void matvec_impl(h2_matrix_s *A, const double *x, double *y, cudaStream_t s) {
             H2_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr = true;
     }
-    for (int l = 1; l < t->nlevels; l++)
-        if ((size_t)A->cmax_level[l] * sizeof(double) > 200 * 1024)
-            fail(H2_ERR_UNIMPLEMENTED, "candidate set too large for the single-CTA upward pass");
-    const int tpt = f64 ? TPT_F64 : TPT_F32;
-    // tiles of the coupling (per matrix) and nearfield (per tree) kernels, built once
+}
+
+// tiles of the coupling (per matrix) and nearfield (per tree) kernels for
+// 32 * tpt targets a tile, built on first use and rebuilt when tpt changes
+void prepare_tiles(h2_matrix_s *A, int tpt, cudaStream_t s) {
+    h2_tree_s *t = A->tree;
+    const int nn = t->nnodes;
     if (A->far_tile_tpt != tpt) {
         std::vector<int32_t> kh = read_vec(A->k.p, nn, s);
         std::vector<int64_t> fp = read_vec(t->far_ptr.p, nn + 1, s);
@@ -322,79 +452,124 @@ void matvec_impl(h2_matrix_s *A, const double *x, double *y, cudaStream_t s) {
             H2_CUDA(cudaStreamSynchronize(s));
         }
     }
+}
+
+}  // namespace
+
+void matvec_impl(h2_matrix_s *A, const double *x, double *y, cudaStream_t s) {
+    matvec_multi_impl(A, x, y, 1, H2_DTYPE_F64, A->tree->n, s);
+}
+
+void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype, int64_t ld, cudaStream_t s) {
+    h2_tree_s *t = A->tree;
+    const int d = t->d;
+    const int64_t n = t->n, nr = n * R;
+    const bool f64 = A->prec == H2_PREC_FP64;
+    if (R == 1) {  // one column: the single-CTA shared-memory upward and downward kernels
+        set_matvec_attrs();
+        for (int l = 1; l < t->nlevels; l++)
+            if ((size_t)A->cmax_level[l] * sizeof(double) > 200 * 1024)
+                fail(H2_ERR_UNIMPLEMENTED, "candidate set too large for the single-CTA upward pass");
+    }
+    prepare_tiles(A, 1, s);
+    const int64_t kt = std::max<int64_t>(A->ktotal, 1);
     DevBuf<double> xm, ym, xh, zh;
-    xm.alloc(n, s);
-    ym.alloc(n, s);
-    int64_t kt = std::max<int64_t>(A->ktotal, 1);
-    xh.alloc(kt, s);
-    zh.alloc(kt, s);
-    H2_CUDA(cudaMemsetAsync(ym.p, 0, n * sizeof(double), s));
-    H2_CUDA(cudaMemsetAsync(zh.p, 0, kt * sizeof(double), s));
-    k_perm_in<<<blocks_for(n, 256), 256, 0, s>>>(x, t->perm.p, n, xm.p);
-    H2_LAUNCH("k_perm_in");
+    xm.alloc(nr, s);
+    ym.alloc(nr, s);
+    xh.alloc(kt * R, s);
+    zh.alloc(kt * R, s);
+    H2_CUDA(cudaMemsetAsync(ym.p, 0, nr * sizeof(double), s));
+    H2_CUDA(cudaMemsetAsync(zh.p, 0, kt * R * sizeof(double), s));
+    if (dtype == H2_DTYPE_F64)
+        k_perm_in_multi<double><<<blocks_for(nr, 256), 256, 0, s>>>(static_cast<const double *>(x), ld, t->perm.p,
+                                                                     n, R, xm.p);
+    else
+        k_perm_in_multi<float><<<blocks_for(nr, 256), 256, 0, s>>>(static_cast<const float *>(x), ld, t->perm.p, n,
+                                                                    R, xm.p);
+    H2_LAUNCH("k_perm_in_multi");
     // upward, deepest level first
     for (int l = t->nlevels - 1; l >= 1; l--) {
         int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
         if (A->kmax_level[l] == 0) continue;
-        size_t sm = (size_t)A->cmax_level[l] * sizeof(double);
         ProfScope ps(KT_UPWARD, s);
-        if (f64)
-            k_upward<double><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
-                                                        A->uptr.p, A->sk_off.p, xm.p, xh.p);
-        else
-            k_upward<float><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
-                                                       A->uptr.p, A->sk_off.p, xm.p, xh.p);
+        if (R == 1) {
+            size_t sm = (size_t)A->cmax_level[l] * sizeof(double);
+            if (f64)
+                k_upward<double><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
+                                                            A->uptr.p, A->sk_off.p, xm.p, xh.p);
+            else
+                k_upward<float><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
+                                                           A->uptr.p, A->sk_off.p, xm.p, xh.p);
+        } else if (f64) {
+            k_upward_multi<double><<<nl, MV_THREADS, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p,
+                                                             A->c.p, A->uptr.p, A->sk_off.p, xm.p, xh.p, R);
+        } else {
+            k_upward_multi<float><<<nl, MV_THREADS, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
+                                                            A->uptr.p, A->sk_off.p, xm.p, xh.p, R);
+        }
         H2_LAUNCH("k_upward");
     }
     // float32 copies of the weights for the float32 N-body kernels
     DevBuf<float> xmf, xhf;
     if (!f64) {
-        xmf.alloc(n, s);
-        xhf.alloc(kt, s);
-        k_to_float<<<blocks_for(n, 256), 256, 0, s>>>(xm.p, n, xmf.p);
-        k_to_float<<<blocks_for(kt, 256), 256, 0, s>>>(xh.p, kt, xhf.p);
+        xmf.alloc(nr, s);
+        xhf.alloc(kt * R, s);
+        k_to_float<<<blocks_for(nr, 256), 256, 0, s>>>(xm.p, nr, xmf.p);
+        k_to_float<<<blocks_for(kt * R, 256), 256, 0, s>>>(xh.p, kt * R, xhf.p);
         H2_LAUNCH("k_to_float");
     }
     // coupling over far pairs: B_ij = K(Xhat_i, Xhat_j) on the fly
     {
         ProfScope ps(KT_COUPLING, s);
         if (f64)
-            nbody_dispatch<double, TPT_F64>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skc[0].p, A->skc[1].p,
-                                            A->skc[2].p, nullptr, nullptr, nullptr, xh.p, zh.p, t->far_ptr.p,
-                                            t->far_idx.p, d, A->kp[0], s);
+            nbody<double>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skc[0].p, A->skc[1].p, A->skc[2].p, nullptr,
+                          nullptr, nullptr, xh.p, zh.p, R, t->far_ptr.p, t->far_idx.p, d, A->kp[0], s);
         else
-            nbody_dispatch<float, TPT_F32>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skr[0].p, A->skr[1].p,
-                                           A->skr[2].p, t->cen[0].p, t->cen[1].p, t->cen[2].p, xhf.p, zh.p,
-                                           t->far_ptr.p, t->far_idx.p, d, A->kp[0], s);
+            nbody<float>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skr[0].p, A->skr[1].p, A->skr[2].p,
+                         t->cenf[0].p, t->cenf[1].p, t->cenf[2].p, xhf.p, zh.p, R, t->far_ptr.p, t->far_idx.p, d,
+                         A->kp[0], s);
     }
     // downward, level 1 first
     for (int l = 1; l < t->nlevels; l++) {
         int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
         if (A->kmax_level[l] == 0) continue;
-        size_t sm = (size_t)A->kmax_level[l] * sizeof(double);
         ProfScope ps(KT_DOWNWARD, s);
-        if (f64)
-            k_downward<double><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
-                                                          A->uptr.p, A->sk_off.p, zh.p, ym.p);
-        else
-            k_downward<float><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p, A->c.p,
-                                                         A->uptr.p, A->sk_off.p, zh.p, ym.p);
+        if (R == 1) {
+            size_t sm = (size_t)A->kmax_level[l] * sizeof(double);
+            if (f64)
+                k_downward<double><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p,
+                                                              A->c.p, A->uptr.p, A->sk_off.p, zh.p, ym.p);
+            else
+                k_downward<float><<<nl, MV_THREADS, sm, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p,
+                                                             A->c.p, A->uptr.p, A->sk_off.p, zh.p, ym.p);
+        } else if (f64) {
+            k_downward_multi<double><<<nl, MV_THREADS, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p,
+                                                               A->c.p, A->uptr.p, A->sk_off.p, zh.p, ym.p, R);
+        } else {
+            k_downward_multi<float><<<nl, MV_THREADS, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->k.p,
+                                                              A->c.p, A->uptr.p, A->sk_off.p, zh.p, ym.p, R);
+        }
         H2_LAUNCH("k_downward");
     }
     // nearfield over near leaf pairs: K(X_i, X_j) on the fly
     {
         ProfScope ps(KT_NEAR, s);
         if (f64)
-            nbody_dispatch<double, TPT_F64>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xs[0].p,
-                                            t->xs[1].p, t->xs[2].p, nullptr, nullptr, nullptr, xm.p, ym.p,
-                                            t->near_ptr.p, t->near_idx.p, d, A->kp[0], s);
+            nbody<double>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xs[0].p, t->xs[1].p,
+                          t->xs[2].p, nullptr, nullptr, nullptr, xm.p, ym.p, R, t->near_ptr.p, t->near_idx.p, d,
+                          A->kp[0], s);
         else
-            nbody_dispatch<float, TPT_F32>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xr[0].p,
-                                           t->xr[1].p, t->xr[2].p, t->cen[0].p, t->cen[1].p, t->cen[2].p, xmf.p, ym.p,
-                                           t->near_ptr.p, t->near_idx.p, d, A->kp[0], s);
+            nbody<float>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xr[0].p, t->xr[1].p,
+                         t->xr[2].p, t->cenf[0].p, t->cenf[1].p, t->cenf[2].p, xmf.p, ym.p, R, t->near_ptr.p,
+                         t->near_idx.p, d, A->kp[0], s);
     }
-    k_perm_out<<<blocks_for(n, 256), 256, 0, s>>>(ym.p, t->perm.p, n, y);
-    H2_LAUNCH("k_perm_out");
+    if (dtype == H2_DTYPE_F64)
+        k_perm_out_multi<double><<<blocks_for(nr, 256), 256, 0, s>>>(ym.p, t->perm.p, n, R, static_cast<double *>(y),
+                                                                      ld);
+    else
+        k_perm_out_multi<float><<<blocks_for(nr, 256), 256, 0, s>>>(ym.p, t->perm.p, n, R, static_cast<float *>(y),
+                                                                     ld);
+    H2_LAUNCH("k_perm_out_multi");
 }
 
 void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z, const int64_t *rows, int64_t nrows,

@@ -199,6 +199,15 @@ __global__ void k_root_coords(const double *x0, const double *x1, const double *
     if (d > 2) r2[p] = h2_split(x2[p] - g->lo[2]);
 }
 
+__global__ void k_centre_split(const double *c0, const double *c1, const double *c2, int nn, int d, const Geom *g,
+                               float2 *f0, float2 *f1, float2 *f2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    f0[i] = h2_split(c0[i] - g->lo[0]);
+    if (d > 1) f1[i] = h2_split(c1[i] - g->lo[1]);
+    if (d > 2) f2[i] = h2_split(c2[i] - g->lo[2]);
+}
+
 __global__ void k_max_leaf(const int32_t *nchild, const int32_t *begin, const int32_t *end, int nn, int32_t *mx) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nn && nchild[i] == 0) atomicMax(mx, end[i] - begin[i]);
@@ -392,6 +401,10 @@ void tree_build_impl(h2_tree_s *t, const double *pts) {
     k_root_coords<<<blocks_for(n, 256), 256, 0, s>>>(t->xs[0].p, t->xs[1].p, t->xs[2].p, n, d, g.p, t->xg[0].p,
                                                      t->xg[1].p, t->xg[2].p);
     H2_LAUNCH("k_root_coords");
+    for (int k = 0; k < 3; k++) t->cenf[k].alloc(k < d ? t->nnodes : 1, s);
+    k_centre_split<<<blocks_for(t->nnodes, 256), 256, 0, s>>>(t->cen[0].p, t->cen[1].p, t->cen[2].p, t->nnodes, d,
+                                                              g.p, t->cenf[0].p, t->cenf[1].p, t->cenf[2].p);
+    H2_LAUNCH("k_centre_split");
     DevBuf<int32_t> mx;
     mx.alloc(1, s);
     H2_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int32_t), s));

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libh2gb300.so")
 
 KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+DTYPE_F64, DTYPE_F32 = 0, 1  # element types of h2_matvec vectors
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NUMERIC", 6: "UNIMPLEMENTED",
           7: "STATE"}
 
@@ -59,7 +60,7 @@ def lib():
             "h2_hidr_get": [vp, i32, vp, vp, i64, C.POINTER(i64)],
             "h2_construct": [vp, vp, i32, vp, dbl, i32, vp, C.POINTER(vp)],
             "h2_matrix_get": [vp, i32, vp, i64, C.POINTER(i64)],
-            "h2_matvec": [vp, vp, vp, i32, vp],
+            "h2_matvec": [vp, vp, vp, i32, i32, i64, i32, vp],
             "h2_exact_rows": [vp, i32, vp, vp, vp, i64, vp, i32, vp],
             "h2_calibrate": [i32, i32, vp, dbl, vp, i32, vp, i32, i32, vp, C.POINTER(i32), C.POINTER(dbl)],
             "h2_free": [vp],
@@ -214,19 +215,38 @@ class H2Matrix(_Handle):
         return out[:ln.value]
 
     def matvec(self, x, y=None, stream=None):
-        """y = K~ x.  x: CUDA float64 tensor (result on the device) or a host
-        array (copied in and out by the library)."""
+        """y = K~ x for a vector x of n entries or an n x nrhs matrix of
+        right-hand sides, float64 or float32 (y takes x's shape and dtype).  A
+        CUDA tensor stays on the device; a host array is copied in and out by
+        the library.  y, if given, must be a contiguous vector of x's dtype
+        (single right-hand side only)."""
+        n = self.tree.n
         if _is_cuda(x):
             import torch
-            if y is None:
-                y = torch.empty_like(x)
-            _check("h2_matvec", lib().h2_matvec(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), 1,
-                                                 _stream(stream)))
-            return y
-        xa = np.ascontiguousarray(x, dtype=np.float64)
-        ya = np.zeros_like(xa) if y is None else y
+            if x.dtype not in (torch.float64, torch.float32):
+                raise TypeError("x must be float64 or float32")
+            dt = DTYPE_F64 if x.dtype == torch.float64 else DTYPE_F32
+            if x.dim() == 1:
+                xc = x.contiguous()
+                if y is None:
+                    y = torch.empty_like(xc)
+                _check("h2_matvec", lib().h2_matvec(self._h, C.c_void_p(xc.data_ptr()), C.c_void_p(y.data_ptr()), 1,
+                                                     dt, n, 1, _stream(stream)))
+                return y
+            nrhs = x.shape[1]
+            xt = x.t().contiguous()  # column-major n x nrhs, ld = n
+            yt = torch.empty_like(xt)
+            _check("h2_matvec", lib().h2_matvec(self._h, C.c_void_p(xt.data_ptr()), C.c_void_p(yt.data_ptr()), nrhs,
+                                                 dt, n, 1, _stream(stream)))
+            return yt.t()
+        xa = np.asarray(x)
+        fdt = np.float32 if xa.dtype == np.float32 else np.float64
+        dt = DTYPE_F32 if fdt == np.float32 else DTYPE_F64
+        nrhs = 1 if xa.ndim == 1 else xa.shape[1]
+        xa = np.asfortranarray(xa, dtype=fdt)
+        ya = np.zeros_like(xa, order="F") if y is None or xa.ndim == 2 else y
         _check("h2_matvec", lib().h2_matvec(self._h, xa.ctypes.data_as(C.c_void_p), ya.ctypes.data_as(C.c_void_p),
-                                             0, _stream(stream)))
+                                             nrhs, dt, n, 0, _stream(stream)))
         return ya
 
 

@@ -7,6 +7,8 @@ within 64 u c / eps of the oracle's (u = 2^-53, the conditioning bound of
 R11^{-1} R12 after truncation at eps), the H^2 matvec within 1e-12 of the oracle's
 H^2 matvec and within 10 eps of the dense product; exact rows within 1e-12.
 Sizes span several levels and tiles and include ragged leaves."""
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -255,3 +257,60 @@ def test_construct_and_matvec_mixed(H2, name, d, n, q, kern, kp, eps, g):
         assert np.array_equal(cand[rows], sk)
         Ui = U[uoff[i]:uoff[i + 1]].reshape(k, nc[i]).T
         assert np.array_equal(Ui[rows], np.eye(k))
+
+
+MULTI_CASES = [
+    ("fp64_coulomb3d", 3, 6000, 64, "coulomb", (), 1e-7, 6, "fp64"),
+    ("mixed_coulomb3d", 3, 8000, 100, "coulomb", (), 1e-5, 7, "mixed"),
+    ("mixed_gauss2d", 2, 6000, 64, "gaussian", (0.2,), 1e-5, 10, "mixed"),
+]
+
+
+@pytest.mark.parametrize("name,d,n,q,kern,kp,eps,g,prec", MULTI_CASES, ids=[c[0] for c in MULTI_CASES])
+def test_matvec_multi_rhs(H2, name, d, n, q, kern, kp, eps, g, prec):
+    """Several right-hand sides at once (launches of 16, 4 and 1 columns for
+    21 columns): each column is the single-vector product of the same matrix;
+    float32 vectors give the same product to float32 rounding; the host path
+    with a leading dimension above n leaves the gaps between columns alone."""
+    pts = I.uniform_cube(n, d, seed=70 + d)
+    nrhs = 21
+    Z = I.standard_normal(n * nrhs, seed=71).reshape(n, nrhs)
+    t = H2.Tree(dev(pts), q)
+    h = H2.Hidr(t, g, g)
+    A = H2.H2Matrix(t, h, kern, kp, eps, prec)
+    Y = A.matvec(dev(Z)).cpu().numpy()
+    assert Y.shape == (n, nrhs)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    for j in [0, 5, 15, 16, 19, 20]:
+        yj = A.matvec(dev(np.ascontiguousarray(Z[:, j]))).cpu().numpy()
+        assert np.linalg.norm(Y[:, j] - yj) <= tol * np.linalg.norm(yj), j
+    # the oracle's float64 H^2 product and the dense product, column by column
+    o, oh, OH = O.build_h2(pts, kern, kp, q, eps, g, g)
+    for j in [0, 20]:
+        yo = OH.matvec(Z[:, j])
+        lim = 1e-12 if prec == "fp64" else 10 * eps
+        assert np.linalg.norm(Y[:, j] - yo) <= lim * np.linalg.norm(yo), j
+        yd = O.dense_matvec(pts, kern, kp, Z[:, j])
+        assert np.linalg.norm(Y[:, j] - yd) <= 10 * eps * np.linalg.norm(yd), j
+    # float32 vectors in and out
+    Y32 = A.matvec(dev(Z.astype(np.float32))).cpu().numpy()
+    assert Y32.dtype == np.float32
+    assert np.linalg.norm(Y32 - Y) <= 1e-5 * np.linalg.norm(Y)
+    # host buffers with ld = n + 7: gaps between columns untouched
+    ld = n + 7
+    xh = np.zeros(ld * nrhs)
+    yh = np.full(ld * nrhs, -7.25)
+    for j in range(nrhs):
+        xh[j * ld:j * ld + n] = Z[:, j]
+    assert H2.lib().h2_matvec(A.handle, xh.ctypes.data_as(C.c_void_p), yh.ctypes.data_as(C.c_void_p), nrhs,
+                              H2.DTYPE_F64, ld, 0, None) == 0
+    for j in range(nrhs):
+        assert np.linalg.norm(yh[j * ld:j * ld + n] - Y[:, j]) <= 1e-14 * np.linalg.norm(Y[:, j]), j
+        assert np.all(yh[j * ld + n:(j + 1) * ld] == -7.25), j
+    # argument checks
+    assert H2.lib().h2_matvec(A.handle, xh.ctypes.data_as(C.c_void_p), yh.ctypes.data_as(C.c_void_p), 0,
+                              H2.DTYPE_F64, ld, 0, None) == 1
+    assert H2.lib().h2_matvec(A.handle, xh.ctypes.data_as(C.c_void_p), yh.ctypes.data_as(C.c_void_p), 2,
+                              H2.DTYPE_F64, n - 1, 0, None) == 1
+    assert H2.lib().h2_matvec(A.handle, xh.ctypes.data_as(C.c_void_p), xh.ctypes.data_as(C.c_void_p), 2,
+                              H2.DTYPE_F64, ld, 0, None) == 1

@@ -178,6 +178,22 @@ h2_status h2_hidr_get(h2_hidr h, int which, int32_t *counts, int32_t *data, int6
 h2_status h2_construct(h2_tree t, h2_hidr h, int kernel, const double *kparams, double id_tol,
                        int precision, void *stream, h2_matrix *out);
 
+/* Construction of nprob independent problems (configuration 4 of the
+ * benchmark plan): matrix p is exactly what h2_construct(trees[p], hidrs[p],
+ * kernels[p], kparams + 4p, id_tols[p], precisions[p]) returns, but the
+ * problems run concurrently, each level-synchronous on one of up to eight
+ * internal streams driven by host threads, so small problems fill the GPU
+ * together.  The work starts after the work already queued on `stream`; on
+ * return `stream` is ordered after every construction and every matrix
+ * belongs to it (its buffers are released on it).  kparams: 4 float64 per
+ * problem, or NULL when no problem needs parameters.  A tree or hidr may
+ * appear in several problems (e.g. one HiDR reused across kernels).
+ * Errors: as h2_construct; on any error no matrix is returned (out[] all
+ * NULL) and the message names the first failing problem. */
+h2_status h2_construct_batched(int nprob, const h2_tree *trees, const h2_hidr *hidrs, const int *kernels,
+                               const double *kparams, const double *id_tols, const int *precisions,
+                               void *stream, h2_matrix *out);
+
 /* what for h2_matrix_get:
  *   H2_MAT_RANK   int32 [nnodes]  k_i (0 where Y_i* is empty; 0 for the root)
  *   H2_MAT_NCAND  int32 [nnodes]  |Xbar_i|

@@ -5,7 +5,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <string>
+#include <thread>
+#include <vector>
+
+#include <mutex>
 
 #include "h2_internal.cuh"
 
@@ -43,17 +48,17 @@ void kparams_check(int kid, const double *kp, double out[4]) {
 }
 
 void pool_keep_memory() {
-    static bool done = false;
-    if (done) return;
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) {
-        cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-            uint64_t thr = UINT64_MAX;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    static std::once_flag done;
+    std::call_once(done, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t thr = UINT64_MAX;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
         }
-    }
-    done = true;
+    });
 }
 
 template <class T>
@@ -260,6 +265,126 @@ h2_status h2_construct(h2_tree th, h2_hidr hh, int kernel, const double *kparams
         }
         t->refs++;
         *out = A;
+    });
+}
+
+h2_status h2_construct_batched(int nprob, const h2_tree *trees, const h2_hidr *hidrs, const int *kernels,
+                               const double *kparams, const double *id_tols, const int *precisions, void *stream,
+                               h2_matrix *out) {
+    return guard([&] {
+        H2_REQUIRE(nprob >= 0, "nprob must be >= 0");
+        if (nprob == 0) return;
+        H2_REQUIRE(trees && hidrs && kernels && id_tols && precisions && out, "NULL argument");
+        for (int p = 0; p < nprob; p++) out[p] = nullptr;
+        struct Job {
+            h2_tree_s *t;
+            h2_hidr_s *h;
+            double kp[4];
+        };
+        std::vector<Job> jobs(nprob);
+        for (int p = 0; p < nprob; p++) {
+            try {
+                jobs[p].t = as_tree(trees[p]);
+                jobs[p].h = as_hidr(hidrs[p]);
+                H2_REQUIRE(jobs[p].h->tree == jobs[p].t, "hidr was built on another tree");
+                H2_REQUIRE(valid_kernel(kernels[p]), "unknown kernel id");
+                H2_REQUIRE(std::isfinite(id_tols[p]) && id_tols[p] >= 0.0, "id_tol must be finite and >= 0");
+                H2_REQUIRE(precisions[p] == H2_PREC_FP64 || precisions[p] == H2_PREC_MIXED, "unknown precision");
+                kparams_check(kernels[p], kparams ? kparams + 4 * p : nullptr, jobs[p].kp);
+            } catch (const Error &e) {
+                fail(e.st, "problem " + std::to_string(p) + ": " + e.msg);
+            }
+        }
+        pool_keep_memory();
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        int dev = 0;
+        H2_CUDA(cudaGetDevice(&dev));
+        const int nw = std::min(nprob, 8);
+        std::vector<cudaStream_t> ws(nw, nullptr);
+        std::vector<cudaEvent_t> done(nw, nullptr);
+        cudaEvent_t ready = nullptr;
+        auto cleanup = [&] {
+            for (int w = 0; w < nw; w++) {
+                if (done[w]) cudaEventDestroy(done[w]);
+                if (ws[w]) cudaStreamDestroy(ws[w]);
+            }
+            if (ready) cudaEventDestroy(ready);
+        };
+        std::vector<h2_matrix_s *> mats(nprob, nullptr);
+        std::vector<h2_status> st(nprob, H2_OK);
+        std::vector<std::string> msg(nprob);
+        try {
+            H2_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+            H2_CUDA(cudaEventRecord(ready, s));  // after the work already queued on stream
+            for (int w = 0; w < nw; w++) {
+                H2_CUDA(cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking));
+                H2_CUDA(cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming));
+                H2_CUDA(cudaStreamWaitEvent(ws[w], ready, 0));
+            }
+            std::atomic<int> next{0};
+            auto worker = [&](int w) {
+                if (cudaSetDevice(dev) != cudaSuccess) return;
+                for (int p = next++; p < nprob; p = next++) {
+                    auto *A = new h2_matrix_s();
+                    A->tree = jobs[p].t;
+                    A->stream = ws[w];
+                    A->kid = kernels[p];
+                    A->id_tol = id_tols[p];
+                    A->prec = precisions[p];
+                    for (int a = 0; a < 4; a++) A->kp[a] = jobs[p].kp[a];
+                    try {
+                        construct_impl(A, jobs[p].h);
+                        mats[p] = A;
+                    } catch (const Error &e) {
+                        st[p] = e.st;
+                        msg[p] = e.msg;
+                    } catch (const std::bad_alloc &) {
+                        st[p] = H2_ERR_OOM;
+                        msg[p] = "host allocation failed";
+                    } catch (...) {
+                        st[p] = H2_ERR_CUDA;
+                        msg[p] = "unknown error";
+                    }
+                    if (!mats[p]) {
+                        A->tag = TAG_DEAD;
+                        delete A;
+                    }
+                }
+            };
+            std::vector<std::thread> th;
+            try {
+                for (int w = 0; w < nw; w++) th.emplace_back(worker, w);
+            } catch (...) {  // no more threads: stop handing out problems, join the started ones
+                next = nprob;
+                for (auto &x : th) x.join();
+                throw;
+            }
+            for (auto &x : th) x.join();
+            // the caller's stream waits for every worker stream; the matrices
+            // then live on it
+            for (int w = 0; w < nw; w++) {
+                H2_CUDA(cudaEventRecord(done[w], ws[w]));
+                H2_CUDA(cudaStreamWaitEvent(s, done[w], 0));
+            }
+            for (int p = 0; p < nprob; p++)
+                if (mats[p]) matrix_rebind(mats[p], s);
+        } catch (...) {
+            for (auto *A : mats)
+                if (A) { matrix_rebind(A, s); A->tag = TAG_DEAD; delete A; }
+            cleanup();
+            throw;
+        }
+        cleanup();
+        for (int p = 0; p < nprob; p++)
+            if (st[p] != H2_OK) {
+                for (auto *A : mats)
+                    if (A) { A->tag = TAG_DEAD; delete A; }
+                fail(st[p], "problem " + std::to_string(p) + ": " + msg[p]);
+            }
+        for (int p = 0; p < nprob; p++) {
+            jobs[p].t->refs++;
+            out[p] = mats[p];
+        }
     });
 }
 

@@ -9,6 +9,8 @@
 // once the downdated value has lost about half its digits.
 #include <climits>
 
+#include <mutex>
+
 #include "h2_internal.cuh"
 
 namespace h2 {
@@ -505,8 +507,8 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     A->ubufs.resize(t->nlevels);
     A->kmax_level.assign(t->nlevels, 0);
     A->cmax_level.assign(t->nlevels, 0);
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [] {
         set_qr_attrs<double>();
         set_qr_attrs<float>();
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -514,8 +516,7 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_LIMIT));
         H2_CUDA(cudaFuncSetAttribute(k_keval_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
-        attr = true;
-    }
+    });
     cudaEvent_t e0, e1;
     H2_CUDA(cudaEventCreate(&e0));
     H2_CUDA(cudaEventCreate(&e1));
@@ -715,13 +716,12 @@ double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *
     mc.alloc(2, s); kk.alloc(1, s); piv.alloc(c, s); off.alloc(4, s);
     H2_CUDA(cudaMemcpyAsync(mc.p, hv, sizeof hv, cudaMemcpyHostToDevice, s));
     H2_CUDA(cudaMemcpyAsync(off.p, offs, sizeof offs, cudaMemcpyHostToDevice, s));
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [] {
         set_qr_attrs<double>();
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_LIMIT));
-        attr = true;
-    }
+    });
     if (qr_smem(c, m) > SMEM_LIMIT) fail(H2_ERR_UNIMPLEMENTED, "calibration block too large");
     launch_cpqr<double>(1, qr_smem(c, m), m, 0, mc.p, mc.p + 1, off.p, A.p, id_tol, kk.p, off.p + 2, piv.p, s);
     H2_LAUNCH("k_cpqr (calibration)");
@@ -756,6 +756,21 @@ double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *
     if (k_out) *k_out = k;
     if (m_out) *m_out = m;
     return td > 0.0 ? sqrt(tn / td) : 0.0;
+}
+
+void matrix_rebind(h2_matrix_s *A, cudaStream_t s) {
+    A->stream = s;
+    A->k.rebind(s);
+    A->c.rebind(s);
+    A->sk_off.rebind(s);
+    A->skel.rebind(s);
+    for (int k = 0; k < 3; k++) {
+        A->skc[k].rebind(s);
+        A->skr[k].rebind(s);
+    }
+    A->uptr.rebind(s);
+    for (auto &b : A->ubufs) b.rebind(s);
+    A->far_tiles.rebind(s);
 }
 
 }  // namespace h2

@@ -62,6 +62,8 @@ struct DevBuf {
         n = 0;
     }
     T *get() const { return p; }
+    // release on st from now on (st must be ordered after every use so far)
+    void rebind(cudaStream_t st) { s = st; }
 };
 
 // copy helpers (synchronous on the stream)
@@ -212,6 +214,8 @@ void tree_build_impl(h2_tree_s *t, const double *pts_dev_rowmajor);
 void lists_build_impl(h2_tree_s *t);
 void hidr_impl(h2_hidr_s *h);
 void construct_impl(h2_matrix_s *A, h2_hidr_s *h);
+// release every buffer of A on s from now on (s ordered after A's construction)
+void matrix_rebind(h2_matrix_s *A, cudaStream_t s);
 void matvec_impl(h2_matrix_s *A, const double *x_dev, double *y_dev, cudaStream_t s);
 // nrhs columns, x and y column-major with leading dimension ld (device)
 void matvec_multi_impl(h2_matrix_s *A, const void *x_dev, void *y_dev, int nrhs, int dtype, int64_t ld,

@@ -9,6 +9,8 @@
 // level run in one launch.
 #include <climits>
 
+#include <mutex>
+
 #include "h2_internal.cuh"
 
 namespace h2 {
@@ -721,12 +723,11 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
     if (nl <= 0) return;
     int G = (int)gridsize(g, d);
     size_t sm = dr_smem_bytes(G);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr;
+    std::call_once(attr, [] {
         size_t mx = std::max(dr_smem_bytes(DR_MAX_GRID), dr_smem_bytes(DR_BIN_MAX));
         H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
-        attr_set = true;
-    }
+    });
     DevBuf<int32_t> bins;
     DevBuf<float> pf;
     bins.alloc((size_t)std::max<int64_t>(ttot, 1) * 2, s);

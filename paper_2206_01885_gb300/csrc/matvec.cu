@@ -413,13 +413,12 @@ void nbody(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32
 
 // the upward/downward kernels' shared-memory opt-in, once per process
 void set_matvec_attrs() {
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [] {
         for (auto f : {(const void *)k_upward<double>, (const void *)k_upward<float>, (const void *)k_downward<double>,
                        (const void *)k_downward<float>})
             H2_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+    });
 }
 
 // tiles of the coupling (per matrix) and nearfield (per tree) kernels for

@@ -1,6 +1,7 @@
 // util.cu -- errors, stream-ordered allocation, exclusive scan and a stable
 // LSD radix sort of 64-bit keys (used for the Morton sort and for ordering the
 // near/far pair lists).
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -43,7 +44,7 @@ struct Pending {
     cudaEvent_t e0, e1;
 };
 std::mutex g_prof_mu;
-bool g_prof_on = false;
+std::atomic<bool> g_prof_on{false};
 double g_prof_ms[KT_COUNT] = {};
 long long g_prof_n[KT_COUNT] = {};
 std::vector<Pending> g_pending;

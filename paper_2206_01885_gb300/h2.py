@@ -68,6 +68,7 @@ def lib():
             "h2_sampled_error": [vp, vp, vp, i64, i64, vp, i32, vp],
             "h2_profile": [i32, i32],
             "h2_exact_rows_noalloc": [vp, i32, vp, vp, vp, i64, vp, vp],
+            "h2_construct_batched": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -196,7 +197,11 @@ class H2Matrix(_Handle):
     """h2_construct: nested bases (Algorithm 2); .matvec applies K~."""
 
     def __init__(self, tree: Tree, hidr: Hidr, kernel, kparams=(), id_tol: float = 1e-6, precision="fp64",
-                 stream=None):
+                 stream=None, _handle=None):
+        if _handle is not None:  # built by construct_batched
+            self._h = _handle
+            self.tree = tree
+            return
         h = C.c_void_p()
         kp = _kparams(kparams)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -260,6 +265,28 @@ def hidr_reduce(tree, g1, g2, stream=None) -> Hidr:
 
 def construct(tree, hidr, kernel, kparams=(), id_tol=1e-6, precision="fp64", stream=None) -> H2Matrix:
     return H2Matrix(tree, hidr, kernel, kparams, id_tol, precision, stream)
+
+
+def construct_batched(problems, stream=None):
+    """h2_construct_batched: problems is a list of (tree, hidr, kernel,
+    kparams, id_tol, precision); returns one H2Matrix per problem, built
+    concurrently on the GPU."""
+    n = len(problems)
+    if n == 0:
+        return []
+    trees = (C.c_void_p * n)(*[p[0].handle for p in problems])
+    hidrs = (C.c_void_p * n)(*[p[1].handle for p in problems])
+    kids = (C.c_int * n)(*[_kid(p[2]) for p in problems])
+    kps = (C.c_double * (4 * n))()
+    for i, p in enumerate(problems):
+        for a, v in enumerate(tuple(p[3])[:4]):
+            kps[4 * i + a] = float(v)
+    tols = (C.c_double * n)(*[float(p[4]) for p in problems])
+    precs = (C.c_int * n)(*[PRECISIONS[p[5]] if isinstance(p[5], str) else int(p[5]) for p in problems])
+    outs = (C.c_void_p * n)()
+    _check("h2_construct_batched", lib().h2_construct_batched(n, trees, hidrs, kids, kps, tols, precs,
+                                                               _stream(stream), outs))
+    return [H2Matrix(p[0], p[1], p[2], _handle=outs[i]) for i, p in enumerate(problems)]
 
 
 def matvec(A: H2Matrix, x, y=None, stream=None):

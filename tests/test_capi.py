@@ -50,6 +50,9 @@ def test_invalid_arguments_are_rejected_without_device_work(L):
     assert L.h2_free(bogus) == 1
     assert L.h2_hidr_reduce(bogus, 3, 3, None, C.byref(out)) == 1
     assert L.h2_matvec(bogus, pts, pts, 1, 0, 10, 0, None) == 1
+    assert L.h2_construct_batched(0, None, None, None, None, None, None, None, None) == 0
+    assert L.h2_construct_batched(-1, None, None, None, None, None, None, None, None) == 1
+    assert L.h2_construct_batched(2, None, None, None, None, None, None, None, None) == 1
     g = C.c_int(0)
     assert L.h2_calibrate(3, 99, None, 1e-6, pts, 5, pts, 5, 8, None, C.byref(g), None) == 1  # kernel id
     buf = C.create_string_buffer(64)

@@ -1,14 +1,22 @@
-"""Full-size parity at the benchmark configuration: 1,048,576 uniform points in
-[0,1]^3 (seed 2), leaf size 256, g = 9, Coulomb, eps = 1e-8, the launch
-configuration bench.py times.
+"""Full-size parity at the benchmark configurations, in the launch configuration
+bench.py times:
 
-The oracle cannot build the whole H^2 matrix at this size in seconds, so the
+  cube1m  1,048,576 uniform points in [0,1]^3 (seed 2), leaf size 256, g = 9,
+          Coulomb, eps = 1e-8 (float64) and 1e-5 (mixed, same grid);
+  gmix2m  2,097,152 points of the 16-component Gaussian mixture in [0,1]^2
+          (seed 3), leaf size 128, Gaussian kernel exp(-r^2/0.04), g = 20,
+          eps = 1e-10 (float64) and 1e-6 (mixed, same grid);
+  sphere8m  8,388,608 points on the unit sphere (seed 5), leaf size 256,
+          Coulomb, g = 8, mixed eps = 1e-6, 16 float32 right-hand sides.
+
+The oracle cannot build the whole H^2 matrix at these sizes in seconds, so the
 checks are: the tree and near/far lists in full (bit-exact); X_i* for every
 node (bit-exact, the oracle's bottom-up pass is cheap); Y_i* for sampled nodes
 (the oracle computes their ancestor chains); ranks, skeletons and U for
-sampled leaves and level-4 parents (float64, same tolerance as the small
-cases); exact rows against the oracle's; and the mixed form against the float64
-form built with the same tolerance and grid."""
+sampled leaves and parents (float64, same tolerance as the small cases); exact
+rows against the oracle's; the mixed form against the float64 form built with
+the same grid; for the sphere, every one of the 16 columns against its own
+single-vector product and the exact rows of two columns."""
 import numpy as np
 import pytest
 
@@ -19,27 +27,36 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-N, Q, G, EPS = 1 << 20, 256, 9, 1e-8
+CONFIGS = {
+    "cube1m": dict(make=lambda: I.uniform_cube(1 << 20, 3, seed=2), q=256, kern="coulomb", kp=(), eps=1e-8, g=9,
+                   eps_m=1e-5, err64=1e-4),
+    "gmix2m": dict(make=lambda: I.gaussian_mixture(1 << 21, seed=3), q=128, kern="gaussian", kp=(0.2,), eps=1e-10,
+                   g=20, eps_m=1e-6, err64=1e-6),
+}
 
 
-@pytest.fixture(scope="module")
-def setup():
+@pytest.fixture(scope="module", params=list(CONFIGS))
+def setup(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2206_01885_gb300 import build as B
     B.build()
     from paper_2206_01885_gb300 import h2
-    pts = I.uniform_cube(N, 3, seed=2)
+    cfg = CONFIGS[request.param]
+    pts = cfg["make"]()
     P = torch.from_numpy(pts).cuda()
-    t = h2.Tree(P, Q)
-    hd = h2.Hidr(t, G, G)
-    A = h2.H2Matrix(t, hd, "coulomb", (), EPS)
-    ot = O.tree_build(pts, Q)
-    return h2, pts, P, t, hd, A, ot
+    t = h2.Tree(P, cfg["q"])
+    hd = h2.Hidr(t, cfg["g"], cfg["g"])
+    A = h2.H2Matrix(t, hd, cfg["kern"], cfg["kp"], cfg["eps"])
+    ot = O.tree_build(pts, cfg["q"])
+    yield h2, pts, P, t, hd, A, ot, cfg
+    A.free()
+    hd.free()
+    t.free()
 
 
 def test_fullsize_tree_and_lists(setup):
-    h2, pts, P, t, hd, A, ot = setup
+    h2, pts, P, t, hd, A, ot, cfg = setup
     for f in ["perm", "keys", "level", "parent", "fchild", "nchild", "begin", "end", "prefix", "lptr",
               "near_ptr", "near_idx", "far_ptr", "far_idx"]:
         got = t.get(f)
@@ -57,12 +74,13 @@ def _sample_nodes(ot, rng):
 
 
 def test_fullsize_hidr_and_bases(setup):
-    h2, pts, P, t, hd, A, ot = setup
+    h2, pts, P, t, hd, A, ot, cfg = setup
     rng = np.random.default_rng(2024)
     deep, shallow, parents = _sample_nodes(ot, rng)
     build = np.zeros(ot.nnodes, dtype=bool)
     build[np.concatenate([deep, shallow, parents])] = True
     need = O.closure_down(ot, build)
+    G = cfg["g"]
     oh = O.Hidr(ot, G, G, need_y=need)  # X* everywhere, Y* on need and its ancestors
     xc, xd = hd.get("x")
     yc, yd = hd.get("y")
@@ -77,7 +95,8 @@ def test_fullsize_hidr_and_bases(setup):
         assert np.array_equal(yd[yo[i]:yo[i + 1]], want), ("Y*", i)
         checked += 1
     assert checked >= len(need.nonzero()[0])
-    OH = O.H2(ot, oh, "coulomb", (), EPS, need=build)
+    EPS = cfg["eps"]
+    OH = O.H2(ot, oh, cfg["kern"], cfg["kp"], EPS, need=build)
     ranks, nc = A.get("rank"), A.get("ncand")
     skel, U = A.get("skel"), A.get("U")
     ko = np.concatenate([[0], np.cumsum(ranks)])
@@ -92,20 +111,67 @@ def test_fullsize_hidr_and_bases(setup):
 
 
 def test_fullsize_exact_rows_and_forms(setup):
-    h2, pts, P, t, hd, A, ot = setup
-    z = I.standard_normal(N, seed=9)
-    rows = I.sample_rows(N, 200, seed=11)
+    h2, pts, P, t, hd, A, ot, cfg = setup
+    n, kern, kp = len(pts), cfg["kern"], cfg["kp"]
+    z = I.standard_normal(n, seed=9)
+    rows = I.sample_rows(n, 200, seed=11)
     Z, R = torch.from_numpy(z).cuda(), torch.from_numpy(rows).cuda()
-    ex = h2.exact_rows(t, "coulomb", (), Z, R).cpu().numpy()
-    want = O.exact_rows(pts, "coulomb", (), z, rows)
+    ex = h2.exact_rows(t, kern, kp, Z, R).cpu().numpy()
+    want = O.exact_rows(pts, kern, kp, z, rows)
     assert np.allclose(ex, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
     # the float64 product on the sampled rows: the error the bench reports
     y64 = A.matvec(Z).cpu().numpy()
     err64 = np.linalg.norm(y64[rows] - want) / np.linalg.norm(want)
-    assert err64 < 1e-4
-    # mixed form at the same tolerance and grid: within 10 eps of the float64 form
-    eps_m = 1e-5
-    A64 = h2.H2Matrix(t, hd, "coulomb", (), eps_m, "fp64")
-    Am = h2.H2Matrix(t, hd, "coulomb", (), eps_m, "mixed")
+    print(f"sampled relative error, float64 form: {err64:.3e}")
+    assert err64 < cfg["err64"]
+    # mixed form at its tolerance on the same grid: within 10 eps of the float64 form
+    eps_m = cfg["eps_m"]
+    A64 = h2.H2Matrix(t, hd, kern, kp, eps_m, "fp64")
+    Am = h2.H2Matrix(t, hd, kern, kp, eps_m, "mixed")
     ya, yb = A64.matvec(Z).cpu().numpy(), Am.matvec(Z).cpu().numpy()
     assert np.linalg.norm(yb - ya) / np.linalg.norm(ya) <= 10 * eps_m
+    A64.free()
+    Am.free()
+
+
+def test_fullsize_sphere_16_rhs():
+    """8,388,608 points on the unit sphere, 16 float32 right-hand sides, mixed
+    form at eps = 1e-6 with g = 8: tree and lists bit-exact; each column of the
+    16-column product equals that column's own product; two columns against
+    exact float64 rows."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_01885_gb300 import build as B
+    B.build()
+    from paper_2206_01885_gb300 import h2
+    n, q, g, eps = 1 << 23, 256, 8, 1e-6
+    pts = I.sphere_surface(n, seed=5)
+    t = h2.Tree(torch.from_numpy(pts).cuda(), q)
+    ot = O.tree_build(pts, q)
+    for f in ["perm", "level", "begin", "end", "near_ptr", "near_idx", "far_ptr", "far_idx"]:
+        got = t.get(f)
+        assert np.array_equal(got, getattr(ot, f).astype(got.dtype)), f
+    del ot
+    hd = h2.Hidr(t, g, g)
+    A = h2.H2Matrix(t, hd, "coulomb", (), eps, "mixed")
+    rng = np.random.default_rng(55)
+    Zh = rng.standard_normal((n, 16)).astype(np.float32)
+    Z = torch.from_numpy(Zh).cuda()
+    Y = A.matvec(Z)
+    assert Y.shape == (n, 16) and Y.dtype == torch.float32
+    Y = Y.cpu().numpy()
+    for j in range(16):
+        yj = A.matvec(Z[:, j].contiguous()).cpu().numpy()
+        assert np.linalg.norm(Y[:, j] - yj) <= 1e-6 * np.linalg.norm(yj), j
+    rows = I.sample_rows(n, 100, seed=56)
+    for j in [0, 15]:
+        zj = Zh[:, j].astype(np.float64)
+        want = O.exact_rows(pts, "coulomb", (), zj, rows)
+        got = h2.exact_rows(t, "coulomb", (), torch.from_numpy(zj).cuda(), torch.from_numpy(rows).cuda())
+        assert np.allclose(got.cpu().numpy(), want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+        err = np.linalg.norm(Y[rows, j] - want) / np.linalg.norm(want)
+        print(f"sampled relative error, column {j}: {err:.3e}")
+        assert err < 1e-3
+    A.free()
+    hd.free()
+    t.free()

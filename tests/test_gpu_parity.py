@@ -314,3 +314,45 @@ def test_matvec_multi_rhs(H2, name, d, n, q, kern, kp, eps, g, prec):
                               H2.DTYPE_F64, n - 1, 0, None) == 1
     assert H2.lib().h2_matvec(A.handle, xh.ctypes.data_as(C.c_void_p), xh.ctypes.data_as(C.c_void_p), 2,
                               H2.DTYPE_F64, ld, 0, None) == 1
+
+
+def test_construct_batched_equals_one_by_one(H2):
+    """h2_construct_batched: independent problems of uneven sizes (cube and
+    sphere, three kernels, both forms, several leaf sizes, one tree and HiDR
+    shared by three kernels) give exactly the matrices of one-by-one
+    h2_construct calls (same kernels and reduction orders: bit-identical ranks,
+    skeletons, U and products); a bad problem fails the whole call."""
+    rng = np.random.default_rng(90)
+    probs, keep = [], []
+    shared_t = H2.Tree(dev(I.uniform_cube(9000, 3, seed=91)), 64)
+    shared_h = H2.Hidr(shared_t, 5, 5)
+    keep += [shared_t, shared_h]
+    for kern, kp in [("coulomb", ()), ("gaussian", (0.5,)), ("multiquadric", ())]:
+        probs.append((shared_t, shared_h, kern, kp, 1e-5, "mixed"))
+    for a in range(9):
+        n = int(np.exp(rng.uniform(np.log(2000), np.log(30000))))
+        pts = I.uniform_cube(n, 3, seed=100 + a) if a % 2 == 0 else I.sphere_surface(n, seed=100 + a)
+        q = [64, 128, 256][a % 3]
+        kern, kp = [("coulomb", ()), ("gaussian", (0.5,)), ("multiquadric", ())][a % 3]
+        t = H2.Tree(dev(pts), q)
+        h = H2.Hidr(t, 5, 5)
+        keep += [t, h]
+        probs.append((t, h, kern, kp, [1e-5, 1e-7][a % 2], ["mixed", "fp64"][a % 2]))
+    mats = H2.construct_batched(probs)
+    assert len(mats) == len(probs)
+    for (t, h, kern, kp, eps, prec), B in zip(probs, mats):
+        A = H2.H2Matrix(t, h, kern, kp, eps, prec)
+        for f in ["rank", "ncand", "skel", "U"]:
+            assert np.array_equal(A.get(f), B.get(f)), (kern, prec, f)
+        z = dev(I.standard_normal(t.n, seed=92))
+        assert torch.equal(A.matvec(z), B.matvec(z)), (kern, prec)
+        A.free()
+    for B in mats:
+        B.free()
+    # a hidr built on another tree: the call fails and returns no matrix
+    bad = [probs[3], (probs[4][0], probs[5][1]) + probs[4][2:]]
+    with pytest.raises(H2.H2Error) as e:
+        H2.construct_batched(bad)
+    assert e.value.status == 1 and "problem 1" in str(e.value)
+    for x in reversed(keep):
+        x.free()

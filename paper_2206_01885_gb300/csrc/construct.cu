@@ -122,19 +122,11 @@ __global__ void k_keval_f32(int lb, const int32_t *ycnt, const int32_t *cc, int3
 }
 
 // (value, index) max with ties to the smaller index
-__device__ __forceinline__ void argmax_merge(double &v, int &i, double v2, int i2) {
-    if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
-}
-
-__device__ double block_sum(double x, double *red) {
-    x = warp_sum(x);
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = x;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
-    return s;
+// (key, index) max with ties to the smaller index; keys are the bit patterns
+// of non-negative doubles, which order like the values (integer compares, no
+// float64 instruction)
+__device__ __forceinline__ void argmax_key(long long &k, int &i, long long k2, int i2) {
+    if (k2 > k || (k2 == k && i2 < i)) { k = k2; i = i2; }
 }
 
 // Column-pivoted Householder QR of each node's block, stopped at the first
@@ -162,14 +154,15 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
     }
     double *nrm = reinterpret_cast<double *>(smem_raw);
     double *nrm0 = nrm + c;
-    double *rowj = nrm0 + c;
-    Real *v = reinterpret_cast<Real *>(rowj + c);
+    Real *rowj = reinterpret_cast<Real *>(nrm0 + c);  // row j of the updated trailing columns
+    Real *v = rowj + c;
     int32_t *pv = reinterpret_cast<int32_t *>(v + m);
     unsigned char *flag = reinterpret_cast<unsigned char *>(pv + c);
     __shared__ double red[QR_WARPS];
-    __shared__ double bval[QR_WARPS];
+    __shared__ long long bkey[QR_WARPS];
     __shared__ int bidx[QR_WARPS];
     __shared__ int s_p, s_stop;
+    __shared__ double s_tau, s_beta, s_sc;
     Real *A = Abase + aoff[a];
     int32_t *piv = pivbase + coff[a];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -184,7 +177,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
         const Real *col = A + (int64_t)l * m;
         Real sp = 0;
         for (int r = lane; r < m; r += 32) sp += col[r] * col[r];
-        double s = warp_sum((double)sp);
+        const double s = (double)warp_sum(sp);
         if (lane == 0) { nrm[l] = SQ ? s : sqrt(s); nrm0[l] = nrm[l]; }
     }
     __syncthreads();
@@ -193,20 +186,21 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
     double r11 = 0.0;
     for (int j = 0; j < kmax; j++) {
         // pivot: largest downdated norm among columns j..c-1
-        double bv = -1.0;
+        long long bk = -1;
         int bi = INT_MAX;
-        for (int l = j + threadIdx.x; l < c; l += blockDim.x) argmax_merge(bv, bi, nrm[l], l);
+        for (int l = j + threadIdx.x; l < c; l += blockDim.x) argmax_key(bk, bi, __double_as_longlong(nrm[l]), l);
         for (int o = 16; o > 0; o >>= 1) {
-            double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+            long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
             int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-            argmax_merge(bv, bi, v2, i2);
+            argmax_key(bk, bi, k2, i2);
         }
-        if (lane == 0) { bval[warp] = bv; bidx[warp] = bi; }
+        if (lane == 0) { bkey[warp] = bk; bidx[warp] = bi; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double vv = bval[0];
+            long long kk2 = bkey[0];
             int ii = bidx[0];
-            for (int w = 1; w < QR_WARPS; w++) argmax_merge(vv, ii, bval[w], bidx[w]);
+            for (int w = 1; w < QR_WARPS; w++) argmax_key(kk2, ii, bkey[w], bidx[w]);
+            const double vv = __longlong_as_double(kk2);
             if (j == 0) r11 = vv;
             s_p = ii;
             // float32 form compares squared norms: nu^2 <= tol^2 r11^2
@@ -228,24 +222,39 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
         }
         __syncthreads();
         // Householder reflector for A[j:m, j]
+        // (per-lane and per-warp partial sums in the block's type, the warps'
+        // sums added in order by thread 0, which also forms the reflector's
+        // scalars once and broadcasts them)
         Real *aj = A + (int64_t)j * m;
         Real part = 0;
         for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) part += aj[r] * aj[r];
-        double sigma = block_sum((double)part, red);
-        double alpha = (double)aj[j];
-        if (alpha == 0.0 && sigma == 0.0) break;  // exactly zero pivot column
-        double tau = 0.0, beta = alpha, sc = 0.0;
-        if (sigma != 0.0) {
-            double xn = sqrt(alpha * alpha + sigma);
-            beta = alpha >= 0.0 ? -xn : xn;
-            tau = (beta - alpha) / beta;
-            sc = 1.0 / (alpha - beta);
+        part = warp_sum(part);
+        if (lane == 0) red[warp] = (double)part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sigma = 0.0;
+            for (int w = 0; w < QR_WARPS; w++) sigma += red[w];
+            const double alpha = (double)aj[j];
+            double tau = 0.0, beta = alpha, sc = 0.0;
+            if (sigma != 0.0) {
+                double xn = sqrt(alpha * alpha + sigma);
+                beta = alpha >= 0.0 ? -xn : xn;
+                tau = (beta - alpha) / beta;
+                sc = 1.0 / (alpha - beta);
+            }
+            s_tau = tau;
+            s_beta = beta;
+            s_sc = sc;
+            s_stop = (alpha == 0.0 && sigma == 0.0) ? 1 : 0;  // exactly zero pivot column
         }
-        const Real scR = (Real)sc;
+        __syncthreads();
+        if (s_stop) break;
+        const bool has_tau = s_tau != 0.0;
+        const Real scR = (Real)s_sc;
         for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) v[r] = aj[r] * scR;
         __syncthreads();
-        if (threadIdx.x == 0) aj[j] = (Real)beta;
-        const Real tauR = (Real)tau;
+        if (threadIdx.x == 0) aj[j] = (Real)s_beta;
+        const Real tauR = (Real)s_tau;
         // apply to the trailing columns (one warp per column); row j of the
         // result goes to shared memory for the norm downdate.  With RPL > 0 a
         // lane keeps its RPL rows of the column in registers: all loads are
@@ -260,7 +269,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
                     int r = j + 1 + lane + 32 * u;
                     a[u] = r < m ? al[r] : (Real)0;
                 }
-                if (tau != 0.0) {
+                if (has_tau) {
                     Real w = 0;
 #pragma unroll
                     for (int u = 0; u < RPL; u++) {
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
                     ajl = ajl - w;
                     if (lane == 0) al[j] = ajl;
                 }
-            } else if (tau != 0.0) {
+            } else if (has_tau) {
                 Real w = 0;
                 for (int r = j + 1 + lane; r < m; r += 32) w += v[r] * al[r];
                 w = warp_sum(w) + ajl;
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
                 ajl = ajl - w;
                 if (lane == 0) al[j] = ajl;
             }
-            if (lane == 0) rowj[l] = (double)ajl;
+            if (lane == 0) rowj[l] = ajl;
         }
         __syncthreads();
         // downdate the norms, one thread per column; flag the ones that have
@@ -295,12 +304,13 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
             double nl = nrm[l];
             flag[l] = 0;
             if (nl != 0.0) {
+                const double rj = (double)rowj[l];
                 if constexpr (SQ) {  // nu^2 - r^2, recomputed once below sqrt(2^-24) nu0^2
-                    double n2 = fma(-rowj[l], rowj[l], nl);
+                    double n2 = fma(-rj, rj, nl);
                     if (!(n2 > tol3z * nrm0[l])) flag[l] = 1;
                     else nrm[l] = n2;
                 } else {
-                    double tt = fabs(rowj[l]) / nl;
+                    double tt = fabs(rj) / nl;
                     tt = 1.0 - tt * tt;
                     if (tt < 0.0) tt = 0.0;
                     double t2 = nl / nrm0[l];
@@ -327,7 +337,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
             } else {
                 for (int r = j + 1 + lane; r < m; r += 32) sp += al[r] * al[r];
             }
-            double s = warp_sum((double)sp);
+            const double s = (double)warp_sum(sp);
             if (lane == 0) { nrm[l] = SQ ? s : sqrt(s); nrm0[l] = nrm[l]; }
         }
         __syncthreads();

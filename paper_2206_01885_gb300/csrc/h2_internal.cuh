@@ -159,6 +159,7 @@ struct h2_tree_s {
     h2::DevBuf<float2> cenf[3];   // cell centre - root corner split into float32 hi + lo (float32 N-body)
     h2::DevBuf<int2> near_tiles;  // (leaf, first target) tiles of the nearfield kernel, built on first use
     int near_tile_tpt = 0;
+    h2::DevBuf<int64_t> near_first, far_first;  // first list entry of each node with index >= its own
     h2::DevBuf<int64_t> leaf_start;  // begin of every node as int64 (nearfield point sets)
     h2::DevBuf<int32_t> leaf_count;  // end - begin of every node
 };
@@ -282,9 +283,26 @@ __device__ __forceinline__ double h2_kappa(int kid, double kp0, double r2) {
 
 // float64 kappa in its fast forms (rsqrt: within 1 ulp of 1/sqrt) for
 // products that are compared with a tolerance rather than bit for bit
+// 1/sqrt(r2) for r2 >= 0, and 0 at r2 = 0 (Coulomb's kappa(x, x) = 0): the PTX
+// approximation rsqrt.approx.ftz.f64 (relative error below 2^-20) refined by
+// one third-order step of the series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + ...,
+// e = 1 - r2 y0^2, which leaves an O(e^3) error below float64 rounding;
+// measured within 1 ulp of rsqrt() over r2 in [1e-300, 1e300].  Subnormal r2
+// (outside the approximation's range) takes rsqrt().
+__device__ __forceinline__ double h2_rsqrt64(double r2) {
+    const long long bits = __double_as_longlong(r2);
+    if (bits < 0x0010000000000000LL) return bits == 0 ? 0.0 : rsqrt(r2);
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(r2));
+    const double t = r2 * y0;
+    const double e = fma(-t, y0, 1.0);
+    const double p = fma(e, 0.375, 0.5);
+    return fma(y0 * e, p, y0);
+}
+
 __device__ __forceinline__ double h2_kappa_fast(int kid, double kp0, double r2) {
     switch (kid) {
-    case H2_K_COULOMB: return r2 > 0.0 ? rsqrt(r2) : 0.0;
+    case H2_K_COULOMB: return h2_rsqrt64(r2);
     case H2_K_GAUSSIAN: return exp(-r2 / (kp0 * kp0));
     case H2_K_EXPONENTIAL: return exp(-sqrt(r2) / kp0);
     case H2_K_MULTIQUADRIC: return sqrt(1.0 + r2);

@@ -267,7 +267,7 @@ __host__ __device__ __forceinline__ size_t dr_smem_bytes(int G) {
 // coordinates of label s are (x0[s], x1[s], x2[s]).
 __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
                                                            DRPoints PT, int32_t *const *outptr, int32_t *outcnt, int lb,
-                                                           int32_t *bin_base, float *pf_base) {
+                                                           int32_t *bin_base, float4 *pq_base) {
     const double *x0 = PT.x[0], *x1 = PT.x[1], *x2 = PT.x[2];
     extern __shared__ unsigned char smem_raw[];
     int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
@@ -364,9 +364,8 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         // search stops after ring r once that sum is below the square of
         // (r + 1/2) h_min - delta, a lower bound for every point in a farther
         // cell (delta = 1e-5 W + 1e-12 R covers the float32 binning error).
-        int32_t *bidx = bin_base + 2 * t0;  // bin of each entry, then labels in bin order
-        int32_t *slab = bidx + nt;
-        float *pf0 = pf_base + 3 * t0, *pf1 = pf0 + nt, *pf2 = pf1 + nt;
+        int32_t *bidx = bin_base + t0;  // bin of each entry
+        float4 *pq = pq_base + t0;      // in bin order: float32 offsets and the label (as bits)
         int *bstart = reinterpret_cast<int *>(smem_raw + dr_bins_offset(G));
         int *bcur = bstart + G + 1;
         const float delf = (float)(1e-5 * W + 1e-12 * PT.R);
@@ -417,9 +416,8 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             if (bi >= 0) {
                 const int pos = base + __popc(peers & lt);
                 const int32_t sid = T[p];
-                slab[pos] = sid;
                 const float2 v0 = PT.xg[0][sid];
-                pf0[pos] = (v0.x - lh[0]) + (v0.y - ll[0]);
+                const float f0 = (v0.x - lh[0]) + (v0.y - ll[0]);
                 float f1 = 0.f, f2 = 0.f;
                 if (d > 1) {
                     const float2 v1 = PT.xg[1][sid];
@@ -429,8 +427,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     const float2 v2 = PT.xg[2][sid];
                     f2 = (v2.x - lh[2]) + (v2.y - ll[2]);
                 }
-                pf1[pos] = f1;
-                pf2[pos] = f2;
+                pq[pos] = make_float4(f0, f1, f2, __int_as_float(sid));
             }
         }
         // grid points: float64 q and its float32 offset qf, computed once each
@@ -495,7 +492,8 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                         cm &= cm - 1;
                         const int pe = bstart[b + 1];
                         for (int p = bstart[b] + lane; p < pe; p += 32) {
-                            const float e0f = pf0[p] - qf[0], e1f = pf1[p] - qf[1], e2f = pf2[p] - qf[2];
+                            const float4 e = pq[p];
+                            const float e0f = e.x - qf[0], e1f = e.y - qf[1], e2f = e.z - qf[2];
                             const float d32 = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f));
                             if (d32 < b2) {
                                 if (d32 < b1) {
@@ -523,7 +521,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             const float limx = m1 + M;
             int32_t winner;
             if (sec > limx) {
-                winner = slab[__shfl_sync(0xffffffffu, p1, w)];
+                winner = __float_as_int(pq[__shfl_sync(0xffffffffu, p1, w)].w);
             } else {
                 // near tie: every point within M of the smallest, in float64;
                 // non-negative doubles order as their bit patterns
@@ -549,16 +547,18 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                             for (int p0 = bstart[b]; p0 < pe; p0 += 32) {
                                 const int p = p0 + lane;
                                 bool c = false;
+                                int32_t id = INT_MAX;
                                 if (p < pe) {
-                                    const float e0f = pf0[p] - qf[0], e1f = pf1[p] - qf[1], e2f = pf2[p] - qf[2];
+                                    const float4 e = pq[p];
+                                    const float e0f = e.x - qf[0], e1f = e.y - qf[1], e2f = e.z - qf[2];
                                     c = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f)) <= limx;
+                                    id = __float_as_int(e.w);
                                 }
                                 unsigned pm = __ballot_sync(0xffffffffu, c);
                                 if (pm == 0u) continue;
                                 long long kk = LLONG_MAX;
-                                int32_t id = INT_MAX;
+                                if (!c) id = INT_MAX;
                                 if (c) {
-                                    id = slab[p];
                                     kk = __double_as_longlong(h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0,
                                                                        d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]));
                                 }
@@ -729,11 +729,11 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
         H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
     });
     DevBuf<int32_t> bins;
-    DevBuf<float> pf;
-    bins.alloc((size_t)std::max<int64_t>(ttot, 1) * 2, s);
-    pf.alloc((size_t)std::max<int64_t>(ttot, 1) * 3, s);
+    DevBuf<float4> pq;
+    bins.alloc((size_t)std::max<int64_t>(ttot, 1), s);
+    pq.alloc((size_t)std::max<int64_t>(ttot, 1), s);
     ProfScope ps(KT_DATAREDUCT, s);
-    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, pts, outptr, outcnt, lb, bins.p, pf.p);
+    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, pts, outptr, outcnt, lb, bins.p, pq.p);
     H2_LAUNCH("k_datareduct");
 }
 

@@ -81,7 +81,7 @@ __global__ void k_downward(int lb, const int32_t *nchild, const int32_t *fchild,
 // kappa for the matvec kernels: fast forms (rsqrt, exp) in float64 or float32
 template <int KID>
 __device__ __forceinline__ double kap(double r2, double p) {  // p: 1/h^2 (Gaussian) or 1/l (exponential)
-    if constexpr (KID == H2_K_COULOMB) return r2 > 0.0 ? rsqrt(r2) : 0.0;
+    if constexpr (KID == H2_K_COULOMB) return h2_rsqrt64(r2);
     else if constexpr (KID == H2_K_GAUSSIAN) return exp(-r2 * p);
     else if constexpr (KID == H2_K_EXPONENTIAL) return exp(-sqrt(r2) * p);
     else return sqrt(1.0 + r2);
@@ -127,6 +127,51 @@ __global__ void k_exact_rows(const int64_t *rows, int64_t nrows, const int32_t *
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
         out[r] = t;
     }
+}
+
+// Chunked form of k_exact_rows: CTA (r, c) sums chunk c (ER_CHUNK points) of
+// row r into part[r * nch + c]; k_exact_sum adds a row's chunks in order.
+// Short CTAs let other streams' kernels take SMs as they retire.
+constexpr int ER_CHUNK = 1 << 16;
+constexpr int ER_THREADS = 256;
+
+__global__ void __launch_bounds__(ER_THREADS)
+    k_exact_part(const int64_t *rows, int64_t nrows, const int32_t *iperm, const double *x0, const double *x1,
+                 const double *x2, const double *zm, int64_t n, int d, int kid, double kp0, int nch, double *part) {
+    __shared__ double red[ER_THREADS / 32];
+    const int64_t r = blockIdx.y;
+    const int c = blockIdx.x;
+    const int64_t row = rows[r];
+    if (row < 0 || row >= n) {  // out-of-range row: NaN instead of an out-of-bounds read
+        if (threadIdx.x == 0) part[r * nch + c] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    const int64_t p = iperm[row];
+    const double a0 = x0[p], a1 = d > 1 ? x1[p] : 0.0, a2 = d > 2 ? x2[p] : 0.0;
+    const int64_t q0 = (int64_t)c * ER_CHUNK, q1 = min(n, q0 + ER_CHUNK);
+    double s = 0.0;
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += ER_THREADS) {
+        double dx = a0 - x0[q], dy = d > 1 ? a1 - x1[q] : 0.0, dz = d > 2 ? a2 - x2[q] : 0.0;
+        double r2 = dx * dx + dy * dy + dz * dz;
+        s += h2_kappa_fast(kid, kp0, r2) * zm[q];
+    }
+    s = warp_sum(s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < ER_THREADS / 32; w++) t += red[w];
+        part[r * nch + c] = t;
+    }
+}
+
+__global__ void k_exact_sum(const double *part, int64_t nrows, int nch, double *out) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    double t = 0.0;
+    for (int c = 0; c < nch; c++) t += part[r * nch + c];
+    out[r] = t;
 }
 
 // err = ||exact - approx[rows]|| / ||exact||, one CTA, fixed reduction order
@@ -350,6 +395,142 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
     }
 }
 
+// Symmetric tiled N-body for one right-hand side.  kappa is symmetric, so the
+// list of node i is walked only from its first entry j >= i: a pair j > i is
+// evaluated once for both out_i += K(X_i, X_j) w_j and out_j += K(X_j, X_i) w_i,
+// and j == i (a leaf's own block) gives the first term only.  A CTA takes a
+// tile of 32 targets of i (one a lane), its warps split the pairs; sources
+// are staged 32 at a time and at step q lane l evaluates source (l + q) mod 32,
+// so every lane meets every staged source once.  The row sum stays in the
+// lane; the column sum of source (l + q) mod 32 rides in lane l and moves one
+// lane down after each step, so after 32 steps lane l holds source l's column
+// sum.  Row sums (per CTA) and column sums (per warp and 32 sources) are
+// added to out with float64 atomics: other CTAs add to the same entries.
+template <class Real, int KID>
+__global__ void __launch_bounds__(NB_WARPS * 32)
+    k_nbody_sym(const int2 *tiles, const int64_t *start, const int32_t *count, const Real *X0, const Real *X1,
+                const Real *X2, const float2 *F0, const float2 *F1, const float2 *F2, const Real *w, double *out,
+                const int64_t *lptr, const int64_t *lfirst, const int32_t *lidx, int d, double kpar) {
+    __shared__ Real stg[NB_WARPS][4][32];  // staged sources of each warp: x, y, z, weight
+    __shared__ double part[NB_WARPS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int2 tl = tiles[blockIdx.x];
+    const int i = tl.x;
+    const int64_t ts = start[i];
+    const int tn = count[i];
+    const int a = tl.y + lane;
+    const bool act = a < tn;
+    const Real p = (Real)kpar;
+    const Real tx0 = act ? X0[ts + a] : (Real)0, tx1 = act && d > 1 ? X1[ts + a] : (Real)0,
+               tx2 = act && d > 2 ? X2[ts + a] : (Real)0;
+    const Real tw = act ? w[ts + a] : (Real)0;
+    Real acc = (Real)0, cmp = (Real)0;
+    for (int64_t e = lfirst[i] + warp; e < lptr[i + 1]; e += NB_WARPS) {
+        const int jn = lidx[e];
+        const bool sym = jn != i;
+        const int64_t ss = start[jn];
+        const int sn = count[jn];
+        Real s0 = tx0, s1 = tx1, s2 = tx2;
+        if constexpr (sizeof(Real) == 4) {  // target coordinates in node jn's frame
+            const float2 a0 = F0[i], b0 = F0[jn];
+            s0 += (a0.x - b0.x) + (a0.y - b0.y);
+            if (d > 1) {
+                const float2 a1 = F1[i], b1 = F1[jn];
+                s1 += (a1.x - b1.x) + (a1.y - b1.y);
+            }
+            if (d > 2) {
+                const float2 a2 = F2[i], b2 = F2[jn];
+                s2 += (a2.x - b2.x) + (a2.y - b2.y);
+            }
+        }
+        Real blk = (Real)0;
+        for (int q0 = 0; q0 < sn; q0 += 32) {
+            const int cnt = min(32, sn - q0);
+            __syncwarp();
+            {  // sources past the end: coordinates 0, weight 0 (their terms vanish)
+                const bool ok = lane < cnt;
+                const int64_t sp = ss + q0 + lane;
+                stg[warp][0][lane] = ok ? X0[sp] : (Real)0;
+                stg[warp][1][lane] = ok && d > 1 ? X1[sp] : (Real)0;
+                stg[warp][2][lane] = ok && d > 2 ? X2[sp] : (Real)0;
+                stg[warp][3][lane] = ok ? w[sp] : (Real)0;
+            }
+            __syncwarp();
+            Real col = (Real)0;
+            if (sym) {
+#pragma unroll 8
+                for (int q = 0; q < 32; q++) {
+                    const int sidx = (lane + q) & 31;
+                    const Real dx = s0 - stg[warp][0][sidx], dy = s1 - stg[warp][1][sidx],
+                               dz = s2 - stg[warp][2][sidx];
+                    const Real kv = kap<KID>(dx * dx + dy * dy + dz * dz, p);
+                    blk += kv * stg[warp][3][sidx];
+                    col += kv * tw;
+                    col = __shfl_sync(0xffffffffu, col, (lane + 1) & 31);
+                }
+                if (lane < cnt) atomicAdd(out + ss + q0 + lane, (double)col);
+            } else {
+                for (int q = 0; q < cnt; q++) {
+                    const Real dx = s0 - stg[warp][0][q], dy = s1 - stg[warp][1][q], dz = s2 - stg[warp][2][q];
+                    blk += kap<KID>(dx * dx + dy * dy + dz * dz, p) * stg[warp][3][q];
+                }
+            }
+        }
+        if constexpr (sizeof(Real) == 8) acc += blk;
+        else two_sum_acc(acc, cmp, blk);
+    }
+    part[warp][lane] = (double)acc + (double)cmp;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int aa = tl.y + threadIdx.x;
+        if (aa < tn) {
+            double sum = 0.0;
+            for (int wv = 0; wv < NB_WARPS; wv++) sum += part[wv][threadIdx.x];
+            atomicAdd(out + ts + aa, sum);
+        }
+    }
+}
+
+// first entry of each node's (sorted) list whose index is >= the node's own
+__global__ void k_list_first(const int64_t *ptr, const int32_t *idx, int nn, int64_t *first) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    int64_t lo = ptr[i], hi = ptr[i + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (idx[mid] < i) lo = mid + 1;
+        else hi = mid;
+    }
+    first[i] = lo;
+}
+
+template <class Real>
+void nbody_sym(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
+               const Real *X1, const Real *X2, const float2 *F0, const float2 *F1, const float2 *F2, const Real *w,
+               double *out, const int64_t *lptr, const int64_t *lfirst, const int32_t *lidx, int d, double kp0,
+               cudaStream_t s) {
+    if (tiles.n == 0) return;
+    const unsigned nb = (unsigned)tiles.n;
+    switch (kid) {
+    case H2_K_COULOMB:
+        k_nbody_sym<Real, H2_K_COULOMB><<<nb, NB_WARPS * 32, 0, s>>>(tiles.p, start, count, X0, X1, X2, F0, F1, F2,
+                                                                      w, out, lptr, lfirst, lidx, d, 0.0);
+        break;
+    case H2_K_GAUSSIAN:
+        k_nbody_sym<Real, H2_K_GAUSSIAN><<<nb, NB_WARPS * 32, 0, s>>>(
+            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, out, lptr, lfirst, lidx, d, 1.0 / (kp0 * kp0));
+        break;
+    case H2_K_EXPONENTIAL:
+        k_nbody_sym<Real, H2_K_EXPONENTIAL><<<nb, NB_WARPS * 32, 0, s>>>(
+            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, out, lptr, lfirst, lidx, d, 1.0 / kp0);
+        break;
+    default:
+        k_nbody_sym<Real, H2_K_MULTIQUADRIC><<<nb, NB_WARPS * 32, 0, s>>>(
+            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, out, lptr, lfirst, lidx, d, 0.0);
+    }
+    H2_LAUNCH("k_nbody_sym");
+}
+
 template <class Real, int R, int TPT>
 void nbody_kid(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
                const Real *X1, const Real *X2, const float2 *F0, const float2 *F1, const float2 *F2, const Real *w,
@@ -471,6 +652,16 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
                 fail(H2_ERR_UNIMPLEMENTED, "candidate set too large for the single-CTA upward pass");
     }
     prepare_tiles(A, 1, s);
+    // one right-hand side: each unordered block pair is evaluated once
+    const bool sym = R == 1;
+    if (sym && !t->near_first.p) {
+        const int nn = t->nnodes;
+        t->near_first.alloc(nn, s);
+        t->far_first.alloc(nn, s);
+        k_list_first<<<blocks_for(nn, 256), 256, 0, s>>>(t->near_ptr.p, t->near_idx.p, nn, t->near_first.p);
+        k_list_first<<<blocks_for(nn, 256), 256, 0, s>>>(t->far_ptr.p, t->far_idx.p, nn, t->far_first.p);
+        H2_LAUNCH("k_list_first");
+    }
     const int64_t kt = std::max<int64_t>(A->ktotal, 1);
     DevBuf<double> xm, ym, xh, zh;
     xm.alloc(nr, s);
@@ -520,7 +711,15 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
     // coupling over far pairs: B_ij = K(Xhat_i, Xhat_j) on the fly
     {
         ProfScope ps(KT_COUPLING, s);
-        if (f64)
+        if (sym && f64)
+            nbody_sym<double>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skc[0].p, A->skc[1].p, A->skc[2].p,
+                              nullptr, nullptr, nullptr, xh.p, zh.p, t->far_ptr.p, t->far_first.p, t->far_idx.p, d,
+                              A->kp[0], s);
+        else if (sym)
+            nbody_sym<float>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skr[0].p, A->skr[1].p, A->skr[2].p,
+                             t->cenf[0].p, t->cenf[1].p, t->cenf[2].p, xhf.p, zh.p, t->far_ptr.p, t->far_first.p,
+                             t->far_idx.p, d, A->kp[0], s);
+        else if (f64)
             nbody<double>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skc[0].p, A->skc[1].p, A->skc[2].p, nullptr,
                           nullptr, nullptr, xh.p, zh.p, R, t->far_ptr.p, t->far_idx.p, d, A->kp[0], s);
         else
@@ -553,7 +752,15 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
     // nearfield over near leaf pairs: K(X_i, X_j) on the fly
     {
         ProfScope ps(KT_NEAR, s);
-        if (f64)
+        if (sym && f64)
+            nbody_sym<double>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xs[0].p, t->xs[1].p,
+                              t->xs[2].p, nullptr, nullptr, nullptr, xm.p, ym.p, t->near_ptr.p, t->near_first.p,
+                              t->near_idx.p, d, A->kp[0], s);
+        else if (sym)
+            nbody_sym<float>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xr[0].p, t->xr[1].p,
+                             t->xr[2].p, t->cenf[0].p, t->cenf[1].p, t->cenf[2].p, xmf.p, ym.p, t->near_ptr.p,
+                             t->near_first.p, t->near_idx.p, d, A->kp[0], s);
+        else if (f64)
             nbody<double>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xs[0].p, t->xs[1].p,
                           t->xs[2].p, nullptr, nullptr, nullptr, xm.p, ym.p, R, t->near_ptr.p, t->near_idx.p, d,
                           A->kp[0], s);
@@ -579,10 +786,19 @@ void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z, c
     k_perm_in<<<blocks_for(n, 256), 256, 0, s>>>(z, t->perm.p, n, zm.p);
     H2_LAUNCH("k_perm_in");
     if (nrows > 0) {
+        const int nch = (int)((n + ER_CHUNK - 1) / ER_CHUNK);
+        const int64_t rb = std::min<int64_t>(nrows, 65535);  // rows per launch (grid y limit)
+        DevBuf<double> part;
+        part.alloc((size_t)rb * nch, s);
         ProfScope ps(KT_EXACT, s);
-        k_exact_rows<<<(unsigned)nrows, 512, 0, s>>>(rows, nrows, t->iperm.p, t->xs[0].p, t->xs[1].p, t->xs[2].p,
-                                                     zm.p, n, t->d, kid, kp[0], out);
-        H2_LAUNCH("k_exact_rows");
+        for (int64_t r0 = 0; r0 < nrows; r0 += rb) {
+            const int64_t nr = std::min<int64_t>(rb, nrows - r0);
+            k_exact_part<<<dim3((unsigned)nch, (unsigned)nr), ER_THREADS, 0, s>>>(
+                rows + r0, nr, t->iperm.p, t->xs[0].p, t->xs[1].p, t->xs[2].p, zm.p, n, t->d, kid, kp[0], nch,
+                part.p);
+            k_exact_sum<<<blocks_for(nr, 256), 256, 0, s>>>(part.p, nr, nch, out + r0);
+            H2_LAUNCH("k_exact_part");
+        }
     }
 }
 

@@ -87,7 +87,7 @@ def _check(call: str, st: int):
 
 def _stream(stream):
     if stream is not None:
-        return C.c_void_p(int(stream))
+        return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 

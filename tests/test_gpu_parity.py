@@ -160,7 +160,8 @@ def test_construct_and_matvec_fp64(H2, name, d, n, q, kern, kp, eps, g):
     assert np.linalg.norm(y - yd) / np.linalg.norm(yd) <= 10 * eps
     # host-pointer matvec is the same product
     yh = A.matvec(z)
-    assert np.array_equal(yh, y)
+    # (block sums meet in float64 atomics, so two products agree to rounding)
+    assert np.linalg.norm(yh - y) <= 1e-14 * np.linalg.norm(y)
 
 
 def test_exact_rows(H2):
@@ -321,7 +322,8 @@ def test_construct_batched_equals_one_by_one(H2):
     sphere, three kernels, both forms, several leaf sizes, one tree and HiDR
     shared by three kernels) give exactly the matrices of one-by-one
     h2_construct calls (same kernels and reduction orders: bit-identical ranks,
-    skeletons, U and products); a bad problem fails the whole call."""
+    skeletons and U; products equal to rounding, since block sums meet in
+    float64 atomics); a bad problem fails the whole call."""
     rng = np.random.default_rng(90)
     probs, keep = [], []
     shared_t = H2.Tree(dev(I.uniform_cube(9000, 3, seed=91)), 64)
@@ -345,7 +347,8 @@ def test_construct_batched_equals_one_by_one(H2):
         for f in ["rank", "ncand", "skel", "U"]:
             assert np.array_equal(A.get(f), B.get(f)), (kern, prec, f)
         z = dev(I.standard_normal(t.n, seed=92))
-        assert torch.equal(A.matvec(z), B.matvec(z)), (kern, prec)
+        ya, yb = A.matvec(z), B.matvec(z)
+        assert torch.linalg.norm(ya - yb) <= 1e-14 * torch.linalg.norm(ya), (kern, prec)
         A.free()
     for B in mats:
         B.free()

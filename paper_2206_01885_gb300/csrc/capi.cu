@@ -2,6 +2,7 @@
 // arguments, owns handle lifetimes and turns internal exceptions into
 // h2_status values plus a thread-local message.  Every compute step runs in
 // the library's CUDA kernels.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -593,31 +594,39 @@ h2_status h2_calibrate(int dim, int kernel, const double *kparams, double eps, c
         pool_keep_memory();
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         DevBuf<double> a[3], b[3];
-        DevBuf<float2> bg[3];
+        DevBuf<float4> bq;
         std::vector<double> col(std::max(n1, n2));
-        std::vector<float2> colf(n2);
+        std::vector<float4> packed(2 * (size_t)n2, make_float4(0.f, 0.f, 0.f, 0.f));
+        long long zbox[6] = {LLONG_MAX, LLONG_MAX, LLONG_MAX, LLONG_MIN, LLONG_MIN, LLONG_MIN};
         DRPoints zb;
         zb.R = 0.0;
+        bq.alloc(2 * (size_t)n2, s);
+        zb.xq = bq.p;
         for (int k = 0; k < 3; k++) {
             a[k].alloc(k < dim ? n1 : 1, s);
             b[k].alloc(k < dim ? n2 : 1, s);
-            bg[k].alloc(k < dim ? n2 : 1, s);
             zb.x[k] = b[k].p;
-            zb.xg[k] = bg[k].p;
             zb.ref[k] = 0.0;
             if (k >= dim) continue;
             for (int i = 0; i < n1; i++) col[i] = z1[(int64_t)i * dim + k];
             H2_CUDA(cudaMemcpyAsync(a[k].p, col.data(), n1 * sizeof(double), cudaMemcpyHostToDevice, s));
             for (int i = 0; i < n2; i++) {
                 col[i] = z2[(int64_t)i * dim + k];
-                float hi = (float)col[i];  // relative to ref = 0, split into float32 hi + lo
-                colf[i] = make_float2(hi, (float)(col[i] - (double)hi));
+                const float hi = (float)col[i];  // relative to ref = 0, split into float32 hi + lo
+                const float lo = (float)(col[i] - (double)hi);
+                float4 &qa = packed[2 * (size_t)i], &qb = packed[2 * (size_t)i + 1];
+                if (k == 0) { qa.x = hi; qa.w = lo; }
+                else if (k == 1) { qa.y = hi; qb.x = lo; }
+                else { qa.z = hi; qb.y = lo; }
                 zb.R = std::max(zb.R, std::fabs(col[i]));
+                zbox[k] = std::min(zbox[k], dkey_host(col[i]));
+                zbox[3 + k] = std::max(zbox[3 + k], dkey_host(col[i]));
             }
             H2_CUDA(cudaMemcpyAsync(b[k].p, col.data(), n2 * sizeof(double), cudaMemcpyHostToDevice, s));
-            H2_CUDA(cudaMemcpyAsync(bg[k].p, colf.data(), n2 * sizeof(float2), cudaMemcpyHostToDevice, s));
             H2_CUDA(cudaStreamSynchronize(s));
         }
+        H2_CUDA(cudaMemcpyAsync(bq.p, packed.data(), packed.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+        H2_CUDA(cudaStreamSynchronize(s));
         const double *za[3] = {a[0].p, a[1].p, a[2].p};
         *g_out = gmax + 1;
         double err = INFINITY;
@@ -625,7 +634,7 @@ h2_status h2_calibrate(int dim, int kernel, const double *kparams, double eps, c
             double gp = 1.0;
             for (int k = 0; k < dim; k++) gp *= g;
             if (gp > 16384) break;
-            err = calib_error_gpu(dim, kernel, kp[0], 1e-2 * eps, za, n1, zb, n2, g, nullptr, nullptr, s);
+            err = calib_error_gpu(dim, kernel, kp[0], 1e-2 * eps, za, n1, zb, zbox, n2, g, nullptr, nullptr, s);
             if (err < 1e-2 * eps) {
                 *g_out = g;
                 break;

@@ -704,11 +704,12 @@ __global__ void k_calib_err(const double *A, int m, int c, int k, const int32_t 
 }  // namespace
 
 double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *const z1s[3], int n1,
-                       const DRPoints &z2, int n2, int g, int *k_out, int *m_out, cudaStream_t s) {
+                       const DRPoints &z2, const long long *z2_box, int n2, int g, int *k_out, int *m_out,
+                       cudaStream_t s) {
     const double *const *z2s = z2.x;
     DevBuf<int32_t> ids;
     ids.alloc(n2, s);
-    int m = (int)datareduct_one(z2, d, n2, g, ids.p, s);
+    int m = (int)datareduct_one(z2, d, n2, g, z2_box, ids.p, s);
     const int c = n1;
     DevBuf<double> A;
     A.alloc((size_t)m * c, s);

@@ -8,6 +8,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <string>
 #include <vector>
@@ -155,7 +156,7 @@ struct h2_tree_s {
     double ms_tree = 0, ms_lists = 0;
     h2::DevBuf<double> cen[3];    // cell centre of every node
     h2::DevBuf<float> xr[3];      // point coordinates relative to their leaf's centre (float32 kernels)
-    h2::DevBuf<float2> xg[3];     // x - root corner split into float32 hi + lo (DataReduct's float32 search)
+    h2::DevBuf<float4> xq;        // x - root corner as float32 hi + lo, two float4 per point (see DRPoints)
     h2::DevBuf<float2> cenf[3];   // cell centre - root corner split into float32 hi + lo (float32 N-body)
     h2::DevBuf<int2> near_tiles;  // (leaf, first target) tiles of the nearfield kernel, built on first use
     int near_tile_tpt = 0;
@@ -174,6 +175,7 @@ struct h2_hidr_s {
     h2::DevBuf<int32_t> xcnt, ycnt;
     h2::DevBuf<int32_t *> xptr, yptr;
     std::vector<h2::DevBuf<int32_t>> xbufs, ybufs;
+    h2::DevBuf<long long> xbox, ybox;  // per node: bounding box of X_i*, Y_i* (6 integer keys)
     std::vector<int> xmax_level, ymax_level;  // host: largest set per level
     int64_t xtotal = 0, ytotal = 0, tmax = 0, ttotal = 0;
     double ms_up = 0, ms_down = 0;
@@ -229,23 +231,33 @@ void exact_rows_noalloc_impl(h2_tree_s *t, int kid, const double *kp, const doub
 void sampled_error_impl(const double *exact, const double *approx, const int64_t *rows, int64_t nrows, int64_t n,
                         double *err_out, cudaStream_t s);
 
-// Coordinates DataReduct reads: float64 x (exact distances) and xg, the
-// float64 difference x - ref (|x - ref| <= R per coordinate) split into a
-// float32 pair {hi, lo} with hi + lo equal to it within 2^-47 R.
+// Coordinates DataReduct reads: float64 x (exact distances) and xq, the
+// float64 difference x - ref (|x - ref| <= R per coordinate) split into float32
+// pairs {hi, lo} with hi + lo equal to it within 2^-47 R, packed in one
+// 32-byte record per point: xq[2s] = {hi0, hi1, hi2, lo0}, xq[2s+1] = {lo1, lo2, 0, 0}.
 struct DRPoints {
     const double *x[3];
-    const float2 *xg[3];
+    const float4 *xq;
     double ref[3];
     double R;
 };
 // one DataReduct over an explicit point set (used by the calibration); ids
-// are labels 0..n-1 of the points.  Output sorted labels.
-int64_t datareduct_one(const DRPoints &pts, int d, int64_t n, int g, int32_t *out_dev, cudaStream_t s);
+// are labels 0..n-1 of the points, box_keys their bounding box as 6
+// order-preserving keys (host).  Output sorted labels.
+int64_t datareduct_one(const DRPoints &pts, int d, int64_t n, int g, const long long *box_keys, int32_t *out_dev,
+                       cudaStream_t s);
+// order-preserving integer key of a float64 (host copy of the device form)
+inline long long dkey_host(double x) {
+    long long b;
+    memcpy(&b, &x, sizeof b);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
 // Section 4.2 test problem at grid size g: relative Frobenius error of
 // K(Z1, Z2) ~= U K(Zhat1, Z2) where U comes from the ID (tolerance id_tol) of
 // K(DataReduct(Z2, g), Z1).  z1s, z2s: device SoA coordinates.
 double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *const z1s[3], int n1,
-                       const DRPoints &z2, int n2, int g, int *k_out, int *m_out, cudaStream_t s);
+                       const DRPoints &z2, const long long *z2_box, int n2, int g, int *k_out, int *m_out,
+                       cudaStream_t s);
 
 }  // namespace h2
 

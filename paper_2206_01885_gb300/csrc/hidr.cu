@@ -58,39 +58,113 @@ __global__ void k_size_down(int lb, int nl, const int32_t *parent, const int64_t
 }
 
 // --------------------------------------------------------------- gathers
+// Bounding boxes are kept as order-preserving integer keys of the float64
+// coordinates (see dkey): box[6 * i + k] = min key, box[6 * i + 3 + k] = max
+// key of coordinate k; an empty set has (LLONG_MAX, LLONG_MIN).  The box of a
+// union is the componentwise min / max of its parts' boxes, exactly.
+__device__ __forceinline__ long long dkey(double x) {
+    long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dkey_inv(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
+// block-wide min of lo[0..2] and max of hi[0..2]; thread 0 writes box[0..5]
+__device__ void block_box_write(long long lo[3], long long hi[3], long long *box) {
+    __shared__ long long red[2][3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < 3; k++) { red[0][k][warp] = lo[k]; red[1][k][warp] = hi[k]; }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; k++) {
+            long long mn = red[0][k][0], mx = red[1][k][0];
+            for (int w = 1; w < nw; w++) { mn = min(mn, red[0][k][w]); mx = max(mx, red[1][k][w]); }
+            box[k] = mn;
+            box[3 + k] = mx;
+        }
+}
+
+__device__ __forceinline__ void box_merge(long long lo[3], long long hi[3], const long long *b) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) { lo[k] = min(lo[k], b[k]); hi[k] = max(hi[k], b[3 + k]); }
+}
+
+// float32 offset of coordinate k of point s from the box corner, from the
+// packed {hi, lo} root-relative pair: (xh - lh) + (xl - ll)
+__device__ __forceinline__ float dr_offset(const float4 *xq, int32_t s, int k, float lh, float ll) {
+    const float4 qa = xq[2 * (int64_t)s];
+    if (k == 0) return (qa.x - lh) + (qa.w - ll);
+    const float4 qb = xq[2 * (int64_t)s + 1];
+    return k == 1 ? (qa.y - lh) + (qb.x - ll) : (qa.z - lh) + (qb.y - ll);
+}
+
+// T_i = S_i: the leaf's points, or the children's X_c* in child order; tbox[a]
+// its bounding box (the leaf's points, or the union of the children's boxes)
 __global__ void k_gather_up(int lb, const int32_t *nchild, const int32_t *fchild, const int32_t *begin,
                             const int32_t *end, int32_t *const *xptr, const int32_t *xcnt, const int64_t *toff,
-                            int32_t *tdata) {
+                            int32_t *tdata, const double *x0, const double *x1, const double *x2, int d,
+                            const long long *xbox, long long *tbox) {
     int a = blockIdx.x;
     int i = lb + a;
     int32_t *dst = tdata + toff[a];
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
     if (nchild[i] == 0) {
         int32_t b0 = begin[i], n = end[i] - begin[i];
-        for (int r = threadIdx.x; r < n; r += blockDim.x) dst[r] = b0 + r;
-        return;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            dst[r] = b0 + r;
+            const long long k0 = dkey(x0[b0 + r]);
+            lo[0] = min(lo[0], k0);
+            hi[0] = max(hi[0], k0);
+            if (d > 1) {
+                const long long k1 = dkey(x1[b0 + r]);
+                lo[1] = min(lo[1], k1);
+                hi[1] = max(hi[1], k1);
+            }
+            if (d > 2) {
+                const long long k2 = dkey(x2[b0 + r]);
+                lo[2] = min(lo[2], k2);
+                hi[2] = max(hi[2], k2);
+            }
+        }
+    } else {
+        int64_t w = 0;
+        for (int c = fchild[i]; c < fchild[i] + nchild[i]; c++) {
+            const int32_t *src = xptr[c];
+            int n = xcnt[c];
+            for (int r = threadIdx.x; r < n; r += blockDim.x) dst[w + r] = src[r];
+            w += n;
+            if (threadIdx.x == 0) box_merge(lo, hi, xbox + 6 * (int64_t)c);
+        }
     }
-    int64_t w = 0;
-    for (int c = fchild[i]; c < fchild[i] + nchild[i]; c++) {
-        const int32_t *src = xptr[c];
-        int n = xcnt[c];
-        for (int r = threadIdx.x; r < n; r += blockDim.x) dst[w + r] = src[r];
-        w += n;
-    }
+    block_box_write(lo, hi, tbox + 6 * (int64_t)a);
 }
 
+// T_i = Y_p* followed by X_j* for j in IL(i); tbox[a] the union of their boxes
 __global__ void k_gather_down(int lb, const int32_t *parent, const int64_t *far_ptr, const int32_t *far_idx,
                               int32_t *const *xptr, const int32_t *xcnt, int32_t *const *yptr, const int32_t *ycnt,
-                              const int64_t *toff, int32_t *tdata) {
+                              const int64_t *toff, int32_t *tdata, const long long *xbox, const long long *ybox,
+                              long long *tbox) {
     int a = blockIdx.x;
     int i = lb + a;
     int32_t *dst = tdata + toff[a];
     int p = parent[i];
     int64_t w = 0;
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
     {
         const int32_t *src = yptr[p];
         int n = ycnt[p];
         for (int r = threadIdx.x; r < n; r += blockDim.x) dst[r] = src[r];
         w = n;
+        if (threadIdx.x == 0 && n > 0) box_merge(lo, hi, ybox + 6 * (int64_t)p);
     }
     for (int64_t e = far_ptr[i]; e < far_ptr[i + 1]; e++) {
         int j = far_idx[e];
@@ -99,6 +173,9 @@ __global__ void k_gather_down(int lb, const int32_t *parent, const int64_t *far_
         for (int r = threadIdx.x; r < n; r += blockDim.x) dst[w + r] = src[r];
         w += n;
     }
+    for (int64_t e = far_ptr[i] + threadIdx.x; e < far_ptr[i + 1]; e += blockDim.x)
+        box_merge(lo, hi, xbox + 6 * (int64_t)far_idx[e]);
+    block_box_write(lo, hi, tbox + 6 * (int64_t)a);
 }
 
 __global__ void k_set_ptrs(int lb, int nl, int32_t *base, const int64_t *off, int32_t **ptr) {
@@ -189,14 +266,6 @@ __device__ void block_scan_inclusive(int *v, int n, int *scratch) {
 }
 
 // order-preserving map of a float64 to a signed 64-bit integer and back
-__device__ __forceinline__ long long dkey(double x) {
-    long long b = __double_as_longlong(x);
-    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double dkey_inv(long long k) {
-    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
-}
-
 __device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax_(double a, double b) { return a > b ? a : b; }
 
@@ -263,17 +332,18 @@ __host__ __device__ __forceinline__ size_t dr_smem_bytes(int G) {
 
 
 
-// One CTA per node.  tdata[toff[a] .. toff[a+1]) are the labels of S (T);
-// coordinates of label s are (x0[s], x1[s], x2[s]).
+// One CTA per node.  tdata[toff[a] .. toff[a+1]) are the labels of S (T),
+// tbox[a] its bounding box; coordinates of label s are (x0[s], x1[s], x2[s]).
+// The box of the result goes to outbox[node].
 __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
                                                            DRPoints PT, int32_t *const *outptr, int32_t *outcnt, int lb,
-                                                           int32_t *bin_base, float4 *pq_base) {
+                                                           int32_t *bin_base, float4 *pq_base, const long long *tbox,
+                                                           long long *outbox) {
     const double *x0 = PT.x[0], *x1 = PT.x[1], *x2 = PT.x[2];
     extern __shared__ unsigned char smem_raw[];
     int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
     __shared__ int32_t tid_s[DR_TILE];
     __shared__ float tf_s[3][DR_TILE];
-    __shared__ long long red[2][3][DR_THREADS / 32];
     __shared__ int scratch[33];
     const int a = blockIdx.x;
     const int node = lb + a;
@@ -289,39 +359,17 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         __syncthreads();
         block_bitonic_sort(win, P);
         for (int i = threadIdx.x; i < nt; i += blockDim.x) out[i] = win[i];
+        if (threadIdx.x < 6) outbox[6 * (int64_t)node + threadIdx.x] = tbox[6 * (int64_t)a + threadIdx.x];
         if (threadIdx.x == 0) outcnt[node] = (int32_t)nt;
         return;
     }
-    // bounding box of S: exact min / max through order-preserving integer keys
-    // of the float64 coordinates (no float64 arithmetic)
-    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-    for (int64_t r = threadIdx.x; r < nt; r += blockDim.x) {
-        int32_t s = T[r];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            if (k >= d) break;
-            long long kv = dkey((k == 0 ? x0 : (k == 1 ? x1 : x2))[s]);
-            lo[k] = min(lo[k], kv);
-            hi[k] = max(hi[k], kv);
-        }
-    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = 0; k < 3; k++)
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
-        }
-    if (lane == 0)
-        for (int k = 0; k < 3; k++) { red[0][k][warp] = lo[k]; red[1][k][warp] = hi[k]; }
-    __syncthreads();
     double l[3] = {0.0, 0.0, 0.0}, h[3] = {0.0, 0.0, 0.0};
-    #pragma unroll
+#pragma unroll
     for (int k = 0; k < 3; k++) {
         if (k >= d) break;
-        long long mn = red[0][k][0], mx = red[1][k][0];
-        for (int w = 1; w < nw; w++) { mn = min(mn, red[0][k][w]); mx = max(mx, red[1][k][w]); }
-        l[k] = dkey_inv(mn);
-        h[k] = __ddiv_rn(__dsub_rn(dkey_inv(mx), l[k]), (double)g);
+        l[k] = dkey_inv(tbox[6 * (int64_t)a + k]);
+        h[k] = __ddiv_rn(__dsub_rn(dkey_inv(tbox[6 * (int64_t)a + 3 + k]), l[k]), (double)g);
     }
     // Both searches below stage float32 offsets from the box corner l,
     //   x - l = (xh - lh) + (xl - ll),
@@ -389,8 +437,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     if (k >= d) break;
                     int cidx = 0;
                     if (!flat[k]) {
-                        const float2 v = PT.xg[k][sid];
-                        const float f = (v.x - lh[k]) + (v.y - ll[k]);
+                        const float f = dr_offset(PT.xq, sid, k, lh[k], ll[k]);
                         cidx = min(max((int)(f * ihf[k]), 0), g - 1);
                     }
                     bi += cidx * stride;
@@ -416,17 +463,10 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             if (bi >= 0) {
                 const int pos = base + __popc(peers & lt);
                 const int32_t sid = T[p];
-                const float2 v0 = PT.xg[0][sid];
-                const float f0 = (v0.x - lh[0]) + (v0.y - ll[0]);
-                float f1 = 0.f, f2 = 0.f;
-                if (d > 1) {
-                    const float2 v1 = PT.xg[1][sid];
-                    f1 = (v1.x - lh[1]) + (v1.y - ll[1]);
-                }
-                if (d > 2) {
-                    const float2 v2 = PT.xg[2][sid];
-                    f2 = (v2.x - lh[2]) + (v2.y - ll[2]);
-                }
+                const float4 qa = PT.xq[2 * (int64_t)sid], qb = PT.xq[2 * (int64_t)sid + 1];
+                const float f0 = (qa.x - lh[0]) + (qa.w - ll[0]);
+                const float f1 = d > 1 ? (qa.y - lh[1]) + (qb.x - ll[1]) : 0.f;
+                const float f2 = d > 2 ? (qa.z - lh[2]) + (qb.y - ll[2]) : 0.f;
                 pq[pos] = make_float4(f0, f1, f2, __int_as_float(sid));
             }
         }
@@ -485,13 +525,32 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     int bin = 0;
                     float lb = 0.f;
                     bool ok = e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, flat, hf, qf, delf, bin, lb);
-                    ok = ok && lb <= lim && bstart[bin + 1] > bstart[bin];
-                    unsigned cm = __ballot_sync(0xffffffffu, ok);
-                    while (cm) {
-                        const int b = __shfl_sync(0xffffffffu, bin, __ffs(cm) - 1);
-                        cm &= cm - 1;
-                        const int pe = bstart[b + 1];
-                        for (int p = bstart[b] + lane; p < pe; p += 32) {
+                    ok = ok && lb <= lim;
+                    // the selected cells' points as one range: lane c's cell is
+                    // [cs, cs + cn), at flat offset exc of the warp's prefix sum
+                    int cs = 0, cn = 0;
+                    if (ok) {
+                        cs = bstart[bin];
+                        cn = bstart[bin + 1] - cs;
+                    }
+                    int inc = cn;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += t;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, inc, 31);
+                    const int exc = inc - cn;
+                    for (int f0 = 0; f0 < total; f0 += 32) {
+                        const int f = f0 + lane;
+                        int src = 0;  // last lane whose range starts at or before f
+#pragma unroll
+                        for (int st = 16; st > 0; st >>= 1) {
+                            const int ex = __shfl_sync(0xffffffffu, exc, src + st);
+                            if (ex <= f) src += st;
+                        }
+                        const int p = __shfl_sync(0xffffffffu, cs, src) + f - __shfl_sync(0xffffffffu, exc, src);
+                        if (f < total) {
                             const float4 e = pq[p];
                             const float e0f = e.x - qf[0], e1f = e.y - qf[1], e2f = e.z - qf[2];
                             const float d32 = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f));
@@ -613,14 +672,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     const int32_t s = T[tb + r];
                     tid_s[r] = s;
 #pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        float f = 0.f;
-                        if (k < d) {
-                            const float2 v = PT.xg[k][s];
-                            f = (v.x - lh[k]) + (v.y - ll[k]);
-                        }
-                        tf_s[k][r] = f;
-                    }
+                    for (int k = 0; k < 3; k++) tf_s[k][r] = k < d ? dr_offset(PT.xq, s, k, lh[k], ll[k]) : 0.f;
                 }
                 __syncthreads();
                 for (int r = 0; r < cnt; r++) {
@@ -668,14 +720,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                         const int32_t s = T[tb + r];
                         tid_s[r] = s;
 #pragma unroll
-                        for (int k = 0; k < 3; k++) {
-                            float f = 0.f;
-                            if (k < d) {
-                                const float2 v = PT.xg[k][s];
-                                f = (v.x - lh[k]) + (v.y - ll[k]);
-                            }
-                            tf_s[k][r] = f;
-                        }
+                        for (int k = 0; k < 3; k++) tf_s[k][r] = k < d ? dr_offset(PT.xq, s, k, lh[k], ll[k]) : 0.f;
                     }
                     __syncthreads();
                     if (need)
@@ -703,6 +748,20 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         }
     }
     __syncthreads();
+    {  // bounding box of the winners
+        long long blo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, bhi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+        for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
+            const int32_t sid = win[gi];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k >= d) break;
+                const long long kv = dkey((k == 0 ? x0 : (k == 1 ? x1 : x2))[sid]);
+                blo[k] = min(blo[k], kv);
+                bhi[k] = max(bhi[k], kv);
+            }
+        }
+        block_box_write(blo, bhi, outbox + 6 * (int64_t)node);
+    }
     int P = 1;
     while (P < G) P <<= 1;
     for (int i = G + threadIdx.x; i < P; i += blockDim.x) win[i] = INT_MAX;
@@ -719,7 +778,8 @@ int64_t gridsize(int g, int d) {
 }
 
 void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, int nl, int g, int d,
-                       const DRPoints &pts, int32_t *const *outptr, int32_t *outcnt, int lb, cudaStream_t s) {
+                       const DRPoints &pts, int32_t *const *outptr, int32_t *outcnt, int lb, const long long *tbox,
+                       long long *outbox, cudaStream_t s) {
     if (nl <= 0) return;
     int G = (int)gridsize(g, d);
     size_t sm = dr_smem_bytes(G);
@@ -733,7 +793,7 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
     bins.alloc((size_t)std::max<int64_t>(ttot, 1), s);
     pq.alloc((size_t)std::max<int64_t>(ttot, 1), s);
     ProfScope ps(KT_DATAREDUCT, s);
-    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, pts, outptr, outcnt, lb, bins.p, pq.p);
+    k_datareduct<<<nl, DR_THREADS, sm, s>>>(toff, tdata, g, d, pts, outptr, outcnt, lb, bins.p, pq.p, tbox, outbox);
     H2_LAUNCH("k_datareduct");
 }
 
@@ -754,11 +814,13 @@ void hidr_impl(h2_hidr_s *h) {
     H2_CUDA(cudaMemsetAsync(h->xptr.p, 0, nn * sizeof(int32_t *), s));
     H2_CUDA(cudaMemsetAsync(h->yptr.p, 0, nn * sizeof(int32_t *), s));
     DRPoints pts;
+    pts.xq = t->xq.p;
     for (int k = 0; k < 3; k++) {
         pts.x[k] = t->xs[k].p;
-        pts.xg[k] = t->xg[k].p;
         pts.ref[k] = t->geom.lo[k];
     }
+    h->xbox.alloc((size_t)nn * 6, s);
+    h->ybox.alloc((size_t)nn * 6, s);
     pts.R = t->geom.side;
     h->xbufs.resize(t->nlevels);
     h->ybufs.resize(t->nlevels);
@@ -766,6 +828,7 @@ void hidr_impl(h2_hidr_s *h) {
     h->ymax_level.assign(t->nlevels, 0);
     DevBuf<int64_t> sz, cap, toff, coff;
     DevBuf<int32_t> tdata;
+    DevBuf<long long> tbox;
     cudaEvent_t e0, e1, e2;
     H2_CUDA(cudaEventCreate(&e0));
     H2_CUDA(cudaEventCreate(&e1));
@@ -787,10 +850,11 @@ void hidr_impl(h2_hidr_s *h) {
         h->xbufs[l].alloc(ctot > 0 ? ctot : 1, s);
         k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, h->xbufs[l].p, coff.p, h->xptr.p);
         H2_LAUNCH("k_set_ptrs");
+        tbox.alloc((size_t)nl * 6, s);
         k_gather_up<<<nl, 256, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, t->end.p, h->xptr.p, h->xcnt.p,
-                                       toff.p, tdata.p);
+                                       toff.p, tdata.p, t->xs[0].p, t->xs[1].p, t->xs[2].p, d, h->xbox.p, tbox.p);
         H2_LAUNCH("k_gather_up");
-        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g1, d, pts, h->xptr.p, h->xcnt.p, lb, s);
+        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g1, d, pts, h->xptr.p, h->xcnt.p, lb, tbox.p, h->xbox.p, s);
         h->xtotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e1, s));
@@ -811,10 +875,11 @@ void hidr_impl(h2_hidr_s *h) {
         h->ybufs[l].alloc(ctot > 0 ? ctot : 1, s);
         k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, h->ybufs[l].p, coff.p, h->yptr.p);
         H2_LAUNCH("k_set_ptrs");
+        tbox.alloc((size_t)nl * 6, s);
         k_gather_down<<<nl, 256, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->xptr.p, h->xcnt.p,
-                                         h->yptr.p, h->ycnt.p, toff.p, tdata.p);
+                                         h->yptr.p, h->ycnt.p, toff.p, tdata.p, h->xbox.p, h->ybox.p, tbox.p);
         H2_LAUNCH("k_gather_down");
-        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, pts, h->yptr.p, h->ycnt.p, lb, s);
+        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, pts, h->yptr.p, h->ycnt.p, lb, tbox.p, h->ybox.p, s);
         h->ytotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e2, s));
@@ -836,11 +901,15 @@ void hidr_impl(h2_hidr_s *h) {
         }
 }
 
-int64_t datareduct_one(const DRPoints &pts, int d, int64_t n, int g, int32_t *out_dev, cudaStream_t s) {
+int64_t datareduct_one(const DRPoints &pts, int d, int64_t n, int g, const long long *box_keys, int32_t *out_dev,
+                       cudaStream_t s) {
     // one node whose set is the labels 0..n-1
     DevBuf<int64_t> toff;
     DevBuf<int32_t> tdata, cnt;
     DevBuf<int32_t *> optr;
+    DevBuf<long long> box;
+    box.alloc(12, s);  // the set's box, then the result's
+    H2_CUDA(cudaMemcpyAsync(box.p, box_keys, 6 * sizeof(long long), cudaMemcpyHostToDevice, s));
     toff.alloc(2, s);
     tdata.alloc(n, s);
     cnt.alloc(1, s);
@@ -851,7 +920,7 @@ int64_t datareduct_one(const DRPoints &pts, int d, int64_t n, int g, int32_t *ou
     H2_CUDA(cudaMemcpyAsync(toff.p, offs, sizeof offs, cudaMemcpyHostToDevice, s));
     H2_CUDA(cudaMemcpyAsync(tdata.p, ids.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     H2_CUDA(cudaMemcpyAsync(optr.p, &out_dev, sizeof(int32_t *), cudaMemcpyHostToDevice, s));
-    launch_datareduct(toff.p, tdata.p, n, 1, g, d, pts, optr.p, cnt.p, 0, s);
+    launch_datareduct(toff.p, tdata.p, n, 1, g, d, pts, optr.p, cnt.p, 0, box.p, box.p + 6, s);
     return read_scalar(cnt.p, s);
 }
 

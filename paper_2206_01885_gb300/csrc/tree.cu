@@ -191,12 +191,14 @@ __device__ __forceinline__ float2 h2_split(double v) {
 }
 
 __global__ void k_root_coords(const double *x0, const double *x1, const double *x2, int64_t n, int d, const Geom *g,
-                              float2 *r0, float2 *r1, float2 *r2) {
+                              float4 *xq) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    r0[p] = h2_split(x0[p] - g->lo[0]);
-    if (d > 1) r1[p] = h2_split(x1[p] - g->lo[1]);
-    if (d > 2) r2[p] = h2_split(x2[p] - g->lo[2]);
+    const float2 a = h2_split(x0[p] - g->lo[0]);
+    const float2 b = d > 1 ? h2_split(x1[p] - g->lo[1]) : make_float2(0.f, 0.f);
+    const float2 c = d > 2 ? h2_split(x2[p] - g->lo[2]) : make_float2(0.f, 0.f);
+    xq[2 * p] = make_float4(a.x, b.x, c.x, a.y);
+    xq[2 * p + 1] = make_float4(b.y, c.y, 0.f, 0.f);
 }
 
 __global__ void k_centre_split(const double *c0, const double *c1, const double *c2, int nn, int d, const Geom *g,
@@ -397,9 +399,8 @@ void tree_build_impl(h2_tree_s *t, const double *pts) {
     k_rel_coords<<<t->nnodes, 128, 0, s>>>(t->nchild.p, t->begin.p, t->end.p, t->cen[0].p, t->cen[1].p, t->cen[2].p,
                                           t->xs[0].p, t->xs[1].p, t->xs[2].p, d, t->xr[0].p, t->xr[1].p, t->xr[2].p);
     H2_LAUNCH("k_rel_coords");
-    for (int k = 0; k < 3; k++) t->xg[k].alloc(k < d ? n : 1, s);
-    k_root_coords<<<blocks_for(n, 256), 256, 0, s>>>(t->xs[0].p, t->xs[1].p, t->xs[2].p, n, d, g.p, t->xg[0].p,
-                                                     t->xg[1].p, t->xg[2].p);
+    t->xq.alloc(2 * n, s);
+    k_root_coords<<<blocks_for(n, 256), 256, 0, s>>>(t->xs[0].p, t->xs[1].p, t->xs[2].p, n, d, g.p, t->xq.p);
     H2_LAUNCH("k_root_coords");
     for (int k = 0; k < 3; k++) t->cenf[k].alloc(k < d ? t->nnodes : 1, s);
     k_centre_split<<<blocks_for(t->nnodes, 256), 256, 0, s>>>(t->cen[0].p, t->cen[1].p, t->cen[2].p, t->nnodes, d,

@@ -132,7 +132,7 @@ __global__ void k_exact_rows(const int64_t *rows, int64_t nrows, const int32_t *
 // Chunked form of k_exact_rows: CTA (r, c) sums chunk c (ER_CHUNK points) of
 // row r into part[r * nch + c]; k_exact_sum adds a row's chunks in order.
 // Short CTAs let other streams' kernels take SMs as they retire.
-constexpr int ER_CHUNK = 1 << 16;
+constexpr int ER_CHUNK = 1 << 14;
 constexpr int ER_THREADS = 256;
 
 __global__ void __launch_bounds__(ER_THREADS)

@@ -142,10 +142,10 @@ __device__ __forceinline__ void argmax_key(long long &k, int &i, long long k2, i
 // value falls below sqrt(2^-24) of its last recomputed value, the float32
 // analogue of LAPACK's sqrt(eps).
 template <class Real, int RPL>
-__global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt, const int32_t *cc,
+__global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr(int lb, const int32_t *ycnt, const int32_t *cc,
                                                      const int64_t *aoff, Real *Abase, double tol, int32_t *kout,
                                                      const int64_t *coff, int32_t *pivbase) {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int a = blockIdx.x, node = lb + a;
     const int m = ycnt[node], c = cc[node];
     if (m == 0 || c == 0) {
@@ -162,10 +162,11 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
     __shared__ long long bkey[QR_WARPS];
     __shared__ int bidx[QR_WARPS];
     __shared__ int s_p, s_stop;
-    __shared__ double s_tau, s_beta, s_sc;
+    __shared__ Real s_tau, s_beta, s_sc;
+    __shared__ int s_has;
     Real *A = Abase + aoff[a];
     int32_t *piv = pivbase + coff[a];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const double tol3z = sqrt(ldexp(1.0, sizeof(Real) == 8 ? -53 : -24));
 
     for (int l = threadIdx.x; l < c; l += blockDim.x) pv[l] = l;
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
     // float64 form: nrm holds column norms (LAPACK downdating); float32 form:
     // nrm holds squared column norms, downdated as nu^2 - r^2 in float64
     constexpr bool SQ = sizeof(Real) == 4;
-    for (int l = warp; l < c; l += QR_WARPS) {
+    for (int l = warp; l < c; l += nwarps) {
         const Real *col = A + (int64_t)l * m;
         Real sp = 0;
         for (int r = lane; r < m; r += 32) sp += col[r] * col[r];
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
         if (threadIdx.x == 0) {
             long long kk2 = bkey[0];
             int ii = bidx[0];
-            for (int w = 1; w < QR_WARPS; w++) argmax_key(kk2, ii, bkey[w], bidx[w]);
+            for (int w = 1; w < nwarps; w++) argmax_key(kk2, ii, bkey[w], bidx[w]);
             const double vv = __longlong_as_double(kk2);
             if (j == 0) r11 = vv;
             s_p = ii;
@@ -231,35 +232,36 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
         part = warp_sum(part);
         if (lane == 0) red[warp] = (double)part;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double sigma = 0.0;
-            for (int w = 0; w < QR_WARPS; w++) sigma += red[w];
-            const double alpha = (double)aj[j];
-            double tau = 0.0, beta = alpha, sc = 0.0;
-            if (sigma != 0.0) {
-                double xn = sqrt(alpha * alpha + sigma);
-                beta = alpha >= 0.0 ? -xn : xn;
+        if (threadIdx.x == 0) {  // in the block's type
+            Real sigma = 0;
+            for (int w = 0; w < nwarps; w++) sigma += (Real)red[w];
+            const Real alpha = aj[j];
+            Real tau = 0, beta = alpha, sc = 0;
+            if (sigma != (Real)0) {
+                Real xn = sqrt(alpha * alpha + sigma);
+                beta = alpha >= (Real)0 ? -xn : xn;
                 tau = (beta - alpha) / beta;
-                sc = 1.0 / (alpha - beta);
+                sc = (Real)1 / (alpha - beta);
             }
             s_tau = tau;
             s_beta = beta;
             s_sc = sc;
-            s_stop = (alpha == 0.0 && sigma == 0.0) ? 1 : 0;  // exactly zero pivot column
+            s_has = tau != (Real)0;
+            s_stop = (alpha == (Real)0 && sigma == (Real)0) ? 1 : 0;  // exactly zero pivot column
         }
         __syncthreads();
         if (s_stop) break;
-        const bool has_tau = s_tau != 0.0;
-        const Real scR = (Real)s_sc;
+        const bool has_tau = s_has != 0;
+        const Real scR = s_sc;
         for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) v[r] = aj[r] * scR;
         __syncthreads();
-        if (threadIdx.x == 0) aj[j] = (Real)s_beta;
-        const Real tauR = (Real)s_tau;
+        if (threadIdx.x == 0) aj[j] = s_beta;
+        const Real tauR = s_tau;
         // apply to the trailing columns (one warp per column); row j of the
         // result goes to shared memory for the norm downdate.  With RPL > 0 a
         // lane keeps its RPL rows of the column in registers: all loads are
         // issued together and the update reuses them.
-        for (int l = j + 1 + warp; l < c; l += QR_WARPS) {
+        for (int l = j + 1 + warp; l < c; l += nwarps) {
             Real *al = A + (int64_t)l * m;
             Real ajl = al[j];
             if constexpr (RPL > 0) {
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_cpqr(int lb, const int32_t *ycnt
             }
         }
         __syncthreads();
-        for (int l = j + 1 + warp; l < c; l += QR_WARPS) {
+        for (int l = j + 1 + warp; l < c; l += nwarps) {
             if (!flag[l]) continue;
             const Real *al = A + (int64_t)l * m;
             Real sp = 0;
@@ -465,10 +467,18 @@ __global__ void k_compact_skel(int nn, const int32_t *kk, const int64_t *off, in
 
 // launch the QR with the smallest register slice that holds the level's tallest
 // block (rows per lane = ceil(mmax / 32)), or the loop form above 1024 rows
+// threads of a k_cpqr CTA for a level with at most cmax columns: a QR step is
+// a chain of block barriers and one-thread scalar work, so narrow blocks run
+// in small CTAs, several to a SM, which hide each other's chains (measured:
+// 128 threads up to 128 columns beat 256 or 512)
+int qr_threads(int cmax) { return cmax <= 128 ? 128 : QR_THREADS; }
+
 template <class Real>
 void launch_cpqr(int nl, size_t smem, int mmax, int lb, const int32_t *ycnt, const int32_t *cc, const int64_t *aoff,
-                 Real *A, double tol, int32_t *kout, const int64_t *coff, int32_t *piv, cudaStream_t s) {
-#define H2_QR(R) k_cpqr<Real, R><<<nl, QR_THREADS, smem, s>>>(lb, ycnt, cc, aoff, A, tol, kout, coff, piv)
+                 Real *A, double tol, int32_t *kout, const int64_t *coff, int32_t *piv, cudaStream_t s,
+                 int cmax = 1 << 30) {
+    const int nthr = qr_threads(cmax);
+#define H2_QR(R) k_cpqr<Real, R><<<nl, nthr, smem, s>>>(lb, ycnt, cc, aoff, A, tol, kout, coff, piv)
     int rpl = (mmax + 31) / 32;
     // the float64 form is bound by the float64 pipe, not by load latency: the
     // loop form keeps its register count (and occupancy) low
@@ -582,10 +592,10 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
             ProfScope ps(KT_CPQR, s);
             if (f64)
                 launch_cpqr<double>(nl, qr_smem(cmax, mmax, esize), mmax, lb, h->ycnt.p, A->c.p, aoff.p,
-                                    reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p, piv.p, s);
+                                    reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p, piv.p, s, cmax);
             else
                 launch_cpqr<float>(nl, qr_smem(cmax, mmax, esize), mmax, lb, h->ycnt.p, A->c.p, aoff.p,
-                                   reinterpret_cast<float *>(Ablk.p), A->id_tol, A->k.p, coff.p, piv.p, s);
+                                   reinterpret_cast<float *>(Ablk.p), A->id_tol, A->k.p, coff.p, piv.p, s, cmax);
             H2_LAUNCH("k_cpqr");
         }
         szk.alloc(nl, s); szu.alloc(nl, s); koff.alloc(nl + 1, s); uoff.alloc(nl + 1, s);
@@ -613,11 +623,11 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         {
             ProfScope ps(KT_SOLVE, s);
             if (f64)
-                k_id_solve<double><<<nl, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(
+                k_id_solve<double><<<nl, qr_threads(cmax), (size_t)P * sizeof(int32_t), s>>>(
                     lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<double *>(Ablk.p),
                     reinterpret_cast<double *>(Ablk.p), coff.p, piv.p, cand.p, A->uptr.p, skptr.p);
             else
-                k_id_solve<float><<<nl, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(
+                k_id_solve<float><<<nl, qr_threads(cmax), (size_t)P * sizeof(int32_t), s>>>(
                     lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<float *>(Ablk.p), Wf.p, coff.p, piv.p,
                     cand.p, A->uptr.p, skptr.p);
             H2_LAUNCH("k_id_solve");

@@ -57,6 +57,11 @@ MIN_SQ = {3: 8, 2: 5}
 PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOPS_PER_PAIR = 11  # 3 sub, 3 mul/add for r^2 (5 flops), 1 rsqrt, 1 fma accumulate (2 flops)
+# DRAM bytes per algorithmic unit (ncu dram__bytes_read.sum + dram__bytes_write.sum
+# over the timed step of the 262,144-point workloads): float64 CPQR bytes per QR
+# flop; mixed-form DataReduct bytes per algorithmic byte.  A changed kernel needs
+# a new capture.
+TRAFFIC_PER_UNIT = {("cpqr", "fp64"): 352.4e9 / 8.7668e10, ("datareduct", "mixed"): 7.726e9 / 3.752e9}
 
 
 def measured_peaks():
@@ -276,19 +281,26 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
     # the exact rows run on a side stream beside the path, so their event span
     # is not their own device time: the dominant kernel is taken from the path
     dom = max((k for k in ktimes if k != "exact_rows"), key=lambda k: ktimes[k]["ms"])
+    # DRAM traffic per launch of the dominant kernel: ncu's dram read + write of
+    # the 262,144-point step per algorithmic unit, scaled to this launch's units
+    traffic_ratio = TRAFFIC_PER_UNIT.get((dom, wl["prec"]))
     launches_per_step = ktimes[dom]["launches"] / args.steps
     dom_ms_per_launch = ktimes[dom]["ms"] / max(1, ktimes[dom]["launches"])
     if dom in work and work[dom][0] == "hbm":
         achieved = work[dom][1] / launches_per_step / (dom_ms_per_launch * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{peak_kind} (copy bandwidth)",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": traffic_ratio * work[dom][1] / launches_per_step if traffic_ratio else None,
+                "peak_source": f"{peak_kind} (copy bandwidth)",
                 "work_per_launch": work[dom][1] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
     elif dom in work:
         peak_src = "derived: GB300 nominal float64 1.25 TFLOP/s" if fp64 else \
             "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
         achieved = work[dom][1] / launches_per_step / (dom_ms_per_launch * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None, "peak_source": peak_src,
+                "frac": achieved / alu_peak,
+                "traffic": traffic_ratio * work[dom][1] / launches_per_step if traffic_ratio else None,
+                "peak_source": peak_src,
                 "work_per_launch": work[dom][1] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "TFLOP/s", "frac": None,

@@ -337,7 +337,7 @@ __host__ __device__ __forceinline__ size_t dr_smem_bytes(int G) {
 // The box of the result goes to outbox[node].
 __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
                                                            DRPoints PT, int32_t *const *outptr, int32_t *outcnt, int lb,
-                                                           int32_t *bin_base, float4 *pq_base, const long long *tbox,
+                                                           int2 *bin_base, float4 *pq_base, const long long *tbox,
                                                            long long *outbox) {
     const double *x0 = PT.x[0], *x1 = PT.x[1], *x2 = PT.x[2];
     extern __shared__ unsigned char smem_raw[];
@@ -412,10 +412,9 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         // search stops after ring r once that sum is below the square of
         // (r + 1/2) h_min - delta, a lower bound for every point in a farther
         // cell (delta = 1e-5 W + 1e-12 R covers the float32 binning error).
-        int32_t *bidx = bin_base + t0;  // bin of each entry
+        int2 *bidx = bin_base + t0;     // bin of each entry and its rank in the bin
         float4 *pq = pq_base + t0;      // in bin order: float32 offsets and the label (as bits)
         int *bstart = reinterpret_cast<int *>(smem_raw + dr_bins_offset(G));
-        int *bcur = bstart + G + 1;
         const float delf = (float)(1e-5 * W + 1e-12 * PT.R);
         const float hminf = (float)hmin;
         for (int b = threadIdx.x; b <= G; b += blockDim.x) bstart[b] = 0;
@@ -423,7 +422,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
         // counting sort into cells.  Consecutive labels are Morton-coherent and
         // mostly share a cell, so the atomics are warp-aggregated: lanes with the
         // same cell elect one leader that adds the group's count, and each lane
-        // takes base + its rank in the group.
+        // takes the old count + its rank in the group as its rank in the bin.
         const unsigned lt = (1u << lane) - 1u;
         for (int64_t p0 = (int64_t)warp * 32; p0 < nt; p0 += blockDim.x) {
             const int64_t p = p0 + lane;
@@ -443,32 +442,26 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     bi += cidx * stride;
                     stride *= g;
                 }
-                bidx[p] = bi;
             }
-            const unsigned peers = __match_any_sync(0xffffffffu, bi);
-            if (bi >= 0 && (peers & lt) == 0u) atomicAdd(&bstart[bi + 1], __popc(peers));
-        }
-        __syncthreads();
-        block_scan_inclusive(bstart, G + 1, scratch);
-        for (int b = threadIdx.x; b < G; b += blockDim.x) bcur[b] = bstart[b];
-        __syncthreads();
-        for (int64_t p0 = (int64_t)warp * 32; p0 < nt; p0 += blockDim.x) {
-            const int64_t p = p0 + lane;
-            const int bi = p < nt ? bidx[p] : -1;
             const unsigned peers = __match_any_sync(0xffffffffu, bi);
             const int leader = __ffs(peers) - 1;
             int base = 0;
-            if (bi >= 0 && lane == leader) base = atomicAdd(&bcur[bi], __popc(peers));
+            if (bi >= 0 && lane == leader) base = atomicAdd(&bstart[bi + 1], __popc(peers));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (bi >= 0) {
-                const int pos = base + __popc(peers & lt);
-                const int32_t sid = T[p];
-                const float4 qa = PT.xq[2 * (int64_t)sid], qb = PT.xq[2 * (int64_t)sid + 1];
-                const float f0 = (qa.x - lh[0]) + (qa.w - ll[0]);
-                const float f1 = d > 1 ? (qa.y - lh[1]) + (qb.x - ll[1]) : 0.f;
-                const float f2 = d > 2 ? (qa.z - lh[2]) + (qb.y - ll[2]) : 0.f;
-                pq[pos] = make_float4(f0, f1, f2, __int_as_float(sid));
-            }
+            if (bi >= 0) bidx[p] = make_int2(bi, base + __popc(peers & lt));
+        }
+        __syncthreads();
+        block_scan_inclusive(bstart, G + 1, scratch);  // bstart[b]: first position of bin b
+        __syncthreads();
+        for (int64_t p = threadIdx.x; p < nt; p += blockDim.x) {
+            const int2 bo = bidx[p];
+            const int pos = bstart[bo.x] + bo.y;
+            const int32_t sid = T[p];
+            const float4 qa = PT.xq[2 * (int64_t)sid], qb = PT.xq[2 * (int64_t)sid + 1];
+            const float f0 = (qa.x - lh[0]) + (qa.w - ll[0]);
+            const float f1 = d > 1 ? (qa.y - lh[1]) + (qb.x - ll[1]) : 0.f;
+            const float f2 = d > 2 ? (qa.z - lh[2]) + (qb.y - ll[2]) : 0.f;
+            pq[pos] = make_float4(f0, f1, f2, __int_as_float(sid));
         }
         // grid points: float64 q and its float32 offset qf, computed once each
         double *qtab = reinterpret_cast<double *>(smem_raw + dr_qtab_offset(G));
@@ -541,15 +534,25 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     }
                     const int total = __shfl_sync(0xffffffffu, inc, 31);
                     const int exc = inc - cn;
+                    // one selected cell (ring 0 always; most searches stop there):
+                    // its range directly, no lane search
+                    const unsigned sel = __ballot_sync(0xffffffffu, cn > 0);
+                    const bool one = (sel & (sel - 1)) == 0u;
+                    const int cs1 = one && sel ? __shfl_sync(0xffffffffu, cs, __ffs(sel) - 1) : 0;
                     for (int f0 = 0; f0 < total; f0 += 32) {
                         const int f = f0 + lane;
-                        int src = 0;  // last lane whose range starts at or before f
+                        int p;
+                        if (one) {
+                            p = cs1 + f;
+                        } else {
+                            int src = 0;  // last lane whose range starts at or before f
 #pragma unroll
-                        for (int st = 16; st > 0; st >>= 1) {
-                            const int ex = __shfl_sync(0xffffffffu, exc, src + st);
-                            if (ex <= f) src += st;
+                            for (int st = 16; st > 0; st >>= 1) {
+                                const int ex = __shfl_sync(0xffffffffu, exc, src + st);
+                                if (ex <= f) src += st;
+                            }
+                            p = __shfl_sync(0xffffffffu, cs, src) + f - __shfl_sync(0xffffffffu, exc, src);
                         }
-                        const int p = __shfl_sync(0xffffffffu, cs, src) + f - __shfl_sync(0xffffffffu, exc, src);
                         if (f < total) {
                             const float4 e = pq[p];
                             const float e0f = e.x - qf[0], e1f = e.y - qf[1], e2f = e.z - qf[2];
@@ -788,7 +791,7 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
         size_t mx = std::max(dr_smem_bytes(DR_MAX_GRID), dr_smem_bytes(DR_BIN_MAX));
         H2_CUDA(cudaFuncSetAttribute(k_datareduct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
     });
-    DevBuf<int32_t> bins;
+    DevBuf<int2> bins;
     DevBuf<float4> pq;
     bins.alloc((size_t)std::max<int64_t>(ttot, 1), s);
     pq.alloc((size_t)std::max<int64_t>(ttot, 1), s);

@@ -45,7 +45,23 @@ WORKLOADS = {
                            rows=1000),
     "cube8k_fp64": dict(n=8000, d=3, kernel="coulomb", kparams=(), q=200, eps=1e-6, prec="fp64", seed=1,
                         rows=1000),
+    # the paper's second dataset: three unit spheres on a unit equilateral triangle
+    "spheres3_1m_fp64": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-8, prec="fp64", seed=6,
+                             rows=1000, points="spheres3", compare="spheres3_1m_mixed"),
+    "spheres3_1m_mixed": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-5, prec="mixed", seed=6,
+                              rows=1000, points="spheres3"),
 }
+
+
+def points_name(wl):
+    return "three unit spheres" if wl.get("points") == "spheres3" else "uniform cube"
+
+
+def workload_points(wl, n, seed):
+    """The workload's point distribution (uniform cube unless it names another)."""
+    if wl.get("points") == "spheres3":
+        return I.three_spheres(n, seed=seed)
+    return I.uniform_cube(n, wl["d"], seed=seed)
 # same-size unit cells at integer offset v are well separated under eq. (1)
 # with tau = 7/10 when |v|^2 >= 8 (3D) / 5 (2D)
 MIN_SQ = {3: 8, 2: 5}
@@ -158,7 +174,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
 
     n, d = wl["n"], wl["d"]
     seed = problem_seed(wl["seed"], rank)  # independent problem per rank
-    pts = I.uniform_cube(n, d, seed=seed)
+    pts = workload_points(wl, n, seed)
     z = I.standard_normal(n, seed=seed + 7)
     rows = I.sample_rows(n, wl["rows"], seed=seed + 9)
     pts_d = torch.from_numpy(pts).to(dev)
@@ -384,7 +400,7 @@ def gpu_arm(args, wl, rank, world, dev):
         "metric": METRIC, "value": prim["value"], "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": prim["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if wl["prec"] == "fp64" else "f32+f64",
-        "data": "synthetic (seeded uniform cube, standard-normal right-hand side)",
+        "data": f"synthetic (seeded {points_name(wl)}, standard-normal right-hand side)",
     }
     result.update({k: v for k, v in prim.items() if k not in ("value", "ms_per_step")})
     other = wl.get("compare")
@@ -404,7 +420,7 @@ def oracle_sample(wl, n_s):
     size, kernel and tolerance at n_s points (calibrated g as on the GPU)."""
     from oracle import h2_oracle as O
     d = wl["d"]
-    pts = I.uniform_cube(n_s, d, seed=wl["seed"])
+    pts = workload_points(wl, n_s, wl["seed"])
     z = I.standard_normal(n_s, seed=wl["seed"] + 7)
     rows = I.sample_rows(n_s, wl["rows"], seed=wl["seed"] + 9)
     g = wl.get("g_oracle")
@@ -451,7 +467,7 @@ def reference_arm(args, wl):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(secs) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded uniform cube)",
+            "data": f"synthetic (seeded {points_name(wl)})",
             "config": {"workload": args.workload, "n": n_s, "leaf_size": wl["q"], "id_tol": wl["eps"],
                        "g": wl["g_oracle"], "note": "bounded sample of the workload on the host cores"},
             "rel_err": errs[-1],

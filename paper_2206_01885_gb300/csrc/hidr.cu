@@ -332,6 +332,134 @@ __host__ __device__ __forceinline__ size_t dr_smem_bytes(int G) {
 
 
 
+// A non-empty cell in the search list: its bin in bits 0..11 and its index
+// along coordinate k in bits 12 + 6k .. 17 + 6k (the binned search has
+// g^d <= 4096, so g <= 64).
+__device__ __forceinline__ int dr_pack_cell(int bin, int d, int g) {
+    int v = bin, rem = bin;
+    for (int k = 0; k < d; k++) {
+        v |= (rem % g) << (12 + 6 * k);
+        rem /= g;
+    }
+    return v;
+}
+
+// Lower bound of the squared distance from the grid point (offset qf) to the
+// packed cell widened by delf per side, and the cell's Chebyshev distance from cid.
+__device__ __forceinline__ float dr_cell_lb(int packed, int d, const int *cid, const bool *flat, const float *hf,
+                                            const float *qf, float delf, int &cheb) {
+    float lb = 0.f;
+    cheb = 0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (k >= d) break;
+        const int ck = (packed >> (12 + 6 * k)) & 63;
+        if (!flat[k]) {
+            cheb = max(cheb, abs(ck - cid[k]));
+            const float lo = (float)ck * hf[k] - delf, hi = (float)(ck + 1) * hf[k] + delf;
+            const float gap = fmaxf(0.f, fmaxf(lo - qf[k], qf[k] - hi));
+            lb = fmaf(gap, gap, lb);
+        }
+    }
+    return lb;
+}
+
+// Float32 top-two over the points of the cells the lanes selected (lane c's
+// cell `bin` when ok), walked as one flat range across the warp: lane c's cell
+// is [cs, cs + cn) at offset exc of the warp's prefix sum of the counts.
+__device__ __forceinline__ void dr_scan_top2(bool ok, int bin, const int *bstart, const float4 *pq, const float *qf,
+                                             float &b1, float &b2, int &p1, int lane) {
+    if (__ballot_sync(0xffffffffu, ok) == 0u) return;
+    int cs = 0, cn = 0;
+    if (ok) {
+        cs = bstart[bin];
+        cn = bstart[bin + 1] - cs;
+    }
+    int inc = cn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    const int exc = inc - cn;
+    // one selected cell (ring 0 always): its range directly, no lane search
+    const unsigned sel = __ballot_sync(0xffffffffu, cn > 0);
+    const bool one = (sel & (sel - 1)) == 0u;
+    const int cs1 = one && sel ? __shfl_sync(0xffffffffu, cs, __ffs(sel) - 1) : 0;
+    for (int f0 = 0; f0 < total; f0 += 32) {
+        const int f = f0 + lane;
+        int p;
+        if (one) {
+            p = cs1 + f;
+        } else {
+            int src = 0;  // last lane whose range starts at or before f
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int ex = __shfl_sync(0xffffffffu, exc, src + st);
+                if (ex <= f) src += st;
+            }
+            p = __shfl_sync(0xffffffffu, cs, src) + f - __shfl_sync(0xffffffffu, exc, src);
+        }
+        if (f < total) {
+            const float4 e = pq[p];
+            const float e0f = e.x - qf[0], e1f = e.y - qf[1], e2f = e.z - qf[2];
+            const float d32 = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f));
+            if (d32 < b2) {
+                if (d32 < b1) {
+                    b2 = b1;
+                    b1 = d32;
+                    p1 = p;
+                } else {
+                    b2 = d32;
+                }
+            }
+        }
+    }
+}
+
+// Near ties: every point of the selected cells whose float32 distance is at
+// most limx, compared in float64 (non-negative doubles order as their bit
+// patterns), the smaller label taking ties; (bk, bl) is the warp's best.
+__device__ __forceinline__ void dr_scan_exact(bool ok, int bin, const int *bstart, const float4 *pq, const float *qf,
+                                              float limx, int d, const double *x0, const double *x1, const double *x2,
+                                              const double *q, long long &bk, int32_t &bl, int lane) {
+    unsigned cm = __ballot_sync(0xffffffffu, ok);
+    while (cm) {
+        const int b = __shfl_sync(0xffffffffu, bin, __ffs(cm) - 1);
+        cm &= cm - 1;
+        const int pe = bstart[b + 1];
+        for (int p0 = bstart[b]; p0 < pe; p0 += 32) {
+            const int p = p0 + lane;
+            bool c = false;
+            int32_t id = INT_MAX;
+            if (p < pe) {
+                const float4 e = pq[p];
+                const float e0f = e.x - qf[0], e1f = e.y - qf[1], e2f = e.z - qf[2];
+                c = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f)) <= limx;
+                id = __float_as_int(e.w);
+            }
+            unsigned pm = __ballot_sync(0xffffffffu, c);
+            if (pm == 0u) continue;
+            long long kk = LLONG_MAX;
+            if (!c) id = INT_MAX;
+            if (c)
+                kk = __double_as_longlong(h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0, d > 2 ? x2[id] : 0.0, q[0], q[1],
+                                                   q[2]));
+            while (pm) {
+                const int s2 = __ffs(pm) - 1;
+                pm &= pm - 1;
+                const long long kv = __shfl_sync(0xffffffffu, kk, s2);
+                const int32_t iv = __shfl_sync(0xffffffffu, id, s2);
+                if (kv < bk || (kv == bk && iv < bl)) {
+                    bk = kv;
+                    bl = iv;
+                }
+            }
+        }
+    }
+}
+
 // One CTA per node.  tdata[toff[a] .. toff[a+1]) are the labels of S (T),
 // tbox[a] its bounding box; coordinates of label s are (x0[s], x1[s], x2[s]).
 // The box of the result goes to outbox[node].
@@ -480,7 +608,16 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     qftab[3 * gi + k] = (float)__dsub_rn(qk, l[k]);
                 }
             }
+        // the non-empty cells, for searches that go past ring 1 (the cursor
+        // area of the bins is free after the scatter; order does not matter)
+        int *nel = bstart + G + 1;
+        __shared__ int s_nne;
+        if (threadIdx.x == 0) s_nne = 0;
         __syncthreads();
+        for (int b = threadIdx.x; b < G; b += blockDim.x)
+            if (bstart[b + 1] > bstart[b]) nel[atomicAdd(&s_nne, 1)] = dr_pack_cell(b, d, g);
+        __syncthreads();
+        const int nne = s_nne;
         for (int gi = warp; gi < G; gi += nw) {
             double q[3] = {0.0, 0.0, 0.0};
             float qf[3] = {0.f, 0.f, 0.f};
@@ -507,11 +644,14 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             float b1 = INFINITY, b2 = INFINITY;  // this lane's two smallest float32 distances
             int p1 = -1;                         // bin-order position of its smallest
             float lim = INFINITY;                // the warp's smallest distance + M
-            int rlast = rmax;
-            for (int r = 0; r <= rmax; r++) {
+            // rings 0 and 1 with the stop test; a search still open after ring 1
+            // (sparse or empty surroundings) scans the non-empty cells instead
+            const int rA = min(rmax, 1);
+            int stage = 2;  // 0 or 1: stopped after that ring; 2: the non-empty cells were scanned
+            for (int r = 0; r <= rA; r++) {
                 const int side = 2 * r + 1;
                 int total = 1;
-                #pragma unroll
+#pragma unroll
                 for (int k = 0; k < 3; k++)
                     if (k < d) total *= flat[k] ? 1 : side;
                 for (int e0 = 0; e0 < total; e0 += 32) {
@@ -519,62 +659,49 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                     float lb = 0.f;
                     bool ok = e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, flat, hf, qf, delf, bin, lb);
                     ok = ok && lb <= lim;
-                    // the selected cells' points as one range: lane c's cell is
-                    // [cs, cs + cn), at flat offset exc of the warp's prefix sum
-                    int cs = 0, cn = 0;
-                    if (ok) {
-                        cs = bstart[bin];
-                        cn = bstart[bin + 1] - cs;
-                    }
-                    int inc = cn;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int t = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += t;
-                    }
-                    const int total = __shfl_sync(0xffffffffu, inc, 31);
-                    const int exc = inc - cn;
-                    // one selected cell (ring 0 always; most searches stop there):
-                    // its range directly, no lane search
-                    const unsigned sel = __ballot_sync(0xffffffffu, cn > 0);
-                    const bool one = (sel & (sel - 1)) == 0u;
-                    const int cs1 = one && sel ? __shfl_sync(0xffffffffu, cs, __ffs(sel) - 1) : 0;
-                    for (int f0 = 0; f0 < total; f0 += 32) {
-                        const int f = f0 + lane;
-                        int p;
-                        if (one) {
-                            p = cs1 + f;
-                        } else {
-                            int src = 0;  // last lane whose range starts at or before f
-#pragma unroll
-                            for (int st = 16; st > 0; st >>= 1) {
-                                const int ex = __shfl_sync(0xffffffffu, exc, src + st);
-                                if (ex <= f) src += st;
-                            }
-                            p = __shfl_sync(0xffffffffu, cs, src) + f - __shfl_sync(0xffffffffu, exc, src);
-                        }
-                        if (f < total) {
-                            const float4 e = pq[p];
-                            const float e0f = e.x - qf[0], e1f = e.y - qf[1], e2f = e.z - qf[2];
-                            const float d32 = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f));
-                            if (d32 < b2) {
-                                if (d32 < b1) {
-                                    b2 = b1;
-                                    b1 = d32;
-                                    p1 = p;
-                                } else {
-                                    b2 = d32;
-                                }
-                            }
-                        }
-                    }
+                    dr_scan_top2(ok, bin, bstart, pq, qf, b1, b2, p1, lane);
                     lim = warp_minf(b1) + M;
                 }
                 // (r + 1/2) h_min - delta and its square rounded down in float32
                 const float rr = ((float)r + 0.5f) * hminf * 0.9999996f - delf;
                 if (rr > 0.f && lim < rr * rr * 0.9999996f) {
-                    rlast = r;
+                    stage = r;
                     break;
+                }
+            }
+            if (stage == 2 && rmax <= 1) stage = rA;  // rings 0..rmax held every cell
+            if (stage == 2) {
+                // the non-empty cell with the smallest bound first (it sets lim when
+                // rings 0 and 1 were empty), then the others whose bound passes
+                float blb = INFINITY;
+                int bbin = -1;
+                for (int e0 = lane; e0 < nne; e0 += 32) {
+                    const int pk = nel[e0];
+                    int cheb;
+                    const float lb = dr_cell_lb(pk, d, cid, flat, hf, qf, delf, cheb);
+                    if (cheb >= 2 && lb < blb) {
+                        blb = lb;
+                        bbin = pk & 4095;
+                    }
+                }
+                const float mlb = warp_minf(blb);
+                const int b0 = __shfl_sync(0xffffffffu, bbin, __ffs(__ballot_sync(0xffffffffu, blb == mlb)) - 1);
+                if (b0 >= 0 && mlb <= lim) {
+                    dr_scan_top2(lane == 0, b0, bstart, pq, qf, b1, b2, p1, lane);
+                    lim = warp_minf(b1) + M;
+                }
+                for (int e0 = 0; e0 < nne; e0 += 32) {
+                    bool ok = false;
+                    int bin = 0;
+                    if (e0 + lane < nne) {
+                        const int pk = nel[e0 + lane];
+                        bin = pk & 4095;
+                        int cheb;
+                        const float lb = dr_cell_lb(pk, d, cid, flat, hf, qf, delf, cheb);
+                        ok = cheb >= 2 && lb <= lim && bin != b0;
+                    }
+                    dr_scan_top2(ok, bin, bstart, pq, qf, b1, b2, p1, lane);
+                    lim = warp_minf(b1) + M;
                 }
             }
             const float m1 = warp_minf(b1);
@@ -585,14 +712,15 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
             if (sec > limx) {
                 winner = __float_as_int(pq[__shfl_sync(0xffffffffu, p1, w)].w);
             } else {
-                // near tie: every point within M of the smallest, in float64;
-                // non-negative doubles order as their bit patterns
+                // near tie: every point within M of the smallest in float64, over
+                // the cells the search visited
                 long long bk = LLONG_MAX;
                 int32_t bl = INT_MAX;
-                for (int r = 0; r <= rlast; r++) {
+                const int rB = stage == 2 ? rA : stage;
+                for (int r = 0; r <= rB; r++) {
                     const int side = 2 * r + 1;
                     int total = 1;
-                    #pragma unroll
+#pragma unroll
                     for (int k = 0; k < 3; k++)
                         if (k < d) total *= flat[k] ? 1 : side;
                     for (int e0 = 0; e0 < total; e0 += 32) {
@@ -601,43 +729,22 @@ __global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, 
                         bool ok =
                             e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, flat, hf, qf, delf, bin, lb);
                         ok = ok && lb <= limx && bstart[bin + 1] > bstart[bin];
-                        unsigned cm = __ballot_sync(0xffffffffu, ok);
-                        while (cm) {
-                            const int b = __shfl_sync(0xffffffffu, bin, __ffs(cm) - 1);
-                            cm &= cm - 1;
-                            const int pe = bstart[b + 1];
-                            for (int p0 = bstart[b]; p0 < pe; p0 += 32) {
-                                const int p = p0 + lane;
-                                bool c = false;
-                                int32_t id = INT_MAX;
-                                if (p < pe) {
-                                    const float4 e = pq[p];
-                                    const float e0f = e.x - qf[0], e1f = e.y - qf[1], e2f = e.z - qf[2];
-                                    c = fmaf(e2f, e2f, fmaf(e1f, e1f, e0f * e0f)) <= limx;
-                                    id = __float_as_int(e.w);
-                                }
-                                unsigned pm = __ballot_sync(0xffffffffu, c);
-                                if (pm == 0u) continue;
-                                long long kk = LLONG_MAX;
-                                if (!c) id = INT_MAX;
-                                if (c) {
-                                    kk = __double_as_longlong(h2_dist2(d, x0[id], d > 1 ? x1[id] : 0.0,
-                                                                       d > 2 ? x2[id] : 0.0, q[0], q[1], q[2]));
-                                }
-                                while (pm) {
-                                    const int s2 = __ffs(pm) - 1;
-                                    pm &= pm - 1;
-                                    const long long kv = __shfl_sync(0xffffffffu, kk, s2);
-                                    const int32_t iv = __shfl_sync(0xffffffffu, id, s2);
-                                    if (kv < bk || (kv == bk && iv < bl)) {
-                                        bk = kv;
-                                        bl = iv;
-                                    }
-                                }
-                            }
-                        }
+                        dr_scan_exact(ok, bin, bstart, pq, qf, limx, d, x0, x1, x2, q, bk, bl, lane);
                     }
                 }
+                if (stage == 2)
+                    for (int e0 = 0; e0 < nne; e0 += 32) {
+                        bool ok = false;
+                        int bin = 0;
+                        if (e0 + lane < nne) {
+                            const int pk = nel[e0 + lane];
+                            bin = pk & 4095;
+                            int cheb;
+                            const float lb = dr_cell_lb(pk, d, cid, flat, hf, qf, delf, cheb);
+                            ok = cheb >= 2 && lb <= limx;
+                        }
+                        dr_scan_exact(ok, bin, bstart, pq, qf, limx, d, x0, x1, x2, q, bk, bl, lane);
+                    }
                 winner = bl;
             }
             if (lane == 0) win[gi] = winner;

@@ -312,8 +312,9 @@ constexpr int DR_BIN_MAX = 4096;    // largest grid binned in shared memory
 constexpr int DR_QTAB = 1024;       // largest grid tabulated in shared memory
 
 // dynamic shared memory of k_datareduct: win (grid-point winners, padded to a
-// power of two), then the bin starts and cursors (2G + 1 ints), then, 8-byte
-// aligned, the grid-point table (3G doubles and 3G floats) when G <= DR_QTAB
+// power of two), then the bin starts (G + 1 ints) and the list of non-empty
+// cells (G ints), then, 8-byte aligned, the grid-point table (3G doubles and 3G
+// floats) when G <= DR_QTAB
 __host__ __device__ __forceinline__ size_t dr_win_bytes(int G) {
     size_t p2 = 1;
     while (p2 < (size_t)G) p2 <<= 1;

@@ -392,10 +392,10 @@ __global__ void __launch_bounds__(QR_THREADS) k_id_solve(int lb, const int32_t *
         __syncthreads();
     }
     for (int i = k - 1; i >= 0; i--) {
-        const double rii = (double)A[i + (int64_t)i * m];
+        const double rinv = 1.0 / (double)A[i + (int64_t)i * m];  // one division per row of the solve
         for (int l = threadIdx.x; l < nr; l += blockDim.x) {
             double *e = W + i + (int64_t)(k + l) * m;
-            *e = *e / rii;
+            *e = *e * rinv;
         }
         __syncthreads();
         const int64_t work = (int64_t)i * nr;

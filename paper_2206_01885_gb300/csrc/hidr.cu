@@ -464,7 +464,7 @@ __device__ __forceinline__ void dr_scan_exact(bool ok, int bin, const int *bstar
 // One CTA per node.  tdata[toff[a] .. toff[a+1]) are the labels of S (T),
 // tbox[a] its bounding box; coordinates of label s are (x0[s], x1[s], x2[s]).
 // The box of the result goes to outbox[node].
-__global__ void __launch_bounds__(DR_THREADS) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
+__global__ void __launch_bounds__(DR_THREADS, 5) k_datareduct(const int64_t *toff, const int32_t *tdata, int g, int d,
                                                            DRPoints PT, int32_t *const *outptr, int32_t *outcnt, int lb,
                                                            int2 *bin_base, float4 *pq_base, const long long *tbox,
                                                            long long *outbox) {

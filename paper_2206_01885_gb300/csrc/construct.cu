@@ -259,45 +259,107 @@ __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr(int lb, const int32_t *y
         const Real tauR = s_tau;
         // apply to the trailing columns (one warp per column); row j of the
         // result goes to shared memory for the norm downdate.  With RPL > 0 a
-        // lane keeps its RPL rows of the column in registers: all loads are
-        // issued together and the update reuses them.
-        for (int l = j + 1 + warp; l < c; l += nwarps) {
-            Real *al = A + (int64_t)l * m;
-            Real ajl = al[j];
-            if constexpr (RPL > 0) {
-                Real a[RPL];
+        // lane keeps its RPL rows in registers and a warp takes two columns at
+        // a time: all their loads are issued together (twice the loads in
+        // flight), each reflector entry is read once for both, and the update
+        // reuses the registers.
+        if constexpr (RPL > 0 && RPL <= 12) {
+            for (int l = j + 1 + warp; l < c; l += 2 * nwarps) {
+                const int l2 = l + nwarps;
+                const bool two = l2 < c;  // (warp-uniform)
+                Real *al = A + (int64_t)l * m;
+                Real *bl = A + (int64_t)(two ? l2 : l) * m;
+                Real ajl = al[j], bjl = two ? bl[j] : (Real)0;
+                Real a2[RPL], b2[RPL];
 #pragma unroll
                 for (int u = 0; u < RPL; u++) {
-                    int r = j + 1 + lane + 32 * u;
-                    a[u] = r < m ? al[r] : (Real)0;
+                    const int r = j + 1 + lane + 32 * u;
+                    a2[u] = r < m ? al[r] : (Real)0;
+                    b2[u] = two && r < m ? bl[r] : (Real)0;
+                }
+                if (has_tau) {
+                    Real wa = 0, wb = 0;
+#pragma unroll
+                    for (int u = 0; u < RPL; u++) {
+                        const int r = j + 1 + lane + 32 * u;
+                        if (r < m) {
+                            const Real vr = v[r];
+                            wa += vr * a2[u];
+                            wb += vr * b2[u];
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        wa += __shfl_xor_sync(0xffffffffu, wa, o);
+                        wb += __shfl_xor_sync(0xffffffffu, wb, o);
+                    }
+                    wa = (wa + ajl) * tauR;
+                    wb = (wb + bjl) * tauR;
+#pragma unroll
+                    for (int u = 0; u < RPL; u++) {
+                        const int r = j + 1 + lane + 32 * u;
+                        if (r < m) {
+                            const Real vr = v[r];
+                            al[r] = a2[u] - wa * vr;
+                            if (two) bl[r] = b2[u] - wb * vr;
+                        }
+                    }
+                    ajl = ajl - wa;
+                    bjl = bjl - wb;
+                    if (lane == 0) {
+                        al[j] = ajl;
+                        if (two) bl[j] = bjl;
+                    }
+                }
+                if (lane == 0) {
+                    rowj[l] = ajl;
+                    if (two) rowj[l2] = bjl;
+                }
+            }
+        } else if constexpr (RPL > 0) {  // longer slices: one column a warp (registers)
+            for (int l = j + 1 + warp; l < c; l += nwarps) {
+                Real *al = A + (int64_t)l * m;
+                Real ajl = al[j];
+                Real a1[RPL];
+#pragma unroll
+                for (int u = 0; u < RPL; u++) {
+                    const int r = j + 1 + lane + 32 * u;
+                    a1[u] = r < m ? al[r] : (Real)0;
                 }
                 if (has_tau) {
                     Real w = 0;
 #pragma unroll
                     for (int u = 0; u < RPL; u++) {
-                        int r = j + 1 + lane + 32 * u;
-                        if (r < m) w += v[r] * a[u];
+                        const int r = j + 1 + lane + 32 * u;
+                        if (r < m) w += v[r] * a1[u];
                     }
                     w = warp_sum(w) + ajl;
                     w = w * tauR;
 #pragma unroll
                     for (int u = 0; u < RPL; u++) {
-                        int r = j + 1 + lane + 32 * u;
-                        if (r < m) al[r] = a[u] - w * v[r];
+                        const int r = j + 1 + lane + 32 * u;
+                        if (r < m) al[r] = a1[u] - w * v[r];
                     }
                     ajl = ajl - w;
                     if (lane == 0) al[j] = ajl;
                 }
-            } else if (has_tau) {
-                Real w = 0;
-                for (int r = j + 1 + lane; r < m; r += 32) w += v[r] * al[r];
-                w = warp_sum(w) + ajl;
-                w = w * tauR;
-                for (int r = j + 1 + lane; r < m; r += 32) al[r] = al[r] - w * v[r];
-                ajl = ajl - w;
-                if (lane == 0) al[j] = ajl;
+                if (lane == 0) rowj[l] = ajl;
             }
-            if (lane == 0) rowj[l] = ajl;
+        } else {
+            for (int l = j + 1 + warp; l < c; l += nwarps) {
+                Real *al = A + (int64_t)l * m;
+                Real ajl = al[j];
+                if (has_tau) {
+                    Real w = 0;
+                    for (int r = j + 1 + lane; r < m; r += 32) w += v[r] * al[r];
+                    w = warp_sum(w) + ajl;
+                    w = w * tauR;
+                    for (int r = j + 1 + lane; r < m; r += 32) al[r] = al[r] - w * v[r];
+                    ajl = ajl - w;
+                    if (lane == 0) al[j] = ajl;
+                }
+                if (lane == 0) rowj[l] = ajl;
+            }
         }
         __syncthreads();
         // downdate the norms, one thread per column; flag the ones that have

@@ -406,12 +406,19 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
 // lane down after each step, so after 32 steps lane l holds source l's column
 // sum.  Row sums (per CTA) and column sums (per warp and 32 sources) are
 // added to out with float64 atomics: other CTAs add to the same entries.
+// a staged source point: coordinates and weight in one 16-byte (float) or
+// 32-byte (double) record, one shared-memory load per evaluation
+template <class Real>
+struct alignas(4 * sizeof(Real)) SrcPt {
+    Real x, y, z, w;
+};
+
 template <class Real, int KID>
 __global__ void __launch_bounds__(NB_WARPS * 32)
     k_nbody_sym(const int2 *tiles, const int64_t *start, const int32_t *count, const Real *X0, const Real *X1,
                 const Real *X2, const float2 *F0, const float2 *F1, const float2 *F2, const Real *w, double *out,
                 const int64_t *lptr, const int64_t *lfirst, const int32_t *lidx, int d, double kpar) {
-    __shared__ Real stg[NB_WARPS][4][32];  // staged sources of each warp: x, y, z, weight
+    __shared__ SrcPt<Real> stg[NB_WARPS][32];  // staged sources of each warp
     __shared__ double part[NB_WARPS][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int2 tl = tiles[blockIdx.x];
@@ -450,29 +457,31 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
             {  // sources past the end: coordinates 0, weight 0 (their terms vanish)
                 const bool ok = lane < cnt;
                 const int64_t sp = ss + q0 + lane;
-                stg[warp][0][lane] = ok ? X0[sp] : (Real)0;
-                stg[warp][1][lane] = ok && d > 1 ? X1[sp] : (Real)0;
-                stg[warp][2][lane] = ok && d > 2 ? X2[sp] : (Real)0;
-                stg[warp][3][lane] = ok ? w[sp] : (Real)0;
+                SrcPt<Real> v;
+                v.x = ok ? X0[sp] : (Real)0;
+                v.y = ok && d > 1 ? X1[sp] : (Real)0;
+                v.z = ok && d > 2 ? X2[sp] : (Real)0;
+                v.w = ok ? w[sp] : (Real)0;
+                stg[warp][lane] = v;
             }
             __syncwarp();
             Real col = (Real)0;
             if (sym) {
 #pragma unroll 8
                 for (int q = 0; q < 32; q++) {
-                    const int sidx = (lane + q) & 31;
-                    const Real dx = s0 - stg[warp][0][sidx], dy = s1 - stg[warp][1][sidx],
-                               dz = s2 - stg[warp][2][sidx];
+                    const SrcPt<Real> sv = stg[warp][(lane + q) & 31];
+                    const Real dx = s0 - sv.x, dy = s1 - sv.y, dz = s2 - sv.z;
                     const Real kv = kap<KID>(dx * dx + dy * dy + dz * dz, p);
-                    blk += kv * stg[warp][3][sidx];
+                    blk += kv * sv.w;
                     col += kv * tw;
                     col = __shfl_sync(0xffffffffu, col, (lane + 1) & 31);
                 }
                 if (lane < cnt) atomicAdd(out + ss + q0 + lane, (double)col);
             } else {
                 for (int q = 0; q < cnt; q++) {
-                    const Real dx = s0 - stg[warp][0][q], dy = s1 - stg[warp][1][q], dz = s2 - stg[warp][2][q];
-                    blk += kap<KID>(dx * dx + dy * dy + dz * dz, p) * stg[warp][3][q];
+                    const SrcPt<Real> sv = stg[warp][q];
+                    const Real dx = s0 - sv.x, dy = s1 - sv.y, dz = s2 - sv.z;
+                    blk += kap<KID>(dx * dx + dy * dy + dz * dz, p) * sv.w;
                 }
             }
         }

@@ -77,7 +77,7 @@ FLOPS_PER_PAIR = 11  # 3 sub, 3 mul/add for r^2 (5 flops), 1 rsqrt, 1 fma accumu
 # over the timed step of the 262,144-point workloads): float64 CPQR bytes per QR
 # flop; mixed-form DataReduct bytes per algorithmic byte.  A changed kernel needs
 # a new capture.
-TRAFFIC_PER_UNIT = {("cpqr", "fp64"): 352.4e9 / 8.7668e10, ("datareduct", "mixed"): 7.726e9 / 3.752e9}
+TRAFFIC_PER_UNIT = {("cpqr", "fp64"): 352.4e9 / 8.7668e10, ("datareduct", "mixed"): 7.856e9 / 3.752e9}
 
 
 def measured_peaks():

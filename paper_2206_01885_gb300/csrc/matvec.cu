@@ -418,7 +418,9 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
     k_nbody_sym(const int2 *tiles, const int64_t *start, const int32_t *count, const Real *X0, const Real *X1,
                 const Real *X2, const float2 *F0, const float2 *F1, const float2 *F2, const Real *w, double *out,
                 const int64_t *lptr, const int64_t *lfirst, const int32_t *lidx, int d, double kpar) {
-    __shared__ SrcPt<Real> stg[NB_WARPS][32];  // staged sources of each warp
+    // staged sources of each warp, stored twice (s and s + 32) so that lane l
+    // reads source (l + q) mod 32 at a fixed base plus q
+    __shared__ SrcPt<Real> stg[NB_WARPS][64];
     __shared__ double part[NB_WARPS][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int2 tl = tiles[blockIdx.x];
@@ -463,13 +465,15 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
                 v.z = ok && d > 2 ? X2[sp] : (Real)0;
                 v.w = ok ? w[sp] : (Real)0;
                 stg[warp][lane] = v;
+                stg[warp][lane + 32] = v;
             }
             __syncwarp();
             Real col = (Real)0;
             if (sym) {
+                const SrcPt<Real> *row = &stg[warp][lane];
 #pragma unroll 8
                 for (int q = 0; q < 32; q++) {
-                    const SrcPt<Real> sv = stg[warp][(lane + q) & 31];
+                    const SrcPt<Real> sv = row[q];
                     const Real dx = s0 - sv.x, dy = s1 - sv.y, dz = s2 - sv.z;
                     const Real kv = kap<KID>(dx * dx + dy * dy + dz * dz, p);
                     blk += kv * sv.w;

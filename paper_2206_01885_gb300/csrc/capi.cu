@@ -571,9 +571,9 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
             auto *A = static_cast<const h2_matrix_s *>(handle);
             snprintf(buf, sizeof buf,
                      "{\"k_total\": %lld, \"u_entries\": %lld, \"k_max\": %d, \"ms_construct\": %.4f, "
-                     "\"qr_flops\": %.6e, \"block_evals\": %.6e, \"precision\": \"%s\"}",
+                     "\"qr_flops\": %.6e, \"block_evals\": %.6e, \"g_max\": %.6e, \"precision\": \"%s\"}",
                      (long long)A->ktotal, (long long)A->utotal, A->kmax, A->ms_construct, A->flops_qr,
-                     A->evals_block, A->prec == H2_PREC_FP64 ? "fp64" : "mixed");
+                     A->evals_block, A->g_max, A->prec == H2_PREC_FP64 ? "fp64" : "mixed");
         } else {
             fail(H2_ERR_INVALID_ARG, "not a live h2 handle");
         }

@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_id_solve(int lb, const int32_t *
                                                          const int32_t *kk, const int64_t *aoff, const Real *Abase,
                                                          double *Wbase, const int64_t *coff, const int32_t *pivbase,
                                                          const int32_t *cand, void *const *uptr,
-                                                         int32_t *const *skptr) {
+                                                         int32_t *const *skptr, unsigned long long *gmax_bits) {
     extern __shared__ unsigned char smem_raw[];
     int32_t *sk = reinterpret_cast<int32_t *>(smem_raw);
     const int a = blockIdx.x, node = lb + a;
@@ -477,7 +477,10 @@ __global__ void __launch_bounds__(QR_THREADS) k_id_solve(int lb, const int32_t *
     for (int64_t e = threadIdx.x; e < (int64_t)c * k; e += blockDim.x) U[e] = (Real)0;
     for (int q = threadIdx.x; q < k; q += blockDim.x) skel[q] = cd[sk[q]];
     __syncthreads();
-    // column of U for pivot p: position of piv[p] in the sorted skeleton
+    // column of U for pivot p: position of piv[p] in the sorted skeleton;
+    // the largest |G| entry goes to *gmax_bits (non-negative doubles order as
+    // their bit patterns)
+    unsigned long long gm = 0;
     for (int64_t e = threadIdx.x; e < (int64_t)(nr + 1) * k; e += blockDim.x) {
         int p = (int)(e % k), l = (int)(e / k);  // l == 0: identity rows, else T column l-1
         int lo = 0, hi = k - 1, key = piv[p];
@@ -486,9 +489,16 @@ __global__ void __launch_bounds__(QR_THREADS) k_id_solve(int lb, const int32_t *
             if (sk[mid] < key) lo = mid + 1;
             else hi = mid;
         }
-        if (l == 0) U[piv[p] + (int64_t)lo * c] = (Real)1;
-        else U[piv[k + l - 1] + (int64_t)lo * c] = (Real)W[p + (int64_t)(k + l - 1) * m];
+        if (l == 0) {
+            U[piv[p] + (int64_t)lo * c] = (Real)1;
+        } else {
+            const double gv = W[p + (int64_t)(k + l - 1) * m];
+            U[piv[k + l - 1] + (int64_t)lo * c] = (Real)gv;
+            gm = max(gm, (unsigned long long)__double_as_longlong(fabs(gv)));
+        }
     }
+    for (int o = 16; o > 0; o >>= 1) gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if ((threadIdx.x & 31) == 0 && gm) atomicMax(gmax_bits, gm);
 }
 
 __global__ void k_ku_sizes(int lb, int nl, const int32_t *kk, const int32_t *cc, int64_t *szk, int64_t *szu) {
@@ -578,6 +588,9 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     const size_t esize = f64 ? sizeof(double) : sizeof(float);
     A->k.alloc(nn, s);
     A->c.alloc(nn, s);
+    DevBuf<unsigned long long> gmax;  // largest |G| entry over all nodes, as float64 bits
+    gmax.alloc(1, s);
+    H2_CUDA(cudaMemsetAsync(gmax.p, 0, sizeof(unsigned long long), s));
     H2_CUDA(cudaMemsetAsync(A->k.p, 0, nn * sizeof(int32_t), s));
     H2_CUDA(cudaMemsetAsync(A->c.p, 0, nn * sizeof(int32_t), s));
     DevBuf<int32_t *> skptr;
@@ -687,11 +700,11 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
             if (f64)
                 k_id_solve<double><<<nl, qr_threads(cmax), (size_t)P * sizeof(int32_t), s>>>(
                     lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<double *>(Ablk.p),
-                    reinterpret_cast<double *>(Ablk.p), coff.p, piv.p, cand.p, A->uptr.p, skptr.p);
+                    reinterpret_cast<double *>(Ablk.p), coff.p, piv.p, cand.p, A->uptr.p, skptr.p, gmax.p);
             else
                 k_id_solve<float><<<nl, qr_threads(cmax), (size_t)P * sizeof(int32_t), s>>>(
                     lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<float *>(Ablk.p), Wf.p, coff.p, piv.p,
-                    cand.p, A->uptr.p, skptr.p);
+                    cand.p, A->uptr.p, skptr.p, gmax.p);
             H2_LAUNCH("k_id_solve");
         }
         A->ktotal += ktot;
@@ -718,6 +731,10 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     A->ms_construct = ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    const unsigned long long gb = read_scalar(gmax.p, s);
+    double gv;
+    memcpy(&gv, &gb, sizeof gv);
+    A->g_max = gv;
 }
 
 namespace {
@@ -823,8 +840,11 @@ double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *
     if (k > 0) {
         int P = 1;
         while (P < k) P <<= 1;
+        DevBuf<unsigned long long> gm;
+        gm.alloc(1, s);
+        H2_CUDA(cudaMemsetAsync(gm.p, 0, sizeof(unsigned long long), s));
         k_id_solve<double><<<1, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(
-            0, mc.p, mc.p + 1, kk.p, off.p, A.p, A.p, off.p + 2, piv.p, cand.p, up.p, sp.p);
+            0, mc.p, mc.p + 1, kk.p, off.p, A.p, A.p, off.p + 2, piv.p, cand.p, up.p, sp.p, gm.p);
         H2_LAUNCH("k_id_solve (calibration)");
     }
     DevBuf<double> num, den;

@@ -204,6 +204,7 @@ struct h2_matrix_s {
     int kmax = 0;
     double ms_construct = 0;
     double flops_qr = 0, evals_block = 0;
+    double g_max = 0;  // largest |G| = |(R11^{-1} R12)^T| entry over all nodes (what strong RRQR would bound)
 };
 
 namespace h2 {

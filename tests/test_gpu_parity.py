@@ -8,6 +8,7 @@ R11^{-1} R12 after truncation at eps), the H^2 matvec within 1e-12 of the oracle
 H^2 matvec and within 10 eps of the dense product; exact rows within 1e-12.
 Sizes span several levels and tiles and include ragged leaves."""
 import ctypes as C
+import json
 
 import numpy as np
 import pytest
@@ -153,6 +154,10 @@ def test_construct_and_matvec_fp64(H2, name, d, n, q, kern, kp, eps, g):
         # and the solve amplifies that by cond(R11) <~ |r_11| / |r_kk| < 1 / eps
         tol = 64 * 2.0 ** -53 * nc[i] / eps
         assert np.max(np.abs(Ui - Uo)) <= tol * max(1.0, np.max(np.abs(Uo))), i
+    # the largest interpolation coefficient |G| (U = P [I; G]), what strong RRQR would bound
+    st = json.loads(A.stats())
+    umax = max(float(np.abs(OH.U(i)).max()) for i in range(1, o.nnodes) if OH.rank(i) > 0)
+    assert abs(max(1.0, st["g_max"]) - umax) <= 1e-6 * umax
     y = A.matvec(dev(z)).cpu().numpy()
     yo = OH.matvec(z)
     assert np.linalg.norm(y - yo) <= 1e-12 * np.linalg.norm(yo)

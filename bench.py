@@ -380,7 +380,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
         "counts": {"nodes": tree_i["nodes"], "levels": tree_i["levels"], "near_pairs": tree_i["near_pairs"],
                    "far_pairs": tree_i["far_pairs"], "k_total": mat_i["k_total"], "k_max": mat_i["k_max"],
                    "qr_flops": qr_flops, "block_evals": block_evals, "coupling_evals": coupling_pairs,
-                   "near_evals": near_pairs},
+                   "near_evals": near_pairs, "g_max": mat_i.get("g_max")},
         "kernels": per_kernel,
         "roofline": roof,
         "clocks": clocks,

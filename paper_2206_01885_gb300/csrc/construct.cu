@@ -71,14 +71,17 @@ __global__ void k_keval_f64(int lb, const int32_t *ycnt, const int32_t *cc, int3
     const int32_t *Y = yptr[i];
     const int32_t *X = cand + coff[a];
     double *A = Abase + aoff[a];
-    int64_t total = (int64_t)m * c;
-    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.y * blockDim.x) {
-        int r = (int)(e % m), l = (int)(e / m);
-        int32_t y = Y[r], x = X[l];
-        double r2 = h2_dist2(d, x0[y], d > 1 ? x1[y] : 0.0, d > 2 ? x2[y] : 0.0, x0[x], d > 1 ? x1[x] : 0.0,
-                             d > 2 ? x2[x] : 0.0);
-        A[e] = h2_kappa(kid, kp0, r2);
+    // columns split over the CTAs of the node, rows over the threads (no
+    // per-element index division)
+    for (int l = blockIdx.y; l < c; l += gridDim.y) {
+        const int32_t x = X[l];
+        const double b0 = x0[x], b1 = d > 1 ? x1[x] : 0.0, b2 = d > 2 ? x2[x] : 0.0;
+        double *Acol = A + (int64_t)l * m;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+            const int32_t y = Y[r];
+            const double r2 = h2_dist2(d, x0[y], d > 1 ? x1[y] : 0.0, d > 2 ? x2[y] : 0.0, b0, b1, b2);
+            Acol[r] = h2_kappa(kid, kp0, r2);
+        }
     }
 }
 

@@ -441,6 +441,7 @@ def oracle_g(wl):
 
 
 def cpu_baseline(wl, n_s):
+    oracle_cores()
     from oracle import h2_oracle as O
     wl = dict(wl)
     wl["g_oracle"] = oracle_g(wl)
@@ -451,7 +452,15 @@ def cpu_baseline(wl, n_s):
             "seconds": sec, "rel_err": err}
 
 
+def oracle_cores():
+    """torchrun sets OMP_NUM_THREADS=1 for every rank; the oracle legs (rank 0
+    alone) use the host cores this process may run on.  Must run before the
+    oracle library is loaded (libgomp reads the variable at load time)."""
+    os.environ["OMP_NUM_THREADS"] = str(len(os.sched_getaffinity(0)))
+
+
 def reference_arm(args, wl):
+    oracle_cores()
     from oracle import h2_oracle as O
     wl = dict(wl)
     wl["g_oracle"] = oracle_g(wl)

@@ -97,6 +97,18 @@ __device__ __forceinline__ float kap(float r2, float p) {
     else if constexpr (KID == H2_K_EXPONENTIAL) return __expf(-sqrtf(r2) * p);
     else return sqrtf(1.0f + r2);
 }
+// kappa for point pairs known to be distinct (r2 > 0): Coulomb skips the
+// r2 = 0 test
+template <int KID, class Real>
+__device__ __forceinline__ Real kap_distinct(Real r2, Real p) {
+    if constexpr (KID == H2_K_COULOMB && sizeof(Real) == 4) {
+        float y;
+        asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(r2));
+        return y;
+    } else {
+        return kap<KID>(r2, p);
+    }
+}
 
 // out[r] = sum_q kappa(x_s, x_q) z_q for s = rows[r]; one CTA per row
 __global__ void k_exact_rows(const int64_t *rows, int64_t nrows, const int32_t *iperm, const double *x0,
@@ -430,7 +442,11 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
     const int a = tl.y + lane;
     const bool act = a < tn;
     const Real p = (Real)kpar;
-    const Real tx0 = act ? X0[ts + a] : (Real)0, tx1 = act && d > 1 ? X1[ts + a] : (Real)0,
+    // lanes past the tile's end and sources past a block's end sit at far,
+    // distinct sentinels with weight 0: every pair evaluated below has r2 > 0
+    // and contributes exactly 0 when either side is padding
+    const Real far_t = (Real)1e18;
+    const Real tx0 = act ? X0[ts + a] : far_t, tx1 = act && d > 1 ? X1[ts + a] : (Real)0,
                tx2 = act && d > 2 ? X2[ts + a] : (Real)0;
     const Real tw = act ? w[ts + a] : (Real)0;
     Real acc = (Real)0, cmp = (Real)0;
@@ -456,11 +472,11 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
         for (int q0 = 0; q0 < sn; q0 += 32) {
             const int cnt = min(32, sn - q0);
             __syncwarp();
-            {  // sources past the end: coordinates 0, weight 0 (their terms vanish)
+            {  // sources past the end: a far sentinel with weight 0 (their terms vanish)
                 const bool ok = lane < cnt;
                 const int64_t sp = ss + q0 + lane;
                 SrcPt<Real> v;
-                v.x = ok ? X0[sp] : (Real)0;
+                v.x = ok ? X0[sp] : -far_t;
                 v.y = ok && d > 1 ? X1[sp] : (Real)0;
                 v.z = ok && d > 2 ? X2[sp] : (Real)0;
                 v.w = ok ? w[sp] : (Real)0;
@@ -475,7 +491,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
                 for (int q = 0; q < 32; q++) {
                     const SrcPt<Real> sv = row[q];
                     const Real dx = s0 - sv.x, dy = s1 - sv.y, dz = s2 - sv.z;
-                    const Real kv = kap<KID>(dx * dx + dy * dy + dz * dz, p);
+                    const Real kv = kap_distinct<KID>(dx * dx + dy * dy + dz * dz, p);
                     blk += kv * sv.w;
                     col += kv * tw;
                     col = __shfl_sync(0xffffffffu, col, (lane + 1) & 31);

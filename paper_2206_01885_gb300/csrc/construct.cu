@@ -114,13 +114,16 @@ __global__ void k_keval_f32(int lb, const int32_t *ycnt, const int32_t *cc, int3
     __syncthreads();
     float *A = Abase + aoff[a];
     const float k0 = (float)kp0;
-    int64_t total = (int64_t)m * c;
-    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.y * blockDim.x) {
-        int r = (int)(e % m), l = (int)(e / m);
-        float dx = ys[3 * r] - xs[3 * l], dy = ys[3 * r + 1] - xs[3 * l + 1], dz = ys[3 * r + 2] - xs[3 * l + 2];
-        float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        A[e] = h2_kappa_f(kid, k0, r2);
+    // one warp per column, lanes over its rows (no index division)
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int l = blockIdx.y * nw + (threadIdx.x >> 5); l < c; l += gridDim.y * nw) {
+        const float bx = xs[3 * l], by = xs[3 * l + 1], bz = xs[3 * l + 2];
+        float *Acol = A + (int64_t)l * m;
+        for (int r = lane; r < m; r += 32) {
+            float dx = ys[3 * r] - bx, dy = ys[3 * r + 1] - by, dz = ys[3 * r + 2] - bz;
+            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            Acol[r] = h2_kappa_f(kid, k0, r2);
+        }
     }
 }
 
@@ -414,6 +417,14 @@ __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr(int lb, const int32_t *y
     if (threadIdx.x == 0) kout[node] = k;
 }
 
+// shared memory of the loop-form solve for ranks up to kmax: the reciprocals
+// of R11's diagonal and the skeleton sort (a power of two >= kmax)
+size_t loop_solve_smem(int kmax) {
+    size_t P = 1;
+    while (P < (size_t)kmax) P <<= 1;
+    return (size_t)kmax * sizeof(double) + P * sizeof(int32_t);
+}
+
 __device__ void bitonic_sort_i32(int32_t *v, int P) {
     for (int kk = 2; kk <= P; kk <<= 1)
         for (int j = kk >> 1; j > 0; j >>= 1) {
@@ -439,34 +450,42 @@ __global__ void __launch_bounds__(QR_THREADS) k_id_solve(int lb, const int32_t *
                                                          double *Wbase, const int64_t *coff, const int32_t *pivbase,
                                                          const int32_t *cand, void *const *uptr,
                                                          int32_t *const *skptr, unsigned long long *gmax_bits) {
-    extern __shared__ unsigned char smem_raw[];
-    int32_t *sk = reinterpret_cast<int32_t *>(smem_raw);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int a = blockIdx.x, node = lb + a;
     const int m = ycnt[node], c = cc[node], k = kk[node];
     if (k == 0) return;
+    double *rinv = reinterpret_cast<double *>(smem_raw);  // 1 / r_ii, one division per row of R11
+    int32_t *sk = reinterpret_cast<int32_t *>(rinv + k);
     const Real *A = Abase + aoff[a];
     double *W = Wbase + aoff[a];
     const int32_t *piv = pivbase + coff[a];
     const int32_t *cd = cand + coff[a];
     const int nr = c - k;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) rinv[i] = 1.0 / (double)A[i + (int64_t)i * m];
     if ((const void *)A != (const void *)W) {  // float32 block: R12 into the float64 workspace
-        for (int64_t e = threadIdx.x; e < (int64_t)k * nr; e += blockDim.x) {
-            int p = (int)(e % k), l = k + (int)(e / k);
-            W[p + (int64_t)l * m] = (double)A[p + (int64_t)l * m];
-        }
-        __syncthreads();
+        for (int l = threadIdx.x >> 5; l < nr; l += blockDim.x >> 5)
+            for (int p = threadIdx.x & 31; p < k; p += 32)
+                W[p + (int64_t)(k + l) * m] = (double)A[p + (int64_t)(k + l) * m];
     }
+    __syncthreads();
     for (int i = k - 1; i >= 0; i--) {
-        const double rinv = 1.0 / (double)A[i + (int64_t)i * m];  // one division per row of the solve
+        const double ri = rinv[i];
         for (int l = threadIdx.x; l < nr; l += blockDim.x) {
             double *e = W + i + (int64_t)(k + l) * m;
-            *e = *e * rinv;
+            *e = *e * ri;
         }
         __syncthreads();
-        const int64_t work = (int64_t)i * nr;
-        for (int64_t e = threadIdx.x; e < work; e += blockDim.x) {
-            int p = (int)(e % i), l = k + (int)(e / i);
-            W[p + (int64_t)l * m] -= (double)A[p + (int64_t)i * m] * W[i + (int64_t)l * m];
+        // the i x nr entries above row i, packed over the threads: (p, l) walks
+        // by blockDim.x entries with one division per row, not per entry
+        if (i > 0 && (int)threadIdx.x < i * nr) {
+            const int dq = blockDim.x / i, dr = blockDim.x % i;
+            int p = threadIdx.x % i, l = threadIdx.x / i;
+            const Real *ai = A + (int64_t)i * m;
+            for (; l < nr; l += dq, p += dr) {
+                if (p >= i) { p -= i; l++; if (l >= nr) break; }
+                double *wl = W + (int64_t)(k + l) * m;
+                wl[p] -= (double)ai[p] * wl[i];
+            }
         }
         __syncthreads();
     }
@@ -484,24 +503,118 @@ __global__ void __launch_bounds__(QR_THREADS) k_id_solve(int lb, const int32_t *
     // the largest |G| entry goes to *gmax_bits (non-negative doubles order as
     // their bit patterns)
     unsigned long long gm = 0;
-    for (int64_t e = threadIdx.x; e < (int64_t)(nr + 1) * k; e += blockDim.x) {
-        int p = (int)(e % k), l = (int)(e / k);  // l == 0: identity rows, else T column l-1
-        int lo = 0, hi = k - 1, key = piv[p];
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (sk[mid] < key) lo = mid + 1;
-            else hi = mid;
-        }
-        if (l == 0) {
-            U[piv[p] + (int64_t)lo * c] = (Real)1;
-        } else {
-            const double gv = W[p + (int64_t)(k + l - 1) * m];
-            U[piv[k + l - 1] + (int64_t)lo * c] = (Real)gv;
-            gm = max(gm, (unsigned long long)__double_as_longlong(fabs(gv)));
+    for (int l = threadIdx.x >> 5; l <= nr; l += blockDim.x >> 5) {  // l == 0: identity rows, else T column l-1
+        for (int p = threadIdx.x & 31; p < k; p += 32) {
+            int lo = 0, hi = k - 1, key = piv[p];
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (sk[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            if (l == 0) {
+                U[piv[p] + (int64_t)lo * c] = (Real)1;
+            } else {
+                const double gv = W[p + (int64_t)(k + l - 1) * m];
+                U[piv[k + l - 1] + (int64_t)lo * c] = (Real)gv;
+                gm = max(gm, (unsigned long long)__double_as_longlong(fabs(gv)));
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
     if ((threadIdx.x & 31) == 0 && gm) atomicMax(gmax_bits, gm);
+}
+
+// The same solve and U for a float32 block of rank up to 128, one lane per
+// column of R12: a warp takes 32 columns and runs the back substitution on all
+// of them at once (a node's columns are split over several CTAs, so the few
+// wide nodes of the upper levels do not run on a handful of SMs).  The
+// multiplier r_pi is the same for every lane and comes from R11's strict upper
+// triangle, staged once per node in float64 (a shared-memory broadcast, with no
+// per-lane conversion); the columns stay in shared memory (entry p of a lane's
+// column at p * 32 + lane, so a warp's accesses never conflict).  Every lane
+// of every float64 instruction does useful work (float64 runs at 1/64 of the
+// float32 rate on this GPU), and no block barrier sits inside the solve.  Each
+// entry takes the operations of the loop form in the same order (subtract
+// r_pi * t_i for i descending, then scale by 1 / r_pp at its own row), so the
+// results are bit-identical.  The column of U that each pivot lands in is its
+// rank among the skeleton labels (no sort).
+constexpr int SOLVE_WARPS = 4;
+constexpr int SOLVE_KMAX = 128;
+
+size_t solve_cols_smem(int kcap) {
+    const size_t tri = (size_t)kcap * (kcap - 1) / 2;
+    return (tri + kcap + (size_t)SOLVE_WARPS * 32 * kcap) * sizeof(double) + 2 * (size_t)kcap * sizeof(int32_t);
+}
+
+__global__ void __launch_bounds__(SOLVE_WARPS * 32) k_id_solve_cols(int kcap, int lb, const int32_t *ycnt,
+                                                                    const int32_t *cc, const int32_t *kk,
+                                                                    const int64_t *aoff, const float *Abase,
+                                                                    const int64_t *coff, const int32_t *pivbase,
+                                                                    const int32_t *cand, void *const *uptr,
+                                                                    int32_t *const *skptr,
+                                                                    unsigned long long *gmax_bits) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *W = reinterpret_cast<double *>(smem_raw);   // SOLVE_WARPS x kcap x 32
+    double *tri = W + (size_t)SOLVE_WARPS * 32 * kcap;  // r_pi (p < i) at i (i - 1) / 2 + p
+    double *rinv = tri + (size_t)kcap * (kcap - 1) / 2;
+    int32_t *pv = reinterpret_cast<int32_t *>(rinv + kcap), *pos = pv + kcap;
+    const int a = blockIdx.x, node = lb + a;
+    const int m = ycnt[node], c = cc[node], k = kk[node];
+    if (k == 0) return;
+    const float *A = Abase + aoff[a];
+    const int32_t *piv = pivbase + coff[a];
+    const int32_t *cd = cand + coff[a];
+    const int nr = c - k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    // the node's columns are split over gridDim.y CTAs of nwarps * 32 columns;
+    // slice 0 also writes the skeleton and U's identity rows
+    const int slice = blockIdx.y, width = nwarps * 32;
+    if (slice > 0 && slice * width >= nr) return;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        rinv[i] = 1.0 / (double)A[i + (int64_t)i * m];
+        pv[i] = piv[i];
+    }
+    for (int i = warp; i < k; i += nwarps)
+        for (int p = lane; p < i; p += 32) tri[i * (i - 1) / 2 + p] = (double)A[p + (int64_t)i * m];
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const int key = pv[i];
+        int r = 0;
+        for (int q = 0; q < k; q++) r += pv[q] < key;
+        pos[i] = r;
+    }
+    __syncthreads();
+    float *U = static_cast<float *>(uptr[node]);
+    if (slice == 0) {
+        int32_t *skel = skptr[node];
+        for (int i = threadIdx.x; i < k; i += blockDim.x) skel[pos[i]] = cd[pv[i]];
+        for (int i = warp; i < k; i += nwarps)  // identity row of skeleton point i, in full
+            for (int q = lane; q < k; q += 32) U[pv[i] + (int64_t)q * c] = q == pos[i] ? 1.0f : 0.0f;
+    }
+    double *w = W + (size_t)warp * 32 * kcap + lane;
+    unsigned long long gm = 0;
+    for (int l0 = slice * width + warp * 32; l0 < nr; l0 += gridDim.y * width) {  // (warp-uniform)
+        const int l = l0 + lane;
+        const bool act = l < nr;
+        const float *r12 = A + (int64_t)(k + (act ? l : 0)) * m;
+        for (int p = 0; p < k; p++) w[p * 32] = act ? (double)r12[p] : 0.0;
+        for (int i = k - 1; i >= 0; i--) {
+            const double wi = w[i * 32] * rinv[i];
+            w[i * 32] = wi;
+            const double *ri = tri + i * (i - 1) / 2;
+            for (int p = 0; p < i; p++) w[p * 32] -= ri[p] * wi;
+        }
+        if (act) {
+            const int64_t row = piv[k + l];
+            for (int p = 0; p < k; p++) {
+                const double g = w[p * 32];
+                U[row + (int64_t)pos[p] * c] = (float)g;
+                gm = max(gm, (unsigned long long)__double_as_longlong(fabs(g)));
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if (lane == 0 && gm) atomicMax(gmax_bits, gm);
 }
 
 __global__ void k_ku_sizes(int lb, int nl, const int32_t *kk, const int32_t *cc, int64_t *szk, int64_t *szu) {
@@ -614,6 +727,8 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_LIMIT));
         H2_CUDA(cudaFuncSetAttribute(k_keval_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_id_solve_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)solve_cols_smem(SOLVE_KMAX)));
     });
     cudaEvent_t e0, e1;
     H2_CUDA(cudaEventCreate(&e0));
@@ -645,7 +760,6 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         cand.alloc(ctot, s);
         piv.alloc(ctot, s);
         Ablk.alloc((size_t)atot * esize, s);
-        if (!f64) Wf.alloc(atot, s);
         k_gather_cand<<<nl, 128, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, A->c.p, A->k.p, skptr.p, coff.p,
                                          cand.p);
         H2_LAUNCH("k_gather_cand");
@@ -696,18 +810,30 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         k_set_ptrs2<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, skbufs[l].p, koff.p, skptr.p, A->ubufs[l].p,
                                                          uoff.p, (int)esize, A->uptr.p);
         H2_LAUNCH("k_set_ptrs2");
-        int P = 1;
-        while (P < kmax) P <<= 1;
         {
             ProfScope ps(KT_SOLVE, s);
-            if (f64)
-                k_id_solve<double><<<nl, qr_threads(cmax), (size_t)P * sizeof(int32_t), s>>>(
+            // float32 blocks: one lane per column; float64 blocks (and larger
+            // ranks): the loop form, whose 512-thread CTAs hold their share of
+            // the float64 pipe beside the other float64 kernels (measured at
+            // 1M: 16.8 ms against 21.8 for the column form)
+            const bool cols = !f64 && kmax <= SOLVE_KMAX;
+            int nrmax = 0;  // most columns of R12 in a node of the level
+            for (int a = 0; a < nl; a++) nrmax = std::max(nrmax, (int)(cs[a] - ks[a]));
+            const dim3 sg(nl, std::max(1, (nrmax + SOLVE_WARPS * 32 - 1) / (SOLVE_WARPS * 32)));
+            if (cols) {
+                k_id_solve_cols<<<sg, SOLVE_WARPS * 32, solve_cols_smem(kmax), s>>>(
+                    kmax, lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<const float *>(Ablk.p), coff.p,
+                    piv.p, cand.p, A->uptr.p, skptr.p, gmax.p);
+            } else if (f64) {
+                k_id_solve<double><<<nl, qr_threads(cmax), loop_solve_smem(kmax), s>>>(
                     lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<double *>(Ablk.p),
                     reinterpret_cast<double *>(Ablk.p), coff.p, piv.p, cand.p, A->uptr.p, skptr.p, gmax.p);
-            else
-                k_id_solve<float><<<nl, qr_threads(cmax), (size_t)P * sizeof(int32_t), s>>>(
+            } else {
+                Wf.alloc(atot, s);
+                k_id_solve<float><<<nl, qr_threads(cmax), loop_solve_smem(kmax), s>>>(
                     lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<float *>(Ablk.p), Wf.p, coff.p, piv.p,
                     cand.p, A->uptr.p, skptr.p, gmax.p);
+            }
             H2_LAUNCH("k_id_solve");
         }
         A->ktotal += ktot;
@@ -841,12 +967,10 @@ double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *
     for (int i = 0; i < c; i++) iota[i] = i;
     H2_CUDA(cudaMemcpyAsync(cand.p, iota.data(), c * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     if (k > 0) {
-        int P = 1;
-        while (P < k) P <<= 1;
         DevBuf<unsigned long long> gm;
         gm.alloc(1, s);
         H2_CUDA(cudaMemsetAsync(gm.p, 0, sizeof(unsigned long long), s));
-        k_id_solve<double><<<1, QR_THREADS, (size_t)P * sizeof(int32_t), s>>>(
+        k_id_solve<double><<<1, QR_THREADS, loop_solve_smem(k), s>>>(
             0, mc.p, mc.p + 1, kk.p, off.p, A.p, A.p, off.p + 2, piv.p, cand.p, up.p, sp.p, gm.p);
         H2_LAUNCH("k_id_solve (calibration)");
     }

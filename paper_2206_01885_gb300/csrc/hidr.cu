@@ -148,33 +148,77 @@ __global__ void k_gather_up(int lb, const int32_t *nchild, const int32_t *fchild
     block_box_write(lo, hi, tbox + 6 * (int64_t)a);
 }
 
-// T_i = Y_p* followed by X_j* for j in IL(i); tbox[a] the union of their boxes
-__global__ void k_gather_down(int lb, const int32_t *parent, const int64_t *far_ptr, const int32_t *far_idx,
-                              int32_t *const *xptr, const int32_t *xcnt, int32_t *const *yptr, const int32_t *ycnt,
-                              const int64_t *toff, int32_t *tdata, const long long *xbox, const long long *ybox,
-                              long long *tbox) {
-    int a = blockIdx.x;
-    int i = lb + a;
+// T_i = Y_p* followed by X_j* for j in IL(i); tbox[a] the union of their boxes.
+// The interaction list is taken in tiles of GD_TILE entries: a block scan of
+// the X_j* sizes gives each segment's place, then one warp copies each segment
+// (no chain of dependent loads along the list).  blockDim.x must be
+// GD_TILE / GD_ITEMS.
+constexpr int GD_ITEMS = 4;
+constexpr int GD_THREADS = 256;
+constexpr int GD_TILE = GD_ITEMS * GD_THREADS;
+
+__global__ void __launch_bounds__(GD_THREADS) k_gather_down(int lb, const int32_t *parent, const int64_t *far_ptr,
+                                                            const int32_t *far_idx, int32_t *const *xptr,
+                                                            const int32_t *xcnt, int32_t *const *yptr,
+                                                            const int32_t *ycnt, const int64_t *toff,
+                                                            int32_t *tdata, const long long *xbox,
+                                                            const long long *ybox, long long *tbox) {
+    __shared__ int32_t s_j[GD_TILE], s_off[GD_TILE + 1];
+    __shared__ int32_t s_wsum[GD_THREADS / 32];
+    const int a = blockIdx.x, i = lb + a;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     int32_t *dst = tdata + toff[a];
-    int p = parent[i];
-    int64_t w = 0;
+    const int p = parent[i];
     long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    int64_t base;
     {
         const int32_t *src = yptr[p];
-        int n = ycnt[p];
+        const int n = ycnt[p];
         for (int r = threadIdx.x; r < n; r += blockDim.x) dst[r] = src[r];
-        w = n;
+        base = n;
         if (threadIdx.x == 0 && n > 0) box_merge(lo, hi, ybox + 6 * (int64_t)p);
     }
-    for (int64_t e = far_ptr[i]; e < far_ptr[i + 1]; e++) {
-        int j = far_idx[e];
-        const int32_t *src = xptr[j];
-        int n = xcnt[j];
-        for (int r = threadIdx.x; r < n; r += blockDim.x) dst[w + r] = src[r];
-        w += n;
+    const int64_t f0 = far_ptr[i], f1 = far_ptr[i + 1];
+    for (int64_t e = f0 + threadIdx.x; e < f1; e += blockDim.x) box_merge(lo, hi, xbox + 6 * (int64_t)far_idx[e]);
+    for (int64_t t0 = f0; t0 < f1; t0 += GD_TILE) {
+        const int nt = (int)min((int64_t)GD_TILE, f1 - t0);
+        // this thread's GD_ITEMS consecutive entries: sizes, then an exclusive block scan
+        int len[GD_ITEMS], tot = 0;
+#pragma unroll
+        for (int q = 0; q < GD_ITEMS; q++) {
+            const int e = threadIdx.x * GD_ITEMS + q;
+            int j = 0, n = 0;
+            if (e < nt) { j = far_idx[t0 + e]; n = xcnt[j]; s_j[e] = j; }
+            len[q] = n;
+            tot += n;
+        }
+        int inc = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) s_wsum[warp] = inc;
+        __syncthreads();
+        int wbase = 0;
+        for (int w = 0; w < warp; w++) wbase += s_wsum[w];
+        int run = wbase + inc - tot;
+#pragma unroll
+        for (int q = 0; q < GD_ITEMS; q++) {
+            const int e = threadIdx.x * GD_ITEMS + q;
+            if (e < nt) s_off[e] = run;
+            run += len[q];
+        }
+        if (threadIdx.x == blockDim.x - 1) s_off[nt] = run;  // (entries past nt add 0)
+        __syncthreads();
+        for (int e = warp; e < nt; e += nwarps) {
+            const int32_t *src = xptr[s_j[e]];
+            const int n = s_off[e + 1] - s_off[e];
+            int32_t *d = dst + base + s_off[e];
+            for (int r = lane; r < n; r += 32) d[r] = src[r];
+        }
+        base += s_off[nt];
+        __syncthreads();
     }
-    for (int64_t e = far_ptr[i] + threadIdx.x; e < far_ptr[i + 1]; e += blockDim.x)
-        box_merge(lo, hi, xbox + 6 * (int64_t)far_idx[e]);
     block_box_write(lo, hi, tbox + 6 * (int64_t)a);
 }
 
@@ -987,7 +1031,7 @@ void hidr_impl(h2_hidr_s *h) {
         k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, h->ybufs[l].p, coff.p, h->yptr.p);
         H2_LAUNCH("k_set_ptrs");
         tbox.alloc((size_t)nl * 6, s);
-        k_gather_down<<<nl, 256, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->xptr.p, h->xcnt.p,
+        k_gather_down<<<nl, GD_THREADS, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->xptr.p, h->xcnt.p,
                                          h->yptr.p, h->ycnt.p, toff.p, tdata.p, h->xbox.p, h->ybox.p, tbox.p);
         H2_LAUNCH("k_gather_down");
         launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, pts, h->yptr.p, h->ycnt.p, lb, tbox.p, h->ybox.p, s);

@@ -48,7 +48,7 @@ typedef int64_t i64;
 typedef uint64_t u64;
 typedef unsigned __int128 u128;
 
-enum { K_COULOMB = 1, K_GAUSSIAN = 2, K_EXPONENTIAL = 3, K_MULTIQUADRIC = 4 };
+enum { K_COULOMB = 1, K_GAUSSIAN = 2, K_EXPONENTIAL = 3, K_MULTIQUADRIC = 4, K_BUMP = 5, K_POWER = 6 };
 
 /* ------------------------------------------------------------------------ */
 /* Kernel functions (section 2, Table 1).                                    */
@@ -66,13 +66,22 @@ static double dist2(const double *a, const double *b, int d) {
 
 /* kappa as a function of the squared distance.  Coulomb: 1/|x-y| with
  * kappa(x,x) = 0 (Table 1 caption).  Gaussian exp(-|x-y|^2 / h^2), exponential
- * exp(-|x-y| / l), multiquadric sqrt(1 + |x-y|^2). */
+ * exp(-|x-y| / l), multiquadric sqrt(1 + |x-y|^2).  Bump: Table 1's kappa_4,
+ * exp(-1 / (1 - a |x-y|^2)) with a = kp[0] (0.1 there), taken as 0 where
+ * a |x-y|^2 >= 1 (the formula's limit there, so the kernel is the smooth
+ * compactly supported bump).  Power: |x-y|^p with p = kp[0] (11 in the data
+ * reduction comparison of section 5.2). */
 static double kfun(int kid, const double *kp, double r2) {
     switch (kid) {
     case K_COULOMB: return r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
     case K_GAUSSIAN: return exp(-(r2 / (kp[0] * kp[0])));
     case K_EXPONENTIAL: return exp(-(sqrt(r2) / kp[0]));
     case K_MULTIQUADRIC: return sqrt(1.0 + r2);
+    case K_BUMP: {
+        double t = kp[0] * r2;
+        return t < 1.0 ? exp(-(1.0 / (1.0 - t))) : 0.0;
+    }
+    case K_POWER: return r2 > 0.0 ? pow(r2, 0.5 * kp[0]) : 0.0;
     default: return NAN;
     }
 }

@@ -60,7 +60,11 @@ typedef enum {
     H2_K_COULOMB = 1,      /* 1/r, and kappa(x, x) = 0 (Table 1 caption)       */
     H2_K_GAUSSIAN = 2,     /* exp(-r^2 / h^2), kparams[0] = h                  */
     H2_K_EXPONENTIAL = 3,  /* exp(-r / l), kparams[0] = l                      */
-    H2_K_MULTIQUADRIC = 4  /* sqrt(1 + r^2)                                    */
+    H2_K_MULTIQUADRIC = 4, /* sqrt(1 + r^2)                                    */
+    H2_K_BUMP = 5,         /* Table 1's kappa_4: exp(-1 / (1 - a r^2)),
+                              kparams[0] = a (0.1 in Table 1); 0 where
+                              a r^2 >= 1 (the formula's limit there)          */
+    H2_K_POWER = 6         /* r^p, kparams[0] = p > 0 (11 in section 5.2)      */
 } h2_kernel_id;
 
 /* arithmetic of h2_construct / h2_matvec */

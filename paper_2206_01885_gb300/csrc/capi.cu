@@ -38,13 +38,17 @@ h2_status guard(F &&f) {
     }
 }
 
-bool valid_kernel(int kid) { return kid >= H2_K_COULOMB && kid <= H2_K_MULTIQUADRIC; }
+bool valid_kernel(int kid) { return kid >= H2_K_COULOMB && kid <= H2_K_POWER; }
 
 void kparams_check(int kid, const double *kp, double out[4]) {
     for (int a = 0; a < 4; a++) out[a] = kp ? kp[a] : 0.0;
     if (kid == H2_K_GAUSSIAN || kid == H2_K_EXPONENTIAL) {
         H2_REQUIRE(kp != nullptr, "this kernel needs kparams[0]");
         H2_REQUIRE(std::isfinite(out[0]) && out[0] > 0.0, "kparams[0] must be a positive length");
+    }
+    if (kid == H2_K_BUMP || kid == H2_K_POWER) {
+        H2_REQUIRE(kp != nullptr, "this kernel needs kparams[0]");
+        H2_REQUIRE(std::isfinite(out[0]) && out[0] > 0.0, "kparams[0] must be positive and finite");
     }
 }
 

@@ -283,13 +283,19 @@ __device__ __forceinline__ double h2_dist2(int d, double a0, double a1, double a
 
 // kappa(x, y) as a function of r^2 = |x - y|^2, float64 (Table 1 and section 2):
 // Coulomb 1/r with kappa(x, x) = 0; Gaussian exp(-r^2/h^2); exponential
-// exp(-r/l); multiquadric sqrt(1 + r^2).
+// exp(-r/l); multiquadric sqrt(1 + r^2); bump (Table 1's kappa_4)
+// exp(-1/(1 - a r^2)), 0 where a r^2 >= 1; power r^p (section 5.2).
 __device__ __forceinline__ double h2_kappa(int kid, double kp0, double r2) {
     switch (kid) {
     case H2_K_COULOMB: return r2 > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(r2)) : 0.0;
     case H2_K_GAUSSIAN: return exp(-__ddiv_rn(r2, __dmul_rn(kp0, kp0)));
     case H2_K_EXPONENTIAL: return exp(-__ddiv_rn(__dsqrt_rn(r2), kp0));
     case H2_K_MULTIQUADRIC: return __dsqrt_rn(__dadd_rn(1.0, r2));
+    case H2_K_BUMP: {
+        const double t = __dmul_rn(kp0, r2);
+        return t < 1.0 ? exp(-__ddiv_rn(1.0, __dadd_rn(1.0, -t))) : 0.0;
+    }
+    case H2_K_POWER: return r2 > 0.0 ? pow(r2, 0.5 * kp0) : 0.0;
     default: return 0.0;
     }
 }
@@ -319,6 +325,11 @@ __device__ __forceinline__ double h2_kappa_fast(int kid, double kp0, double r2) 
     case H2_K_GAUSSIAN: return exp(-r2 / (kp0 * kp0));
     case H2_K_EXPONENTIAL: return exp(-sqrt(r2) / kp0);
     case H2_K_MULTIQUADRIC: return sqrt(1.0 + r2);
+    case H2_K_BUMP: {
+        const double t = kp0 * r2;
+        return t < 1.0 ? exp(-1.0 / (1.0 - t)) : 0.0;
+    }
+    case H2_K_POWER: return r2 > 0.0 ? pow(r2, 0.5 * kp0) : 0.0;
     default: return 0.0;
     }
 }
@@ -330,6 +341,11 @@ __device__ __forceinline__ float h2_kappa_f(int kid, float kp0, float r2) {
     case H2_K_GAUSSIAN: return __expf(-r2 / (kp0 * kp0));
     case H2_K_EXPONENTIAL: return __expf(-sqrtf(r2) / kp0);
     case H2_K_MULTIQUADRIC: return sqrtf(1.0f + r2);
+    case H2_K_BUMP: {
+        const float t = kp0 * r2;
+        return t < 1.0f ? __expf(__fdividef(-1.0f, 1.0f - t)) : 0.0f;
+    }
+    case H2_K_POWER: return r2 > 0.0f ? __powf(r2, 0.5f * kp0) : 0.0f;
     default: return 0.0f;
     }
 }

@@ -9,6 +9,8 @@
 // Vectors live in Morton order inside; x and y are permuted at the ends.
 #include <mutex>
 
+#include <cfloat>
+
 #include "h2_internal.cuh"
 
 // Scratch of h2_exact_rows_noalloc: the right-hand side permuted to Morton
@@ -79,12 +81,18 @@ __global__ void k_downward(int lb, const int32_t *nchild, const int32_t *fchild,
 }
 
 // kappa for the matvec kernels: fast forms (rsqrt, exp) in float64 or float32
+// (p: 1/h^2 Gaussian, 1/l exponential, a bump, p/2 power; see kap_param)
 template <int KID>
-__device__ __forceinline__ double kap(double r2, double p) {  // p: 1/h^2 (Gaussian) or 1/l (exponential)
+__device__ __forceinline__ double kap(double r2, double p) {
     if constexpr (KID == H2_K_COULOMB) return h2_rsqrt64(r2);
     else if constexpr (KID == H2_K_GAUSSIAN) return exp(-r2 * p);
     else if constexpr (KID == H2_K_EXPONENTIAL) return exp(-sqrt(r2) * p);
-    else return sqrt(1.0 + r2);
+    else if constexpr (KID == H2_K_BUMP) {
+        const double t = r2 * p;
+        return t < 1.0 ? exp(-1.0 / (1.0 - t)) : 0.0;
+    } else if constexpr (KID == H2_K_POWER) {  // (kept finite: the symmetric kernel's padding has weight 0)
+        return r2 > 0.0 ? fmin(pow(r2, p), DBL_MAX) : 0.0;
+    } else return sqrt(1.0 + r2);
 }
 template <int KID>
 __device__ __forceinline__ float kap(float r2, float p) {
@@ -95,7 +103,22 @@ __device__ __forceinline__ float kap(float r2, float p) {
     }
     else if constexpr (KID == H2_K_GAUSSIAN) return __expf(-r2 * p);
     else if constexpr (KID == H2_K_EXPONENTIAL) return __expf(-sqrtf(r2) * p);
-    else return sqrtf(1.0f + r2);
+    else if constexpr (KID == H2_K_BUMP) {
+        const float t = r2 * p;
+        return t < 1.0f ? __expf(__fdividef(-1.0f, 1.0f - t)) : 0.0f;
+    } else if constexpr (KID == H2_K_POWER) {  // (kept finite, as above)
+        return r2 > 0.0f ? fminf(__powf(r2, p), FLT_MAX) : 0.0f;
+    } else return sqrtf(1.0f + r2);
+}
+// the kernel parameter in the form kap takes
+inline double kap_param(int kid, double kp0) {
+    switch (kid) {
+    case H2_K_GAUSSIAN: return 1.0 / (kp0 * kp0);
+    case H2_K_EXPONENTIAL: return 1.0 / kp0;
+    case H2_K_BUMP: return kp0;
+    case H2_K_POWER: return 0.5 * kp0;
+    default: return 0.0;
+    }
 }
 // kappa for point pairs known to be distinct (r2 > 0): Coulomb skips the
 // r2 = 0 test
@@ -540,23 +563,19 @@ void nbody_sym(int kid, const DevBuf<int2> &tiles, const int64_t *start, const i
                cudaStream_t s) {
     if (tiles.n == 0) return;
     const unsigned nb = (unsigned)tiles.n;
+    const double p = kap_param(kid, kp0);
+#define H2_SYM(K)                                                                                                  \
+    k_nbody_sym<Real, K><<<nb, NB_WARPS * 32, 0, s>>>(tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, out, lptr, \
+                                                      lfirst, lidx, d, p)
     switch (kid) {
-    case H2_K_COULOMB:
-        k_nbody_sym<Real, H2_K_COULOMB><<<nb, NB_WARPS * 32, 0, s>>>(tiles.p, start, count, X0, X1, X2, F0, F1, F2,
-                                                                      w, out, lptr, lfirst, lidx, d, 0.0);
-        break;
-    case H2_K_GAUSSIAN:
-        k_nbody_sym<Real, H2_K_GAUSSIAN><<<nb, NB_WARPS * 32, 0, s>>>(
-            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, out, lptr, lfirst, lidx, d, 1.0 / (kp0 * kp0));
-        break;
-    case H2_K_EXPONENTIAL:
-        k_nbody_sym<Real, H2_K_EXPONENTIAL><<<nb, NB_WARPS * 32, 0, s>>>(
-            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, out, lptr, lfirst, lidx, d, 1.0 / kp0);
-        break;
-    default:
-        k_nbody_sym<Real, H2_K_MULTIQUADRIC><<<nb, NB_WARPS * 32, 0, s>>>(
-            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, out, lptr, lfirst, lidx, d, 0.0);
+    case H2_K_COULOMB: H2_SYM(H2_K_COULOMB); break;
+    case H2_K_GAUSSIAN: H2_SYM(H2_K_GAUSSIAN); break;
+    case H2_K_EXPONENTIAL: H2_SYM(H2_K_EXPONENTIAL); break;
+    case H2_K_BUMP: H2_SYM(H2_K_BUMP); break;
+    case H2_K_POWER: H2_SYM(H2_K_POWER); break;
+    default: H2_SYM(H2_K_MULTIQUADRIC);
     }
+#undef H2_SYM
     H2_LAUNCH("k_nbody_sym");
 }
 
@@ -566,23 +585,19 @@ void nbody_kid(int kid, const DevBuf<int2> &tiles, const int64_t *start, const i
                int ws, double *out, int os, const int64_t *lptr, const int32_t *lidx, int d, double kp0,
                cudaStream_t s) {
     const unsigned nb = (unsigned)tiles.n;
+    const double p = kap_param(kid, kp0);
+#define H2_NB(K)                                                                                                   \
+    k_nbody<Real, K, R, TPT><<<nb, NB_WARPS * 32, 0, s>>>(tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, ws, out, \
+                                                          os, lptr, lidx, d, p)
     switch (kid) {
-    case H2_K_COULOMB:
-        k_nbody<Real, H2_K_COULOMB, R, TPT><<<nb, NB_WARPS * 32, 0, s>>>(tiles.p, start, count, X0, X1, X2, F0, F1,
-                                                                         F2, w, ws, out, os, lptr, lidx, d, 0.0);
-        break;
-    case H2_K_GAUSSIAN:
-        k_nbody<Real, H2_K_GAUSSIAN, R, TPT><<<nb, NB_WARPS * 32, 0, s>>>(
-            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, ws, out, os, lptr, lidx, d, 1.0 / (kp0 * kp0));
-        break;
-    case H2_K_EXPONENTIAL:
-        k_nbody<Real, H2_K_EXPONENTIAL, R, TPT><<<nb, NB_WARPS * 32, 0, s>>>(
-            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, ws, out, os, lptr, lidx, d, 1.0 / kp0);
-        break;
-    default:
-        k_nbody<Real, H2_K_MULTIQUADRIC, R, TPT><<<nb, NB_WARPS * 32, 0, s>>>(
-            tiles.p, start, count, X0, X1, X2, F0, F1, F2, w, ws, out, os, lptr, lidx, d, 0.0);
+    case H2_K_COULOMB: H2_NB(H2_K_COULOMB); break;
+    case H2_K_GAUSSIAN: H2_NB(H2_K_GAUSSIAN); break;
+    case H2_K_EXPONENTIAL: H2_NB(H2_K_EXPONENTIAL); break;
+    case H2_K_BUMP: H2_NB(H2_K_BUMP); break;
+    case H2_K_POWER: H2_NB(H2_K_POWER); break;
+    default: H2_NB(H2_K_MULTIQUADRIC);
     }
+#undef H2_NB
     H2_LAUNCH("k_nbody");
 }
 

@@ -55,5 +55,10 @@ def test_invalid_arguments_are_rejected_without_device_work(L):
     assert L.h2_construct_batched(2, None, None, None, None, None, None, None, None) == 1
     g = C.c_int(0)
     assert L.h2_calibrate(3, 99, None, 1e-6, pts, 5, pts, 5, 8, None, C.byref(g), None) == 1  # kernel id
+    for kid in (5, 6):  # bump and power need a positive kparams[0]
+        assert L.h2_calibrate(3, kid, None, 1e-6, pts, 5, pts, 5, 8, None, C.byref(g), None) == 1
+        neg = (C.c_double * 4)(-1.0, 0.0, 0.0, 0.0)
+        assert L.h2_calibrate(3, kid, neg, 1e-6, pts, 5, pts, 5, 8, None, C.byref(g), None) == 1
+        assert b"kparams" in L.h2_last_error()
     buf = C.create_string_buffer(64)
     assert L.h2_get_stats(bogus, buf, 64) == 1

@@ -2,7 +2,8 @@
 
 - One HiDR for every kernel (section 6.1.3): the reduced sets X_i*, Y_i* depend
   only on the points, so one tree and one HiDR serve Coulomb, Gaussians of
-  bandwidth 10^k (k = -2..2), exponential and multiquadric kernels; each
+  bandwidth 10^k (k = -2..2), exponential, multiquadric, Table 1's bump
+  kernel and the |x-y|^11 of section 5.2; each
   float64 product equals the oracle's H^2 product on the same reduction
   (1e-12) and the dense product within 10 eps.
 - The paper's three-sphere dataset (section 6.1.1): three unit spheres with
@@ -34,7 +35,8 @@ def dev(a):
 
 
 KERNELS = [("coulomb", ()), ("gaussian", (0.01,)), ("gaussian", (0.1,)), ("gaussian", (1.0,)),
-           ("gaussian", (10.0,)), ("gaussian", (100.0,)), ("exponential", (0.2,)), ("multiquadric", ())]
+           ("gaussian", (10.0,)), ("gaussian", (100.0,)), ("exponential", (0.2,)), ("multiquadric", ()),
+           ("bump", (0.1,)), ("power", (11.0,))]
 
 
 def test_one_hidr_for_every_kernel(H2):

@@ -123,6 +123,9 @@ CONSTRUCT_CASES = [
     ("gauss2d", 2, 6000, 64, "gaussian", (0.2,), 1e-6, 10),
     ("expo2d", 2, 5000, 50, "exponential", (0.1,), 1e-6, 10),
     ("mq3d", 3, 4000, 64, "multiquadric", (), 1e-7, 6),
+    # Table 1's bump kernel (kappa_4) and the |x-y|^11 of section 5.2
+    ("bump3d", 3, 4000, 64, "bump", (0.1,), 1e-7, 6),
+    ("power3d", 3, 4000, 64, "power", (11.0,), 1e-7, 6),
 ]
 
 
@@ -179,6 +182,11 @@ def test_exact_rows(H2):
     assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
     got_h = H2.exact_rows(t, "coulomb", (), z, rows)
     assert np.array_equal(got_h, got)
+    for kern, kp in [("gaussian", (0.3,)), ("exponential", (0.2,)), ("multiquadric", ()), ("bump", (0.1,)),
+                     ("power", (11.0,))]:
+        got = H2.exact_rows(t, kern, kp, dev(z), dev(rows)).cpu().numpy()
+        want = O.exact_rows(pts, kern, kp, z, rows)
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max()), kern
 
 
 def test_degenerate_paths(H2):
@@ -225,6 +233,8 @@ MIXED_CASES = [
     ("coulomb3d_deep", 3, 20000, 40, "coulomb", (), 1e-4, 5),
     ("gauss2d", 2, 6000, 64, "gaussian", (0.2,), 1e-5, 10),
     ("expo2d", 2, 5000, 50, "exponential", (0.1,), 1e-5, 10),
+    ("bump3d", 3, 4000, 64, "bump", (0.1,), 1e-5, 6),
+    ("power3d", 3, 4000, 64, "power", (11.0,), 1e-5, 6),
 ]
 
 
@@ -269,6 +279,8 @@ MULTI_CASES = [
     ("fp64_coulomb3d", 3, 6000, 64, "coulomb", (), 1e-7, 6, "fp64"),
     ("mixed_coulomb3d", 3, 8000, 100, "coulomb", (), 1e-5, 7, "mixed"),
     ("mixed_gauss2d", 2, 6000, 64, "gaussian", (0.2,), 1e-5, 10, "mixed"),
+    ("fp64_bump3d", 3, 5000, 64, "bump", (0.1,), 1e-7, 6, "fp64"),
+    ("mixed_power3d", 3, 5000, 64, "power", (11.0,), 1e-5, 6, "mixed"),
 ]
 
 

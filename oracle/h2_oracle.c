@@ -48,7 +48,7 @@ typedef int64_t i64;
 typedef uint64_t u64;
 typedef unsigned __int128 u128;
 
-enum { K_COULOMB = 1, K_GAUSSIAN = 2, K_EXPONENTIAL = 3, K_MULTIQUADRIC = 4, K_BUMP = 5, K_POWER = 6 };
+enum { K_COULOMB = 1, K_GAUSSIAN = 2, K_EXPONENTIAL = 3, K_MULTIQUADRIC = 4, K_BUMP = 5, K_POWER = 6, K_COSDOT = 7 };
 
 /* ------------------------------------------------------------------------ */
 /* Kernel functions (section 2, Table 1).                                    */
@@ -84,6 +84,18 @@ static double kfun(int kid, const double *kp, double r2) {
     case K_POWER: return r2 > 0.0 ? pow(r2, 0.5 * kp[0]) : 0.0;
     default: return NAN;
     }
+}
+
+/* kappa(a, b) for two points: Table 1's kappa_3 = cos(a . b) from the points
+ * themselves (it is not a function of |a - b|), every other kernel from
+ * |a - b|^2. */
+static double kxy(int kid, const double *kp, const double *a, const double *b, int d) {
+    if (kid == K_COSDOT) {
+        double s = 0.0;
+        for (int k = 0; k < d; k++) s = s + a[k] * b[k];
+        return cos(s);
+    }
+    return kfun(kid, kp, dist2(a, b, d));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -603,7 +615,7 @@ static void kernel_block(const otree *t, int kid, const double *kp, const i64 *Y
     int d = t->d;
     for (int l = 0; l < c; l++)
         for (int r = 0; r < m; r++)
-            A[(i64)l * m + r] = kfun(kid, kp, dist2(t->x + Y[r] * d, t->x + Xb[l] * d, d));
+            A[(i64)l * m + r] = kxy(kid, kp, t->x + Y[r] * d, t->x + Xb[l] * d, d);
 }
 
 /* need: per-node flag (NULL = all); the basis is also built for every
@@ -735,7 +747,7 @@ void or_matvec(const oh2 *H, const double *x, double *y) {
             for (int a = 0; a < H->k[i]; a++) {
                 double s = 0.0;
                 for (int b = 0; b < H->k[j]; b++)
-                    s = s + kfun(H->kid, H->kp, dist2(t->x + H->skel[i][a] * d, t->x + H->skel[j][b] * d, d)) * xh[j][b];
+                    s = s + kxy(H->kid, H->kp, t->x + H->skel[i][a] * d, t->x + H->skel[j][b] * d, d) * xh[j][b];
                 zh[i][a] = zh[i][a] + s;
             }
         }
@@ -766,7 +778,7 @@ void or_matvec(const oh2 *H, const double *x, double *y) {
             for (i64 a = t->begin[i]; a < t->end[i]; a++) {
                 double s = 0.0;
                 for (i64 b = t->begin[j]; b < t->end[j]; b++)
-                    s = s + kfun(H->kid, H->kp, dist2(t->x + a * d, t->x + b * d, d)) * xm[b];
+                    s = s + kxy(H->kid, H->kp, t->x + a * d, t->x + b * d, d) * xm[b];
                 ym[a] += s;
             }
         }
@@ -797,7 +809,7 @@ void or_exact_rows(const double *pts, i64 n, int d, int kid, const double *kp, c
 #pragma omp for schedule(dynamic, 1)
         for (i64 r = 0; r < nrows; r++) {
             const double *xr = pts + rows[r] * d;
-            for (i64 j = 0; j < n; j++) term[j] = kfun(kid, kpl, dist2(xr, pts + j * d, d)) * z[j];
+            for (i64 j = 0; j < n; j++) term[j] = kxy(kid, kpl, xr, pts + j * d, d) * z[j];
             out[r] = pairwise(term, n);
         }
         free(term);
@@ -826,7 +838,7 @@ double or_calib_error(int d, int kid, const double *kp, double id_tol, const dou
     int m = (int)or_datareduct(Z2, d, S, n2, g, R);
     double *A = malloc(sizeof(double) * (i64)m * n1);
     for (int l = 0; l < n1; l++)
-        for (int r = 0; r < m; r++) A[(i64)l * m + r] = kfun(kid, kpl, dist2(Z2 + R[r] * d, Z1 + (i64)l * d, d));
+        for (int r = 0; r < m; r++) A[(i64)l * m + r] = kxy(kid, kpl, Z2 + R[r] * d, Z1 + (i64)l * d, d);
     int *piv = malloc(sizeof(int) * n1);
     int kmax = m < n1 ? m : n1;
     double *T = malloc(sizeof(double) * ((i64)kmax * n1 + 1));
@@ -835,12 +847,12 @@ double or_calib_error(int d, int kid, const double *kp, double id_tol, const dou
      * is approximated by sum_p T[p, l-k] K(Z1[piv[p]], Z2) (kappa symmetric) */
     double *Ks = malloc(sizeof(double) * ((i64)k * n2 + 1));
     for (int p = 0; p < k; p++)
-        for (int b = 0; b < n2; b++) Ks[(i64)p * n2 + b] = kfun(kid, kpl, dist2(Z1 + (i64)piv[p] * d, Z2 + (i64)b * d, d));
+        for (int b = 0; b < n2; b++) Ks[(i64)p * n2 + b] = kxy(kid, kpl, Z1 + (i64)piv[p] * d, Z2 + (i64)b * d, d);
     double num = 0.0, den = 0.0;
     for (int l = 0; l < n1; l++) {
         int a = piv[l];
         for (int b = 0; b < n2; b++) {
-            double kab = kfun(kid, kpl, dist2(Z1 + (i64)a * d, Z2 + (i64)b * d, d));
+            double kab = kxy(kid, kpl, Z1 + (i64)a * d, Z2 + (i64)b * d, d);
             den = den + kab * kab;
             if (l < k) continue;
             double s = 0.0;

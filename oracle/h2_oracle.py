@@ -26,7 +26,8 @@ _LIB = os.path.join(_BUILD, "liboracle_h2.so")
 _lock = threading.Lock()
 _lib = None
 
-KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4, "bump": 5, "power": 6}
+KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4, "bump": 5, "power": 6,
+           "cosdot": 7}
 
 
 def build(force: bool = False) -> str:

@@ -148,11 +148,11 @@ def test_dense_golden(golden_dir):
     gold = json.load(open(os.path.join(golden_dir, "kernel_3pt.json")))
     pts = np.array(gold["points"])
     z = np.array(gold["z"])
-    env = {"exp": math.exp, "sqrt": math.sqrt}
+    env = {"exp": math.exp, "sqrt": math.sqrt, "cos": math.cos}
     for name, kern, kp in [("coulomb", "coulomb", ()), ("gaussian_h1", "gaussian", (1.0,)),
                            ("exponential_l1", "exponential", (1.0,)), ("multiquadric", "multiquadric", ()),
                            ("bump_a0.1", "bump", (0.1,)), ("bump_a0.25", "bump", (0.25,)),
-                           ("power_p11", "power", (11.0,))]:
+                           ("power_p11", "power", (11.0,)), ("cosdot", "cosdot", ())]:
         want = np.array([eval(e, env) for e in gold[name]])
         got = O.dense_matvec(pts, kern, kp, z)
         assert np.allclose(got, want, rtol=1e-15, atol=0), name
@@ -187,6 +187,7 @@ def test_h2_exact_without_reduction_or_truncation(d, n, q, kern, kp):
     (3, 4000, 64, "gaussian", (0.5,), 1e-5, 7),
     (3, 4000, 64, "bump", (0.1,), 1e-6, 6),
     (3, 4000, 64, "power", (11.0,), 1e-6, 6),
+    (3, 4000, 64, "cosdot", (), 1e-6, 6),
 ])
 def test_h2_matvec_error_within_10eps(d, n, q, kern, kp, eps, g):
     pts = I.uniform_cube(n, d, seed=50 + d)

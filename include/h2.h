@@ -55,7 +55,8 @@ typedef enum {
     H2_ERR_STATE = 7          /* handle in the wrong state / has dependents    */
 } h2_status;
 
-/* kernel functions kappa(x, y) as functions of r = |x - y| (section 2, Table 1) */
+/* kernel functions kappa(x, y) (section 2, Table 1): functions of r = |x - y|,
+   except H2_K_COSDOT */
 typedef enum {
     H2_K_COULOMB = 1,      /* 1/r, and kappa(x, x) = 0 (Table 1 caption)       */
     H2_K_GAUSSIAN = 2,     /* exp(-r^2 / h^2), kparams[0] = h                  */
@@ -64,7 +65,9 @@ typedef enum {
     H2_K_BUMP = 5,         /* Table 1's kappa_4: exp(-1 / (1 - a r^2)),
                               kparams[0] = a (0.1 in Table 1); 0 where
                               a r^2 >= 1 (the formula's limit there)          */
-    H2_K_POWER = 6         /* r^p, kparams[0] = p > 0 (11 in section 5.2)      */
+    H2_K_POWER = 6,        /* r^p, kparams[0] = p > 0 (11 in section 5.2)      */
+    H2_K_COSDOT = 7        /* Table 1's kappa_3: cos(x . y), of the points
+                              themselves (not of r); no kparams                */
 } h2_kernel_id;
 
 /* arithmetic of h2_construct / h2_matvec */

@@ -38,7 +38,7 @@ h2_status guard(F &&f) {
     }
 }
 
-bool valid_kernel(int kid) { return kid >= H2_K_COULOMB && kid <= H2_K_POWER; }
+bool valid_kernel(int kid) { return kid >= H2_K_COULOMB && kid <= H2_K_COSDOT; }
 
 void kparams_check(int kid, const double *kp, double out[4]) {
     for (int a = 0; a < 4; a++) out[a] = kp ? kp[a] : 0.0;

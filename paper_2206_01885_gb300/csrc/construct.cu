@@ -79,8 +79,7 @@ __global__ void k_keval_f64(int lb, const int32_t *ycnt, const int32_t *cc, int3
         double *Acol = A + (int64_t)l * m;
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
             const int32_t y = Y[r];
-            const double r2 = h2_dist2(d, x0[y], d > 1 ? x1[y] : 0.0, d > 2 ? x2[y] : 0.0, b0, b1, b2);
-            Acol[r] = h2_kappa(kid, kp0, r2);
+            Acol[r] = h2_kxy(kid, kp0, d, x0[y], d > 1 ? x1[y] : 0.0, d > 2 ? x2[y] : 0.0, b0, b1, b2);
         }
     }
 }
@@ -98,7 +97,10 @@ __global__ void k_keval_f32(int lb, const int32_t *ycnt, const int32_t *cc, int3
     const int32_t *Y = yptr[i];
     const int32_t *X = cand + coff[a];
     float *ys = sp_, *xs = sp_ + 3 * m;
-    const double o0 = cen0[i], o1 = d > 1 ? cen1[i] : 0.0, o2 = d > 2 ? cen2[i] : 0.0;
+    // (cos(x . y) takes absolute coordinates; every other kernel relative ones)
+    const bool cosdot = kid == H2_K_COSDOT;
+    const double o0 = cosdot ? 0.0 : cen0[i], o1 = d > 1 && !cosdot ? cen1[i] : 0.0,
+                 o2 = d > 2 && !cosdot ? cen2[i] : 0.0;
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
         int32_t y = Y[r];
         ys[3 * r] = (float)(x0[y] - o0);
@@ -119,10 +121,15 @@ __global__ void k_keval_f32(int lb, const int32_t *ycnt, const int32_t *cc, int3
     for (int l = blockIdx.y * nw + (threadIdx.x >> 5); l < c; l += gridDim.y * nw) {
         const float bx = xs[3 * l], by = xs[3 * l + 1], bz = xs[3 * l + 2];
         float *Acol = A + (int64_t)l * m;
-        for (int r = lane; r < m; r += 32) {
-            float dx = ys[3 * r] - bx, dy = ys[3 * r + 1] - by, dz = ys[3 * r + 2] - bz;
-            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            Acol[r] = h2_kappa_f(kid, k0, r2);
+        if (cosdot) {
+            for (int r = lane; r < m; r += 32)
+                Acol[r] = __cosf(fmaf(ys[3 * r + 2], bz, fmaf(ys[3 * r + 1], by, ys[3 * r] * bx)));
+        } else {
+            for (int r = lane; r < m; r += 32) {
+                float dx = ys[3 * r] - bx, dy = ys[3 * r + 1] - by, dz = ys[3 * r + 2] - bz;
+                float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                Acol[r] = h2_kappa_f(kid, k0, r2);
+            }
         }
     }
 }
@@ -633,7 +640,8 @@ __global__ void k_set_ptrs2(int lb, int nl, int32_t *kbase, const int64_t *koff,
     uptr[lb + a] = ubase + uoff[a] * esize;
 }
 
-// contiguous skeletons (node order) and their coordinates
+// contiguous skeletons (node order) and their coordinates (float32: relative
+// to the node's centre c, or absolute when c is null)
 __global__ void k_compact_skel(int nn, const int32_t *kk, const int64_t *off, int32_t *const *skptr, int32_t *skel,
                                const double *x0, const double *x1, const double *x2, int d, double *s0, double *s1,
                                double *s2, const double *c0, const double *c1, const double *c2, float *r0,
@@ -642,14 +650,15 @@ __global__ void k_compact_skel(int nn, const int32_t *kk, const int64_t *off, in
     if (i >= nn) return;
     int k = kk[i];
     const int32_t *src = skptr[i];
+    const double o0 = c0 ? c0[i] : 0.0, o1 = c1 && d > 1 ? c1[i] : 0.0, o2 = c2 && d > 2 ? c2[i] : 0.0;
     for (int q = threadIdx.x; q < k; q += blockDim.x) {
         int32_t p = src[q];
         int64_t o = off[i] + q;
         skel[o] = p;
         s0[o] = x0[p];
-        r0[o] = (float)(x0[p] - c0[i]);
-        if (d > 1) { s1[o] = x1[p]; r1[o] = (float)(x1[p] - c1[i]); }
-        if (d > 2) { s2[o] = x2[p]; r2[o] = (float)(x2[p] - c2[i]); }
+        r0[o] = (float)(x0[p] - o0);
+        if (d > 1) { s1[o] = x1[p]; r1[o] = (float)(x1[p] - o1); }
+        if (d > 2) { s2[o] = x2[p]; r2[o] = (float)(x2[p] - o2); }
     }
 }
 
@@ -848,10 +857,13 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         A->skc[k].alloc(kt > 0 ? kt : 1, s);
         A->skr[k].alloc(kt > 0 ? kt : 1, s);
     }
-    k_compact_skel<<<std::max(1, nn), 128, 0, s>>>(nn, A->k.p, A->sk_off.p, skptr.p, A->skel.p, t->xs[0].p,
-                                                    t->xs[1].p, t->xs[2].p, d, A->skc[0].p, A->skc[1].p, A->skc[2].p,
-                                                    t->cen[0].p, t->cen[1].p, t->cen[2].p, A->skr[0].p, A->skr[1].p,
-                                                    A->skr[2].p);
+    // float32 skeleton coordinates: relative to the node's centre, or absolute
+    // for cos(x . y)
+    const bool rel = A->kid != H2_K_COSDOT;
+    k_compact_skel<<<std::max(1, nn), 128, 0, s>>>(
+        nn, A->k.p, A->sk_off.p, skptr.p, A->skel.p, t->xs[0].p, t->xs[1].p, t->xs[2].p, d, A->skc[0].p,
+        A->skc[1].p, A->skc[2].p, rel ? t->cen[0].p : nullptr, rel ? t->cen[1].p : nullptr,
+        rel ? t->cen[2].p : nullptr, A->skr[0].p, A->skr[1].p, A->skr[2].p);
     H2_LAUNCH("k_compact_skel");
     H2_CUDA(cudaEventRecord(e1, s));
     H2_CUDA(cudaEventSynchronize(e1));
@@ -875,9 +887,8 @@ __global__ void k_calib_block(const int32_t *ids, int m, int c, const double *y0
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         int r = (int)(e % m), l = (int)(e / m);
         int32_t y = ids[r];
-        double r2 = h2_dist2(d, y0[y], d > 1 ? y1[y] : 0.0, d > 2 ? y2[y] : 0.0, x0[l], d > 1 ? x1[l] : 0.0,
-                             d > 2 ? x2[l] : 0.0);
-        A[e] = h2_kappa(kid, kp0, r2);
+        A[e] = h2_kxy(kid, kp0, d, y0[y], d > 1 ? y1[y] : 0.0, d > 2 ? y2[y] : 0.0, x0[l], d > 1 ? x1[l] : 0.0,
+                      d > 2 ? x2[l] : 0.0);
     }
 }
 
@@ -893,14 +904,14 @@ __global__ void k_calib_err(const double *A, int m, int c, int k, const int32_t 
     double sn = 0.0, sd = 0.0;
     for (int b = threadIdx.x; b < n2; b += blockDim.x) {
         double zb0 = b0[b], zb1 = d > 1 ? b1[b] : 0.0, zb2 = d > 2 ? b2[b] : 0.0;
-        double kv = h2_kappa(kid, kp0, h2_dist2(d, a0[pl], d > 1 ? a1[pl] : 0.0, d > 2 ? a2[pl] : 0.0, zb0, zb1, zb2));
+        double kv = h2_kxy(kid, kp0, d, a0[pl], d > 1 ? a1[pl] : 0.0, d > 2 ? a2[pl] : 0.0, zb0, zb1, zb2);
         sd += kv * kv;
         if (l >= k) {
             double s = 0.0;
             for (int p = 0; p < k; p++) {
                 int pp = piv[p];
                 s += A[p + (int64_t)l * m] *
-                     h2_kappa(kid, kp0, h2_dist2(d, a0[pp], d > 1 ? a1[pp] : 0.0, d > 2 ? a2[pp] : 0.0, zb0, zb1, zb2));
+                     h2_kxy(kid, kp0, d, a0[pp], d > 1 ? a1[pp] : 0.0, d > 2 ? a2[pp] : 0.0, zb0, zb1, zb2);
             }
             double e = kv - s;
             sn += e * e;

@@ -334,6 +334,31 @@ __device__ __forceinline__ double h2_kappa_fast(int kid, double kp0, double r2) 
     }
 }
 
+// x . y with explicitly rounded operations in the order x0 y0 + x1 y1 + x2 y2
+// (bit-identical to a plain IEEE evaluation in this order)
+__device__ __forceinline__ double h2_dot(int d, double a0, double a1, double a2, double b0, double b1, double b2) {
+    double s = __dmul_rn(a0, b0);
+    if (d > 1) s = __dadd_rn(s, __dmul_rn(a1, b1));
+    if (d > 2) s = __dadd_rn(s, __dmul_rn(a2, b2));
+    return s;
+}
+
+// kappa of two points, float64: Table 1's kappa_3 = cos(x . y) from the points,
+// every other kernel from their squared distance (h2_kappa)
+__device__ __forceinline__ double h2_kxy(int kid, double kp0, int d, double a0, double a1, double a2, double b0,
+                                         double b1, double b2) {
+    if (kid == H2_K_COSDOT) return cos(h2_dot(d, a0, a1, a2, b0, b1, b2));
+    return h2_kappa(kid, kp0, h2_dist2(d, a0, a1, a2, b0, b1, b2));
+}
+
+// the same in the fast forms of h2_kappa_fast (contracted arithmetic)
+__device__ __forceinline__ double h2_kxy_fast(int kid, double kp0, double a0, double a1, double a2, double b0,
+                                              double b1, double b2) {
+    if (kid == H2_K_COSDOT) return cos(a0 * b0 + a1 * b1 + a2 * b2);
+    const double dx = a0 - b0, dy = a1 - b1, dz = a2 - b2;
+    return h2_kappa_fast(kid, kp0, dx * dx + dy * dy + dz * dz);
+}
+
 // float32 kappa for the mixed-precision path
 __device__ __forceinline__ float h2_kappa_f(int kid, float kp0, float r2) {
     switch (kid) {

@@ -133,6 +133,22 @@ __device__ __forceinline__ Real kap_distinct(Real r2, Real p) {
     }
 }
 
+// kappa of a target t and a source s: cos(t . s) for Table 1's kappa_3 (both
+// in absolute coordinates), every other kernel from |t - s|^2 (DISTINCT: the
+// points are known to differ)
+template <int KID, bool DISTINCT, class Real>
+__device__ __forceinline__ Real kap_pt(Real t0, Real t1, Real t2, Real s0, Real s1, Real s2, Real p) {
+    if constexpr (KID == H2_K_COSDOT) {
+        const Real x = t0 * s0 + t1 * s1 + t2 * s2;
+        if constexpr (sizeof(Real) == 4) return __cosf(x);
+        else return cos(x);
+    } else {
+        const Real dx = t0 - s0, dy = t1 - s1, dz = t2 - s2;
+        if constexpr (DISTINCT) return kap_distinct<KID>(dx * dx + dy * dy + dz * dz, p);
+        else return kap<KID>(dx * dx + dy * dy + dz * dz, p);
+    }
+}
+
 // out[r] = sum_q kappa(x_s, x_q) z_q for s = rows[r]; one CTA per row
 __global__ void k_exact_rows(const int64_t *rows, int64_t nrows, const int32_t *iperm, const double *x0,
                              const double *x1, const double *x2, const double *zm, int64_t n, int d, int kid,
@@ -148,11 +164,8 @@ __global__ void k_exact_rows(const int64_t *rows, int64_t nrows, const int32_t *
     int64_t p = iperm[row];
     double a0 = x0[p], a1 = d > 1 ? x1[p] : 0.0, a2 = d > 2 ? x2[p] : 0.0;
     double s = 0.0;
-    for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
-        double dx = a0 - x0[q], dy = d > 1 ? a1 - x1[q] : 0.0, dz = d > 2 ? a2 - x2[q] : 0.0;
-        double r2 = dx * dx + dy * dy + dz * dz;
-        s += h2_kappa_fast(kid, kp0, r2) * zm[q];
-    }
+    for (int64_t q = threadIdx.x; q < n; q += blockDim.x)
+        s += h2_kxy_fast(kid, kp0, a0, a1, a2, x0[q], d > 1 ? x1[q] : 0.0, d > 2 ? x2[q] : 0.0) * zm[q];
     s = warp_sum(s);
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = s;
@@ -185,11 +198,8 @@ __global__ void __launch_bounds__(ER_THREADS)
     const double a0 = x0[p], a1 = d > 1 ? x1[p] : 0.0, a2 = d > 2 ? x2[p] : 0.0;
     const int64_t q0 = (int64_t)c * ER_CHUNK, q1 = min(n, q0 + ER_CHUNK);
     double s = 0.0;
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += ER_THREADS) {
-        double dx = a0 - x0[q], dy = d > 1 ? a1 - x1[q] : 0.0, dz = d > 2 ? a2 - x2[q] : 0.0;
-        double r2 = dx * dx + dy * dy + dz * dz;
-        s += h2_kappa_fast(kid, kp0, r2) * zm[q];
-    }
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += ER_THREADS)
+        s += h2_kxy_fast(kid, kp0, a0, a1, a2, x0[q], d > 1 ? x1[q] : 0.0, d > 2 ? x2[q] : 0.0) * zm[q];
     s = warp_sum(s);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = s;
@@ -398,8 +408,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
                 const Real a0 = row[0], a1 = row[1], a2 = row[2];
 #pragma unroll
                 for (int u = 0; u < TPT; u++) {
-                    const Real dx = sh[u][0] - a0, dy = sh[u][1] - a1, dz = sh[u][2] - a2;
-                    const Real kv = kap<KID>(dx * dx + dy * dy + dz * dz, p);
+                    const Real kv = kap_pt<KID, false>(sh[u][0], sh[u][1], sh[u][2], a0, a1, a2, p);
 #pragma unroll
                     for (int j = 0; j < R; j++) blk[u][j] += kv * row[4 + j];
                 }
@@ -467,8 +476,9 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
     const Real p = (Real)kpar;
     // lanes past the tile's end and sources past a block's end sit at far,
     // distinct sentinels with weight 0: every pair evaluated below has r2 > 0
-    // and contributes exactly 0 when either side is padding
-    const Real far_t = (Real)1e18;
+    // and contributes exactly 0 when either side is padding (cos(x . y) needs
+    // no distinct points: its padding sits at the origin)
+    const Real far_t = KID == H2_K_COSDOT ? (Real)0 : (Real)1e18;
     const Real tx0 = act ? X0[ts + a] : far_t, tx1 = act && d > 1 ? X1[ts + a] : (Real)0,
                tx2 = act && d > 2 ? X2[ts + a] : (Real)0;
     const Real tw = act ? w[ts + a] : (Real)0;
@@ -513,8 +523,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
 #pragma unroll 8
                 for (int q = 0; q < 32; q++) {
                     const SrcPt<Real> sv = row[q];
-                    const Real dx = s0 - sv.x, dy = s1 - sv.y, dz = s2 - sv.z;
-                    const Real kv = kap_distinct<KID>(dx * dx + dy * dy + dz * dz, p);
+                    const Real kv = kap_pt<KID, true>(s0, s1, s2, sv.x, sv.y, sv.z, p);
                     blk += kv * sv.w;
                     col += kv * tw;
                     col = __shfl_sync(0xffffffffu, col, (lane + 1) & 31);
@@ -523,8 +532,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
             } else {
                 for (int q = 0; q < cnt; q++) {
                     const SrcPt<Real> sv = stg[warp][q];
-                    const Real dx = s0 - sv.x, dy = s1 - sv.y, dz = s2 - sv.z;
-                    blk += kap<KID>(dx * dx + dy * dy + dz * dz, p) * sv.w;
+                    blk += kap_pt<KID, false>(s0, s1, s2, sv.x, sv.y, sv.z, p) * sv.w;
                 }
             }
         }
@@ -573,6 +581,7 @@ void nbody_sym(int kid, const DevBuf<int2> &tiles, const int64_t *start, const i
     case H2_K_EXPONENTIAL: H2_SYM(H2_K_EXPONENTIAL); break;
     case H2_K_BUMP: H2_SYM(H2_K_BUMP); break;
     case H2_K_POWER: H2_SYM(H2_K_POWER); break;
+    case H2_K_COSDOT: H2_SYM(H2_K_COSDOT); break;
     default: H2_SYM(H2_K_MULTIQUADRIC);
     }
 #undef H2_SYM
@@ -595,6 +604,7 @@ void nbody_kid(int kid, const DevBuf<int2> &tiles, const int64_t *start, const i
     case H2_K_EXPONENTIAL: H2_NB(H2_K_EXPONENTIAL); break;
     case H2_K_BUMP: H2_NB(H2_K_BUMP); break;
     case H2_K_POWER: H2_NB(H2_K_POWER); break;
+    case H2_K_COSDOT: H2_NB(H2_K_COSDOT); break;
     default: H2_NB(H2_K_MULTIQUADRIC);
     }
 #undef H2_NB
@@ -752,6 +762,24 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
         k_to_float<<<blocks_for(kt * R, 256), 256, 0, s>>>(xh.p, kt * R, xhf.p);
         H2_LAUNCH("k_to_float");
     }
+    // float32 point coordinates and centre splits of the N-body kernels: the
+    // tree's node-relative ones, or for cos(x . y) absolute coordinates and
+    // zero centres (the skeletons' are absolute already)
+    const float *PX[3] = {t->xr[0].p, t->xr[1].p, t->xr[2].p};
+    const float2 *CF[3] = {t->cenf[0].p, t->cenf[1].p, t->cenf[2].p};
+    DevBuf<float> xabs[3];
+    DevBuf<float2> czero;
+    if (!f64 && A->kid == H2_K_COSDOT) {
+        for (int k = 0; k < d; k++) {
+            xabs[k].alloc(n, s);
+            k_to_float<<<blocks_for(n, 256), 256, 0, s>>>(t->xs[k].p, n, xabs[k].p);
+            PX[k] = xabs[k].p;
+        }
+        H2_LAUNCH("k_to_float");
+        czero.alloc(t->nnodes, s);
+        H2_CUDA(cudaMemsetAsync(czero.p, 0, t->nnodes * sizeof(float2), s));
+        CF[0] = CF[1] = CF[2] = czero.p;
+    }
     // coupling over far pairs: B_ij = K(Xhat_i, Xhat_j) on the fly
     {
         ProfScope ps(KT_COUPLING, s);
@@ -760,16 +788,14 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
                               nullptr, nullptr, nullptr, xh.p, zh.p, t->far_ptr.p, t->far_first.p, t->far_idx.p, d,
                               A->kp[0], s);
         else if (sym)
-            nbody_sym<float>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skr[0].p, A->skr[1].p, A->skr[2].p,
-                             t->cenf[0].p, t->cenf[1].p, t->cenf[2].p, xhf.p, zh.p, t->far_ptr.p, t->far_first.p,
-                             t->far_idx.p, d, A->kp[0], s);
+            nbody_sym<float>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skr[0].p, A->skr[1].p, A->skr[2].p, CF[0],
+                             CF[1], CF[2], xhf.p, zh.p, t->far_ptr.p, t->far_first.p, t->far_idx.p, d, A->kp[0], s);
         else if (f64)
             nbody<double>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skc[0].p, A->skc[1].p, A->skc[2].p, nullptr,
                           nullptr, nullptr, xh.p, zh.p, R, t->far_ptr.p, t->far_idx.p, d, A->kp[0], s);
         else
-            nbody<float>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skr[0].p, A->skr[1].p, A->skr[2].p,
-                         t->cenf[0].p, t->cenf[1].p, t->cenf[2].p, xhf.p, zh.p, R, t->far_ptr.p, t->far_idx.p, d,
-                         A->kp[0], s);
+            nbody<float>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skr[0].p, A->skr[1].p, A->skr[2].p, CF[0],
+                         CF[1], CF[2], xhf.p, zh.p, R, t->far_ptr.p, t->far_idx.p, d, A->kp[0], s);
     }
     // downward, level 1 first
     for (int l = 1; l < t->nlevels; l++) {
@@ -801,17 +827,15 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
                               t->xs[2].p, nullptr, nullptr, nullptr, xm.p, ym.p, t->near_ptr.p, t->near_first.p,
                               t->near_idx.p, d, A->kp[0], s);
         else if (sym)
-            nbody_sym<float>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xr[0].p, t->xr[1].p,
-                             t->xr[2].p, t->cenf[0].p, t->cenf[1].p, t->cenf[2].p, xmf.p, ym.p, t->near_ptr.p,
-                             t->near_first.p, t->near_idx.p, d, A->kp[0], s);
+            nbody_sym<float>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, PX[0], PX[1], PX[2], CF[0],
+                             CF[1], CF[2], xmf.p, ym.p, t->near_ptr.p, t->near_first.p, t->near_idx.p, d, A->kp[0], s);
         else if (f64)
             nbody<double>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xs[0].p, t->xs[1].p,
                           t->xs[2].p, nullptr, nullptr, nullptr, xm.p, ym.p, R, t->near_ptr.p, t->near_idx.p, d,
                           A->kp[0], s);
         else
-            nbody<float>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xr[0].p, t->xr[1].p,
-                         t->xr[2].p, t->cenf[0].p, t->cenf[1].p, t->cenf[2].p, xmf.p, ym.p, R, t->near_ptr.p,
-                         t->near_idx.p, d, A->kp[0], s);
+            nbody<float>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, PX[0], PX[1], PX[2], CF[0], CF[1],
+                         CF[2], xmf.p, ym.p, R, t->near_ptr.p, t->near_idx.p, d, A->kp[0], s);
     }
     if (dtype == H2_DTYPE_F64)
         k_perm_out_multi<double><<<blocks_for(nr, 256), 256, 0, s>>>(ym.p, t->perm.p, n, R, static_cast<double *>(y),

@@ -18,7 +18,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libh2gb300.so")
 
-KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4, "bump": 5, "power": 6}
+KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4, "bump": 5, "power": 6,
+           "cosdot": 7}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 DTYPE_F64, DTYPE_F32 = 0, 1  # element types of h2_matvec vectors
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NUMERIC", 6: "UNIMPLEMENTED",

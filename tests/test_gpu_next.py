@@ -3,7 +3,7 @@
 - One HiDR for every kernel (section 6.1.3): the reduced sets X_i*, Y_i* depend
   only on the points, so one tree and one HiDR serve Coulomb, Gaussians of
   bandwidth 10^k (k = -2..2), exponential, multiquadric, Table 1's bump
-  kernel and the |x-y|^11 of section 5.2; each
+  kernel and cos(x . y), and the |x-y|^11 of section 5.2; each
   float64 product equals the oracle's H^2 product on the same reduction
   (1e-12) and the dense product within 10 eps.
 - The paper's three-sphere dataset (section 6.1.1): three unit spheres with
@@ -36,7 +36,7 @@ def dev(a):
 
 KERNELS = [("coulomb", ()), ("gaussian", (0.01,)), ("gaussian", (0.1,)), ("gaussian", (1.0,)),
            ("gaussian", (10.0,)), ("gaussian", (100.0,)), ("exponential", (0.2,)), ("multiquadric", ()),
-           ("bump", (0.1,)), ("power", (11.0,))]
+           ("bump", (0.1,)), ("power", (11.0,)), ("cosdot", ())]
 
 
 def test_one_hidr_for_every_kernel(H2):

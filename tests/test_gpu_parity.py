@@ -126,6 +126,8 @@ CONSTRUCT_CASES = [
     # Table 1's bump kernel (kappa_4) and the |x-y|^11 of section 5.2
     ("bump3d", 3, 4000, 64, "bump", (0.1,), 1e-7, 6),
     ("power3d", 3, 4000, 64, "power", (11.0,), 1e-7, 6),
+    # Table 1's kappa_3 = cos(x . y), not a function of |x - y|
+    ("cosdot3d", 3, 4000, 64, "cosdot", (), 1e-7, 6),
 ]
 
 
@@ -183,7 +185,7 @@ def test_exact_rows(H2):
     got_h = H2.exact_rows(t, "coulomb", (), z, rows)
     assert np.array_equal(got_h, got)
     for kern, kp in [("gaussian", (0.3,)), ("exponential", (0.2,)), ("multiquadric", ()), ("bump", (0.1,)),
-                     ("power", (11.0,))]:
+                     ("power", (11.0,)), ("cosdot", ())]:
         got = H2.exact_rows(t, kern, kp, dev(z), dev(rows)).cpu().numpy()
         want = O.exact_rows(pts, kern, kp, z, rows)
         assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max()), kern
@@ -235,6 +237,7 @@ MIXED_CASES = [
     ("expo2d", 2, 5000, 50, "exponential", (0.1,), 1e-5, 10),
     ("bump3d", 3, 4000, 64, "bump", (0.1,), 1e-5, 6),
     ("power3d", 3, 4000, 64, "power", (11.0,), 1e-5, 6),
+    ("cosdot3d", 3, 4000, 64, "cosdot", (), 1e-5, 6),
 ]
 
 
@@ -281,6 +284,7 @@ MULTI_CASES = [
     ("mixed_gauss2d", 2, 6000, 64, "gaussian", (0.2,), 1e-5, 10, "mixed"),
     ("fp64_bump3d", 3, 5000, 64, "bump", (0.1,), 1e-7, 6, "fp64"),
     ("mixed_power3d", 3, 5000, 64, "power", (11.0,), 1e-5, 6, "mixed"),
+    ("mixed_cosdot3d", 3, 5000, 64, "cosdot", (), 1e-5, 6, "mixed"),
 ]
 
 

@@ -588,6 +588,46 @@ int or_id(double *A, int m, int c, double eps, int *piv, double *T) {
     return k;
 }
 
+/* Bounded interpolation coefficients (eq. (3): ||G||_max bounded by a
+ * prescribed constant f).  After or_id, while some |T[p, l]| > f (the largest
+ * one, ties to the first in column-major order), skeleton column piv[p] and
+ * non-skeleton column piv[k + l] trade places: with g = T[p, l],
+ *   A[:, piv[k + l]] = sum_q A[:, piv[q]] T[q, l]
+ * solved for A[:, piv[p]] and substituted into every other column gives
+ *   T'[p, m] = T[p, m] / g,  T'[q, m] = T[q, m] - T[q, l] T'[p, m]  (m != l),
+ *   T'[q, l] = -(T[q, l] / g),  T'[p, l] = 1 / g               (q != p),
+ * a Gauss-Jordan pivot on T.  Each exchange multiplies the volume of the
+ * skeleton columns by |g| > f, so the loop ends; it stops after maxex
+ * exchanges in any case.  Returns the number of exchanges. */
+int or_id_bound(int k, int nr, int *piv, double *T, double f, int maxex) {
+    int nex = 0;
+    while (nex < maxex) {
+        int bp = -1, bl = -1;
+        double bv = f;
+        for (int l = 0; l < nr; l++)
+            for (int p = 0; p < k; p++) {
+                double v = fabs(T[(i64)l * k + p]);
+                if (v > bv) { bv = v; bp = p; bl = l; }
+            }
+        if (bp < 0) break;
+        double g = T[(i64)bl * k + bp];
+        for (int m = 0; m < nr; m++)
+            if (m != bl) T[(i64)m * k + bp] = T[(i64)m * k + bp] / g;
+        for (int m = 0; m < nr; m++) {
+            if (m == bl) continue;
+            double tp = T[(i64)m * k + bp];
+            for (int q = 0; q < k; q++)
+                if (q != bp) T[(i64)m * k + q] = T[(i64)m * k + q] - T[(i64)bl * k + q] * tp;
+        }
+        for (int q = 0; q < k; q++)
+            if (q != bp) T[(i64)bl * k + q] = -(T[(i64)bl * k + q] / g);
+        T[(i64)bl * k + bp] = 1.0 / g;
+        int ti = piv[bp]; piv[bp] = piv[k + bl]; piv[k + bl] = ti;
+        nex++;
+    }
+    return nex;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 2: nested bases, bottom level to top level.                     */
 /* ------------------------------------------------------------------------ */
@@ -597,6 +637,8 @@ typedef struct {
     int kid;
     double kp[4];
     double eps;
+    double gbound;   /* f of or_id_bound, 0 = no exchanges                   */
+    i64 nex;         /* exchanges made                                       */
     int nnodes;
     int *k;          /* rank k_i (-1 = not computed)                        */
     int *c;          /* |Xbar_i|                                             */
@@ -621,10 +663,10 @@ static void kernel_block(const otree *t, int kid, const double *kp, const i64 *Y
 /* need: per-node flag (NULL = all); the basis is also built for every
  * descendant of a flagged node.  Y_i* must be available for those nodes. */
 oh2 *or_construct(const otree *t, const ohidr *h, int kid, const double *kp, double eps,
-                  const unsigned char *need) {
+                  const unsigned char *need, double gbound) {
     int nn = t->nnodes;
     oh2 *H = calloc(1, sizeof(oh2));
-    H->t = t; H->kid = kid; H->eps = eps; H->nnodes = nn;
+    H->t = t; H->kid = kid; H->eps = eps; H->nnodes = nn; H->gbound = gbound;
     for (int a = 0; a < 4; a++) H->kp[a] = kp ? kp[a] : 0.0;
     H->k = malloc(sizeof(int) * nn); H->c = malloc(sizeof(int) * nn);
     H->skel = calloc(nn, sizeof(i64 *)); H->U = calloc(nn, sizeof(double *));
@@ -666,6 +708,11 @@ oh2 *or_construct(const otree *t, const ohidr *h, int kid, const double *kp, dou
             int kmax = m < c ? m : c;
             double *T = malloc(sizeof(double) * ((i64)kmax * c + 1));
             int k = or_id(A, m, c, eps, piv, T);
+            if (gbound > 0.0 && k > 0) {
+                int nx = or_id_bound(k, c - k, piv, T, gbound, 8 * k);
+#pragma omp atomic
+                H->nex += nx;
+            }
             /* sorted skeleton; sigma[p] = column of U for the p-th pivot */
             int *sk = malloc(sizeof(int) * (k > 0 ? k : 1));
             int *sigma = malloc(sizeof(int) * (k > 0 ? k : 1));
@@ -693,6 +740,7 @@ oh2 *or_construct(const otree *t, const ohidr *h, int kid, const double *kp, dou
 
 /* rank/skeleton/basis getters. which: 0 -> k, 1 -> c; skeleton copy; U copy */
 int or_h2_rank(const oh2 *H, int node, int which) { return which ? H->c[node] : H->k[node]; }
+i64 or_h2_exchanges(const oh2 *H) { return H->nex; }
 void or_h2_skel(const oh2 *H, int node, i64 *out) { if (H->k[node] > 0) memcpy(out, H->skel[node], sizeof(i64) * H->k[node]); }
 void or_h2_U(const oh2 *H, int node, double *out) {
     if (H->k[node] > 0) memcpy(out, H->U[node], sizeof(double) * (i64)H->c[node] * H->k[node]);

@@ -65,7 +65,11 @@ def lib():
             L.or_id.restype = i32
             L.or_id.argtypes = [vp, i32, i32, dbl, vp, vp]
             L.or_construct.restype = vp
-            L.or_construct.argtypes = [vp, vp, i32, vp, dbl, vp]
+            L.or_construct.argtypes = [vp, vp, i32, vp, dbl, vp, dbl]
+            L.or_id_bound.restype = i32
+            L.or_id_bound.argtypes = [i32, i32, vp, vp, dbl, i32]
+            L.or_h2_exchanges.restype = i64
+            L.or_h2_exchanges.argtypes = [vp]
             L.or_h2_rank.restype = i32
             L.or_h2_rank.argtypes = [vp, i32, i32]
             L.or_h2_skel.argtypes = [vp, i32, vp]
@@ -244,17 +248,32 @@ def interp_decomp(A: np.ndarray, eps: float):
     return k, piv[:c].copy(), Tm
 
 
+def id_bound(k: int, piv: np.ndarray, T: np.ndarray, f: float, maxex: int | None = None):
+    """The exchanges of eq. (3)'s bound ||G||_max <= f applied to an ID from
+    interp_decomp.  Returns (number of exchanges, piv', T')."""
+    c = len(piv)
+    nr = c - k
+    pv = np.ascontiguousarray(piv, dtype=np.int32).copy()
+    t = np.zeros(max(k * nr, 1))
+    t[: k * nr] = np.asarray(T, dtype=np.float64).T.reshape(-1)
+    nex = lib().or_id_bound(k, nr, _p(pv), _p(t), f, 8 * k if maxex is None else maxex)
+    return nex, pv, t[: k * nr].reshape((nr, k)).T.copy()
+
+
 class H2:
     """Nested bases of Algorithm 2 and the H^2 matvec."""
 
     def __init__(self, tree: Tree, hidr: Hidr, kernel, kparams=(), eps: float = 1e-6,
-                 need: np.ndarray | None = None):
+                 need: np.ndarray | None = None, g_bound: float = 0.0):
         self.tree, self.hidr = tree, hidr
         self.kid = _kid(kernel)
         self.kp = _kp(kparams)
         flags = None if need is None else np.ascontiguousarray(need, dtype=np.uint8)
         self.handle = lib().or_construct(tree.handle, hidr.handle, self.kid, _p(self.kp), eps,
-                                         _p(flags) if flags is not None else None)
+                                         _p(flags) if flags is not None else None, g_bound)
+
+    def exchanges(self) -> int:
+        return lib().or_h2_exchanges(self.handle)
 
     def rank(self, node: int) -> int:
         return lib().or_h2_rank(self.handle, node, 0)
@@ -344,9 +363,9 @@ def closure_down(tree: Tree, flags: np.ndarray) -> np.ndarray:
     return f
 
 
-def build_h2(points, kernel, kparams, leaf_size, eps, g1, g2, tau=(7, 10)):
+def build_h2(points, kernel, kparams, leaf_size, eps, g1, g2, tau=(7, 10), g_bound=0.0):
     """Tree, lists, HiDR and the full construction, for small problems."""
     t = tree_build(points, leaf_size, tau)
     h = Hidr(t, g1, g2)
-    H = H2(t, h, kernel, kparams, eps)
+    H = H2(t, h, kernel, kparams, eps, g_bound=g_bound)
     return t, h, H

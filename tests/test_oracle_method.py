@@ -251,3 +251,56 @@ def test_id_reflector_is_stable_for_nearly_aligned_columns():
     k, piv, T = O.interp_decomp(A, 0.0)
     assert k == 6 and np.all(np.isfinite(T))
     assert np.allclose(A[:, piv[6:]], A[:, piv[:6]] @ T, rtol=0, atol=1e-13)
+
+
+# ----------------------------------------- eq. (3)'s bound on ||G||_max
+def _kahan_rank_k(k, c, extra, m, seed):
+    """Q [R11 R12] with R11 the k x k Kahan matrix (all columns of norm 1, so
+    column pivoting keeps their order; a relative 1e-7 taper fixes it) and the
+    extra columns continuing its pattern: exact rank k, and R11^{-1} R12 grows
+    like (1 + c)^k, the classic case where column pivoting leaves |G| large."""
+    s = np.sqrt(1 - c * c)
+    R = np.zeros((k, k + extra))
+    for i in range(k):
+        R[i, i] = s ** i
+        R[i, i + 1:] = -c * s ** i
+    R = R * (1 + 1e-7 * np.arange(k + extra, 0, -1))[None, :]
+    Q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((m, m)))
+    return Q[:, :k] @ R
+
+
+def test_id_bound_exchanges_reach_the_bound_and_keep_the_id_exact():
+    A = _kahan_rank_k(6, 0.6, 2, 9, 0)
+    k, piv, T = O.interp_decomp(A, 1e-12)
+    assert k == 6 and list(piv) == list(range(8)) and np.abs(T).max() > 6
+    vol0 = abs(np.linalg.det(A[:, piv[:k]].T @ A[:, piv[:k]]))
+    nex, piv2, T2 = O.id_bound(k, piv, T, 2.0)
+    assert nex >= 1 and np.abs(T2).max() <= 2.0
+    assert sorted(piv2) == list(range(8))
+    # exact rank: the exchanged T is the least-squares ID of the new skeleton, exact
+    S, Rr = piv2[:k], piv2[k:]
+    G = np.linalg.lstsq(A[:, S], A[:, Rr], rcond=None)[0]
+    assert np.abs(G - T2).max() <= 1e-12
+    assert np.abs(A[:, S] @ T2 - A[:, Rr]).max() <= 1e-13
+    # each exchange multiplies the skeleton's volume by |g| > f
+    vol = abs(np.linalg.det(A[:, S].T @ A[:, S]))
+    assert vol >= vol0 * 4.0 ** nex * (1 - 1e-9)
+
+
+def test_id_bound_leaves_a_bounded_id_alone():
+    A = np.random.default_rng(5).standard_normal((12, 9))
+    k, piv, T = O.interp_decomp(A, 1e-3)
+    f = max(1.0, float(np.abs(T).max())) * 1.01 if T.size else 1.0
+    nex, piv2, T2 = O.id_bound(k, piv, T, f)
+    assert nex == 0 and np.array_equal(piv2, piv) and np.array_equal(T2, T)
+
+
+def test_h2_with_bounded_g():
+    pts = I.uniform_cube(6000, 3, seed=53)
+    z = I.standard_normal(6000, seed=51)
+    yd = O.dense_matvec(pts, "coulomb", (), z)
+    t, h, H = O.build_h2(pts, "coulomb", (), 100, 1e-6, 7, 7, g_bound=1.1)
+    assert H.exchanges() > 0
+    umax = max(float(np.abs(H.U(i)).max()) for i in range(1, t.nnodes) if H.rank(i) > 0)
+    assert umax <= 1.1
+    assert np.linalg.norm(H.matvec(z) - yd) <= 10 * 1e-6 * np.linalg.norm(yd)

@@ -185,6 +185,28 @@ h2_status h2_hidr_get(h2_hidr h, int which, int32_t *counts, int32_t *data, int6
 h2_status h2_construct(h2_tree t, h2_hidr h, int kernel, const double *kparams, double id_tol,
                        int precision, void *stream, h2_matrix *out);
 
+/* Options of h2_construct_ex; zero-initialised options are h2_construct's. */
+typedef struct {
+    double g_bound; /* f > 1: bound ||G||_max by f as below; 0: no exchanges */
+} h2_construct_opts;
+
+/* h2_construct with options (opts may be NULL: exactly h2_construct).
+ * Eq. (3) asks for an ID whose ||G||_max is bounded by a prescribed constant
+ * (the property strong RRQR provides).  With g_bound = f > 1, after each
+ * node's column-pivoted QR and solve, while some |G[p, l]| > f (the largest;
+ * ties to the first in column-major order of G^T, p + l k), skeleton candidate
+ * p and non-skeleton candidate l trade places by a Gauss-Jordan pivot on G:
+ * with g = G[p, l], G'[p, m] = G[p, m] / g and G'[q, m] = G[q, m] -
+ * G[q, l] G'[p, m] (m != l), G'[q, l] = -G[q, l] / g (q != p), G'[p, l] = 1 / g.
+ * Each exchange grows the skeleton columns' volume by a factor |g| > f, so the
+ * loop ends; it is cut at 8 k exchanges per node in any case.  The count is
+ * the matrix statistic "exchanges".  The parent's candidates are the
+ * children's final skeletons, so the bound holds at every level.
+ * Errors: as h2_construct; H2_ERR_INVALID_ARG if g_bound is neither 0 nor a
+ * finite number > 1. */
+h2_status h2_construct_ex(h2_tree t, h2_hidr h, int kernel, const double *kparams, double id_tol,
+                          int precision, const h2_construct_opts *opts, void *stream, h2_matrix *out);
+
 /* Construction of nprob independent problems (configuration 4 of the
  * benchmark plan): matrix p is exactly what h2_construct(trees[p], hidrs[p],
  * kernels[p], kparams + 4p, id_tols[p], precisions[p]) returns, but the

@@ -245,6 +245,11 @@ h2_status h2_hidr_get(h2_hidr hh, int which, int32_t *counts, int32_t *data, int
 
 h2_status h2_construct(h2_tree th, h2_hidr hh, int kernel, const double *kparams, double id_tol, int precision,
                        void *stream, h2_matrix *out) {
+    return h2_construct_ex(th, hh, kernel, kparams, id_tol, precision, nullptr, stream, out);
+}
+
+h2_status h2_construct_ex(h2_tree th, h2_hidr hh, int kernel, const double *kparams, double id_tol,
+                          int precision, const h2_construct_opts *opts, void *stream, h2_matrix *out) {
     return guard([&] {
         H2_REQUIRE(out != nullptr, "out is NULL");
         *out = nullptr;
@@ -254,12 +259,15 @@ h2_status h2_construct(h2_tree th, h2_hidr hh, int kernel, const double *kparams
         H2_REQUIRE(valid_kernel(kernel), "unknown kernel id");
         H2_REQUIRE(std::isfinite(id_tol) && id_tol >= 0.0, "id_tol must be finite and >= 0");
         H2_REQUIRE(precision == H2_PREC_FP64 || precision == H2_PREC_MIXED, "unknown precision");
+        const double gb = opts ? opts->g_bound : 0.0;
+        H2_REQUIRE(gb == 0.0 || (std::isfinite(gb) && gb > 1.0), "g_bound must be 0 or a finite number > 1");
         auto *A = new h2_matrix_s();
         A->tree = t;
         A->stream = static_cast<cudaStream_t>(stream);
         A->kid = kernel;
         A->id_tol = id_tol;
         A->prec = precision;
+        A->g_bound = gb;
         try {
             kparams_check(kernel, kparams, A->kp);
             construct_impl(A, h);
@@ -575,9 +583,11 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
             auto *A = static_cast<const h2_matrix_s *>(handle);
             snprintf(buf, sizeof buf,
                      "{\"k_total\": %lld, \"u_entries\": %lld, \"k_max\": %d, \"ms_construct\": %.4f, "
-                     "\"qr_flops\": %.6e, \"block_evals\": %.6e, \"g_max\": %.6e, \"precision\": \"%s\"}",
+                     "\"qr_flops\": %.6e, \"block_evals\": %.6e, \"g_max\": %.6e, \"g_bound\": %.6e, "
+                     "\"exchanges\": %lld, \"precision\": \"%s\"}",
                      (long long)A->ktotal, (long long)A->utotal, A->kmax, A->ms_construct, A->flops_qr,
-                     A->evals_block, A->g_max, A->prec == H2_PREC_FP64 ? "fp64" : "mixed");
+                     A->evals_block, A->g_max, A->g_bound, (long long)A->exchanges,
+                     A->prec == H2_PREC_FP64 ? "fp64" : "mixed");
         } else {
             fail(H2_ERR_INVALID_ARG, "not a live h2 handle");
         }

@@ -447,16 +447,60 @@ __device__ void bitonic_sort_i32(int32_t *v, int P) {
         }
 }
 
+// U_i = P [I; G] from G^T = W[p + (k + l) m] (p < k, l < c - k) and the pivot
+// order piv: the skeleton sorted by Morton position (its candidates' labels
+// cd[.] go to skel), U's column for pivot p the position of piv[p] among the
+// sorted skeleton; the largest |G| entry goes to *gmax_bits (non-negative
+// doubles order as their bit patterns).  sk: shared scratch of a power of two
+// >= k entries.  Called by every thread of the CTA.
+template <class Real>
+__device__ void id_write_u(int m, int c, int k, const double *W, const int32_t *piv, const int32_t *cd, Real *U,
+                           int32_t *skel, int32_t *sk, unsigned long long *gmax_bits) {
+    const int nr = c - k;
+    int P = 1;
+    while (P < k) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < k ? piv[i] : INT_MAX;
+    __syncthreads();
+    bitonic_sort_i32(sk, P);
+    for (int64_t e = threadIdx.x; e < (int64_t)c * k; e += blockDim.x) U[e] = (Real)0;
+    for (int q = threadIdx.x; q < k; q += blockDim.x) skel[q] = cd[sk[q]];
+    __syncthreads();
+    // column of U for pivot p: position of piv[p] in the sorted skeleton;
+    // the largest |G| entry goes to *gmax_bits (non-negative doubles order as
+    // their bit patterns)
+    unsigned long long gm = 0;
+    for (int l = threadIdx.x >> 5; l <= nr; l += blockDim.x >> 5) {  // l == 0: identity rows, else T column l-1
+        for (int p = threadIdx.x & 31; p < k; p += 32) {
+            int lo = 0, hi = k - 1, key = piv[p];
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (sk[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            if (l == 0) {
+                U[piv[p] + (int64_t)lo * c] = (Real)1;
+            } else {
+                const double gv = W[p + (int64_t)(k + l - 1) * m];
+                U[piv[k + l - 1] + (int64_t)lo * c] = (Real)gv;
+                gm = max(gm, (unsigned long long)__double_as_longlong(fabs(gv)));
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if ((threadIdx.x & 31) == 0 && gm) atomicMax(gmax_bits, gm);
+}
+
 // T = R11^{-1} R12 in float64 (right-looking back substitution in the
-// workspace W, which for a float64 block is the block itself), then U_i
-// (c x k, column-major, columns in sorted-skeleton order, stored as Real) and
-// the sorted skeleton's Morton positions.
+// workspace W, which for a float64 block is the block itself), then, with
+// write_u, U_i (c x k, column-major, columns in sorted-skeleton order, stored as
+// Real) and the sorted skeleton's Morton positions.
 template <class Real>
 __global__ void __launch_bounds__(QR_THREADS) k_id_solve(int lb, const int32_t *ycnt, const int32_t *cc,
                                                          const int32_t *kk, const int64_t *aoff, const Real *Abase,
                                                          double *Wbase, const int64_t *coff, const int32_t *pivbase,
                                                          const int32_t *cand, void *const *uptr,
-                                                         int32_t *const *skptr, unsigned long long *gmax_bits) {
+                                                         int32_t *const *skptr, unsigned long long *gmax_bits,
+                                                         bool write_u) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int a = blockIdx.x, node = lb + a;
     const int m = ycnt[node], c = cc[node], k = kk[node];
@@ -496,39 +540,92 @@ __global__ void __launch_bounds__(QR_THREADS) k_id_solve(int lb, const int32_t *
         }
         __syncthreads();
     }
-    int P = 1;
-    while (P < k) P <<= 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < k ? piv[i] : INT_MAX;
-    __syncthreads();
-    bitonic_sort_i32(sk, P);
-    Real *U = static_cast<Real *>(uptr[node]);
-    int32_t *skel = skptr[node];
-    for (int64_t e = threadIdx.x; e < (int64_t)c * k; e += blockDim.x) U[e] = (Real)0;
-    for (int q = threadIdx.x; q < k; q += blockDim.x) skel[q] = cd[sk[q]];
-    __syncthreads();
-    // column of U for pivot p: position of piv[p] in the sorted skeleton;
-    // the largest |G| entry goes to *gmax_bits (non-negative doubles order as
-    // their bit patterns)
-    unsigned long long gm = 0;
-    for (int l = threadIdx.x >> 5; l <= nr; l += blockDim.x >> 5) {  // l == 0: identity rows, else T column l-1
-        for (int p = threadIdx.x & 31; p < k; p += 32) {
-            int lo = 0, hi = k - 1, key = piv[p];
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (sk[mid] < key) lo = mid + 1;
-                else hi = mid;
-            }
-            if (l == 0) {
-                U[piv[p] + (int64_t)lo * c] = (Real)1;
-            } else {
-                const double gv = W[p + (int64_t)(k + l - 1) * m];
-                U[piv[k + l - 1] + (int64_t)lo * c] = (Real)gv;
-                gm = max(gm, (unsigned long long)__double_as_longlong(fabs(gv)));
+    if (write_u) id_write_u<Real>(m, c, k, W, piv, cd, static_cast<Real *>(uptr[node]), skptr[node], sk, gmax_bits);
+}
+
+// eq. (3)'s bound ||G||_max <= f, on G^T = W[p + (k + l) m] as k_id_solve
+// leaves it: while some |G[p, l]| > f (the largest, ties to the first in the
+// order p + l k), skeleton candidate piv[p] and non-skeleton candidate
+// piv[k + l] trade places by a Gauss-Jordan pivot on G.  With g = G[p, l]:
+// G'[p, m] = G[p, m] / g and G'[q, m] = G[q, m] - G[q, l] G'[p, m] for m != l,
+// G'[q, l] = -(G[q, l] / g) for q != p, G'[p, l] = 1 / g, each operation
+// explicitly rounded in this order.  Each exchange multiplies the skeleton
+// columns' volume by |g| > f; at most 8k exchanges.  Then U_i from the final
+// G and pivot order as k_id_solve writes it, and the count adds to *nex_total.
+constexpr int EX_THREADS = 256;
+
+template <class Real>
+__global__ void __launch_bounds__(EX_THREADS) k_id_exchange(int lb, const int32_t *ycnt, const int32_t *cc,
+                                                            const int32_t *kk, const int64_t *aoff, double *Wbase,
+                                                            const int64_t *coff, int32_t *pivbase,
+                                                            const int32_t *cand, void *const *uptr,
+                                                            int32_t *const *skptr, unsigned long long *gmax_bits,
+                                                            double f, unsigned long long *nex_total) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int32_t *sk = reinterpret_cast<int32_t *>(smem_raw);
+    __shared__ long long s_key[EX_THREADS / 32];
+    __shared__ int s_idx[EX_THREADS / 32];
+    __shared__ int s_p, s_l;
+    __shared__ double s_g;
+    const int a = blockIdx.x, node = lb + a;
+    const int m = ycnt[node], c = cc[node], k = kk[node];
+    if (k == 0) return;
+    double *W = Wbase + aoff[a];
+    int32_t *piv = pivbase + coff[a];
+    const int nr = c - k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int nex = 0;
+    while (nr > 0 && nex < 8 * k) {
+        long long bk = -1;
+        int bi = INT_MAX;
+        for (int l = warp; l < nr; l += nwarps)
+            for (int p = lane; p < k; p += 32)
+                argmax_key(bk, bi, __double_as_longlong(fabs(W[p + (int64_t)(k + l) * m])), p + l * k);
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            argmax_key(bk, bi, k2, i2);
+        }
+        if (lane == 0) { s_key[warp] = bk; s_idx[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < nwarps; w++) argmax_key(bk, bi, s_key[w], s_idx[w]);
+            s_p = -1;
+            if (__longlong_as_double(bk) > f) {
+                s_p = bi % k;
+                s_l = bi / k;
+                s_g = W[s_p + (int64_t)(k + s_l) * m];
             }
         }
+        __syncthreads();
+        const int p = s_p, l = s_l;
+        const double g = s_g;
+        if (p < 0) break;
+        double *gl = W + (int64_t)(k + l) * m;  // column l of G^T
+        for (int mm = threadIdx.x; mm < nr; mm += blockDim.x)
+            if (mm != l) W[p + (int64_t)(k + mm) * m] = __ddiv_rn(W[p + (int64_t)(k + mm) * m], g);
+        __syncthreads();
+        for (int mm = warp; mm < nr; mm += nwarps) {
+            if (mm == l) continue;
+            double *gm = W + (int64_t)(k + mm) * m;
+            const double tp = gm[p];
+            for (int q = lane; q < k; q += 32)
+                if (q != p) gm[q] = __dsub_rn(gm[q], __dmul_rn(gl[q], tp));
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < k; q += blockDim.x)
+            if (q != p) gl[q] = -__ddiv_rn(gl[q], g);
+        if (threadIdx.x == 0) {
+            gl[p] = __ddiv_rn(1.0, g);
+            const int32_t t = piv[p];
+            piv[p] = piv[k + l];
+            piv[k + l] = t;
+        }
+        __syncthreads();
+        nex++;
     }
-    for (int o = 16; o > 0; o >>= 1) gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
-    if ((threadIdx.x & 31) == 0 && gm) atomicMax(gmax_bits, gm);
+    if (threadIdx.x == 0 && nex > 0) atomicAdd(nex_total, (unsigned long long)nex);
+    id_write_u<Real>(m, c, k, W, piv, cand + coff[a], static_cast<Real *>(uptr[node]), skptr[node], sk, gmax_bits);
 }
 
 // The same solve and U for a float32 block of rank up to 128, one lane per
@@ -713,9 +810,11 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     const size_t esize = f64 ? sizeof(double) : sizeof(float);
     A->k.alloc(nn, s);
     A->c.alloc(nn, s);
-    DevBuf<unsigned long long> gmax;  // largest |G| entry over all nodes, as float64 bits
+    DevBuf<unsigned long long> gmax, nexd;  // largest |G| entry over all nodes (float64 bits); exchanges
     gmax.alloc(1, s);
+    nexd.alloc(1, s);
     H2_CUDA(cudaMemsetAsync(gmax.p, 0, sizeof(unsigned long long), s));
+    H2_CUDA(cudaMemsetAsync(nexd.p, 0, sizeof(unsigned long long), s));
     H2_CUDA(cudaMemsetAsync(A->k.p, 0, nn * sizeof(int32_t), s));
     H2_CUDA(cudaMemsetAsync(A->c.p, 0, nn * sizeof(int32_t), s));
     DevBuf<int32_t *> skptr;
@@ -825,7 +924,8 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
             // ranks): the loop form, whose 512-thread CTAs hold their share of
             // the float64 pipe beside the other float64 kernels (measured at
             // 1M: 16.8 ms against 21.8 for the column form)
-            const bool cols = !f64 && kmax <= SOLVE_KMAX;
+            const bool cols = !f64 && kmax <= SOLVE_KMAX && A->g_bound == 0.0;
+            const bool bound = A->g_bound > 0.0;  // exchanges, then U (k_id_exchange)
             int nrmax = 0;  // most columns of R12 in a node of the level
             for (int a = 0; a < nl; a++) nrmax = std::max(nrmax, (int)(cs[a] - ks[a]));
             const dim3 sg(nl, std::max(1, (nrmax + SOLVE_WARPS * 32 - 1) / (SOLVE_WARPS * 32)));
@@ -836,14 +936,26 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
             } else if (f64) {
                 k_id_solve<double><<<nl, qr_threads(cmax), loop_solve_smem(kmax), s>>>(
                     lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<double *>(Ablk.p),
-                    reinterpret_cast<double *>(Ablk.p), coff.p, piv.p, cand.p, A->uptr.p, skptr.p, gmax.p);
+                    reinterpret_cast<double *>(Ablk.p), coff.p, piv.p, cand.p, A->uptr.p, skptr.p, gmax.p, !bound);
             } else {
                 Wf.alloc(atot, s);
                 k_id_solve<float><<<nl, qr_threads(cmax), loop_solve_smem(kmax), s>>>(
                     lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<float *>(Ablk.p), Wf.p, coff.p, piv.p,
-                    cand.p, A->uptr.p, skptr.p, gmax.p);
+                    cand.p, A->uptr.p, skptr.p, gmax.p, !bound);
             }
             H2_LAUNCH("k_id_solve");
+            if (bound) {
+                const size_t sm = loop_solve_smem(kmax) - (size_t)kmax * sizeof(double);  // the sort scratch
+                if (f64)
+                    k_id_exchange<double><<<nl, EX_THREADS, sm, s>>>(
+                        lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<double *>(Ablk.p), coff.p, piv.p,
+                        cand.p, A->uptr.p, skptr.p, gmax.p, A->g_bound, nexd.p);
+                else
+                    k_id_exchange<float><<<nl, EX_THREADS, sm, s>>>(lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, Wf.p,
+                                                                    coff.p, piv.p, cand.p, A->uptr.p, skptr.p,
+                                                                    gmax.p, A->g_bound, nexd.p);
+                H2_LAUNCH("k_id_exchange");
+            }
         }
         A->ktotal += ktot;
         A->utotal += utot;
@@ -876,6 +988,7 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     double gv;
     memcpy(&gv, &gb, sizeof gv);
     A->g_max = gv;
+    A->exchanges = (int64_t)read_scalar(nexd.p, s);
 }
 
 namespace {
@@ -982,7 +1095,7 @@ double calib_error_gpu(int d, int kid, double kp0, double id_tol, const double *
         gm.alloc(1, s);
         H2_CUDA(cudaMemsetAsync(gm.p, 0, sizeof(unsigned long long), s));
         k_id_solve<double><<<1, QR_THREADS, loop_solve_smem(k), s>>>(
-            0, mc.p, mc.p + 1, kk.p, off.p, A.p, A.p, off.p + 2, piv.p, cand.p, up.p, sp.p, gm.p);
+            0, mc.p, mc.p + 1, kk.p, off.p, A.p, A.p, off.p + 2, piv.p, cand.p, up.p, sp.p, gm.p, true);
         H2_LAUNCH("k_id_solve (calibration)");
     }
     DevBuf<double> num, den;

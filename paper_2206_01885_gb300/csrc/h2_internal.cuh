@@ -205,6 +205,8 @@ struct h2_matrix_s {
     double ms_construct = 0;
     double flops_qr = 0, evals_block = 0;
     double g_max = 0;  // largest |G| = |(R11^{-1} R12)^T| entry over all nodes (what strong RRQR would bound)
+    double g_bound = 0;       // f of the exchanges bounding ||G||_max (0: none)
+    int64_t exchanges = 0;    // exchanges made
 };
 
 namespace h2 {

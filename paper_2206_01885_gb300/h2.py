@@ -46,6 +46,10 @@ class _Params(C.Structure):
     _fields_ = [("leaf_size", C.c_int), ("tau_num", C.c_int), ("tau_den", C.c_int)]
 
 
+class _ConstructOpts(C.Structure):
+    _fields_ = [("g_bound", C.c_double)]
+
+
 def lib():
     """Load the shared library (built by ``build.build()``)."""
     global _lib
@@ -60,6 +64,7 @@ def lib():
             "h2_hidr_reduce": [vp, i32, i32, vp, C.POINTER(vp)],
             "h2_hidr_get": [vp, i32, vp, vp, i64, C.POINTER(i64)],
             "h2_construct": [vp, vp, i32, vp, dbl, i32, vp, C.POINTER(vp)],
+            "h2_construct_ex": [vp, vp, i32, vp, dbl, i32, C.POINTER(_ConstructOpts), vp, C.POINTER(vp)],
             "h2_matrix_get": [vp, i32, vp, i64, C.POINTER(i64)],
             "h2_matvec": [vp, vp, vp, i32, i32, i64, i32, vp],
             "h2_exact_rows": [vp, i32, vp, vp, vp, i64, vp, i32, vp],
@@ -198,7 +203,9 @@ class H2Matrix(_Handle):
     """h2_construct: nested bases (Algorithm 2); .matvec applies K~."""
 
     def __init__(self, tree: Tree, hidr: Hidr, kernel, kparams=(), id_tol: float = 1e-6, precision="fp64",
-                 stream=None, _handle=None):
+                 stream=None, g_bound: float = 0.0, _handle=None):
+        """g_bound = f > 1 bounds ||G||_max by f through exchanges after the
+        QR (h2_construct_ex); 0 is the plain column-pivoted ID."""
         if _handle is not None:  # built by construct_batched
             self._h = _handle
             self.tree = tree
@@ -206,8 +213,9 @@ class H2Matrix(_Handle):
         h = C.c_void_p()
         kp = _kparams(kparams)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        _check("h2_construct", lib().h2_construct(tree.handle, hidr.handle, _kid(kernel), kp, float(id_tol), prec,
-                                                   _stream(stream), C.byref(h)))
+        opts = _ConstructOpts(float(g_bound))
+        _check("h2_construct_ex", lib().h2_construct_ex(tree.handle, hidr.handle, _kid(kernel), kp, float(id_tol),
+                                                         prec, C.byref(opts), _stream(stream), C.byref(h)))
         self._h = h.value
         self.tree = tree
 

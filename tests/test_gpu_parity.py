@@ -380,3 +380,45 @@ def test_construct_batched_equals_one_by_one(H2):
     assert e.value.status == 1 and "problem 1" in str(e.value)
     for x in reversed(keep):
         x.free()
+
+
+def test_bounded_g_exchanges(H2):
+    """Eq. (3)'s bound ||G||_max <= f by exchanges after the QR: float64
+    ranks, skeletons, U and the number of exchanges equal the oracle's with
+    the same f; every U entry within f; both forms within 10 eps of the dense
+    product; an f that is neither 0 nor above 1 is rejected."""
+    n, q, eps, g, f = 6000, 100, 1e-6, 7, 1.1
+    pts = I.uniform_cube(n, 3, seed=53)
+    z = I.standard_normal(n, seed=51)
+    t = H2.Tree(dev(pts), q)
+    h = H2.Hidr(t, g, g)
+    A = H2.H2Matrix(t, h, "coulomb", (), eps, "fp64", g_bound=f)
+    o, oh, OH = O.build_h2(pts, "coulomb", (), q, eps, g, g, g_bound=f)
+    st = json.loads(A.stats())
+    assert st["exchanges"] == OH.exchanges() > 0
+    ranks, nc = A.get("rank"), A.get("ncand")
+    skel, U = A.get("skel"), A.get("U")
+    assert np.array_equal(ranks, np.array([max(OH.rank(i), 0) for i in range(o.nnodes)]))
+    koff = np.concatenate([[0], np.cumsum(ranks)])
+    uoff = np.concatenate([[0], np.cumsum(ranks.astype(np.int64) * nc)])
+    for i in range(1, o.nnodes):
+        k = ranks[i]
+        if k == 0:
+            continue
+        assert np.array_equal(skel[koff[i]:koff[i + 1]], OH.skeleton(i)), i
+        Ui = U[uoff[i]:uoff[i + 1]].reshape(k, nc[i]).T
+        assert np.max(np.abs(Ui - OH.U(i))) <= 64 * 2.0 ** -53 * nc[i] / eps * max(1.0, np.abs(OH.U(i)).max()), i
+    assert st["g_max"] <= f
+    yd = O.dense_matvec(pts, "coulomb", (), z)
+    y = A.matvec(dev(z)).cpu().numpy()
+    assert np.linalg.norm(y - yd) <= 10 * eps * np.linalg.norm(yd)
+    Am = H2.H2Matrix(t, h, "coulomb", (), 1e-5, "mixed", g_bound=f)
+    stm = json.loads(Am.stats())
+    assert stm["exchanges"] > 0 and stm["g_max"] <= f
+    ym = Am.matvec(dev(z)).cpu().numpy()
+    assert np.linalg.norm(ym - yd) <= 10 * 1e-5 * np.linalg.norm(yd)
+    for bad in (0.5, 1.0, float("nan"), -2.0):
+        with pytest.raises(RuntimeError):
+            H2.H2Matrix(t, h, "coulomb", (), eps, "fp64", g_bound=bad)
+    Am.free()
+    A.free()

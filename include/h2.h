@@ -296,6 +296,22 @@ h2_status h2_exact_rows_noalloc(h2_tree t, int kernel, const double *kparams, co
 h2_status h2_sampled_error(const double *exact, const double *approx, const int64_t *rows, int64_t nrows,
                            int64_t n, double *err_out, int on_device, void *stream);
 
+/* ----------------------------------------------------------- autotune --- */
+/* Leaf-size autotuner (leaf sizes of batched problems "chosen by the
+ * autotuner"; the paper fixes q by hand): for each of the ncand leaf sizes
+ * cands[c] (>= 1), builds the tree (tau 7/10), the HiDR (g1 = g2 = g), the
+ * construction (kernel, kparams, id_tol, precision) and one float64 matvec on
+ * pts, reps times (>= 1), and keeps the least device time (CUDA events on
+ * stream) of tree + HiDR + construction + matvec in times[c] (ms, host, may
+ * be NULL).  *best = the fastest candidate's leaf size (ties to the first).
+ * pts: n x dim float64 row-major, on the device if pts_on_device else on the
+ * host; pass a subsample to keep the search cheap (the costs per point vary
+ * little with n above ~1e5).  Synchronises.
+ * Errors: those of the calls it makes, and H2_ERR_INVALID_ARG. */
+h2_status h2_autotune_leaf(const double *pts, int64_t n, int dim, int pts_on_device, const int *cands,
+                           int ncand, int g, int kernel, const double *kparams, double id_tol, int precision,
+                           int reps, void *stream, int *best, double *times);
+
 /* ------------------------------------------------------------- common --- */
 /* Release any handle returned above (NULL is a no-op).  Device memory is
  * returned on the handle's stream, which must still exist. */

@@ -525,6 +525,72 @@ h2_status h2_exact_rows_noalloc(h2_tree th, int kernel, const double *kparams, c
     });
 }
 
+h2_status h2_autotune_leaf(const double *pts, int64_t n, int dim, int pts_on_device, const int *cands,
+                           int ncand, int g, int kernel, const double *kparams, double id_tol, int precision,
+                           int reps, void *stream, int *best, double *times) {
+    return guard([&] {
+        H2_REQUIRE(cands != nullptr && ncand >= 1, "no candidate leaf sizes");
+        H2_REQUIRE(best != nullptr, "best is NULL");
+        H2_REQUIRE(reps >= 1, "reps must be >= 1");
+        H2_REQUIRE(n >= 1, "n must be >= 1");
+        for (int c = 0; c < ncand; c++) H2_REQUIRE(cands[c] >= 1, "leaf sizes must be >= 1");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        DevBuf<double> x, y;
+        x.alloc(n, s);
+        y.alloc(n, s);
+        H2_CUDA(cudaMemsetAsync(x.p, 0, n * sizeof(double), s));
+        struct Events {  // destroyed on every way out
+            cudaEvent_t a = nullptr, b = nullptr;
+            ~Events() {
+                if (a) cudaEventDestroy(a);
+                if (b) cudaEventDestroy(b);
+            }
+        } ev;
+        H2_CUDA(cudaEventCreate(&ev.a));
+        H2_CUDA(cudaEventCreate(&ev.b));
+        cudaEvent_t e0 = ev.a, e1 = ev.b;
+        double best_ms = 0.0;
+        // a failing call's status and message pass through; the handles of
+        // the round in progress are released on the way out
+        auto run = [&](int q) -> double {
+            h2_tree_params prm{q, 7, 10};
+            h2_tree t = nullptr;
+            h2_hidr h = nullptr;
+            h2_matrix A = nullptr;
+            h2_status st = H2_OK;
+            H2_CUDA(cudaEventRecord(e0, s));
+            st = h2_tree_build(pts, n, dim, pts_on_device, &prm, stream, &t);
+            if (st == H2_OK) st = h2_hidr_reduce(t, g, g, stream, &h);
+            if (st == H2_OK) st = h2_construct(t, h, kernel, kparams, id_tol, precision, stream, &A);
+            if (st == H2_OK) st = h2_matvec(A, x.p, y.p, 1, H2_DTYPE_F64, n, 1, stream);
+            std::string msg = st == H2_OK ? std::string() : std::string(h2_last_error());
+            float ms = 0.f;
+            if (st == H2_OK) {
+                H2_CUDA(cudaEventRecord(e1, s));
+                H2_CUDA(cudaEventSynchronize(e1));
+                H2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            }
+            h2_free(A);
+            h2_free(h);
+            h2_free(t);
+            if (st != H2_OK) fail(st, msg);
+            return ms;
+        };
+        for (int c = 0; c < ncand; c++) {
+            double tmin = 0.0;
+            for (int r = 0; r < reps; r++) {
+                const double ms = run(cands[c]);
+                tmin = r == 0 ? ms : std::min(tmin, ms);
+            }
+            if (times) times[c] = tmin;
+            if (c == 0 || tmin < best_ms) {
+                best_ms = tmin;
+                *best = cands[c];
+            }
+        }
+    });
+}
+
 h2_status h2_free(void *handle) {
     return guard([&] {
         if (!handle) return;

@@ -65,6 +65,7 @@ def lib():
             "h2_hidr_get": [vp, i32, vp, vp, i64, C.POINTER(i64)],
             "h2_construct": [vp, vp, i32, vp, dbl, i32, vp, C.POINTER(vp)],
             "h2_construct_ex": [vp, vp, i32, vp, dbl, i32, C.POINTER(_ConstructOpts), vp, C.POINTER(vp)],
+            "h2_autotune_leaf": [vp, i64, i32, i32, vp, i32, i32, i32, vp, dbl, i32, i32, vp, C.POINTER(i32), vp],
             "h2_matrix_get": [vp, i32, vp, i64, C.POINTER(i64)],
             "h2_matvec": [vp, vp, vp, i32, i32, i64, i32, vp],
             "h2_exact_rows": [vp, i32, vp, vp, vp, i64, vp, i32, vp],
@@ -296,6 +297,29 @@ def construct_batched(problems, stream=None):
     _check("h2_construct_batched", lib().h2_construct_batched(n, trees, hidrs, kids, kps, tols, precs,
                                                                _stream(stream), outs))
     return [H2Matrix(p[0], p[1], p[2], _handle=outs[i]) for i, p in enumerate(problems)]
+
+
+def autotune_leaf(points, candidates=(64, 128, 256), g=7, kernel="coulomb", kparams=(), id_tol=1e-5,
+                  precision="mixed", reps=2, stream=None):
+    """h2_autotune_leaf: the leaf size among candidates with the least device
+    time of tree + HiDR + construction + one matvec on points (a CUDA tensor
+    or host array, n x d float64).  Returns (best, {q: ms})."""
+    c = list(candidates)
+    cands = (C.c_int * len(c))(*c)
+    times = (C.c_double * len(c))()
+    best = C.c_int(0)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if _is_cuda(points):
+        pts = points.contiguous()
+        ptr, on_dev = C.c_void_p(pts.data_ptr()), 1
+    else:
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        ptr, on_dev = pts.ctypes.data_as(C.c_void_p), 0
+    n, d = pts.shape
+    _check("h2_autotune_leaf", lib().h2_autotune_leaf(ptr, n, d, on_dev, cands, len(c), int(g), _kid(kernel),
+                                                       _kparams(kparams), float(id_tol), prec, int(reps),
+                                                       _stream(stream), C.byref(best), times))
+    return best.value, {q: times[i] for i, q in enumerate(c)}
 
 
 def matvec(A: H2Matrix, x, y=None, stream=None):

@@ -60,5 +60,10 @@ def test_invalid_arguments_are_rejected_without_device_work(L):
         neg = (C.c_double * 4)(-1.0, 0.0, 0.0, 0.0)
         assert L.h2_calibrate(3, kid, neg, 1e-6, pts, 5, pts, 5, 8, None, C.byref(g), None) == 1
         assert b"kparams" in L.h2_last_error()
+    b = C.c_int(0)
+    assert L.h2_autotune_leaf(pts, 10, 3, 0, None, 0, 7, 1, None, 1e-5, 1, 1, None, C.byref(b), None) == 1
+    cands = (C.c_int * 2)(64, 0)
+    assert L.h2_autotune_leaf(pts, 10, 3, 0, cands, 2, 7, 1, None, 1e-5, 1, 1, None, C.byref(b), None) == 1
+    assert b"leaf" in L.h2_last_error()
     buf = C.create_string_buffer(64)
     assert L.h2_get_stats(bogus, buf, 64) == 1

@@ -422,3 +422,15 @@ def test_bounded_g_exchanges(H2):
             H2.H2Matrix(t, h, "coulomb", (), eps, "fp64", g_bound=bad)
     Am.free()
     A.free()
+
+
+def test_autotune_leaf(H2):
+    """The leaf-size autotuner returns the candidate with the least measured
+    time, from device or host points, and every candidate's time."""
+    pts = I.uniform_cube(100000, 3, seed=90)
+    best, times = H2.autotune_leaf(dev(pts), (64, 128, 256), g=6, id_tol=1e-5, precision="mixed")
+    assert set(times) == {64, 128, 256} and all(v > 0 for v in times.values())
+    assert best == min(times, key=lambda q: (times[q], [64, 128, 256].index(q)))
+    best_h, times_h = H2.autotune_leaf(pts[:20000], (32, 256), g=5, kernel="gaussian", kparams=(0.5,),
+                                       precision="fp64", reps=1)
+    assert best_h in (32, 256) and set(times_h) == {32, 256}

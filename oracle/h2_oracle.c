@@ -408,6 +408,77 @@ i64 or_datareduct(const double *xs, int d, const i64 *S, i64 ns, int g, i64 *out
     return w;
 }
 
+/* DataReduct, surface-based (section 3.3): the reference set Q lies on three
+ * ellipsoids centred at the centre c of S's bounding box [l, u], with
+ * semi-axes gamma (u_k - l_k) for gamma = 0.3, 0.6, 1.2, ne = floor(g^d / 3)
+ * points on each; every q takes its nearest point of S (float64 squared
+ * distance, ties to the smaller label), and the winners, deduplicated and
+ * sorted, form X*.  The paper leaves the points on the ellipsoids open; here
+ * they are the unit directions of the Fibonacci lattice in 3D,
+ *   z_j = 1 - (2j + 1) / ne, rho_j = sqrt(1 - z_j^2), phi_j = j pi (3 - sqrt 5),
+ *   u_j = (rho_j cos phi_j, rho_j sin phi_j, z_j),
+ * and equal angles theta_j = 2 pi (j + 1/2) / ne in 2D, u_j = (cos, sin), so
+ * q = c + (gamma (u - l)) * u_j per coordinate.  |S| <= g^d returns S. */
+static const double SURF_GAMMA[3] = {0.3, 0.6, 1.2};
+static const double SURF_PI = 3.14159265358979323846;
+
+static void surf_dir(int d, int ne, int j, double *u) {
+    if (d == 3) {
+        double z = 1.0 - (2.0 * j + 1.0) / ne;
+        double rho = sqrt(1.0 - z * z);
+        double phi = j * (SURF_PI * (3.0 - sqrt(5.0)));
+        u[0] = rho * cos(phi); u[1] = rho * sin(phi); u[2] = z;
+    } else {
+        double th = 2.0 * SURF_PI * (j + 0.5) / ne;
+        u[0] = cos(th); u[1] = sin(th); u[2] = 0.0;
+    }
+}
+
+i64 or_datareduct_surface(const double *xs, int d, const i64 *S, i64 ns, int g, i64 *out) {
+    i64 r = ipow(g, d);
+    if (ns <= r || d < 2) {
+        memcpy(out, S, sizeof(i64) * ns);
+        qsort(out, ns, sizeof(i64), cmp_i64);
+        return ns;
+    }
+    double l[3], u[3];
+    for (int k = 0; k < d; k++) { l[k] = xs[S[0] * d + k]; u[k] = l[k]; }
+    for (i64 a = 1; a < ns; a++)
+        for (int k = 0; k < d; k++) {
+            double v = xs[S[a] * d + k];
+            if (v < l[k]) l[k] = v;
+            if (v > u[k]) u[k] = v;
+        }
+    int ne = (int)(r / 3);
+    i64 m = 0;
+    for (int e = 0; e < 3; e++)
+        for (int j = 0; j < ne; j++) {
+            double dir[3], qp[3];
+            surf_dir(d, ne, j, dir);
+            for (int k = 0; k < d; k++) {
+                double c = (l[k] + u[k]) * 0.5;
+                double a = SURF_GAMMA[e] * (u[k] - l[k]);
+                qp[k] = c + a * dir[k];
+            }
+            i64 best = -1; double bd = 0.0;
+            for (i64 b = 0; b < ns; b++) {
+                double dd = dist2(xs + S[b] * d, qp, d);
+                if (best < 0 || dd < bd || (dd == bd && S[b] < best)) { bd = dd; best = S[b]; }
+            }
+            out[m++] = best;
+        }
+    qsort(out, m, sizeof(i64), cmp_i64);
+    i64 w = 0;
+    for (i64 a = 0; a < m; a++)
+        if (w == 0 || out[a] != out[w - 1]) out[w++] = out[a];
+    return w;
+}
+
+/* the DataReduct of HiDR: method 0 volume-based, 1 surface-based */
+static i64 datareduct_m(int method, const double *xs, int d, const i64 *S, i64 ns, int g, i64 *out) {
+    return method == 1 ? or_datareduct_surface(xs, d, S, ns, g, out) : or_datareduct(xs, d, S, ns, g, out);
+}
+
 /* ------------------------------------------------------------------------ */
 /* HiDR, Algorithm 1.                                                        */
 /* ------------------------------------------------------------------------ */
@@ -421,7 +492,7 @@ typedef struct {
 /* need_y: per-node flag (NULL = all) of nodes whose Y* is wanted; Y* is then
  * also computed for every ancestor of a flagged node.  X* is computed for all
  * non-root nodes. */
-ohidr *or_hidr(const otree *t, int g1, int g2, const unsigned char *need_y) {
+ohidr *or_hidr(const otree *t, int g1, int g2, const unsigned char *need_y, int method) {
     int nn = t->nnodes, d = t->d;
     ohidr *h = calloc(1, sizeof(ohidr));
     h->nnodes = nn; h->g1 = g1; h->g2 = g2;
@@ -453,7 +524,7 @@ ohidr *or_hidr(const otree *t, int g1, int g2, const unsigned char *need_y) {
             }
             i64 cap = ns < ipow(g1, d) ? ns : ipow(g1, d);
             h->xs[i] = malloc(sizeof(i64) * (cap > 0 ? cap : 1));
-            h->nx[i] = or_datareduct(t->x, d, S, ns, g1, h->xs[i]);
+            h->nx[i] = datareduct_m(method, t->x, d, S, ns, g1, h->xs[i]);
             free(S);
         }
     }
@@ -478,7 +549,7 @@ ohidr *or_hidr(const otree *t, int g1, int g2, const unsigned char *need_y) {
             }
             i64 cap = nt < ipow(g2, d) ? nt : ipow(g2, d);
             h->ys[i] = malloc(sizeof(i64) * cap);
-            h->ny[i] = or_datareduct(t->x, d, T, nt, g2, h->ys[i]);
+            h->ny[i] = datareduct_m(method, t->x, d, T, nt, g2, h->ys[i]);
             free(T);
         }
     }

@@ -57,8 +57,10 @@ def lib():
             L.or_tree_free.argtypes = [vp]
             L.or_datareduct.restype = i64
             L.or_datareduct.argtypes = [vp, i32, vp, i64, i32, vp]
+            L.or_datareduct_surface.restype = i64
+            L.or_datareduct_surface.argtypes = [vp, i32, vp, i64, i32, vp]
             L.or_hidr.restype = vp
-            L.or_hidr.argtypes = [vp, i32, i32, vp]
+            L.or_hidr.argtypes = [vp, i32, i32, vp, i32]
             L.or_hidr_get.restype = i64
             L.or_hidr_get.argtypes = [vp, i32, i32, vp]
             L.or_hidr_free.argtypes = [vp]
@@ -195,28 +197,34 @@ def tree_build(points: np.ndarray, leaf_size: int, tau=(7, 10)) -> Tree:
     return t
 
 
-def datareduct(coords: np.ndarray, labels: np.ndarray, g: int) -> np.ndarray:
-    """DataReduct(S, g^d) (section 3.3, volume-based).  ``coords`` indexed by
-    label; ``labels`` the members of S.  Returns the sorted reduced labels."""
+DR_METHODS = {"volume": 0, "surface": 1}
+
+
+def datareduct(coords: np.ndarray, labels: np.ndarray, g: int, method: str = "volume") -> np.ndarray:
+    """DataReduct(S, g^d) (section 3.3, volume- or surface-based).  ``coords``
+    indexed by label; ``labels`` the members of S.  Returns the sorted reduced
+    labels."""
     L = lib()
     xs = np.ascontiguousarray(coords, dtype=np.float64)
     if xs.ndim == 1:
         xs = xs[:, None]
     S = np.ascontiguousarray(labels, dtype=np.int64)
     out = np.zeros(max(len(S), 1), dtype=np.int64)
-    m = L.or_datareduct(_p(xs), xs.shape[1], _p(S), len(S), g, _p(out))
+    f = L.or_datareduct_surface if DR_METHODS[method] == 1 else L.or_datareduct
+    m = f(_p(xs), xs.shape[1], _p(S), len(S), g, _p(out))
     return out[:m].copy()
 
 
 class Hidr:
     """X_i*, Y_i* of Algorithm 1."""
 
-    def __init__(self, tree: Tree, g1: int, g2: int, need_y: np.ndarray | None = None):
+    def __init__(self, tree: Tree, g1: int, g2: int, need_y: np.ndarray | None = None, method: str = "volume"):
         self.tree, self.g1, self.g2 = tree, g1, g2
         flags = None
         if need_y is not None:
             flags = np.ascontiguousarray(need_y, dtype=np.uint8)
-        self.handle = lib().or_hidr(tree.handle, g1, g2, _p(flags) if flags is not None else None)
+        self.handle = lib().or_hidr(tree.handle, g1, g2, _p(flags) if flags is not None else None,
+                                    DR_METHODS[method])
 
     def get(self, node: int, which: str) -> np.ndarray | None:
         w = 0 if which == "x" else 1

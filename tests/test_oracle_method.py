@@ -66,11 +66,12 @@ def _farfield_points(t, i):
     return pts
 
 
-@pytest.mark.parametrize("d,n,q,g", [(3, 3000, 30, 3), (2, 2500, 20, 4)])
-def test_hidr_invariants(d, n, q, g):
+@pytest.mark.parametrize("d,n,q,g,method", [(3, 3000, 30, 3, "volume"), (2, 2500, 20, 4, "volume"),
+                                            (3, 3000, 30, 3, "surface"), (2, 2500, 20, 4, "surface")])
+def test_hidr_invariants(d, n, q, g, method):
     pts = I.uniform_cube(n, d, seed=7 + d)
     t = O.tree_build(pts, q)
-    h = O.Hidr(t, g, g)
+    h = O.Hidr(t, g, g, method=method)
     r = g ** d
     for i in range(1, t.nnodes):
         xs = h.get(i, "x")
@@ -304,3 +305,48 @@ def test_h2_with_bounded_g():
     umax = max(float(np.abs(H.U(i)).max()) for i in range(1, t.nnodes) if H.rank(i) > 0)
     assert umax <= 1.1
     assert np.linalg.norm(H.matvec(z) - yd) <= 10 * 1e-6 * np.linalg.norm(yd)
+
+
+# ------------------------------------------ surface-based DataReduct (section 3.3)
+def _surface_dirs(d, ne):
+    """unit directions of the reading: the Fibonacci lattice (3D), equal angles (2D)"""
+    out = []
+    for j in range(ne):
+        if d == 3:
+            z = 1.0 - (2.0 * j + 1.0) / ne
+            rho = math.sqrt(1.0 - z * z)
+            phi = j * (math.pi * (3.0 - math.sqrt(5.0)))
+            out.append((rho * math.cos(phi), rho * math.sin(phi), z))
+        else:
+            th = 2.0 * math.pi * (j + 0.5) / ne
+            out.append((math.cos(th), math.sin(th)))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("d,g", [(3, 4), (2, 9)])
+def test_surface_datareduct_finds_points_on_its_ellipsoids(d, g):
+    """S = the corners of a box (fixing the bounding box [l, u] and so the
+    ellipsoids: centre (l + u) / 2, semi-axes gamma (u - l)), the points of the
+    gamma = 0.3 ellipsoid (inside the box; the 0.6 and 1.2 ones reach outside
+    it) and random interior points: every reference point on the gamma = 0.3
+    ellipsoid finds itself (distance 0)."""
+    lo, hi = np.array([0.0, -1.0, 2.0][:d]), np.array([1.0, 1.5, 2.5][:d])
+    corners = np.array(np.meshgrid(*[[a, b] for a, b in zip(lo, hi)], indexing="ij")).reshape(d, -1).T
+    ne = g ** d // 3
+    u = _surface_dirs(d, ne)
+    c, w = (lo + hi) * 0.5, hi - lo
+    on = [c + (0.3 * w) * u]
+    rnd = lo + (hi - lo) * np.random.default_rng(4).random((400, d))
+    X = np.concatenate([corners] + on + [rnd])
+    labels = np.arange(len(X))
+    got = O.datareduct(X, labels, g, "surface")
+    assert np.all(np.diff(got) > 0) and len(got) <= 3 * ne
+    want = set(range(len(corners), len(corners) + ne))
+    assert want <= set(got.tolist())
+    # the other two ellipsoids pick further points of S
+    assert len(set(got.tolist()) - want) >= 1
+
+
+def test_surface_datareduct_small_set_is_identity():
+    X = I.uniform_cube(20, 3, seed=8)
+    assert np.array_equal(O.datareduct(X, np.arange(20)[::-1].copy(), 3, "surface"), np.arange(20))

@@ -159,6 +159,24 @@ h2_status h2_calibrate(int dim, int kernel, const double *kparams, double eps,
  * H2_ERR_CUDA. */
 h2_status h2_hidr_reduce(h2_tree t, int g1, int g2, void *stream, h2_hidr *out);
 
+/* DataReduct variants of section 3.3 for h2_hidr_reduce_ex */
+typedef enum {
+    H2_DR_VOLUME = 0, /* h2_hidr_reduce's: nearest points to a g^d tensor grid */
+    H2_DR_SURFACE = 1 /* nearest points to floor(g^d / 3) reference points on
+                         each of three ellipsoids centred at the centre c of
+                         the set's bounding box [l, u], semi-axes gamma (u - l)
+                         for gamma = 0.3, 0.6, 1.2: q = c + (gamma (u - l)) *
+                         dir_j, dir_j the Fibonacci-lattice unit directions
+                         in 3D (z_j = 1 - (2j + 1) / ne, rho_j = sqrt(1 -
+                         z_j^2), phi_j = j pi (3 - sqrt 5)) and the equal
+                         angles 2 pi (j + 1/2) / ne in 2D; same nearest-point
+                         rule, deduplicated and sorted                       */
+} h2_datareduct;
+
+/* h2_hidr_reduce with the DataReduct variant `method` (h2_datareduct).
+ * Errors: as h2_hidr_reduce; H2_ERR_INVALID_ARG for an unknown method. */
+h2_status h2_hidr_reduce_ex(h2_tree t, int g1, int g2, int method, void *stream, h2_hidr *out);
+
 /* which: 0 = X_i*, 1 = Y_i*.  Fills counts (int32 [nnodes], may be NULL) and,
  * if data is not NULL, the concatenation over nodes in node order of the
  * sorted Morton positions (int32, cap elements).  *total = sum of counts.

@@ -22,6 +22,7 @@ LIB = os.path.join(BUILD, "libh2gb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+                 "-Xcompiler", "-ffp-contract=off",
                  "--expt-relaxed-constexpr", "-cudart", "shared", f"-I{INCLUDE}"]
 
 

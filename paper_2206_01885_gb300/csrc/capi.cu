@@ -196,9 +196,14 @@ h2_status h2_tree_get(h2_tree th, int what, void *buf, int64_t cap, int64_t *len
 }
 
 h2_status h2_hidr_reduce(h2_tree th, int g1, int g2, void *stream, h2_hidr *out) {
+    return h2_hidr_reduce_ex(th, g1, g2, H2_DR_VOLUME, stream, out);
+}
+
+h2_status h2_hidr_reduce_ex(h2_tree th, int g1, int g2, int method, void *stream, h2_hidr *out) {
     return guard([&] {
         H2_REQUIRE(out != nullptr, "out is NULL");
         *out = nullptr;
+        H2_REQUIRE(method == H2_DR_VOLUME || method == H2_DR_SURFACE, "unknown DataReduct method");
         h2_tree_s *t = as_tree(th);
         H2_REQUIRE(g1 >= 1 && g2 >= 1, "g1 and g2 must be >= 1");
         auto *h = new h2_hidr_s();
@@ -206,6 +211,7 @@ h2_status h2_hidr_reduce(h2_tree th, int g1, int g2, void *stream, h2_hidr *out)
         h->stream = static_cast<cudaStream_t>(stream);
         h->g1 = g1;
         h->g2 = g2;
+        h->method = method;
         try {
             hidr_impl(h);
         } catch (...) {
@@ -642,9 +648,9 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
             auto *h = static_cast<const h2_hidr_s *>(handle);
             snprintf(buf, sizeof buf,
                      "{\"g1\": %d, \"g2\": %d, \"x_total\": %lld, \"y_total\": %lld, \"t_max_level\": %lld, "
-                     "\"t_total\": %lld, \"ms_up\": %.4f, \"ms_down\": %.4f}",
+                     "\"t_total\": %lld, \"ms_up\": %.4f, \"ms_down\": %.4f, \"method\": \"%s\"}",
                      h->g1, h->g2, (long long)h->xtotal, (long long)h->ytotal, (long long)h->tmax,
-                     (long long)h->ttotal, h->ms_up, h->ms_down);
+                     (long long)h->ttotal, h->ms_up, h->ms_down, h->method == H2_DR_SURFACE ? "surface" : "volume");
         } else if (tag == TAG_MATRIX) {
             auto *A = static_cast<const h2_matrix_s *>(handle);
             snprintf(buf, sizeof buf,

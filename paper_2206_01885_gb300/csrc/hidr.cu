@@ -926,6 +926,204 @@ __global__ void __launch_bounds__(DR_THREADS, 5) k_datareduct(const int64_t *tof
     if (threadIdx.x == 0) outcnt[node] = m;
 }
 
+// Surface-based DataReduct (section 3.3): the reference set is ne points on
+// each of three ellipsoids centred at the centre c of the set's box [l, u],
+// semi-axes gamma (u - l) for gamma = 0.3, 0.6, 1.2 (q = c + (gamma (u - l)) *
+// dir_j per coordinate, each operation explicitly rounded in that order; the
+// unit directions dir_j come precomputed from the host); every reference point
+// takes its nearest point of the set (float64 squared distance, ties to the
+// smaller label), the winners deduplicated and sorted.  The search is the
+// brute-force sweep of k_datareduct with float32 top-two distances and a
+// float64 re-scan on near ties; the reference points reach 1.7 box widths from
+// the corner, so M takes twice the box's extent.
+constexpr int DS_THREADS = 256;
+constexpr int DS_QPT = 4;
+
+__global__ void __launch_bounds__(DS_THREADS)
+    k_datareduct_surface(const int64_t *toff, const int32_t *tdata, int g, int d, DRPoints PT, const double *dirs,
+                         int ne, int32_t *const *outptr, int32_t *outcnt, int lb, const long long *tbox,
+                         long long *outbox) {
+    const double *x0 = PT.x[0], *x1 = PT.x[1], *x2 = PT.x[2];
+    extern __shared__ unsigned char smem_raw[];
+    int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
+    __shared__ int32_t tid_s[DR_TILE];
+    __shared__ float tf_s[3][DR_TILE];
+    __shared__ int scratch[33];
+    const int a = blockIdx.x;
+    const int node = lb + a;
+    const int64_t t0 = toff[a], nt = toff[a + 1] - toff[a];
+    const int32_t *T = tdata + t0;
+    int32_t *out = outptr[node];
+    int G = 1;
+    for (int k = 0; k < d; k++) G *= g;
+    if (nt <= G) {  // DataReduct returns S itself
+        int P = 1;
+        while (P < nt) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) win[i] = i < nt ? T[i] : INT_MAX;
+        __syncthreads();
+        block_bitonic_sort(win, P);
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) out[i] = win[i];
+        if (threadIdx.x < 6) outbox[6 * (int64_t)node + threadIdx.x] = tbox[6 * (int64_t)a + threadIdx.x];
+        if (threadIdx.x == 0) outcnt[node] = (int32_t)nt;
+        return;
+    }
+    const int NQ = 3 * ne;
+    double l[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0}, w[3] = {0.0, 0.0, 0.0};
+    float lh[3] = {0.f, 0.f, 0.f}, ll[3] = {0.f, 0.f, 0.f};
+    double W = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (k >= d) break;
+        l[k] = dkey_inv(tbox[6 * (int64_t)a + k]);
+        const double u = dkey_inv(tbox[6 * (int64_t)a + 3 + k]);
+        c[k] = __dmul_rn(__dadd_rn(l[k], u), 0.5);
+        w[k] = __dsub_rn(u, l[k]);
+        W = dmax_(W, w[k]);
+        const double Lk = l[k] - PT.ref[k];
+        lh[k] = (float)Lk;
+        ll[k] = (float)(Lk - (double)lh[k]);
+    }
+    const double E = 2.0 * W;
+    const float M = (float)(8e-6 * E * E + 1e-12 * E * PT.R);
+    auto refpt = [&](int qi, double *q) {
+        const int e = qi / ne, j = qi - e * ne;
+        const double ge = e == 0 ? 0.3 : (e == 1 ? 0.6 : 1.2);
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            q[k] = k < d ? __dadd_rn(c[k], __dmul_rn(__dmul_rn(ge, w[k]), dirs[3 * j + k])) : 0.0;
+    };
+    for (int qbase = 0; qbase < NQ; qbase += DS_THREADS * DS_QPT) {
+        float qf[DS_QPT][3], b1[DS_QPT], b2[DS_QPT];
+        int32_t i1[DS_QPT];
+#pragma unroll
+        for (int j = 0; j < DS_QPT; j++) {
+            const int qi = qbase + j * DS_THREADS + threadIdx.x;
+            double q[3] = {0.0, 0.0, 0.0};
+            if (qi < NQ) refpt(qi, q);
+#pragma unroll
+            for (int k = 0; k < 3; k++) qf[j][k] = k < d ? (float)__dsub_rn(q[k], l[k]) : 0.0f;
+            b1[j] = INFINITY;
+            b2[j] = INFINITY;
+            i1[j] = INT_MAX;
+        }
+        for (int64_t tb = 0; tb < nt; tb += DR_TILE) {
+            const int cnt = (int)(nt - tb < DR_TILE ? nt - tb : DR_TILE);
+            __syncthreads();
+            for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+                const int32_t sid = T[tb + r];
+                tid_s[r] = sid;
+#pragma unroll
+                for (int k = 0; k < 3; k++) tf_s[k][r] = k < d ? dr_offset(PT.xq, sid, k, lh[k], ll[k]) : 0.f;
+            }
+            __syncthreads();
+            for (int r = 0; r < cnt; r++) {
+                const float f0 = tf_s[0][r], f1 = tf_s[1][r], f2 = tf_s[2][r];
+#pragma unroll
+                for (int j = 0; j < DS_QPT; j++) {
+                    const float e0 = f0 - qf[j][0], e1 = f1 - qf[j][1], e2 = f2 - qf[j][2];
+                    const float d32 = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
+                    if (d32 < b2[j]) {
+                        if (d32 < b1[j]) {
+                            b2[j] = b1[j];
+                            b1[j] = d32;
+                            i1[j] = tid_s[r];
+                        } else {
+                            b2[j] = d32;
+                        }
+                    }
+                }
+            }
+        }
+        // near ties: every point within M of the smallest, in float64
+#pragma unroll
+        for (int j = 0; j < DS_QPT; j++) {
+            const int qi = qbase + j * DS_THREADS + threadIdx.x;
+            const float limx = b1[j] + M;
+            const bool need = qi < NQ && !(b2[j] > limx);
+            if (!__syncthreads_or(need)) continue;
+            double q[3] = {0.0, 0.0, 0.0};
+            if (qi < NQ) refpt(qi, q);
+            long long bk = LLONG_MAX;
+            int32_t bl = INT_MAX;
+            for (int64_t tb = 0; tb < nt; tb += DR_TILE) {
+                const int cnt = (int)(nt - tb < DR_TILE ? nt - tb : DR_TILE);
+                __syncthreads();
+                for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+                    const int32_t sid = T[tb + r];
+                    tid_s[r] = sid;
+#pragma unroll
+                    for (int k = 0; k < 3; k++) tf_s[k][r] = k < d ? dr_offset(PT.xq, sid, k, lh[k], ll[k]) : 0.f;
+                }
+                __syncthreads();
+                if (need)
+                    for (int r = 0; r < cnt; r++) {
+                        const float e0 = tf_s[0][r] - qf[j][0], e1 = tf_s[1][r] - qf[j][1], e2 = tf_s[2][r] - qf[j][2];
+                        if (fmaf(e2, e2, fmaf(e1, e1, e0 * e0)) <= limx) {
+                            const int32_t sid = tid_s[r];
+                            const long long kk = __double_as_longlong(
+                                h2_dist2(d, x0[sid], d > 1 ? x1[sid] : 0.0, d > 2 ? x2[sid] : 0.0, q[0], q[1], q[2]));
+                            if (kk < bk || (kk == bk && sid < bl)) {
+                                bk = kk;
+                                bl = sid;
+                            }
+                        }
+                    }
+            }
+            if (need) i1[j] = bl;
+        }
+#pragma unroll
+        for (int j = 0; j < DS_QPT; j++) {
+            const int qi = qbase + j * DS_THREADS + threadIdx.x;
+            if (qi < NQ) win[qi] = i1[j];
+        }
+    }
+    __syncthreads();
+    {  // bounding box of the winners
+        long long blo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, bhi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+        for (int qi = threadIdx.x; qi < NQ; qi += blockDim.x) {
+            const int32_t sid = win[qi];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k >= d) break;
+                const long long kv = dkey((k == 0 ? x0 : (k == 1 ? x1 : x2))[sid]);
+                blo[k] = min(blo[k], kv);
+                bhi[k] = max(bhi[k], kv);
+            }
+        }
+        block_box_write(blo, bhi, outbox + 6 * (int64_t)node);
+    }
+    int P = 1;
+    while (P < NQ) P <<= 1;
+    for (int i = NQ + threadIdx.x; i < P; i += blockDim.x) win[i] = INT_MAX;
+    __syncthreads();
+    block_bitonic_sort(win, P);
+    int m = block_unique_write(win, P, out, scratch);
+    if (threadIdx.x == 0) outcnt[node] = m;
+}
+
+// unit directions of the surface reference points: the Fibonacci lattice in
+// 3D (z_j = 1 - (2j + 1) / ne, rho = sqrt(1 - z^2), phi_j = j pi (3 - sqrt 5)),
+// equal angles 2 pi (j + 1/2) / ne in 2D; host arithmetic without contraction
+std::vector<double> surface_dirs(int d, int ne) {
+    const double pi = 3.14159265358979323846;
+    std::vector<double> v((size_t)3 * std::max(ne, 1), 0.0);
+    for (int j = 0; j < ne; j++) {
+        if (d == 3) {
+            const double z = 1.0 - (2.0 * j + 1.0) / ne;
+            const double rho = std::sqrt(1.0 - z * z);
+            const double phi = j * (pi * (3.0 - std::sqrt(5.0)));
+            v[3 * j] = rho * std::cos(phi);
+            v[3 * j + 1] = rho * std::sin(phi);
+            v[3 * j + 2] = z;
+        } else {
+            const double th = 2.0 * pi * (j + 0.5) / ne;
+            v[3 * j] = std::cos(th);
+            v[3 * j + 1] = std::sin(th);
+        }
+    }
+    return v;
+}
+
 int64_t gridsize(int g, int d) {
     int64_t G = 1;
     for (int k = 0; k < d; k++) G *= g;
@@ -934,9 +1132,28 @@ int64_t gridsize(int g, int d) {
 
 void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, int nl, int g, int d,
                        const DRPoints &pts, int32_t *const *outptr, int32_t *outcnt, int lb, const long long *tbox,
-                       long long *outbox, cudaStream_t s) {
+                       long long *outbox, cudaStream_t s, int method = 0) {
     if (nl <= 0) return;
     int G = (int)gridsize(g, d);
+    if (method == 1) {  // surface-based
+        static std::once_flag sattr;
+        std::call_once(sattr, [] {
+            H2_CUDA(cudaFuncSetAttribute(k_datareduct_surface, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(DR_MAX_GRID * sizeof(int32_t))));
+        });
+        const int ne = d >= 2 ? G / 3 : 0;
+        const std::vector<double> hd = surface_dirs(d, ne);
+        DevBuf<double> dirs;
+        dirs.alloc(hd.size(), s);
+        H2_CUDA(cudaMemcpyAsync(dirs.p, hd.data(), hd.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        int P = 1;
+        while (P < G) P <<= 1;
+        ProfScope ps(KT_DATAREDUCT, s);
+        k_datareduct_surface<<<nl, DS_THREADS, (size_t)P * sizeof(int32_t), s>>>(toff, tdata, g, d, pts, dirs.p, ne,
+                                                                                 outptr, outcnt, lb, tbox, outbox);
+        H2_LAUNCH("k_datareduct_surface");  // (a pageable-source copy has read hd when it returns)
+        return;
+    }
     size_t sm = dr_smem_bytes(G);
     static std::once_flag attr;
     std::call_once(attr, [] {
@@ -1009,7 +1226,8 @@ void hidr_impl(h2_hidr_s *h) {
         k_gather_up<<<nl, 256, 0, s>>>(lb, t->nchild.p, t->fchild.p, t->begin.p, t->end.p, h->xptr.p, h->xcnt.p,
                                        toff.p, tdata.p, t->xs[0].p, t->xs[1].p, t->xs[2].p, d, h->xbox.p, tbox.p);
         H2_LAUNCH("k_gather_up");
-        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g1, d, pts, h->xptr.p, h->xcnt.p, lb, tbox.p, h->xbox.p, s);
+        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g1, d, pts, h->xptr.p, h->xcnt.p, lb, tbox.p, h->xbox.p, s,
+                          h->method);
         h->xtotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e1, s));
@@ -1034,7 +1252,8 @@ void hidr_impl(h2_hidr_s *h) {
         k_gather_down<<<nl, GD_THREADS, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->xptr.p, h->xcnt.p,
                                          h->yptr.p, h->ycnt.p, toff.p, tdata.p, h->xbox.p, h->ybox.p, tbox.p);
         H2_LAUNCH("k_gather_down");
-        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, pts, h->yptr.p, h->ycnt.p, lb, tbox.p, h->ybox.p, s);
+        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, pts, h->yptr.p, h->ycnt.p, lb, tbox.p, h->ybox.p, s,
+                          h->method);
         h->ytotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e2, s));

@@ -18,6 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libh2gb300.so")
 
+DR_METHODS = {"volume": 0, "surface": 1}
 KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4, "bump": 5, "power": 6,
            "cosdot": 7}
 PRECISIONS = {"fp64": 0, "mixed": 1}
@@ -64,6 +65,7 @@ def lib():
             "h2_hidr_reduce": [vp, i32, i32, vp, C.POINTER(vp)],
             "h2_hidr_get": [vp, i32, vp, vp, i64, C.POINTER(i64)],
             "h2_construct": [vp, vp, i32, vp, dbl, i32, vp, C.POINTER(vp)],
+            "h2_hidr_reduce_ex": [vp, i32, i32, i32, vp, C.POINTER(vp)],
             "h2_construct_ex": [vp, vp, i32, vp, dbl, i32, C.POINTER(_ConstructOpts), vp, C.POINTER(vp)],
             "h2_autotune_leaf": [vp, i64, i32, i32, vp, i32, i32, i32, vp, dbl, i32, i32, vp, C.POINTER(i32), vp],
             "h2_matrix_get": [vp, i32, vp, i64, C.POINTER(i64)],
@@ -180,9 +182,11 @@ class Tree(_Handle):
 class Hidr(_Handle):
     """h2_hidr_reduce: X_i*, Y_i* of Algorithm 1."""
 
-    def __init__(self, tree: Tree, g1: int, g2: int, stream=None):
+    def __init__(self, tree: Tree, g1: int, g2: int, stream=None, method: str = "volume"):
+        """method: the DataReduct of section 3.3, "volume" or "surface"."""
         h = C.c_void_p()
-        _check("h2_hidr_reduce", lib().h2_hidr_reduce(tree.handle, int(g1), int(g2), _stream(stream), C.byref(h)))
+        _check("h2_hidr_reduce_ex", lib().h2_hidr_reduce_ex(tree.handle, int(g1), int(g2), DR_METHODS[method],
+                                                             _stream(stream), C.byref(h)))
         self._h = h.value
         self.tree = tree
 

@@ -111,6 +111,42 @@ def test_hidr_bit_exact(H2, name, d, n, q, g1, g2):
             assert np.array_equal(got, want), (which, i)
 
 
+SURFACE_CASES = [("cube3d", 3, 6000, 60, 4, 5), ("gmix2d", 2, 8000, 30, 6, 7), ("cube3d_big", 3, 40000, 64, 5, 6),
+                 ("lattice3d", 3, 20000, 32, 4, 4), ("plane3d", 3, 20000, 64, 4, 5), ("same3d", 3, 3400, 64, 3, 3)]
+
+
+@pytest.mark.parametrize("name,d,n,q,g1,g2", SURFACE_CASES, ids=[c[0] for c in SURFACE_CASES])
+def test_hidr_surface_bit_exact(H2, name, d, n, q, g1, g2):
+    """The surface-based DataReduct (section 3.3) through HiDR: X_i*, Y_i*
+    bit-exact against the oracle's."""
+    pts = _hidr_points(name, d, n)
+    t = H2.Tree(dev(pts), q)
+    h = H2.Hidr(t, g1, g2, method="surface")
+    assert json.loads(h.stats())["method"] == "surface"
+    o = O.tree_build(pts, q)
+    oh = O.Hidr(o, g1, g2, method="surface")
+    for which in ["x", "y"]:
+        cnt, data = h.get(which)
+        off = np.concatenate([[0], np.cumsum(cnt)])
+        for i in range(1, t.nnodes):
+            assert np.array_equal(data[off[i]:off[i + 1]], oh.get(i, which)), (which, i)
+
+
+def test_surface_reduction_builds_accurate_h2(H2):
+    n, q, g, eps = 6000, 100, 7, 1e-6
+    pts = I.uniform_cube(n, 3, seed=53)
+    z = I.standard_normal(n, seed=51)
+    t = H2.Tree(dev(pts), q)
+    h = H2.Hidr(t, g, g, method="surface")
+    A = H2.H2Matrix(t, h, "coulomb", (), eps, "fp64")
+    y = A.matvec(dev(z)).cpu().numpy()
+    o = O.tree_build(pts, q)
+    yo = O.H2(o, O.Hidr(o, g, g, method="surface"), "coulomb", (), eps).matvec(z)
+    assert np.linalg.norm(y - yo) <= 1e-12 * np.linalg.norm(yo)
+    yd = O.dense_matvec(pts, "coulomb", (), z)
+    assert np.linalg.norm(y - yd) <= 10 * eps * np.linalg.norm(yd)
+
+
 def _node_cands(o, H, i):
     if o.nchild[i] == 0:
         return np.arange(o.begin[i], o.end[i])

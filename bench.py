@@ -50,18 +50,50 @@ WORKLOADS = {
                              rows=1000, points="spheres3", compare="spheres3_1m_mixed"),
     "spheres3_1m_mixed": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-5, prec="mixed", seed=6,
                               rows=1000, points="spheres3"),
+    # 2D mixture of 16 Gaussians, Gaussian kernel exp(-r^2/0.04); g fixed (the
+    # unit-cell calibration sets sit where this kernel is ~e^-100)
+    "gmix2m_fp64": dict(n=1 << 21, d=2, kernel="gaussian", kparams=(0.2,), q=128, eps=1e-10, prec="fp64", seed=3,
+                        rows=1000, points="gmix2d", g=20, compare="gmix2m_mixed"),
+    "gmix2m_mixed": dict(n=1 << 21, d=2, kernel="gaussian", kparams=(0.2,), q=128, eps=1e-6, prec="mixed", seed=3,
+                         rows=1000, points="gmix2d", g=20),
+    # 8,388,608 points on the unit sphere, 16 float32 right-hand sides (the
+    # sampled error is taken on the first column)
+    "sphere8m_mixed16": dict(n=1 << 23, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-6, prec="mixed", seed=5,
+                             rows=2000, points="sphere", g=8, rhs=16),
 }
 
 
+POINT_NAMES = {"spheres3": "three unit spheres", "gmix2d": "2D mixture of 16 Gaussians",
+               "sphere": "unit sphere surface"}
+
+
 def points_name(wl):
-    return "three unit spheres" if wl.get("points") == "spheres3" else "uniform cube"
+    return POINT_NAMES.get(wl.get("points"), "uniform cube")
 
 
 def workload_points(wl, n, seed):
     """The workload's point distribution (uniform cube unless it names another)."""
-    if wl.get("points") == "spheres3":
+    kind = wl.get("points")
+    if kind == "spheres3":
         return I.three_spheres(n, seed=seed)
+    if kind == "gmix2d":
+        return I.gaussian_mixture(n, seed=seed)
+    if kind == "sphere":
+        return I.sphere_surface(n, seed=seed)
     return I.uniform_cube(n, wl["d"], seed=seed)
+
+
+def workload_rhs(wl, n, seed):
+    """(right-hand side given to the matvec, its first column in float64 for
+    the exact rows): one float64 vector, or rhs float32 columns"""
+    R = wl.get("rhs", 1)
+    if R == 1:
+        z = I.standard_normal(n, seed=seed)
+        return z, z
+    Z = I.standard_normal(n * R, seed=seed).reshape(n, R).astype(np.float32)
+    return Z, np.ascontiguousarray(Z[:, 0], dtype=np.float64)
+
+
 # same-size unit cells at integer offset v are well separated under eq. (1)
 # with tau = 7/10 when |v|^2 >= 8 (3D) / 5 (2D)
 MIN_SQ = {3: 8, 2: 5}
@@ -175,19 +207,24 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
     n, d = wl["n"], wl["d"]
     seed = problem_seed(wl["seed"], rank)  # independent problem per rank
     pts = workload_points(wl, n, seed)
-    z = I.standard_normal(n, seed=seed + 7)
+    R = wl.get("rhs", 1)
+    zm, z = workload_rhs(wl, n, seed + 7)  # matvec input; its first column (float64) for the exact rows
     rows = I.sample_rows(n, wl["rows"], seed=seed + 9)
     pts_d = torch.from_numpy(pts).to(dev)
-    z_d = torch.from_numpy(z).to(dev)
+    zm_d = torch.from_numpy(zm).to(dev)
+    z_d = zm_d if R == 1 else torch.from_numpy(z).to(dev)
     rows_d = torch.from_numpy(rows).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
 
     # r1 = r2 = g^d from epsilon (Algorithm 2 step 2), data-independent
     t0 = time.perf_counter()
-    z1, z2 = I.calibration_sets(d, MIN_SQ[d])
-    g, cal_err = h2.calibrate(d, wl["kernel"], wl["kparams"], wl["eps"], z1, z2, gmax=16)
+    if "g" in wl:  # fixed by the workload
+        g, cal_err = wl["g"], None
+    else:
+        z1, z2 = I.calibration_sets(d, MIN_SQ[d])
+        g, cal_err = h2.calibrate(d, wl["kernel"], wl["kparams"], wl["eps"], z1, z2, gmax=16)
     cal_ms = (time.perf_counter() - t0) * 1e3
-    if g > 16:
+    if g > 16 and "g" not in wl:
         raise RuntimeError(f"calibration did not converge for eps={wl['eps']}")
 
     # the path runs on a high-priority stream; the exact rows (side stream, low
@@ -199,7 +236,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
     prev_stream = torch.cuda.current_stream()
     torch.cuda.set_stream(stream)
 
-    def step(p_in, z_in, rows_in):
+    def step(p_in, zm_in, z_in, rows_in):
         # the exact rows need only the tree and z: they run on a second stream
         # while HiDR, construction and the matvec run on the first
         t = h2.Tree(p_in, wl["q"])
@@ -208,15 +245,15 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
             ex = h2.exact_rows(t, wl["kernel"], wl["kparams"], z_in, rows_in, stream=side)
         hd = h2.Hidr(t, g, g)
         A = h2.H2Matrix(t, hd, wl["kernel"], wl["kparams"], wl["eps"], wl["prec"])
-        y = A.matvec(z_in)
+        y = A.matvec(zm_in)
         stream.wait_stream(side)
         ex.record_stream(stream)
-        err = h2.sampled_error(ex, y, rows_in)
+        err = h2.sampled_error(ex, y if R == 1 else y[:, 0].double().contiguous(), rows_in)
         info = (json.loads(t.stats()), json.loads(hd.stats()), json.loads(A.stats()))
         return t, hd, A, y, err, info
 
     for _ in range(args.warmup):
-        out = step(pts_d, z_d, rows_d)
+        out = step(pts_d, zm_d, z_d, rows_d)
         del out
     torch.cuda.synchronize()
     last = None
@@ -233,7 +270,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        t, hd, A, y, err, info = step(pts_d, z_d, rows_d)
+        t, hd, A, y, err, info = step(pts_d, zm_d, z_d, rows_d)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -326,7 +363,8 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
     e2e = None
     if with_e2e:  # end to end through host buffers (pinned), copies inside the timed region
         pts_h = torch.from_numpy(pts).pin_memory()
-        z_h = torch.from_numpy(z).pin_memory()
+        zm_h = torch.from_numpy(zm).pin_memory()
+        z_h = zm_h if R == 1 else torch.from_numpy(z).pin_memory()
         rows_h = torch.from_numpy(rows)
         e2e_ms = []
         for _ in range(max(1, min(args.steps, 2))):
@@ -343,17 +381,22 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
             job.start()
             hd2 = h2.Hidr(t2, g, g)
             A2 = h2.H2Matrix(t2, hd2, wl["kernel"], wl["kparams"], wl["eps"], wl["prec"])
-            y_h = A2.matvec(z_h.numpy())
+            y_h = A2.matvec(zm_h.numpy())
             job.join()
-            err_h = h2.sampled_error(ex_box["ex"], y_h, rows_h.numpy())
+            err_h = h2.sampled_error(ex_box["ex"], y_h if R == 1 else np.ascontiguousarray(y_h[:, 0], np.float64),
+                                     rows_h.numpy())
             torch.cuda.synchronize()
             e2e_ms.append((time.perf_counter() - w0) * 1e3)
             A2.free()
             hd2.free()
             t2.free()
         r = len(rows)
+        # in: points, z of the exact rows, the matvec input, the float64 product
+        # column and the rows (twice) and exact sums of the error; out: the
+        # product, the exact sums and the error
         e2e = {"value": world * n / (statistics.median(e2e_ms) * 1e-3), "unit": "points/s",
-               "h2d_bytes_per_step": 8 * (d * n + n + n + r + n + r + r), "d2h_bytes_per_step": 8 * (n + r + 1),
+               "h2d_bytes_per_step": 8 * d * n + z.nbytes + zm.nbytes + 8 * (n + r + r + r),
+               "d2h_bytes_per_step": zm.nbytes + 8 * (r + 1),
                "ms_per_step": statistics.median(e2e_ms), "rel_err": err_h}
 
     torch.cuda.synchronize()
@@ -371,7 +414,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
         "ms_per_step": ms_per_step,
         "config": {"workload": args.workload if wl is WORKLOADS[args.workload] else wl["name"], "n": n, "dim": d,
                    "kernel": wl["kernel"], "leaf_size": wl["q"], "id_tol": wl["eps"], "precision": wl["prec"],
-                   "g": g, "r1": g ** d, "r2": g ** d, "tau": "7/10", "sampled_rows": len(rows), "rhs": 1,
+                   "g": g, "r1": g ** d, "r2": g ** d, "tau": "7/10", "sampled_rows": len(rows), "rhs": R,
                    "l2": "flushed (256 MB write) between timed steps, outside the timed interval",
                    "parallelism": f"{world} independent problem(s), one per GPU"},
         "rel_err": last_err,
@@ -396,11 +439,13 @@ def gpu_arm(args, wl, rank, world, dev):
     B.build()
     torch.cuda.set_device(dev)
     prim = measure_form(args, wl, rank, world, dev, with_e2e=True)
+    R = wl.get("rhs", 1)
     result = {
         "metric": METRIC, "value": prim["value"], "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": prim["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if wl["prec"] == "fp64" else "f32+f64",
-        "data": f"synthetic (seeded {points_name(wl)}, standard-normal right-hand side)",
+        "data": f"synthetic (seeded {points_name(wl)}, "
+                + ("standard-normal right-hand side)" if R == 1 else f"{R} float32 standard-normal right-hand sides)"),
     }
     result.update({k: v for k, v in prim.items() if k not in ("value", "ms_per_step")})
     other = wl.get("compare")
@@ -435,6 +480,8 @@ def oracle_sample(wl, n_s):
 
 
 def oracle_g(wl):
+    if "g" in wl:  # fixed by the workload
+        return wl["g"]
     from oracle import h2_oracle as O
     z1, z2 = I.calibration_sets(wl["d"], MIN_SQ[wl["d"]])
     return O.calibrate(wl["d"], wl["kernel"], wl["kparams"], wl["eps"], z1, z2, gmax=16)

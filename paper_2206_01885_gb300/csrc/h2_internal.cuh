@@ -322,17 +322,31 @@ __device__ __forceinline__ double h2_rsqrt64(double r2) {
     return fma(y0 * e, p, y0);
 }
 
-__device__ __forceinline__ double h2_kappa_fast(int kid, double kp0, double r2) {
+// p: the kernel parameter in the form h2_kappa_param gives (a reciprocal
+// formed once per launch instead of a float64 division per evaluation)
+__device__ __forceinline__ double h2_kappa_fast(int kid, double p, double r2) {
     switch (kid) {
     case H2_K_COULOMB: return h2_rsqrt64(r2);
-    case H2_K_GAUSSIAN: return exp(-r2 / (kp0 * kp0));
-    case H2_K_EXPONENTIAL: return exp(-sqrt(r2) / kp0);
+    case H2_K_GAUSSIAN: return exp(-r2 * p);
+    case H2_K_EXPONENTIAL: return exp(-sqrt(r2) * p);
     case H2_K_MULTIQUADRIC: return sqrt(1.0 + r2);
     case H2_K_BUMP: {
-        const double t = kp0 * r2;
+        const double t = p * r2;
         return t < 1.0 ? exp(-1.0 / (1.0 - t)) : 0.0;
     }
-    case H2_K_POWER: return r2 > 0.0 ? pow(r2, 0.5 * kp0) : 0.0;
+    case H2_K_POWER: return r2 > 0.0 ? pow(r2, p) : 0.0;
+    default: return 0.0;
+    }
+}
+
+// kparams[0] in the form the fast kernels take: 1/h^2 (Gaussian), 1/l
+// (exponential), a (bump), p/2 (power), unused otherwise
+inline double h2_kappa_param(int kid, double kp0) {
+    switch (kid) {
+    case H2_K_GAUSSIAN: return 1.0 / (kp0 * kp0);
+    case H2_K_EXPONENTIAL: return 1.0 / kp0;
+    case H2_K_BUMP: return kp0;
+    case H2_K_POWER: return 0.5 * kp0;
     default: return 0.0;
     }
 }
@@ -354,12 +368,13 @@ __device__ __forceinline__ double h2_kxy(int kid, double kp0, int d, double a0, 
     return h2_kappa(kid, kp0, h2_dist2(d, a0, a1, a2, b0, b1, b2));
 }
 
-// the same in the fast forms of h2_kappa_fast (contracted arithmetic)
-__device__ __forceinline__ double h2_kxy_fast(int kid, double kp0, double a0, double a1, double a2, double b0,
+// the same in the fast forms of h2_kappa_fast (contracted arithmetic; p as
+// h2_kappa_param gives it)
+__device__ __forceinline__ double h2_kxy_fast(int kid, double p, double a0, double a1, double a2, double b0,
                                               double b1, double b2) {
     if (kid == H2_K_COSDOT) return cos(a0 * b0 + a1 * b1 + a2 * b2);
     const double dx = a0 - b0, dy = a1 - b1, dz = a2 - b2;
-    return h2_kappa_fast(kid, kp0, dx * dx + dy * dy + dz * dz);
+    return h2_kappa_fast(kid, p, dx * dx + dy * dy + dz * dz);
 }
 
 // float32 kappa for the mixed-precision path

@@ -111,15 +111,7 @@ __device__ __forceinline__ float kap(float r2, float p) {
     } else return sqrtf(1.0f + r2);
 }
 // the kernel parameter in the form kap takes
-inline double kap_param(int kid, double kp0) {
-    switch (kid) {
-    case H2_K_GAUSSIAN: return 1.0 / (kp0 * kp0);
-    case H2_K_EXPONENTIAL: return 1.0 / kp0;
-    case H2_K_BUMP: return kp0;
-    case H2_K_POWER: return 0.5 * kp0;
-    default: return 0.0;
-    }
-}
+inline double kap_param(int kid, double kp0) { return h2_kappa_param(kid, kp0); }
 // kappa for point pairs known to be distinct (r2 > 0): Coulomb skips the
 // r2 = 0 test
 template <int KID, class Real>
@@ -149,10 +141,11 @@ __device__ __forceinline__ Real kap_pt(Real t0, Real t1, Real t2, Real s0, Real 
     }
 }
 
-// out[r] = sum_q kappa(x_s, x_q) z_q for s = rows[r]; one CTA per row
+// out[r] = sum_q kappa(x_s, x_q) z_q for s = rows[r]; one CTA per row (kpar:
+// the kernel parameter as h2_kappa_param gives it)
 __global__ void k_exact_rows(const int64_t *rows, int64_t nrows, const int32_t *iperm, const double *x0,
                              const double *x1, const double *x2, const double *zm, int64_t n, int d, int kid,
-                             double kp0, double *out) {
+                             double kpar, double *out) {
     __shared__ double red[32];
     int64_t r = blockIdx.x;
     if (r >= nrows) return;
@@ -165,7 +158,7 @@ __global__ void k_exact_rows(const int64_t *rows, int64_t nrows, const int32_t *
     double a0 = x0[p], a1 = d > 1 ? x1[p] : 0.0, a2 = d > 2 ? x2[p] : 0.0;
     double s = 0.0;
     for (int64_t q = threadIdx.x; q < n; q += blockDim.x)
-        s += h2_kxy_fast(kid, kp0, a0, a1, a2, x0[q], d > 1 ? x1[q] : 0.0, d > 2 ? x2[q] : 0.0) * zm[q];
+        s += h2_kxy_fast(kid, kpar, a0, a1, a2, x0[q], d > 1 ? x1[q] : 0.0, d > 2 ? x2[q] : 0.0) * zm[q];
     s = warp_sum(s);
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = s;
@@ -185,7 +178,7 @@ constexpr int ER_THREADS = 256;
 
 __global__ void __launch_bounds__(ER_THREADS)
     k_exact_part(const int64_t *rows, int64_t nrows, const int32_t *iperm, const double *x0, const double *x1,
-                 const double *x2, const double *zm, int64_t n, int d, int kid, double kp0, int nch, double *part) {
+                 const double *x2, const double *zm, int64_t n, int d, int kid, double kpar, int nch, double *part) {
     __shared__ double red[ER_THREADS / 32];
     const int64_t r = blockIdx.y;
     const int c = blockIdx.x;
@@ -199,7 +192,7 @@ __global__ void __launch_bounds__(ER_THREADS)
     const int64_t q0 = (int64_t)c * ER_CHUNK, q1 = min(n, q0 + ER_CHUNK);
     double s = 0.0;
     for (int64_t q = q0 + threadIdx.x; q < q1; q += ER_THREADS)
-        s += h2_kxy_fast(kid, kp0, a0, a1, a2, x0[q], d > 1 ? x1[q] : 0.0, d > 2 ? x2[q] : 0.0) * zm[q];
+        s += h2_kxy_fast(kid, kpar, a0, a1, a2, x0[q], d > 1 ? x1[q] : 0.0, d > 2 ? x2[q] : 0.0) * zm[q];
     s = warp_sum(s);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = s;
@@ -862,8 +855,8 @@ void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z, c
         for (int64_t r0 = 0; r0 < nrows; r0 += rb) {
             const int64_t nr = std::min<int64_t>(rb, nrows - r0);
             k_exact_part<<<dim3((unsigned)nch, (unsigned)nr), ER_THREADS, 0, s>>>(
-                rows + r0, nr, t->iperm.p, t->xs[0].p, t->xs[1].p, t->xs[2].p, zm.p, n, t->d, kid, kp[0], nch,
-                part.p);
+                rows + r0, nr, t->iperm.p, t->xs[0].p, t->xs[1].p, t->xs[2].p, zm.p, n, t->d, kid,
+                h2_kappa_param(kid, kp[0]), nch, part.p);
             k_exact_sum<<<blocks_for(nr, 256), 256, 0, s>>>(part.p, nr, nch, out + r0);
             H2_LAUNCH("k_exact_part");
         }
@@ -906,7 +899,7 @@ void exact_rows_noalloc_impl(h2_tree_s *t, int kid, const double *kp, const doub
     H2_LAUNCH("k_perm_in (noalloc)");
     if (nrows > 0) {
         k_exact_rows<<<(unsigned)nrows, 512, 0, s>>>(rows, nrows, t->iperm.p, t->xs[0].p, t->xs[1].p, t->xs[2].p,
-                                                     zm, n, t->d, kid, kp[0], out);
+                                                     zm, n, t->d, kid, h2_kappa_param(kid, kp[0]), out);
         H2_LAUNCH("k_exact_rows (noalloc)");
     }
 }

@@ -339,13 +339,13 @@ h2_status h2_free(void *handle);
 const char *h2_last_error(void);
 
 /* JSON object with counters and per-phase device times (ms) of a tree, hidr
- * or matrix handle, written to json (cap bytes, NUL-terminated).  A matrix
- * reports, among others, its total and largest rank, QR flops and g_max, the
- * largest |G| entry of the interpolation matrices U_i = P [I; G] (the quantity
- * strong RRQR, which the paper names, would bound; the build pivots by column
- * norms and reports it instead).  With
- * handle == NULL: the per-kernel totals {"name": {"ms", "launches"}} collected
- * while profiling is enabled. */
+ * or matrix handle, written to json (cap bytes, NUL-terminated).  A hidr
+ * reports its DataReduct "method" ("volume" or "surface").  A matrix reports,
+ * among others, its total and largest rank, QR flops and g_max, the largest
+ * |G| entry of the interpolation matrices U_i = P [I; G] (the quantity strong
+ * RRQR, which the paper names, bounds), and "g_bound" and "exchanges" of
+ * h2_construct_ex (0 for h2_construct).  With handle == NULL: the per-kernel
+ * totals {"name": {"ms", "launches"}} collected while profiling is enabled. */
 h2_status h2_get_stats(const void *handle, char *json, int64_t cap);
 
 /* Per-kernel timing: when enabled, the main kernels are bracketed by CUDA

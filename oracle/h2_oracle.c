@@ -474,8 +474,49 @@ i64 or_datareduct_surface(const double *xs, int d, const i64 *S, i64 ns, int g, 
     return w;
 }
 
-/* the DataReduct of HiDR: method 0 volume-based, 1 surface-based */
+/* DataReduct by farthest point sampling (section 3.3): X* starts with the
+ * point of S of smallest label and grows by the point of S farthest from X*
+ * (largest float64 squared distance to its nearest member of X*, ties to the
+ * smaller label) until it holds g^d points; returned sorted.  The paper leaves
+ * the first point open; the smallest label is this build's reading.  |S| <= g^d
+ * returns S. */
+i64 or_datareduct_fps(const double *xs, int d, const i64 *S, i64 ns, int g, i64 *out) {
+    i64 r = ipow(g, d);
+    if (ns <= r) {
+        memcpy(out, S, sizeof(i64) * ns);
+        qsort(out, ns, sizeof(i64), cmp_i64);
+        return ns;
+    }
+    double *md = malloc(sizeof(double) * ns);      /* squared distance to X* */
+    unsigned char *in = calloc((size_t)ns, 1);      /* member of X* */
+    i64 f = 0;
+    for (i64 a = 0; a < ns; a++) {
+        md[a] = INFINITY;
+        if (S[a] < S[f]) f = a;
+    }
+    for (i64 m = 0; m < r; m++) {
+        out[m] = S[f];
+        in[f] = 1;
+        if (m + 1 == r) break;
+        i64 b = -1;
+        for (i64 a = 0; a < ns; a++) {
+            if (in[a]) continue;
+            double dd = dist2(xs + S[a] * d, xs + S[f] * d, d);
+            if (dd < md[a]) md[a] = dd;
+            if (b < 0 || md[a] > md[b] || (md[a] == md[b] && S[a] < S[b])) b = a;
+        }
+        f = b;
+    }
+    free(md);
+    free(in);
+    qsort(out, r, sizeof(i64), cmp_i64);
+    return r;
+}
+
+/* the DataReduct of HiDR: method 0 volume-based, 1 surface-based, 2 farthest
+ * point sampling */
 static i64 datareduct_m(int method, const double *xs, int d, const i64 *S, i64 ns, int g, i64 *out) {
+    if (method == 2) return or_datareduct_fps(xs, d, S, ns, g, out);
     return method == 1 ? or_datareduct_surface(xs, d, S, ns, g, out) : or_datareduct(xs, d, S, ns, g, out);
 }
 

@@ -59,6 +59,8 @@ def lib():
             L.or_datareduct.argtypes = [vp, i32, vp, i64, i32, vp]
             L.or_datareduct_surface.restype = i64
             L.or_datareduct_surface.argtypes = [vp, i32, vp, i64, i32, vp]
+            L.or_datareduct_fps.restype = i64
+            L.or_datareduct_fps.argtypes = [vp, i32, vp, i64, i32, vp]
             L.or_hidr.restype = vp
             L.or_hidr.argtypes = [vp, i32, i32, vp, i32]
             L.or_hidr_get.restype = i64
@@ -197,11 +199,11 @@ def tree_build(points: np.ndarray, leaf_size: int, tau=(7, 10)) -> Tree:
     return t
 
 
-DR_METHODS = {"volume": 0, "surface": 1}
+DR_METHODS = {"volume": 0, "surface": 1, "fps": 2}
 
 
 def datareduct(coords: np.ndarray, labels: np.ndarray, g: int, method: str = "volume") -> np.ndarray:
-    """DataReduct(S, g^d) (section 3.3, volume- or surface-based).  ``coords``
+    """DataReduct(S, g^d) (section 3.3: volume- or surface-based, or farthest point sampling).  ``coords``
     indexed by label; ``labels`` the members of S.  Returns the sorted reduced
     labels."""
     L = lib()
@@ -210,7 +212,7 @@ def datareduct(coords: np.ndarray, labels: np.ndarray, g: int, method: str = "vo
         xs = xs[:, None]
     S = np.ascontiguousarray(labels, dtype=np.int64)
     out = np.zeros(max(len(S), 1), dtype=np.int64)
-    f = L.or_datareduct_surface if DR_METHODS[method] == 1 else L.or_datareduct
+    f = {0: L.or_datareduct, 1: L.or_datareduct_surface, 2: L.or_datareduct_fps}[DR_METHODS[method]]
     m = f(_p(xs), xs.shape[1], _p(S), len(S), g, _p(out))
     return out[:m].copy()
 

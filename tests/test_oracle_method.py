@@ -67,7 +67,8 @@ def _farfield_points(t, i):
 
 
 @pytest.mark.parametrize("d,n,q,g,method", [(3, 3000, 30, 3, "volume"), (2, 2500, 20, 4, "volume"),
-                                            (3, 3000, 30, 3, "surface"), (2, 2500, 20, 4, "surface")])
+                                            (3, 3000, 30, 3, "surface"), (2, 2500, 20, 4, "surface"),
+                                            (3, 3000, 30, 3, "fps"), (2, 2500, 20, 4, "fps")])
 def test_hidr_invariants(d, n, q, g, method):
     pts = I.uniform_cube(n, d, seed=7 + d)
     t = O.tree_build(pts, q)
@@ -350,3 +351,30 @@ def test_surface_datareduct_finds_points_on_its_ellipsoids(d, g):
 def test_surface_datareduct_small_set_is_identity():
     X = I.uniform_cube(20, 3, seed=8)
     assert np.array_equal(O.datareduct(X, np.arange(20)[::-1].copy(), 3, "surface"), np.arange(20))
+
+
+# ------------------------------------------ farthest point sampling (section 3.3)
+def test_fps_worked_example():
+    """Points 0, 1, 2, 3, 10 on a line (labels in that order), g^2 = 4 picks:
+    0 (smallest label); 10 (farthest from {0}); 3 (squared distances 1, 4, 9 to
+    {0, 10}); then 1 and 2 tie at squared distance 1 and the smaller label, 1,
+    wins."""
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0], [3.0, 0.0], [10.0, 0.0]])
+    got = O.datareduct(X, np.array([4, 2, 0, 3, 1]), 2, "fps")
+    assert got.tolist() == [0, 1, 3, 4]
+
+
+@pytest.mark.parametrize("d,n,g", [(3, 700, 4), (2, 500, 6)])
+def test_fps_covering_radius_at_most_separation(d, n, g):
+    """FPS picks each point at the largest distance to the set so far, so every
+    point left out is no farther from the picked set than any two picked points
+    are from each other."""
+    X = I.uniform_cube(n, d, seed=17 + d)
+    got = O.datareduct(X, np.arange(n), g, "fps")
+    assert len(got) == g ** d and got[0] == 0 and np.all(np.diff(got) > 0)
+    P = X[got]
+    rest = np.setdiff1d(np.arange(n), got)
+    cover = np.sqrt(((X[rest][:, None, :] - P[None, :, :]) ** 2).sum(-1)).min(1).max()
+    D = np.sqrt(((P[:, None, :] - P[None, :, :]) ** 2).sum(-1))
+    np.fill_diagonal(D, np.inf)
+    assert cover <= D.min() * (1 + 1e-12)

@@ -162,7 +162,7 @@ h2_status h2_hidr_reduce(h2_tree t, int g1, int g2, void *stream, h2_hidr *out);
 /* DataReduct variants of section 3.3 for h2_hidr_reduce_ex */
 typedef enum {
     H2_DR_VOLUME = 0, /* h2_hidr_reduce's: nearest points to a g^d tensor grid */
-    H2_DR_SURFACE = 1 /* nearest points to floor(g^d / 3) reference points on
+    H2_DR_SURFACE = 1, /* nearest points to floor(g^d / 3) reference points on
                          each of three ellipsoids centred at the centre c of
                          the set's bounding box [l, u], semi-axes gamma (u - l)
                          for gamma = 0.3, 0.6, 1.2: q = c + (gamma (u - l)) *
@@ -171,6 +171,12 @@ typedef enum {
                          z_j^2), phi_j = j pi (3 - sqrt 5)) and the equal
                          angles 2 pi (j + 1/2) / ne in 2D; same nearest-point
                          rule, deduplicated and sorted                       */
+    H2_DR_FPS = 2     /* farthest point sampling: start at the smallest label,
+                         add the point farthest from the chosen ones (float64
+                         squared distance to the nearest of them, ties to the
+                         smaller label) until g^d are chosen; sequential by
+                         nature (g^d rounds over the set per node), so meant
+                         for small problems                                  */
 } h2_datareduct;
 
 /* h2_hidr_reduce with the DataReduct variant `method` (h2_datareduct).

@@ -203,7 +203,8 @@ h2_status h2_hidr_reduce_ex(h2_tree th, int g1, int g2, int method, void *stream
     return guard([&] {
         H2_REQUIRE(out != nullptr, "out is NULL");
         *out = nullptr;
-        H2_REQUIRE(method == H2_DR_VOLUME || method == H2_DR_SURFACE, "unknown DataReduct method");
+        H2_REQUIRE(method == H2_DR_VOLUME || method == H2_DR_SURFACE || method == H2_DR_FPS,
+                   "unknown DataReduct method");
         h2_tree_s *t = as_tree(th);
         H2_REQUIRE(g1 >= 1 && g2 >= 1, "g1 and g2 must be >= 1");
         auto *h = new h2_hidr_s();
@@ -650,7 +651,7 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
                      "{\"g1\": %d, \"g2\": %d, \"x_total\": %lld, \"y_total\": %lld, \"t_max_level\": %lld, "
                      "\"t_total\": %lld, \"ms_up\": %.4f, \"ms_down\": %.4f, \"method\": \"%s\"}",
                      h->g1, h->g2, (long long)h->xtotal, (long long)h->ytotal, (long long)h->tmax,
-                     (long long)h->ttotal, h->ms_up, h->ms_down, h->method == H2_DR_SURFACE ? "surface" : "volume");
+                     (long long)h->ttotal, h->ms_up, h->ms_down, h->method == H2_DR_SURFACE ? "surface" : (h->method == H2_DR_FPS ? "fps" : "volume"));
         } else if (tag == TAG_MATRIX) {
             auto *A = static_cast<const h2_matrix_s *>(handle);
             snprintf(buf, sizeof buf,

@@ -1101,6 +1101,131 @@ __global__ void __launch_bounds__(DS_THREADS)
     if (threadIdx.x == 0) outcnt[node] = m;
 }
 
+// DataReduct by farthest point sampling (section 3.3): X* starts with the
+// point of smallest label and grows by the point farthest from X* (largest
+// float64 squared distance to its nearest member, ties to the smaller label)
+// until it holds g^d points; sorted on output.  One CTA a node; md holds each
+// point's squared distance to X* (negative once the point is in X*).  g^d
+// rounds of a block-wide update and argmax over the set: exact, but costly on
+// large sets by its sequential nature.
+constexpr int FPS_THREADS = 512;
+
+__device__ __forceinline__ void fps_better(long long &k, int32_t &lab, int &pos, long long k2, int32_t lab2,
+                                           int pos2) {
+    if (k2 > k || (k2 == k && lab2 < lab)) { k = k2; lab = lab2; pos = pos2; }
+}
+
+__global__ void __launch_bounds__(FPS_THREADS)
+    k_datareduct_fps(const int64_t *toff, const int32_t *tdata, int g, int d, DRPoints PT, double *mdbase,
+                     int32_t *const *outptr, int32_t *outcnt, int lb, const long long *tbox, long long *outbox) {
+    const double *x0 = PT.x[0], *x1 = PT.x[1], *x2 = PT.x[2];
+    extern __shared__ unsigned char smem_raw[];
+    int32_t *win = reinterpret_cast<int32_t *>(smem_raw);  // [P]
+    __shared__ long long s_key[FPS_THREADS / 32];
+    __shared__ int32_t s_lab[FPS_THREADS / 32];
+    __shared__ int s_pos[FPS_THREADS / 32];
+    __shared__ int s_f;
+    __shared__ int scratch[33];
+    const int a = blockIdx.x;
+    const int node = lb + a;
+    const int64_t t0 = toff[a], nt64 = toff[a + 1] - toff[a];
+    const int32_t *T = tdata + t0;
+    int32_t *out = outptr[node];
+    int G = 1;
+    for (int k = 0; k < d; k++) G *= g;
+    if (nt64 <= G) {  // DataReduct returns S itself
+        int P = 1;
+        while (P < nt64) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) win[i] = i < nt64 ? T[i] : INT_MAX;
+        __syncthreads();
+        block_bitonic_sort(win, P);
+        for (int i = threadIdx.x; i < nt64; i += blockDim.x) out[i] = win[i];
+        if (threadIdx.x < 6) outbox[6 * (int64_t)node + threadIdx.x] = tbox[6 * (int64_t)a + threadIdx.x];
+        if (threadIdx.x == 0) outcnt[node] = (int32_t)nt64;
+        return;
+    }
+    const int nt = (int)nt64;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double *md = mdbase + t0;
+    // the first point: the smallest label
+    {
+        long long bk = LLONG_MIN;
+        int32_t bl = INT_MAX;
+        int bp = -1;
+        for (int p = threadIdx.x; p < nt; p += blockDim.x) {
+            md[p] = INFINITY;
+            fps_better(bk, bl, bp, 0, T[p], p);  // equal keys: the label decides
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            fps_better(bk, bl, bp, __shfl_xor_sync(0xffffffffu, bk, o), __shfl_xor_sync(0xffffffffu, bl, o),
+                       __shfl_xor_sync(0xffffffffu, bp, o));
+        if (lane == 0) { s_key[warp] = bk; s_lab[warp] = bl; s_pos[warp] = bp; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < nw; w++) fps_better(bk, bl, bp, s_key[w], s_lab[w], s_pos[w]);
+            s_f = bp;
+        }
+        __syncthreads();
+    }
+    for (int m = 0; m < G; m++) {
+        const int f = s_f;
+        const int32_t fl = T[f];
+        if (threadIdx.x == 0) {
+            win[m] = fl;
+            md[f] = -1.0;
+        }
+        if (m + 1 == G) break;
+        __syncthreads();
+        const double f0 = x0[fl], f1 = d > 1 ? x1[fl] : 0.0, f2 = d > 2 ? x2[fl] : 0.0;
+        long long bk = LLONG_MIN;
+        int32_t bl = INT_MAX;
+        int bp = -1;
+        for (int p = threadIdx.x; p < nt; p += blockDim.x) {
+            double v = md[p];
+            if (v < 0.0) continue;
+            const int32_t sid = T[p];
+            const double dd = h2_dist2(d, x0[sid], d > 1 ? x1[sid] : 0.0, d > 2 ? x2[sid] : 0.0, f0, f1, f2);
+            if (dd < v) {
+                v = dd;
+                md[p] = v;
+            }
+            fps_better(bk, bl, bp, __double_as_longlong(v), sid, p);
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            fps_better(bk, bl, bp, __shfl_xor_sync(0xffffffffu, bk, o), __shfl_xor_sync(0xffffffffu, bl, o),
+                       __shfl_xor_sync(0xffffffffu, bp, o));
+        if (lane == 0) { s_key[warp] = bk; s_lab[warp] = bl; s_pos[warp] = bp; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < nw; w++) fps_better(bk, bl, bp, s_key[w], s_lab[w], s_pos[w]);
+            s_f = bp;
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    {  // bounding box of the picked points
+        long long blo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, bhi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+        for (int i = threadIdx.x; i < G; i += blockDim.x) {
+            const int32_t sid = win[i];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k >= d) break;
+                const long long kv = dkey((k == 0 ? x0 : (k == 1 ? x1 : x2))[sid]);
+                blo[k] = min(blo[k], kv);
+                bhi[k] = max(bhi[k], kv);
+            }
+        }
+        block_box_write(blo, bhi, outbox + 6 * (int64_t)node);
+    }
+    int P = 1;
+    while (P < G) P <<= 1;
+    for (int i = G + threadIdx.x; i < P; i += blockDim.x) win[i] = INT_MAX;
+    __syncthreads();
+    block_bitonic_sort(win, P);
+    int m = block_unique_write(win, P, out, scratch);
+    if (threadIdx.x == 0) outcnt[node] = m;
+}
+
 // unit directions of the surface reference points: the Fibonacci lattice in
 // 3D (z_j = 1 - (2j + 1) / ne, rho = sqrt(1 - z^2), phi_j = j pi (3 - sqrt 5)),
 // equal angles 2 pi (j + 1/2) / ne in 2D; host arithmetic without contraction
@@ -1135,6 +1260,22 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
                        long long *outbox, cudaStream_t s, int method = 0) {
     if (nl <= 0) return;
     int G = (int)gridsize(g, d);
+    if (method == 2) {  // farthest point sampling
+        static std::once_flag fattr;
+        std::call_once(fattr, [] {
+            H2_CUDA(cudaFuncSetAttribute(k_datareduct_fps, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(DR_MAX_GRID * sizeof(int32_t))));
+        });
+        DevBuf<double> md;
+        md.alloc((size_t)std::max<int64_t>(ttot, 1), s);
+        int P = 1;
+        while (P < G) P <<= 1;
+        ProfScope ps(KT_DATAREDUCT, s);
+        k_datareduct_fps<<<nl, FPS_THREADS, (size_t)P * sizeof(int32_t), s>>>(toff, tdata, g, d, pts, md.p, outptr,
+                                                                              outcnt, lb, tbox, outbox);
+        H2_LAUNCH("k_datareduct_fps");
+        return;
+    }
     if (method == 1) {  // surface-based
         static std::once_flag sattr;
         std::call_once(sattr, [] {

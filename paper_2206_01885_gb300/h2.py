@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libh2gb300.so")
 
-DR_METHODS = {"volume": 0, "surface": 1}
+DR_METHODS = {"volume": 0, "surface": 1, "fps": 2}
 KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4, "bump": 5, "power": 6,
            "cosdot": 7}
 PRECISIONS = {"fp64": 0, "mixed": 1}
@@ -183,7 +183,7 @@ class Hidr(_Handle):
     """h2_hidr_reduce: X_i*, Y_i* of Algorithm 1."""
 
     def __init__(self, tree: Tree, g1: int, g2: int, stream=None, method: str = "volume"):
-        """method: the DataReduct of section 3.3, "volume" or "surface"."""
+        """method: the DataReduct of section 3.3, "volume", "surface" or "fps"."""
         h = C.c_void_p()
         _check("h2_hidr_reduce_ex", lib().h2_hidr_reduce_ex(tree.handle, int(g1), int(g2), DR_METHODS[method],
                                                              _stream(stream), C.byref(h)))

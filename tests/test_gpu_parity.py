@@ -115,16 +115,17 @@ SURFACE_CASES = [("cube3d", 3, 6000, 60, 4, 5), ("gmix2d", 2, 8000, 30, 6, 7), (
                  ("lattice3d", 3, 20000, 32, 4, 4), ("plane3d", 3, 20000, 64, 4, 5), ("same3d", 3, 3400, 64, 3, 3)]
 
 
+@pytest.mark.parametrize("method", ["surface", "fps"])
 @pytest.mark.parametrize("name,d,n,q,g1,g2", SURFACE_CASES, ids=[c[0] for c in SURFACE_CASES])
-def test_hidr_surface_bit_exact(H2, name, d, n, q, g1, g2):
-    """The surface-based DataReduct (section 3.3) through HiDR: X_i*, Y_i*
-    bit-exact against the oracle's."""
+def test_hidr_variants_bit_exact(H2, name, d, n, q, g1, g2, method):
+    """The surface-based and farthest-point-sampling DataReducts (section 3.3)
+    through HiDR: X_i*, Y_i* bit-exact against the oracle's."""
     pts = _hidr_points(name, d, n)
     t = H2.Tree(dev(pts), q)
-    h = H2.Hidr(t, g1, g2, method="surface")
-    assert json.loads(h.stats())["method"] == "surface"
+    h = H2.Hidr(t, g1, g2, method=method)
+    assert json.loads(h.stats())["method"] == method
     o = O.tree_build(pts, q)
-    oh = O.Hidr(o, g1, g2, method="surface")
+    oh = O.Hidr(o, g1, g2, method=method)
     for which in ["x", "y"]:
         cnt, data = h.get(which)
         off = np.concatenate([[0], np.cumsum(cnt)])

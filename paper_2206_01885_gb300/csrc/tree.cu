@@ -422,7 +422,7 @@ void lists_build_impl(h2_tree_s *t) {
     DevBuf<int8_t> cls;
     DevBuf<int64_t> nexp, off;
     DevBuf<uint64_t> farbuf, nearbuf;
-    DevBuf<unsigned long long> ctr;  // [0..1] this round's far/near counts, [2..3] cursors
+    DevBuf<unsigned long long> ctr;  // [0..1] this traversal step's far/near counts, [2..3] cursors
     ctr.alloc(4, s);
     H2_CUDA(cudaMemsetAsync(ctr.p, 0, 4 * sizeof(unsigned long long), s));
     F.alloc(1024, s);

@@ -80,6 +80,7 @@ typedef enum {
 typedef struct h2_tree_s *h2_tree;
 typedef struct h2_hidr_s *h2_hidr;
 typedef struct h2_matrix_s *h2_matrix;
+typedef struct h2_graph_s *h2_graph;
 
 /* Algorithm 2 inputs "separation ratio tau" and "leaf size q".  tau is the
  * rational tau_num / tau_den so that eq. (1) is decided exactly in integers
@@ -279,6 +280,22 @@ enum { H2_DTYPE_F64 = 0, H2_DTYPE_F32 = 1 };
  * Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM, H2_ERR_CUDA, H2_ERR_UNIMPLEMENTED. */
 h2_status h2_matvec(h2_matrix A, const void *x, void *y, int nrhs, int dtype, int64_t ld, int on_device,
                     void *stream);
+
+/* Repeated products through a CUDA graph (no counterpart in the paper: it
+ * serves callers that apply one matrix many times, e.g. iterative solvers).
+ * h2_matvec_graph_create runs h2_matvec(A, x, y, nrhs, dtype, ld, on_device
+ * = 1, stream) once, waits for it, then records the same product on device
+ * buffers x and y (same meaning and checks as h2_matvec) into a CUDA graph
+ * with its own scratch.  h2_matvec_graph_launch replays it on `stream`: fill
+ * x, launch, read y once the stream reaches that point.  Each replay computes
+ * y = K~ x for x's contents at that time, like a fresh h2_matvec call (the
+ * float64 atomics make two products agree to rounding, not bit for bit).
+ * While a graph lives, h2_free of its matrix fails with H2_ERR_STATE; free
+ * the graph (h2_free) first.  Errors: as h2_matvec; H2_ERR_CUDA if the
+ * capture or instantiation fails. */
+h2_status h2_matvec_graph_create(h2_matrix A, void *x, void *y, int nrhs, int dtype, int64_t ld, void *stream,
+                                 h2_graph *out);
+h2_status h2_matvec_graph_launch(h2_graph g, void *stream);
 
 /* ---------------------------------------------------------- exact rows --- */
 /* The reference of the section 6 error ||K z - K~ z|| / ||K z||: for each

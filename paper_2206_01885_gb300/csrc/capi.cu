@@ -455,26 +455,46 @@ h2_status h2_matrix_get(h2_matrix ah, int what, void *buf, int64_t cap, int64_t 
     });
 }
 
+namespace {
+// h2_matvec's argument checks
+void matvec_args_check(h2_matrix_s *A, const void *x, const void *y, int nrhs, int dtype, int64_t ld) {
+    H2_REQUIRE(x != nullptr && y != nullptr, "x or y is NULL");
+    H2_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    H2_REQUIRE(dtype == H2_DTYPE_F64 || dtype == H2_DTYPE_F32, "dtype must be H2_DTYPE_F64 or H2_DTYPE_F32");
+    const int64_t n = A->tree->n;
+    H2_REQUIRE(ld >= n, "ld must be >= n");
+    const size_t es = dtype == H2_DTYPE_F64 ? sizeof(double) : sizeof(float);
+    const size_t span = ((size_t)(nrhs - 1) * (size_t)ld + (size_t)n) * es;
+    const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
+    H2_REQUIRE(xb + span <= yb || yb + span <= xb, "x and y overlap");
+}
+
+// the product on device buffers
+void matvec_device(h2_matrix_s *A, const void *x, void *y, int nrhs, int dtype, int64_t ld, cudaStream_t s) {
+    if (nrhs == 1 && dtype == H2_DTYPE_F64)
+        matvec_impl(A, static_cast<const double *>(x), static_cast<double *>(y), s);
+    else
+        matvec_multi_impl(A, x, y, nrhs, dtype, ld, s);
+}
+
+h2_graph_s *as_graph(void *h) {
+    auto *g = static_cast<h2_graph_s *>(h);
+    if (!g || g->tag != TAG_GRAPH) fail(H2_ERR_INVALID_ARG, "not a graph handle");
+    return g;
+}
+}  // namespace
+
 h2_status h2_matvec(h2_matrix ah, const void *x, void *y, int nrhs, int dtype, int64_t ld, int on_device,
                     void *stream) {
     return guard([&] {
         h2_matrix_s *A = as_matrix(ah);
-        H2_REQUIRE(x != nullptr && y != nullptr, "x or y is NULL");
-        H2_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
-        H2_REQUIRE(dtype == H2_DTYPE_F64 || dtype == H2_DTYPE_F32, "dtype must be H2_DTYPE_F64 or H2_DTYPE_F32");
+        matvec_args_check(A, x, y, nrhs, dtype, ld);
         const int64_t n = A->tree->n;
-        H2_REQUIRE(ld >= n, "ld must be >= n");
         const size_t es = dtype == H2_DTYPE_F64 ? sizeof(double) : sizeof(float);
-        const size_t span = ((size_t)(nrhs - 1) * (size_t)ld + (size_t)n) * es;
-        const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
-        H2_REQUIRE(xb + span <= yb || yb + span <= xb, "x and y overlap");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const bool single = nrhs == 1 && dtype == H2_DTYPE_F64;
         if (on_device) {
-            if (single)
-                matvec_impl(A, static_cast<const double *>(x), static_cast<double *>(y), s);
-            else
-                matvec_multi_impl(A, x, y, nrhs, dtype, ld, s);
+            matvec_device(A, x, y, nrhs, dtype, ld, s);
             return;
         }
         DevBuf<char> xd, yd;
@@ -487,6 +507,65 @@ h2_status h2_matvec(h2_matrix ah, const void *x, void *y, int nrhs, int dtype, i
             matvec_multi_impl(A, xd.p, yd.p, nrhs, dtype, n, s);
         H2_CUDA(cudaMemcpy2DAsync(y, ld * es, yd.p, n * es, n * es, nrhs, cudaMemcpyDeviceToHost, s));
         H2_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+h2_status h2_matvec_graph_create(h2_matrix ah, void *x, void *y, int nrhs, int dtype, int64_t ld, void *stream,
+                                 h2_graph *out) {
+    return guard([&] {
+        H2_REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        h2_matrix_s *A = as_matrix(ah);
+        matvec_args_check(A, x, y, nrhs, dtype, ld);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        // one ordinary product: tiles, list starts and kernel attributes are set
+        // up on first use, with host synchronisations a capture cannot hold
+        matvec_device(A, x, y, nrhs, dtype, ld, s);
+        H2_CUDA(cudaStreamSynchronize(s));
+        cudaStream_t cs = nullptr;
+        H2_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        const bool prof = profiling_enabled();
+        if (prof) profile_set(false, false);  // no timing events inside the graph
+        auto *G = new h2_graph_s();
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        std::string msg;
+        if (e == cudaSuccess) {
+            try {
+                matvec_device(A, x, y, nrhs, dtype, ld, cs);
+            } catch (const h2::Error &ex) {
+                msg = ex.msg;
+            } catch (...) {
+                msg = "error during capture";
+            }
+            cudaGraph_t gr = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+            G->graph = gr;
+            if (msg.empty() && e2 != cudaSuccess) msg = cudaGetErrorString(e2);
+            if (msg.empty()) {
+                const cudaError_t e3 = cudaGraphInstantiate(&G->exec, G->graph, 0);
+                if (e3 != cudaSuccess) msg = cudaGetErrorString(e3);
+            }
+        } else {
+            msg = cudaGetErrorString(e);
+        }
+        cudaStreamDestroy(cs);
+        if (prof) profile_set(true, false);
+        if (!msg.empty()) {
+            cudaGetLastError();
+            G->tag = TAG_DEAD;
+            delete G;
+            fail(H2_ERR_CUDA, "matvec graph: " + msg);
+        }
+        G->A = A;
+        A->refs++;
+        *out = G;
+    });
+}
+
+h2_status h2_matvec_graph_launch(h2_graph gh, void *stream) {
+    return guard([&] {
+        h2_graph_s *G = as_graph(gh);
+        H2_CUDA(cudaGraphLaunch(G->exec, static_cast<cudaStream_t>(stream)));
     });
 }
 
@@ -614,9 +693,15 @@ h2_status h2_free(void *handle) {
             delete h;
         } else if (tag == TAG_MATRIX) {
             auto *A = static_cast<h2_matrix_s *>(handle);
+            if (A->refs > 0) fail(H2_ERR_STATE, "matrix still has live graph handles");
             A->tree->refs--;
             A->tag = TAG_DEAD;
             delete A;
+        } else if (tag == TAG_GRAPH) {
+            auto *G = static_cast<h2_graph_s *>(handle);
+            G->A->refs--;
+            G->tag = TAG_DEAD;
+            delete G;
         } else {
             fail(H2_ERR_INVALID_ARG, "not a live h2 handle");
         }

@@ -118,7 +118,13 @@ inline int blocks_for(int64_t n, int threads) {
 }
 
 // ---------------------------------------------------------------- handles
-enum : uint32_t { TAG_TREE = 0x48325452u, TAG_HIDR = 0x48324844u, TAG_MATRIX = 0x48324d58u, TAG_DEAD = 0xdeadbeefu };
+enum : uint32_t {
+    TAG_TREE = 0x48325452u,
+    TAG_HIDR = 0x48324844u,
+    TAG_MATRIX = 0x48324d58u,
+    TAG_GRAPH = 0x48324750u,
+    TAG_DEAD = 0xdeadbeefu
+};
 
 struct Geom {
     double lo[3];
@@ -208,6 +214,18 @@ struct h2_matrix_s {
     double g_max = 0;  // largest |G| = |(R11^{-1} R12)^T| entry over all nodes (what strong RRQR would bound)
     double g_bound = 0;       // f of the exchanges bounding ||G||_max (0: none)
     int64_t exchanges = 0;    // exchanges made
+};
+
+// a matvec recorded as a CUDA graph (h2_matvec_graph_create)
+struct h2_graph_s {
+    uint32_t tag = h2::TAG_GRAPH;
+    h2_matrix_s *A = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~h2_graph_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
 };
 
 namespace h2 {

@@ -67,6 +67,8 @@ def lib():
             "h2_construct": [vp, vp, i32, vp, dbl, i32, vp, C.POINTER(vp)],
             "h2_hidr_reduce_ex": [vp, i32, i32, i32, vp, C.POINTER(vp)],
             "h2_construct_ex": [vp, vp, i32, vp, dbl, i32, C.POINTER(_ConstructOpts), vp, C.POINTER(vp)],
+            "h2_matvec_graph_create": [vp, vp, vp, i32, i32, i64, vp, C.POINTER(vp)],
+            "h2_matvec_graph_launch": [vp, vp],
             "h2_autotune_leaf": [vp, i64, i32, i32, vp, i32, i32, i32, vp, dbl, i32, i32, vp, C.POINTER(i32), vp],
             "h2_matrix_get": [vp, i32, vp, i64, C.POINTER(i64)],
             "h2_matvec": [vp, vp, vp, i32, i32, i64, i32, vp],
@@ -224,6 +226,22 @@ class H2Matrix(_Handle):
         self._h = h.value
         self.tree = tree
 
+    def capture_matvec(self, x, y, stream=None) -> "MatvecGraph":
+        """h2_matvec_graph_create: y = K~ x recorded as a CUDA graph on these
+        device vectors (n entries, float64 or float32, contiguous, one dtype);
+        .launch() replays it for x's contents at that time."""
+        import torch
+        n = self.tree.n
+        ok = _is_cuda(x) and _is_cuda(y) and x.dtype == y.dtype and x.dtype in (torch.float64, torch.float32)
+        if not ok or x.shape != (n,) or y.shape != (n,) or not (x.is_contiguous() and y.is_contiguous()):
+            raise TypeError("x and y must be contiguous CUDA vectors of n entries and one float dtype")
+        dt = DTYPE_F64 if x.dtype == torch.float64 else DTYPE_F32
+        g = C.c_void_p()
+        _check("h2_matvec_graph_create", lib().h2_matvec_graph_create(self._h, C.c_void_p(x.data_ptr()),
+                                                                       C.c_void_p(y.data_ptr()), 1, dt, n,
+                                                                       _stream(stream), C.byref(g)))
+        return MatvecGraph(g.value, self, x, y)
+
     def get(self, what: str) -> np.ndarray:
         code, dt = MAT_FIELDS[what]
         ln = C.c_int64(0)
@@ -267,6 +285,19 @@ class H2Matrix(_Handle):
         _check("h2_matvec", lib().h2_matvec(self._h, xa.ctypes.data_as(C.c_void_p), ya.ctypes.data_as(C.c_void_p),
                                              nrhs, dt, n, 0, _stream(stream)))
         return ya
+
+
+class MatvecGraph(_Handle):
+    """A product recorded by H2Matrix.capture_matvec; holds its matrix and
+    buffers alive."""
+
+    def __init__(self, handle, A, x, y):
+        self._h = handle
+        self.A, self.x, self.y = A, x, y
+
+    def launch(self, stream=None):
+        _check("h2_matvec_graph_launch", lib().h2_matvec_graph_launch(self._h, _stream(stream)))
+        return self.y
 
 
 def tree_build(points, leaf_size, tau=(7, 10), stream=None) -> Tree:

@@ -65,5 +65,8 @@ def test_invalid_arguments_are_rejected_without_device_work(L):
     cands = (C.c_int * 2)(64, 0)
     assert L.h2_autotune_leaf(pts, 10, 3, 0, cands, 2, 7, 1, None, 1e-5, 1, 1, None, C.byref(b), None) == 1
     assert b"leaf" in L.h2_last_error()
+    gh = C.c_void_p()
+    assert L.h2_matvec_graph_create(bogus, pts, pts, 1, 0, 10, None, C.byref(gh)) == 1 and gh.value is None
+    assert L.h2_matvec_graph_launch(bogus, None) == 1
     buf = C.create_string_buffer(64)
     assert L.h2_get_stats(bogus, buf, 64) == 1

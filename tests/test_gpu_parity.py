@@ -471,3 +471,33 @@ def test_autotune_leaf(H2):
     best_h, times_h = H2.autotune_leaf(pts[:20000], (32, 256), g=5, kernel="gaussian", kparams=(0.5,),
                                        precision="fp64", reps=1)
     assert best_h in (32, 256) and set(times_h) == {32, 256}
+
+
+@pytest.mark.parametrize("prec,dtype", [("fp64", "float64"), ("mixed", "float32")])
+def test_matvec_graph(H2, prec, dtype):
+    """A product recorded as a CUDA graph (h2_matvec_graph_create) replays
+    y = K~ x for the vector x holds at launch time; its matrix cannot be
+    freed while the graph lives."""
+    n, q, g, eps = 6000, 64, 6, 1e-6
+    pts = I.uniform_cube(n, 3, seed=95)
+    t = H2.Tree(dev(pts), q)
+    h = H2.Hidr(t, g, g)
+    A = H2.H2Matrix(t, h, "coulomb", (), eps, prec)
+    tdt = getattr(torch, dtype)
+    x = dev(I.standard_normal(n, seed=96)).to(tdt)
+    y = torch.zeros(n, dtype=tdt, device="cuda")
+    G = A.capture_matvec(x, y)
+    for seed in (97, 98):
+        z = dev(I.standard_normal(n, seed=seed)).to(tdt)
+        x.copy_(z)
+        G.launch()
+        torch.cuda.synchronize()
+        want = A.matvec(z).double().cpu().numpy()
+        got = y.double().cpu().numpy()
+        tol = 1e-14 if prec == "fp64" else 1e-6
+        assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), seed
+    with pytest.raises(H2.H2Error) as e:
+        A.free()
+    assert e.value.status == 7  # H2_ERR_STATE
+    G.free()
+    A.free()

@@ -25,8 +25,11 @@ struct Error {
 
 [[noreturn]] void fail(h2_status st, const std::string &msg);
 void cuda_check(cudaError_t e, const char *what, const char *file, int line);
+void note_launches(int k);  // adds to the library's count of kernel launches
+long long launches_total();
 #define H2_CUDA(call) ::h2::cuda_check((call), #call, __FILE__, __LINE__)
-#define H2_LAUNCH(what) ::h2::cuda_check(cudaGetLastError(), what, __FILE__, __LINE__)
+// after each kernel launch: count it and surface a launch error
+#define H2_LAUNCH(what) (::h2::note_launches(1), ::h2::cuda_check(cudaGetLastError(), what, __FILE__, __LINE__))
 #define H2_REQUIRE(cond, msg)                                             \
     do {                                                                  \
         if (!(cond)) ::h2::fail(H2_ERR_INVALID_ARG, std::string(msg));    \

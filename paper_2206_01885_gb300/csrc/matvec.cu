@@ -707,6 +707,7 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
         t->far_first.alloc(nn, s);
         k_list_first<<<blocks_for(nn, 256), 256, 0, s>>>(t->near_ptr.p, t->near_idx.p, nn, t->near_first.p);
         k_list_first<<<blocks_for(nn, 256), 256, 0, s>>>(t->far_ptr.p, t->far_idx.p, nn, t->far_first.p);
+        note_launches(1);  // (two launches above)
         H2_LAUNCH("k_list_first");
     }
     const int64_t kt = std::max<int64_t>(A->ktotal, 1);
@@ -753,6 +754,7 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
         xhf.alloc(kt * R, s);
         k_to_float<<<blocks_for(nr, 256), 256, 0, s>>>(xm.p, nr, xmf.p);
         k_to_float<<<blocks_for(kt * R, 256), 256, 0, s>>>(xh.p, kt * R, xhf.p);
+        note_launches(1);
         H2_LAUNCH("k_to_float");
     }
     // float32 point coordinates and centre splits of the N-body kernels: the
@@ -768,6 +770,7 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
             k_to_float<<<blocks_for(n, 256), 256, 0, s>>>(t->xs[k].p, n, xabs[k].p);
             PX[k] = xabs[k].p;
         }
+        note_launches(d - 1);
         H2_LAUNCH("k_to_float");
         czero.alloc(t->nnodes, s);
         H2_CUDA(cudaMemsetAsync(czero.p, 0, t->nnodes * sizeof(float2), s));
@@ -858,6 +861,7 @@ void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z, c
                 rows + r0, nr, t->iperm.p, t->xs[0].p, t->xs[1].p, t->xs[2].p, zm.p, n, t->d, kid,
                 h2_kappa_param(kid, kp[0]), nch, part.p);
             k_exact_sum<<<blocks_for(nr, 256), 256, 0, s>>>(part.p, nr, nch, out + r0);
+            note_launches(1);
             H2_LAUNCH("k_exact_part");
         }
     }

@@ -12,6 +12,12 @@ namespace h2 {
 
 void fail(h2_status st, const std::string &msg) { throw Error{st, msg}; }
 
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
 void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
     if (e == cudaSuccess) return;
     char buf[512];
@@ -95,7 +101,8 @@ std::string profile_json() {
                  g_prof_ms[k], g_prof_n[k]);
         out += buf;
     }
-    return out + "}";
+    snprintf(buf, sizeof buf, ", \"launches_total\": %lld", launches_total());
+    return out + buf + "}";
 }
 
 ProfScope::ProfScope(int k, cudaStream_t st) : kind(k), s(st) {

@@ -424,9 +424,20 @@ def profile(enable: bool = True, reset: bool = True):
     _check("h2_profile", lib().h2_profile(int(enable), int(reset)))
 
 
-def kernel_times() -> dict:
-    """{kernel: {"ms": total, "launches": n}} collected while profiling."""
+def _global_stats() -> dict:
     import json
     buf = C.create_string_buffer(8192)
     _check("h2_get_stats", lib().h2_get_stats(None, buf, 8192))
     return json.loads(buf.value.decode())
+
+
+def kernel_times() -> dict:
+    """{kernel: {"ms": total, "launches": n}} collected while profiling."""
+    st = _global_stats()
+    st.pop("launches_total", None)
+    return st
+
+
+def launches_total() -> int:
+    """Kernel launches the library has made in this process."""
+    return int(_global_stats()["launches_total"])

@@ -511,7 +511,12 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
             }
             __syncwarp();
             Real col = (Real)0;
-            if (sym) {
+            // a short last chunk skips the rotation's padding steps: its cnt
+            // sources are read as broadcasts and each one's column sum is
+            // reduced across the warp (cheaper than 32 rotation steps up to
+            // about 24 sources in float64, 16 in float32)
+            constexpr int ROT_MIN = sizeof(Real) == 8 ? 24 : 16;
+            if (sym && cnt > ROT_MIN) {
                 const SrcPt<Real> *row = &stg[warp][lane];
 #pragma unroll 8
                 for (int q = 0; q < 32; q++) {
@@ -522,6 +527,14 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
                     col = __shfl_sync(0xffffffffu, col, (lane + 1) & 31);
                 }
                 if (lane < cnt) atomicAdd(out + ss + q0 + lane, (double)col);
+            } else if (sym) {
+                for (int q = 0; q < cnt; q++) {  // (cnt is the same in every lane)
+                    const SrcPt<Real> sv = stg[warp][q];
+                    const Real kv = kap_pt<KID, true>(s0, s1, s2, sv.x, sv.y, sv.z, p);
+                    blk += kv * sv.w;
+                    const Real c = warp_sum(kv * tw);
+                    if (lane == 0) atomicAdd(out + ss + q0 + q, (double)c);
+                }
             } else {
                 for (int q = 0; q < cnt; q++) {
                     const SrcPt<Real> sv = stg[warp][q];

@@ -172,7 +172,8 @@ def test_exact_rows_summation_against_fsum():
 
 
 @pytest.mark.parametrize("d,n,q,kern,kp", [(3, 1200, 40, "coulomb", ()), (2, 1500, 30, "gaussian", (0.2,)),
-                                           (3, 1000, 50, "multiquadric", ())])
+                                           (3, 1000, 50, "multiquadric", ()), (3, 1000, 50, "bump", (0.1,)),
+                                           (3, 900, 50, "power", (11.0,)), (3, 1000, 50, "cosdot", ())])
 def test_h2_exact_without_reduction_or_truncation(d, n, q, kern, kp):
     pts = I.uniform_cube(n, d, seed=41)
     z = I.standard_normal(n, seed=42)

@@ -475,6 +475,13 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
     const Real tx0 = act ? X0[ts + a] : far_t, tx1 = act && d > 1 ? X1[ts + a] : (Real)0,
                tx2 = act && d > 2 ? X2[ts + a] : (Real)0;
     const Real tw = act ? w[ts + a] : (Real)0;
+    // a short tile (the last of a node, e.g. 11 of a 43-point skeleton) turns
+    // the roles around: lanes take sources, targets are broadcast, so no lane
+    // evaluates a padding target (cheaper than the rotation up to about 24
+    // targets in float64, 12 in float32)
+    const int tcount = min(32, tn - tl.y);
+    constexpr int SHORT_T = sizeof(Real) == 8 ? 24 : 12;
+    const bool short_tile = tcount <= SHORT_T;
     Real acc = (Real)0, cmp = (Real)0;
     for (int64_t e = lfirst[i] + warp; e < lptr[i + 1]; e += NB_WARPS) {
         const int jn = lidx[e];
@@ -516,7 +523,18 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
             // reduced across the warp (cheaper than 32 rotation steps up to
             // about 24 sources in float64, 16 in float32)
             constexpr int ROT_MIN = sizeof(Real) == 8 ? 24 : 16;
-            if (sym && cnt > ROT_MIN) {
+            if (sym && short_tile) {
+                const SrcPt<Real> sv = stg[warp][lane];  // (lanes past cnt: the weight-0 sentinel)
+                for (int t = 0; t < tcount; t++) {      // (tcount is the same in every lane)
+                    const Real a0 = __shfl_sync(0xffffffffu, s0, t), a1 = __shfl_sync(0xffffffffu, s1, t),
+                               a2 = __shfl_sync(0xffffffffu, s2, t), aw = __shfl_sync(0xffffffffu, tw, t);
+                    const Real kv = kap_pt<KID, true>(a0, a1, a2, sv.x, sv.y, sv.z, p);
+                    col += kv * aw;
+                    const Real r = warp_sum(kv * sv.w);
+                    if (lane == t) blk += r;
+                }
+                if (lane < cnt) atomicAdd(out + ss + q0 + lane, (double)col);
+            } else if (sym && cnt > ROT_MIN) {
                 const SrcPt<Real> *row = &stg[warp][lane];
 #pragma unroll 8
                 for (int q = 0; q < 32; q++) {

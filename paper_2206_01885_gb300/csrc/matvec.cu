@@ -443,6 +443,11 @@ __global__ void __launch_bounds__(NB_WARPS * 32)
 // lane down after each step, so after 32 steps lane l holds source l's column
 // sum.  Row sums (per CTA) and column sums (per warp and 32 sources) are
 // added to out with float64 atomics: other CTAs add to the same entries.
+// Padding is skipped where it would dominate: a block's short last chunk of
+// sources is read by broadcast with one warp sum per source's column, and a
+// node's short last tile of targets runs with lanes over the sources and the
+// targets broadcast by shuffles (see the thresholds below).
+
 // a staged source point: coordinates and weight in one 16-byte (float) or
 // 32-byte (double) record, one shared-memory load per evaluation
 template <class Real>

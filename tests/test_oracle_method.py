@@ -236,6 +236,23 @@ def test_calibration_picks_smallest_g():
     assert e_g < 1e-6 <= e_prev
 
 
+@pytest.mark.parametrize("d,min_sq", [(2, 5), (3, 8)])
+def test_calibration_on_exact_rank_kernels(d, min_sq):
+    # |x - y|^p has rank 1 for p = 0 and rank d + 2 for p = 2 (|x|^2 - 2 x.y + |y|^2):
+    # the ID must reveal exactly that rank, one representor (g = 1) reproduces the
+    # constant kernel, and the 2^d bins of g = 2 hold at least d + 2 points in general
+    # position, so g = 2 reproduces the squared distance to rounding while g = 1 cannot.
+    z1, z2 = I.calibration_sets(d, min_sq, n1=256, n2=1024)
+    e, k, _ = O.calib_error(d, "power", (0.0,), 1e-8, z1, z2, 1)
+    assert k == 1 and e < 1e-14
+    assert O.calibrate(d, "power", (0.0,), 1e-6, z1, z2, gmax=12) == 1
+    e1, k1, _ = O.calib_error(d, "power", (2.0,), 1e-8, z1, z2, 1)
+    e2, k2, _ = O.calib_error(d, "power", (2.0,), 1e-8, z1, z2, 2)
+    assert k1 == 1 and e1 > 0.1
+    assert k2 == d + 2 and e2 < 1e-14
+    assert O.calibrate(d, "power", (2.0,), 1e-6, z1, z2, gmax=12) == 2
+
+
 def test_id_tie_goes_to_first_column():
     # equal column norms everywhere: the pivot order must be 0, 1, 2, ...
     k, piv, T = O.interp_decomp(np.eye(5), 0.0)

@@ -33,7 +33,9 @@
  *     S to each of the g^d cell-centred points of a tensor grid over the
  *     bounding box of S (ties to the smaller Morton position), deduplicated;
  *   - getBasis: Businger-Golub column pivoting, LAPACK-style norm downdating,
- *     stop at the first step whose pivot norm is <= eps * |r_11|.
+ *     stop at the first step whose pivot norm is <= eps * |r_11|;
+ *   - optionally (il_reduce), Y_i* also takes the reduction of its
+ *     interaction-list part on that part's own box (a variant, off by default).
  */
 #include <math.h>
 #include <stdint.h>
@@ -530,10 +532,33 @@ typedef struct {
     i64 *nx, *ny;       /* sizes; -1 = not computed                     */
 } ohidr;
 
+/* a and b sorted and free of repeats: writes their union, sorted, to out and
+ * returns its size */
+static i64 union_sorted(const i64 *a, i64 na, const i64 *b, i64 nb, i64 *out) {
+    i64 u = 0, v = 0, w = 0;
+    while (u < na || v < nb) {
+        i64 x;
+        if (v == nb || (u < na && a[u] < b[v])) x = a[u++];
+        else if (u == na || b[v] < a[u]) x = b[v++];
+        else { x = a[u++]; v++; }
+        out[w++] = x;
+    }
+    return w;
+}
+
 /* need_y: per-node flag (NULL = all) of nodes whose Y* is wanted; Y* is then
  * also computed for every ancestor of a flagged node.  X* is computed for all
- * non-root nodes. */
-ohidr *or_hidr(const otree *t, int g1, int g2, const unsigned char *need_y, int method) {
+ * non-root nodes.
+ *
+ * il_reduce = 0 is Algorithm 1 as printed.  il_reduce = 1 adds to each Y_i* the
+ * reduction of the interaction-list part alone, DataReduct(union of X_j* over
+ * j in IL(i), r2), whose reference grid spans only the box of those nearby
+ * nodes: Y_i* = DataReduct(T_i, r2) u DataReduct(IL part, r2), at most 2 r2
+ * points.  The grid over all of T_i spans nearly the whole domain at every
+ * depth (Y_p* covers the parent's farfield), so on deep trees it leaves the
+ * closest far nodes with a few samples or none; the second grid scales with
+ * the node. */
+ohidr *or_hidr(const otree *t, int g1, int g2, const unsigned char *need_y, int method, int il_reduce) {
     int nn = t->nnodes, d = t->d;
     ohidr *h = calloc(1, sizeof(ohidr));
     h->nnodes = nn; h->g1 = g1; h->g2 = g2;
@@ -588,9 +613,19 @@ ohidr *or_hidr(const otree *t, int g1, int g2, const unsigned char *need_y, int 
                 memcpy(T + w, h->xs[j], sizeof(i64) * h->nx[j]);
                 w += h->nx[j];
             }
-            i64 cap = nt < ipow(g2, d) ? nt : ipow(g2, d);
-            h->ys[i] = malloc(sizeof(i64) * cap);
+            i64 gd = ipow(g2, d), nil = nt - h->ny[p];
+            i64 cap = nt < gd ? nt : gd;
+            i64 capl = il_reduce && nil > 0 ? (nil < gd ? nil : gd) : 0;
+            h->ys[i] = malloc(sizeof(i64) * (cap + capl));
             h->ny[i] = datareduct_m(method, t->x, d, T, nt, g2, h->ys[i]);
+            if (capl > 0) {
+                i64 *A = malloc(sizeof(i64) * cap), *B = malloc(sizeof(i64) * capl);
+                i64 na = h->ny[i];
+                memcpy(A, h->ys[i], sizeof(i64) * na);
+                i64 nb = datareduct_m(method, t->x, d, T + h->ny[p], nil, g2, B);
+                h->ny[i] = union_sorted(A, na, B, nb, h->ys[i]);
+                free(A); free(B);
+            }
             free(T);
         }
     }

@@ -62,7 +62,7 @@ def lib():
             L.or_datareduct_fps.restype = i64
             L.or_datareduct_fps.argtypes = [vp, i32, vp, i64, i32, vp]
             L.or_hidr.restype = vp
-            L.or_hidr.argtypes = [vp, i32, i32, vp, i32]
+            L.or_hidr.argtypes = [vp, i32, i32, vp, i32, i32]
             L.or_hidr_get.restype = i64
             L.or_hidr_get.argtypes = [vp, i32, i32, vp]
             L.or_hidr_free.argtypes = [vp]
@@ -218,15 +218,18 @@ def datareduct(coords: np.ndarray, labels: np.ndarray, g: int, method: str = "vo
 
 
 class Hidr:
-    """X_i*, Y_i* of Algorithm 1."""
+    """X_i*, Y_i* of Algorithm 1.  ``il_reduce`` adds to each Y_i* the reduction
+    of its interaction-list part alone (DataReduct over the union of X_j*,
+    j in IL(i), on that part's own box), so |Y_i*| <= 2 g2^d."""
 
-    def __init__(self, tree: Tree, g1: int, g2: int, need_y: np.ndarray | None = None, method: str = "volume"):
-        self.tree, self.g1, self.g2 = tree, g1, g2
+    def __init__(self, tree: Tree, g1: int, g2: int, need_y: np.ndarray | None = None, method: str = "volume",
+                 il_reduce: bool = False):
+        self.tree, self.g1, self.g2, self.il_reduce = tree, g1, g2, il_reduce
         flags = None
         if need_y is not None:
             flags = np.ascontiguousarray(need_y, dtype=np.uint8)
         self.handle = lib().or_hidr(tree.handle, g1, g2, _p(flags) if flags is not None else None,
-                                    DR_METHODS[method])
+                                    DR_METHODS[method], int(il_reduce))
 
     def get(self, node: int, which: str) -> np.ndarray | None:
         w = 0 if which == "x" else 1
@@ -373,9 +376,9 @@ def closure_down(tree: Tree, flags: np.ndarray) -> np.ndarray:
     return f
 
 
-def build_h2(points, kernel, kparams, leaf_size, eps, g1, g2, tau=(7, 10), g_bound=0.0):
+def build_h2(points, kernel, kparams, leaf_size, eps, g1, g2, tau=(7, 10), g_bound=0.0, il_reduce=False):
     """Tree, lists, HiDR and the full construction, for small problems."""
     t = tree_build(points, leaf_size, tau)
-    h = Hidr(t, g1, g2)
+    h = Hidr(t, g1, g2, il_reduce=il_reduce)
     H = H2(t, h, kernel, kparams, eps, g_bound=g_bound)
     return t, h, H

@@ -5,7 +5,8 @@ What pins what (each against something other than the oracle itself):
     special case), the subset / size rules, ties to the smaller label;
   * HiDR (Algorithm 1, Theorem 3.1): subset and size invariants, Y_i* inside
     the farfield found by brute force, and the no-reduction case where X_i* = X_i
-    and Y_i* is the whole farfield;
+    and Y_i* is the whole farfield; with the interaction-list reduction, Y_i*
+    equals the union of the two scipy reductions it is defined by;
   * getBasis (eqs. (3)-(5)): LAPACK geqp3 pivots and R diagonal through scipy,
     exact rank on products of random factors, U[Xhat,:] = I;
   * matvec: the hand-computed dense product, math.fsum for the exact sums,
@@ -87,6 +88,46 @@ def test_hidr_invariants(d, n, q, g, method):
         far = _farfield_points(t, i)
         assert set(ys.tolist()) <= far
         assert (len(ys) == 0) == (len(far) == 0)
+
+
+def _kdtree_reduce(X, labels, g):
+    """DataReduct(S, g^d) by its definition, through scipy: S itself when it has
+    at most g^d points, else the nearest point of S to each cell-centred point
+    of the g^d grid over S's bounding box."""
+    labels = np.asarray(labels, dtype=np.int64)
+    d = X.shape[1]
+    if len(labels) <= g ** d:
+        return np.unique(labels)
+    P = X[labels]
+    l, u = P.min(0), P.max(0)
+    axes = [l[k] + (np.arange(g) + 0.5) * ((u[k] - l[k]) / g) for k in range(d)]
+    Q = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, d)
+    _, nn = cKDTree(P).query(Q)
+    return np.unique(labels[nn])
+
+
+@pytest.mark.parametrize("d,n,q,g", [(3, 3000, 30, 3), (2, 2500, 20, 4), (3, 6000, 40, 4)])
+def test_hidr_il_reduce_adds_the_interaction_list_reduction(d, n, q, g):
+    # Y_i* = DataReduct(T_i) u DataReduct(union of X_j*, j in IL(i)), T_i = Y_p* u that union
+    pts = I.uniform_cube(n, d, seed=7 + d)
+    t = O.tree_build(pts, q)
+    h0 = O.Hidr(t, g, g)
+    h = O.Hidr(t, g, g, il_reduce=True)
+    grew = 0
+    empty = np.zeros(0, dtype=np.int64)
+    for i in range(1, t.nnodes):
+        assert np.array_equal(h.get(i, "x"), h0.get(i, "x"))
+        far = t.far(i)
+        il = np.concatenate([h.get(int(j), "x") for j in far]) if len(far) else empty
+        T = np.concatenate([h.get(int(t.parent[i]), "y") if t.parent[i] > 0 else empty, il])
+        want = np.union1d(_kdtree_reduce(t.x, T, g) if len(T) else empty,
+                          _kdtree_reduce(t.x, il, g) if len(il) else empty)
+        ys = h.get(i, "y")
+        assert np.array_equal(ys, want), i
+        assert len(ys) <= 2 * g ** d
+        assert set(ys.tolist()) <= _farfield_points(t, i)
+        grew += len(ys) > len(_kdtree_reduce(t.x, T, g) if len(T) else empty)
+    assert grew > 0
 
 
 def test_hidr_no_reduction_gives_full_sets():
@@ -203,6 +244,16 @@ def test_h2_matvec_error_within_10eps(d, n, q, kern, kp, eps, g):
     # it must actually compress: some far pairs and ranks below the candidates
     assert len(t.far_idx) > 0
     assert any(0 < H.rank(i) < H.ncand(i) for i in range(t.nnodes))
+
+
+def test_h2_with_il_reduce_within_10eps():
+    pts = I.uniform_cube(4000, 3, seed=53)
+    z = I.standard_normal(4000, seed=51)
+    t, h, H = O.build_h2(pts, "coulomb", (), 64, 1e-6, 5, 5, il_reduce=True)
+    assert max(len(h.get(i, "y")) for i in range(1, t.nnodes)) > 5 ** 3  # rows beyond one grid
+    yd = O.dense_matvec(pts, "coulomb", (), z)
+    err = np.linalg.norm(H.matvec(z) - yd) / np.linalg.norm(yd)
+    assert err <= 1e-5, err
 
 
 def test_nested_skeletons_and_identity_rows():

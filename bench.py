@@ -54,6 +54,12 @@ WORKLOADS = {
     # eps = 1e-6 and g = 8: the setting whose sampled error at 1M meets 1e-5
     "cube1m_mixed_tau05": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-6, prec="mixed",
                                seed=2, rows=1000, g=8, tau=(1, 2)),
+    # HiDR with the interaction-list reduction: each Y_i* also reduces its
+    # interaction-list part on that part's own box (at most 2 g^3 points)
+    "cube1m_fp64_ilr": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-8, prec="fp64", seed=2,
+                            rows=1000, il_reduce=True, compare="cube1m_mixed_ilr"),
+    "cube1m_mixed_ilr": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-5, prec="mixed", seed=2,
+                             rows=1000, il_reduce=True),
     # 2D mixture of 16 Gaussians, Gaussian kernel exp(-r^2/0.04); g fixed (the
     # unit-cell calibration sets sit where this kernel is ~e^-100)
     "gmix2m_fp64": dict(n=1 << 21, d=2, kernel="gaussian", kparams=(0.2,), q=128, eps=1e-10, prec="fp64", seed=3,
@@ -247,7 +253,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
         side.wait_stream(stream)
         with torch.cuda.stream(side):
             ex = h2.exact_rows(t, wl["kernel"], wl["kparams"], z_in, rows_in, stream=side)
-        hd = h2.Hidr(t, g, g)
+        hd = h2.Hidr(t, g, g, il_reduce=wl.get("il_reduce", False))
         A = h2.H2Matrix(t, hd, wl["kernel"], wl["kparams"], wl["eps"], wl["prec"])
         y = A.matvec(zm_in)
         stream.wait_stream(side)
@@ -385,7 +391,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
                                              stream=side)
             job = threading.Thread(target=exact_job)
             job.start()
-            hd2 = h2.Hidr(t2, g, g)
+            hd2 = h2.Hidr(t2, g, g, il_reduce=wl.get("il_reduce", False))
             A2 = h2.H2Matrix(t2, hd2, wl["kernel"], wl["kparams"], wl["eps"], wl["prec"])
             y_h = A2.matvec(zm_h.numpy())
             job.join()
@@ -421,6 +427,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
         "config": {"workload": args.workload if wl is WORKLOADS[args.workload] else wl["name"], "n": n, "dim": d,
                    "kernel": wl["kernel"], "leaf_size": wl["q"], "id_tol": wl["eps"], "precision": wl["prec"],
                    "g": g, "r1": g ** d, "r2": g ** d, "tau": "%d/%d" % wl.get("tau", (7, 10)),
+                   "il_reduce": bool(wl.get("il_reduce", False)),
                    "sampled_rows": len(rows), "rhs": R,
                    "l2": "flushed (256 MB write) between timed steps, outside the timed interval",
                    "parallelism": f"{world} independent problem(s), one per GPU"},
@@ -478,7 +485,7 @@ def oracle_sample(wl, n_s):
     g = wl.get("g_oracle")
     t0 = time.perf_counter()
     t = O.tree_build(pts, wl["q"], wl.get("tau", (7, 10)))
-    h = O.Hidr(t, g, g)
+    h = O.Hidr(t, g, g, il_reduce=wl.get("il_reduce", False))
     H = O.H2(t, h, wl["kernel"], wl["kparams"], wl["eps"])
     y = H.matvec(z)
     ex = O.exact_rows(pts, wl["kernel"], wl["kparams"], z, rows)

@@ -180,8 +180,20 @@ typedef enum {
                          for small problems                                  */
 } h2_datareduct;
 
-/* h2_hidr_reduce with the DataReduct variant `method` (h2_datareduct).
- * Errors: as h2_hidr_reduce; H2_ERR_INVALID_ARG for an unknown method. */
+/* Flag ORed into h2_hidr_reduce_ex's method: each Y_i* also takes the
+ * reduction of its interaction-list part alone, on that part's own bounding
+ * box: Y_i* = DataReduct(T_i, g2^d) u DataReduct(union of X_j* over j in IL(i),
+ * g2^d), deduplicated and sorted, at most 2 g2^d points (a variant of
+ * Algorithm 1's top-down step).  The grid over all of T_i spans nearly the
+ * whole domain at every depth, because Y_p* covers the parent's farfield; the
+ * second grid scales with the node, so deep nodes' closest far nodes keep
+ * their samples.  Requires g2^dim <= 4096. */
+#define H2_HIDR_IL_REDUCE 0x100
+
+/* h2_hidr_reduce with the DataReduct variant `method` (h2_datareduct),
+ * optionally ORed with H2_HIDR_IL_REDUCE.
+ * Errors: as h2_hidr_reduce; H2_ERR_INVALID_ARG for an unknown method or flag,
+ * or for H2_HIDR_IL_REDUCE with g2^dim > 4096. */
 h2_status h2_hidr_reduce_ex(h2_tree t, int g1, int g2, int method, void *stream, h2_hidr *out);
 
 /* which: 0 = X_i*, 1 = Y_i*.  Fills counts (int32 [nnodes], may be NULL) and,

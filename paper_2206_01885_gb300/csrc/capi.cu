@@ -203,16 +203,24 @@ h2_status h2_hidr_reduce_ex(h2_tree th, int g1, int g2, int method, void *stream
     return guard([&] {
         H2_REQUIRE(out != nullptr, "out is NULL");
         *out = nullptr;
+        const bool il = (method & H2_HIDR_IL_REDUCE) != 0;
+        method &= ~H2_HIDR_IL_REDUCE;
         H2_REQUIRE(method == H2_DR_VOLUME || method == H2_DR_SURFACE || method == H2_DR_FPS,
-                   "unknown DataReduct method");
+                   "unknown DataReduct method or flag");
         h2_tree_s *t = as_tree(th);
         H2_REQUIRE(g1 >= 1 && g2 >= 1, "g1 and g2 must be >= 1");
+        if (il) {
+            int64_t G = 1;
+            for (int k = 0; k < t->d; k++) G = std::min<int64_t>(G * g2, 1 << 20);
+            H2_REQUIRE(G <= 4096, "the interaction-list reduction needs g2^dim <= 4096");
+        }
         auto *h = new h2_hidr_s();
         h->tree = t;
         h->stream = static_cast<cudaStream_t>(stream);
         h->g1 = g1;
         h->g2 = g2;
         h->method = method;
+        h->il_reduce = il;
         try {
             hidr_impl(h);
         } catch (...) {
@@ -734,9 +742,12 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
             auto *h = static_cast<const h2_hidr_s *>(handle);
             snprintf(buf, sizeof buf,
                      "{\"g1\": %d, \"g2\": %d, \"x_total\": %lld, \"y_total\": %lld, \"t_max_level\": %lld, "
-                     "\"t_total\": %lld, \"ms_up\": %.4f, \"ms_down\": %.4f, \"method\": \"%s\"}",
+                     "\"t_total\": %lld, \"ms_up\": %.4f, \"ms_down\": %.4f, \"method\": \"%s\", "
+                     "\"il_reduce\": %s}",
                      h->g1, h->g2, (long long)h->xtotal, (long long)h->ytotal, (long long)h->tmax,
-                     (long long)h->ttotal, h->ms_up, h->ms_down, h->method == H2_DR_SURFACE ? "surface" : (h->method == H2_DR_FPS ? "fps" : "volume"));
+                     (long long)h->ttotal, h->ms_up, h->ms_down,
+                     h->method == H2_DR_SURFACE ? "surface" : (h->method == H2_DR_FPS ? "fps" : "volume"),
+                     h->il_reduce ? "true" : "false");
         } else if (tag == TAG_MATRIX) {
             auto *A = static_cast<const h2_matrix_s *>(handle);
             snprintf(buf, sizeof buf,

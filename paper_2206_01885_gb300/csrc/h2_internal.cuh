@@ -181,6 +181,7 @@ struct h2_hidr_s {
     cudaStream_t stream = nullptr;
     int g1 = 0, g2 = 0;
     int method = 0;  // DataReduct: 0 volume-based, 1 surface-based, 2 farthest point sampling
+    bool il_reduce = false;  // Y_i* also takes the reduction of its interaction-list part alone
     // per node: count and device pointer into one of the per-level buffers
     h2::DevBuf<int32_t> xcnt, ycnt;
     h2::DevBuf<int32_t *> xptr, yptr;

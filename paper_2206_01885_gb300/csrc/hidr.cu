@@ -38,9 +38,12 @@ __global__ void k_size_up(int lb, int nl, const int32_t *nchild, const int32_t *
     cap[a] = s < G ? s : G;
 }
 
-// |T_i| = |Y_p*| + sum over j in IL(i) of |X_j*|; one warp per node
+// |T_i| = |Y_p*| + sum over j in IL(i) of |X_j*|; one warp per node.  With
+// szl (the interaction-list reduction), szl[a] = the interaction-list part's
+// size, capl[a] its reduced set's capacity, and cap[a] holds both reductions.
 __global__ void k_size_down(int lb, int nl, const int32_t *parent, const int64_t *far_ptr, const int32_t *far_idx,
-                            const int32_t *xcnt, const int32_t *ycnt, int g, int d, int64_t *sz, int64_t *cap) {
+                            const int32_t *xcnt, const int32_t *ycnt, int g, int d, int64_t *sz, int64_t *cap,
+                            int64_t *szl, int64_t *capl) {
     int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (a >= nl) return;
@@ -49,11 +52,18 @@ __global__ void k_size_down(int lb, int nl, const int32_t *parent, const int64_t
     for (int64_t e = far_ptr[i] + lane; e < far_ptr[i + 1]; e += 32) s += xcnt[far_idx[e]];
     s = warp_sum(s);
     if (lane == 0) {
+        const int64_t sl = s;
         s += ycnt[parent[i]];
         int64_t G = 1;
         for (int k = 0; k < d; k++) G *= g;
         sz[a] = s;
         cap[a] = s < G ? s : G;
+        if (szl) {
+            const int64_t cl = sl < G ? sl : G;
+            szl[a] = sl;
+            capl[a] = cl;
+            cap[a] += cl;
+        }
     }
 }
 
@@ -222,6 +232,21 @@ __global__ void __launch_bounds__(GD_THREADS) k_gather_down(int lb, const int32_
     block_box_write(lo, hi, tbox + 6 * (int64_t)a);
 }
 
+// The interaction-list part of T_i (what follows Y_p* there) copied to its own
+// segment tl[loff[a] .. loff[a+1]), and its box, the union of the X_j* boxes
+// over j in IL(i), to lbox[a]
+__global__ void k_gather_il(int lb, const int32_t *parent, const int64_t *far_ptr, const int32_t *far_idx,
+                            const int32_t *ycnt, const int64_t *toff, const int32_t *tdata, const int64_t *loff,
+                            int32_t *tl, const long long *xbox, long long *lbox) {
+    const int a = blockIdx.x, i = lb + a;
+    const int64_t src = toff[a] + ycnt[parent[i]], dst = loff[a], n = loff[a + 1] - loff[a];
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) tl[dst + r] = tdata[src + r];
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    for (int64_t e = far_ptr[i] + threadIdx.x; e < far_ptr[i + 1]; e += blockDim.x)
+        box_merge(lo, hi, xbox + 6 * (int64_t)far_idx[e]);
+    block_box_write(lo, hi, lbox + 6 * (int64_t)a);
+}
+
 __global__ void k_set_ptrs(int lb, int nl, int32_t *base, const int64_t *off, int32_t **ptr) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < nl) ptr[lb + a] = base + off[a];
@@ -276,6 +301,32 @@ __device__ int block_unique_write(const int32_t *v, int P, int32_t *out, int *sc
     int total = scratch[32];
     __syncthreads();
     return total;
+}
+
+// Y_i* u (the interaction-list part's reduced set lptr[a]): both sorted and
+// free of repeats; their union, sorted, replaces Y_i* in place (its buffer
+// holds both capacities), and Y_i*'s box takes the union of the two boxes.
+// Dynamic shared memory: the next power of two >= |Y_i*| + |lptr[a]| int32.
+__global__ void k_merge_il(int lb, int32_t *const *yptr, int32_t *ycnt, long long *ybox, int32_t *const *lptr,
+                           const int32_t *lcnt, const long long *lobox) {
+    extern __shared__ int32_t mv[];
+    __shared__ int scratch[33];
+    const int a = blockIdx.x, i = lb + a;
+    const int na = ycnt[i], nb = lcnt[a];
+    int32_t *y = yptr[i];
+    const int32_t *b = lptr[a];
+    int P = 1;
+    while (P < na + nb) P <<= 1;
+    for (int r = threadIdx.x; r < P; r += blockDim.x) mv[r] = r < na ? y[r] : (r < na + nb ? b[r - na] : INT_MAX);
+    __syncthreads();
+    block_bitonic_sort(mv, P);
+    const int m = block_unique_write(mv, P, y, scratch);
+    if (threadIdx.x == 0) ycnt[i] = m;
+    if (threadIdx.x < 3) {
+        const int k = threadIdx.x;
+        ybox[6 * (int64_t)i + k] = min(ybox[6 * (int64_t)i + k], lobox[6 * (int64_t)a + k]);
+        ybox[6 * (int64_t)i + 3 + k] = max(ybox[6 * (int64_t)i + 3 + k], lobox[6 * (int64_t)a + 3 + k]);
+    }
 }
 
 // in-place inclusive scan of v[0..n) in shared memory by the whole block
@@ -1372,13 +1423,28 @@ void hidr_impl(h2_hidr_s *h) {
         h->xtotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e1, s));
-    // top-down: Y_i* = DataReduct(Y_p* u X_j* (j in IL(i)), g2^d), level 1 first
+    // top-down: Y_i* = DataReduct(Y_p* u X_j* (j in IL(i)), g2^d), level 1 first;
+    // with the interaction-list reduction, u DataReduct(X_j* (j in IL(i)), g2^d)
+    const bool il = h->il_reduce;
+    DevBuf<int64_t> szl, capl, loff, lcoff;
+    DevBuf<int32_t> tl, lbuf, lcnt;
+    DevBuf<int32_t *> lptr;
+    DevBuf<long long> lbox, lobox;
+    size_t merge_smem = 0;
+    if (il) {
+        int P = 1;
+        while (P < 2 * gridsize(h->g2, d)) P <<= 1;
+        merge_smem = (size_t)P * sizeof(int32_t);
+        H2_REQUIRE(merge_smem <= 48 * 1024, "the interaction-list reduction needs g2^dim <= 4096");
+    }
     for (int l = 1; l < t->nlevels; l++) {
         int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
         sz.alloc(nl, s); cap.alloc(nl, s); toff.alloc(nl + 1, s); coff.alloc(nl + 1, s);
+        if (il) { szl.alloc(nl, s); capl.alloc(nl, s); loff.alloc(nl + 1, s); lcoff.alloc(nl + 1, s); }
         k_size_down<<<blocks_for((int64_t)nl * 32, 256), 256, 0, s>>>(lb, nl, t->parent.p, t->far_ptr.p,
                                                                        t->far_idx.p, h->xcnt.p, h->ycnt.p, h->g2, d,
-                                                                       sz.p, cap.p);
+                                                                       sz.p, cap.p, il ? szl.p : nullptr,
+                                                                       il ? capl.p : nullptr);
         H2_LAUNCH("k_size_down");
         scan_exclusive(sz.p, toff.p, nl, s);
         scan_exclusive(cap.p, coff.p, nl, s);
@@ -1395,6 +1461,27 @@ void hidr_impl(h2_hidr_s *h) {
         H2_LAUNCH("k_gather_down");
         launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, pts, h->yptr.p, h->ycnt.p, lb, tbox.p, h->ybox.p, s,
                           h->method);
+        if (il) {
+            scan_exclusive(szl.p, loff.p, nl, s);
+            scan_exclusive(capl.p, lcoff.p, nl, s);
+            const int64_t ltot = read_scalar(loff.p + nl, s), lctot = read_scalar(lcoff.p + nl, s);
+            tl.alloc(ltot > 0 ? ltot : 1, s);
+            lbuf.alloc(lctot > 0 ? lctot : 1, s);
+            lptr.alloc(nl, s);
+            lcnt.alloc(nl, s);
+            lbox.alloc((size_t)nl * 6, s);
+            lobox.alloc((size_t)nl * 6, s);
+            k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(0, nl, lbuf.p, lcoff.p, lptr.p);
+            H2_LAUNCH("k_set_ptrs");
+            k_gather_il<<<nl, 256, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->ycnt.p, toff.p, tdata.p,
+                                           loff.p, tl.p, h->xbox.p, lbox.p);
+            H2_LAUNCH("k_gather_il");
+            // outputs indexed from 0: lptr, lcnt and lobox hold this level's nodes only
+            launch_datareduct(loff.p, tl.p, ltot, nl, h->g2, d, pts, lptr.p, lcnt.p, 0, lbox.p, lobox.p, s,
+                              h->method);
+            k_merge_il<<<nl, 256, merge_smem, s>>>(lb, h->yptr.p, h->ycnt.p, h->ybox.p, lptr.p, lcnt.p, lobox.p);
+            H2_LAUNCH("k_merge_il");
+        }
         h->ytotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e2, s));

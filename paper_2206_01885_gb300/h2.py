@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libh2gb300.so")
 
 DR_METHODS = {"volume": 0, "surface": 1, "fps": 2}
+HIDR_IL_REDUCE = 0x100  # H2_HIDR_IL_REDUCE, ORed into the method
 KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4, "bump": 5, "power": 6,
            "cosdot": 7}
 PRECISIONS = {"fp64": 0, "mixed": 1}
@@ -184,10 +185,13 @@ class Tree(_Handle):
 class Hidr(_Handle):
     """h2_hidr_reduce: X_i*, Y_i* of Algorithm 1."""
 
-    def __init__(self, tree: Tree, g1: int, g2: int, stream=None, method: str = "volume"):
-        """method: the DataReduct of section 3.3, "volume", "surface" or "fps"."""
+    def __init__(self, tree: Tree, g1: int, g2: int, stream=None, method: str = "volume", il_reduce: bool = False):
+        """method: the DataReduct of section 3.3, "volume", "surface" or "fps".
+        il_reduce: each Y_i* also takes the reduction of its interaction-list
+        part alone, on that part's own box (H2_HIDR_IL_REDUCE)."""
         h = C.c_void_p()
-        _check("h2_hidr_reduce_ex", lib().h2_hidr_reduce_ex(tree.handle, int(g1), int(g2), DR_METHODS[method],
+        flags = DR_METHODS[method] | (HIDR_IL_REDUCE if il_reduce else 0)
+        _check("h2_hidr_reduce_ex", lib().h2_hidr_reduce_ex(tree.handle, int(g1), int(g2), flags,
                                                              _stream(stream), C.byref(h)))
         self._h = h.value
         self.tree = tree

@@ -49,6 +49,10 @@ def test_invalid_arguments_are_rejected_without_device_work(L):
     bogus = (C.c_uint32 * 4)(1, 2, 3, 4)
     assert L.h2_free(bogus) == 1
     assert L.h2_hidr_reduce(bogus, 3, 3, None, C.byref(out)) == 1
+    assert L.h2_hidr_reduce_ex(bogus, 3, 3, 0x200, None, C.byref(out)) == 1  # unknown flag
+    assert b"flag" in L.h2_last_error()
+    assert L.h2_hidr_reduce_ex(bogus, 3, 3, 3 | h2.HIDR_IL_REDUCE, None, C.byref(out)) == 1  # unknown method
+    assert L.h2_hidr_reduce_ex(bogus, 3, 3, h2.HIDR_IL_REDUCE, None, C.byref(out)) == 1  # bogus tree
     assert L.h2_matvec(bogus, pts, pts, 1, 0, 10, 0, None) == 1
     assert L.h2_construct_batched(0, None, None, None, None, None, None, None, None) == 0
     assert L.h2_construct_batched(-1, None, None, None, None, None, None, None, None) == 1

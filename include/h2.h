@@ -222,9 +222,25 @@ h2_status h2_hidr_get(h2_hidr h, int which, int32_t *counts, int32_t *data, int6
 h2_status h2_construct(h2_tree t, h2_hidr h, int kernel, const double *kparams, double id_tol,
                        int precision, void *stream, h2_matrix *out);
 
+/* Memory mode of the coupling blocks B_ij = K(Xhat_i, Xhat_j) (far pairs)
+ * and nearfield blocks K(X_i, X_j) (near leaf pairs) that Algorithm 2 forms
+ * after the bases.  ON_THE_FLY evaluates them inside every h2_matvec;
+ * STORE evaluates each once at construction and keeps it on the device
+ * (kappa is symmetric: one block per unordered pair, row-major, in the
+ * matrix's precision -- float64, or float32 in the mixed form), and every
+ * later single-right-hand-side product reads the stored blocks; AUTO stores
+ * them when they fit (as STORE's budget below) and the form is float64, the
+ * one whose on-the-fly evaluation costs more than reading a stored entry. */
+enum { H2_MEM_ON_THE_FLY = 0, H2_MEM_STORE = 1, H2_MEM_AUTO = 2 };
+
 /* Options of h2_construct_ex; zero-initialised options are h2_construct's. */
 typedef struct {
-    double g_bound; /* f > 1: bound ||G||_max by f as below; 0: no exchanges */
+    double g_bound;      /* f > 1: bound ||G||_max by f as below; 0: no exchanges */
+    int mem_mode;        /* H2_MEM_ON_THE_FLY (0), H2_MEM_STORE or H2_MEM_AUTO       */
+    double mem_fraction; /* share of the device's free memory (cudaMemGetInfo at
+                            construction) the stored blocks may take, in (0, 1];
+                            0 means 0.5.  STORE above it fails with H2_ERR_OOM;
+                            AUTO above it stays on the fly                      */
 } h2_construct_opts;
 
 /* h2_construct with options (opts may be NULL: exactly h2_construct).
@@ -239,8 +255,15 @@ typedef struct {
  * loop ends; it is cut at 8 k exchanges per node in any case.  The count is
  * the matrix statistic "exchanges".  The parent's candidates are the
  * children's final skeletons, so the bound holds at every level.
+ * mem_mode (Algorithm 2's coupling and nearfield blocks, stored or not):
+ * with the blocks stored, h2_matvec with nrhs = 1 reads them (several
+ * right-hand sides still evaluate on the fly); the product equals the
+ * on-the-fly one to rounding (the stored entries are the values the
+ * on-the-fly kernels compute).  The matrix statistics report "mem_mode",
+ * "stored_bytes" and the fill time "ms_blocks".
  * Errors: as h2_construct; H2_ERR_INVALID_ARG if g_bound is neither 0 nor a
- * finite number > 1. */
+ * finite number > 1, for an unknown mem_mode or a mem_fraction outside
+ * [0, 1]; H2_ERR_OOM when STORE's blocks exceed the budget. */
 h2_status h2_construct_ex(h2_tree t, h2_hidr h, int kernel, const double *kparams, double id_tol,
                           int precision, const h2_construct_opts *opts, void *stream, h2_matrix *out);
 
@@ -326,7 +349,9 @@ h2_status h2_exact_rows(h2_tree t, int kernel, const double *kparams, const doub
  * that forbid allocator calls (cudaMalloc can synchronise the device and fail
  * under memory pressure).  The paper has no counterpart; it computes exactly
  * what h2_exact_rows computes.  Differences from h2_exact_rows:
- *   - z, rows and out must be device pointers (no host staging);
+ *   - z, rows and out must be device (or managed) memory of the current
+ *     device (no host staging); a host pointer is refused with
+ *     H2_ERR_INVALID_ARG before anything is launched;
  *   - the tree may hold at most 1,048,576 points: the permuted right-hand side
  *     is kept in a fixed 8 MiB array inside the library image, which every GPU
  *     that loads the library holds until the process exits; larger trees are
@@ -364,6 +389,19 @@ h2_status h2_sampled_error(const double *exact, const double *approx, const int6
 h2_status h2_autotune_leaf(const double *pts, int64_t n, int dim, int pts_on_device, const int *cands,
                            int ncand, int g, int kernel, const double *kparams, double id_tol, int precision,
                            int reps, void *stream, int *best, double *times);
+
+/* ------------------------------------------------------- fault testing --- */
+/* Host-side allocation-failure injection, for testing the error paths (the
+ * paper has no counterpart).  Resets the library's count of device
+ * allocations to 0 and arms the k-th allocation from now on (k >= 1) to fail
+ * as if the device were out of memory: the call making it returns H2_ERR_OOM,
+ * hands out no handle (*out = NULL), releases what it had allocated, and
+ * leaves every existing handle and the CUDA context usable.  k = 0 disarms.
+ * *allocs_since_last (may be NULL) receives the number of device allocations
+ * made since the previous h2_debug_fail_alloc call.  The count is process-wide:
+ * concurrent calls on other threads draw from it too.
+ * Errors: H2_ERR_INVALID_ARG (k < 0). */
+h2_status h2_debug_fail_alloc(int64_t k, int64_t *allocs_since_last);
 
 /* ------------------------------------------------------------- common --- */
 /* Release any handle returned above (NULL is a no-op).  Device memory is

@@ -66,6 +66,24 @@ void pool_keep_memory() {
     });
 }
 
+// A pointer the kernels will dereference must be device (or managed) memory of
+// the current device.  cudaPointerGetAttributes allocates nothing; an
+// unregistered or pinned host pointer is refused here instead of faulting a
+// kernel later.
+void require_device_ptr(const void *p, const char *name) {
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h2::fail(H2_ERR_INVALID_ARG, std::string(name) + " is not a device pointer");
+    }
+    int dev = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    const bool on_gpu = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (!on_gpu || a.device != dev)
+        h2::fail(H2_ERR_INVALID_ARG, std::string(name) + " must be device memory of the current device");
+}
+
 template <class T>
 void copy_out(const std::vector<T> &v, void *buf, int64_t cap, int64_t *len) {
     if (len) *len = (int64_t)v.size();
@@ -276,6 +294,10 @@ h2_status h2_construct_ex(h2_tree th, h2_hidr hh, int kernel, const double *kpar
         H2_REQUIRE(precision == H2_PREC_FP64 || precision == H2_PREC_MIXED, "unknown precision");
         const double gb = opts ? opts->g_bound : 0.0;
         H2_REQUIRE(gb == 0.0 || (std::isfinite(gb) && gb > 1.0), "g_bound must be 0 or a finite number > 1");
+        const int mm = opts ? opts->mem_mode : H2_MEM_ON_THE_FLY;
+        H2_REQUIRE(mm == H2_MEM_ON_THE_FLY || mm == H2_MEM_STORE || mm == H2_MEM_AUTO, "unknown mem_mode");
+        const double mf = opts ? opts->mem_fraction : 0.0;
+        H2_REQUIRE(std::isfinite(mf) && mf >= 0.0 && mf <= 1.0, "mem_fraction must be in [0, 1]");
         auto *A = new h2_matrix_s();
         A->tree = t;
         A->stream = static_cast<cudaStream_t>(stream);
@@ -283,9 +305,13 @@ h2_status h2_construct_ex(h2_tree th, h2_hidr hh, int kernel, const double *kpar
         A->id_tol = id_tol;
         A->prec = precision;
         A->g_bound = gb;
+        A->mem_mode = mm;
+        A->mem_fraction = mf > 0.0 ? mf : 0.5;
         try {
             kparams_check(kernel, kparams, A->kp);
             construct_impl(A, h);
+            if (mm == H2_MEM_STORE || (mm == H2_MEM_AUTO && precision == H2_PREC_FP64))
+                store_blocks_impl(A, mm, A->mem_fraction);
         } catch (...) {
             A->tag = TAG_DEAD;
             delete A;
@@ -615,7 +641,20 @@ h2_status h2_exact_rows_noalloc(h2_tree th, int kernel, const double *kparams, c
         H2_REQUIRE(nrows >= 0 && nrows < (int64_t)INT32_MAX, "bad nrows");
         double kp[4];
         kparams_check(kernel, kparams, kp);
+        require_device_ptr(z, "z");
+        if (nrows > 0) {
+            require_device_ptr(rows, "rows");
+            require_device_ptr(out, "out");
+        }
         exact_rows_noalloc_impl(t, kernel, kp, z, rows, nrows, out, static_cast<cudaStream_t>(stream));
+    });
+}
+
+h2_status h2_debug_fail_alloc(int64_t k, int64_t *allocs_since_last) {
+    return guard([&] {
+        H2_REQUIRE(k >= 0, "k must be >= 0");
+        const int64_t made = debug_fail_alloc(k);
+        if (allocs_since_last) *allocs_since_last = made;
     });
 }
 
@@ -753,10 +792,14 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
             snprintf(buf, sizeof buf,
                      "{\"k_total\": %lld, \"u_entries\": %lld, \"k_max\": %d, \"ms_construct\": %.4f, "
                      "\"qr_flops\": %.6e, \"block_evals\": %.6e, \"g_max\": %.6e, \"g_bound\": %.6e, "
-                     "\"exchanges\": %lld, \"precision\": \"%s\"}",
+                     "\"exchanges\": %lld, \"precision\": \"%s\", \"mem_mode\": \"%s\", "
+                     "\"stored_bytes\": %lld, \"stored_far_bytes\": %lld, \"stored_near_bytes\": %lld, "
+                     "\"planned_bytes\": %lld, \"ms_blocks\": %.4f}",
                      (long long)A->ktotal, (long long)A->utotal, A->kmax, A->ms_construct, A->flops_qr,
                      A->evals_block, A->g_max, A->g_bound, (long long)A->exchanges,
-                     A->prec == H2_PREC_FP64 ? "fp64" : "mixed");
+                     A->prec == H2_PREC_FP64 ? "fp64" : "mixed", A->stored ? "stored" : "on_the_fly",
+                     (long long)(A->stored_far_bytes + A->stored_near_bytes), (long long)A->stored_far_bytes,
+                     (long long)A->stored_near_bytes, (long long)A->stored_bytes_plan, A->ms_blocks);
         } else {
             fail(H2_ERR_INVALID_ARG, "not a live h2 handle");
         }

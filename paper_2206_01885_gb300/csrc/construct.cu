@@ -1125,6 +1125,10 @@ void matrix_rebind(h2_matrix_s *A, cudaStream_t s) {
     A->uptr.rebind(s);
     for (auto &b : A->ubufs) b.rebind(s);
     A->far_tiles.rebind(s);
+    A->far_blk.rebind(s);
+    A->near_blk.rebind(s);
+    A->far_boff.rebind(s);
+    A->near_boff.rebind(s);
 }
 
 }  // namespace h2

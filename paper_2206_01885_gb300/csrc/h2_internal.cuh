@@ -38,6 +38,7 @@ long long launches_total();
 // ----------------------------------------------------------- device memory
 void *dmalloc_bytes(size_t bytes, cudaStream_t s);
 void dfree_bytes(void *p, cudaStream_t s);
+int64_t debug_fail_alloc(int64_t k);  // arm the k-th allocation to fail; returns the count since the last arming
 
 // Owning device array, released on the stream it was allocated on.
 template <class T>
@@ -57,8 +58,8 @@ struct DevBuf {
     void alloc(size_t count, cudaStream_t st) {
         release();
         s = st;
-        n = count;
-        p = count ? static_cast<T *>(dmalloc_bytes(count * sizeof(T), st)) : nullptr;
+        if (count) p = static_cast<T *>(dmalloc_bytes(count * sizeof(T), st));  // throws on failure
+        n = count;  // only once the memory exists: a failed alloc leaves an empty buffer
     }
     void release() {
         if (p) dfree_bytes(p, s);
@@ -101,7 +102,7 @@ void radix_sort(uint64_t *keys, int32_t *vals, int64_t n, int nbits, cudaStream_
 // launched on; totals are read through h2_get_stats(NULL, ...).
 enum KernelKind {
     KT_DATAREDUCT = 0, KT_KEVAL, KT_CPQR, KT_SOLVE, KT_UPWARD, KT_COUPLING, KT_DOWNWARD, KT_NEAR, KT_EXACT,
-    KT_SORT, KT_LISTS, KT_COUNT
+    KT_SORT, KT_LISTS, KT_FILL, KT_COUPLING_ST, KT_NEAR_ST, KT_COUNT
 };
 extern const char *const kernel_kind_names[KT_COUNT];
 bool profiling_enabled();
@@ -218,6 +219,16 @@ struct h2_matrix_s {
     double g_max = 0;  // largest |G| = |(R11^{-1} R12)^T| entry over all nodes (what strong RRQR would bound)
     double g_bound = 0;       // f of the exchanges bounding ||G||_max (0: none)
     int64_t exchanges = 0;    // exchanges made
+    // stored coupling and nearfield blocks (memory mode STORE, or AUTO when
+    // they fit): per list entry e with j >= i the row-major block K(i, j) at
+    // element offset *_boff[e] (-1: not stored)
+    int mem_mode = 0;                  // requested: H2_MEM_ON_THE_FLY / STORE / AUTO
+    double mem_fraction = 0.5;         // share of the free device memory the blocks may take
+    bool stored = false;               // blocks stored (the products read them)
+    h2::DevBuf<unsigned char> far_blk, near_blk;
+    h2::DevBuf<int64_t> far_boff, near_boff;
+    int64_t stored_far_bytes = 0, stored_near_bytes = 0, stored_bytes_plan = 0;
+    double ms_blocks = 0;
 };
 
 // a matvec recorded as a CUDA graph (h2_matvec_graph_create)
@@ -251,6 +262,15 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x_dev, void *y_dev, int nrhs,
                        cudaStream_t s);
 void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z_dev, const int64_t *rows_dev,
                      int64_t nrows, double *out_dev, cudaStream_t s);
+// evaluate and keep the coupling and nearfield blocks (mode H2_MEM_STORE:
+// H2_ERR_OOM above `fraction` of the free memory; H2_MEM_AUTO: keep them
+// only when they fit)
+void store_blocks_impl(h2_matrix_s *A, int mode, double fraction);
+// y += stored-block product of one list (one right-hand side)
+template <class Real>
+void stored_product(const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const void *blk,
+                    const int64_t *boff, const Real *w, double *out, const int64_t *lptr, const int64_t *lfirst,
+                    const int32_t *lidx, cudaStream_t s);
 
 void exact_rows_noalloc_impl(h2_tree_s *t, int kid, const double *kp, const double *z_dev, const int64_t *rows_dev,
                              int64_t nrows, double *out_dev, cudaStream_t s);

@@ -306,6 +306,9 @@ __device__ int block_unique_write(const int32_t *v, int P, int32_t *out, int *sc
 // Y_i* u (the interaction-list part's reduced set lptr[a]): both sorted and
 // free of repeats; their union, sorted, replaces Y_i* in place (its buffer
 // holds both capacities), and Y_i*'s box takes the union of the two boxes.
+// A node with an empty interaction list (common at levels 1-2) has an empty
+// second part whose box is DataReduct's empty-set sentinel (LLONG_MAX lows,
+// LLONG_MIN highs), so the min/max below leave Y_i*'s box unchanged.
 // Dynamic shared memory: the next power of two >= |Y_i*| + |lptr[a]| int32.
 __global__ void k_merge_il(int lb, int32_t *const *yptr, int32_t *ycnt, long long *ybox, int32_t *const *lptr,
                            const int32_t *lcnt, const long long *lobox) {
@@ -1420,7 +1423,6 @@ void hidr_impl(h2_hidr_s *h) {
         H2_LAUNCH("k_gather_up");
         launch_datareduct(toff.p, tdata.p, ttot, nl, h->g1, d, pts, h->xptr.p, h->xcnt.p, lb, tbox.p, h->xbox.p, s,
                           h->method);
-        h->xtotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e1, s));
     // top-down: Y_i* = DataReduct(Y_p* u X_j* (j in IL(i)), g2^d), level 1 first;
@@ -1482,7 +1484,6 @@ void hidr_impl(h2_hidr_s *h) {
             k_merge_il<<<nl, 256, merge_smem, s>>>(lb, h->yptr.p, h->ycnt.p, h->ybox.p, lptr.p, lcnt.p, lobox.p);
             H2_LAUNCH("k_merge_il");
         }
-        h->ytotal += ctot;
     }
     H2_CUDA(cudaEventRecord(e2, s));
     H2_CUDA(cudaEventSynchronize(e2));
@@ -1494,12 +1495,17 @@ void hidr_impl(h2_hidr_s *h) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
-    // per-level maxima of |X*| and |Y*| for later launch sizing
+    // per-level maxima of |X*| and |Y*| for later launch sizing, and the
+    // totals of the sets as built (the buffers' capacities can be larger:
+    // DataReduct deduplicates, and the interaction-list merge drops repeats)
     std::vector<int32_t> xc = read_vec(h->xcnt.p, nn, s), yc = read_vec(h->ycnt.p, nn, s);
+    h->xtotal = h->ytotal = 0;
     for (int l = 0; l < t->nlevels; l++)
         for (int i = t->lptr[l]; i < t->lptr[l + 1]; i++) {
             h->xmax_level[l] = std::max(h->xmax_level[l], (int)xc[i]);
             h->ymax_level[l] = std::max(h->ymax_level[l], (int)yc[i]);
+            h->xtotal += xc[i];
+            h->ytotal += yc[i];
         }
 }
 

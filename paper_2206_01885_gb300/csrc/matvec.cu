@@ -12,6 +12,7 @@
 #include <cfloat>
 
 #include "h2_internal.cuh"
+#include "kappa_fast.cuh"
 
 // Scratch of h2_exact_rows_noalloc: the right-hand side permuted to Morton
 // order.  It lives in the library image, so every GPU that loads the library
@@ -77,67 +78,6 @@ __global__ void k_downward(int lb, const int32_t *nchild, const int32_t *fchild,
         double s = 0.0;
         for (int a = 0; a < k; a++) s += (double)U[r + (int64_t)a * c] * sz_[a];
         out[r] += s;
-    }
-}
-
-// kappa for the matvec kernels: fast forms (rsqrt, exp) in float64 or float32
-// (p: 1/h^2 Gaussian, 1/l exponential, a bump, p/2 power; see kap_param)
-template <int KID>
-__device__ __forceinline__ double kap(double r2, double p) {
-    if constexpr (KID == H2_K_COULOMB) return h2_rsqrt64(r2);
-    else if constexpr (KID == H2_K_GAUSSIAN) return exp(-r2 * p);
-    else if constexpr (KID == H2_K_EXPONENTIAL) return exp(-sqrt(r2) * p);
-    else if constexpr (KID == H2_K_BUMP) {
-        const double t = r2 * p;
-        return t < 1.0 ? exp(-1.0 / (1.0 - t)) : 0.0;
-    } else if constexpr (KID == H2_K_POWER) {  // (kept finite: the symmetric kernel's padding has weight 0)
-        return r2 > 0.0 ? fmin(pow(r2, p), DBL_MAX) : 0.0;
-    } else return sqrt(1.0 + r2);
-}
-template <int KID>
-__device__ __forceinline__ float kap(float r2, float p) {
-    if constexpr (KID == H2_K_COULOMB) {
-        float y;
-        asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(r2));  // relative error below 2^-22
-        return r2 > 0.0f ? y : 0.0f;
-    }
-    else if constexpr (KID == H2_K_GAUSSIAN) return __expf(-r2 * p);
-    else if constexpr (KID == H2_K_EXPONENTIAL) return __expf(-sqrtf(r2) * p);
-    else if constexpr (KID == H2_K_BUMP) {
-        const float t = r2 * p;
-        return t < 1.0f ? __expf(__fdividef(-1.0f, 1.0f - t)) : 0.0f;
-    } else if constexpr (KID == H2_K_POWER) {  // (kept finite, as above)
-        return r2 > 0.0f ? fminf(__powf(r2, p), FLT_MAX) : 0.0f;
-    } else return sqrtf(1.0f + r2);
-}
-// the kernel parameter in the form kap takes
-inline double kap_param(int kid, double kp0) { return h2_kappa_param(kid, kp0); }
-// kappa for point pairs known to be distinct (r2 > 0): Coulomb skips the
-// r2 = 0 test
-template <int KID, class Real>
-__device__ __forceinline__ Real kap_distinct(Real r2, Real p) {
-    if constexpr (KID == H2_K_COULOMB && sizeof(Real) == 4) {
-        float y;
-        asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(r2));
-        return y;
-    } else {
-        return kap<KID>(r2, p);
-    }
-}
-
-// kappa of a target t and a source s: cos(t . s) for Table 1's kappa_3 (both
-// in absolute coordinates), every other kernel from |t - s|^2 (DISTINCT: the
-// points are known to differ)
-template <int KID, bool DISTINCT, class Real>
-__device__ __forceinline__ Real kap_pt(Real t0, Real t1, Real t2, Real s0, Real s1, Real s2, Real p) {
-    if constexpr (KID == H2_K_COSDOT) {
-        const Real x = t0 * s0 + t1 * s1 + t2 * s2;
-        if constexpr (sizeof(Real) == 4) return __cosf(x);
-        else return cos(x);
-    } else {
-        const Real dx = t0 - s0, dy = t1 - s1, dz = t2 - s2;
-        if constexpr (DISTINCT) return kap_distinct<KID>(dx * dx + dy * dy + dz * dz, p);
-        else return kap<KID>(dx * dx + dy * dy + dz * dz, p);
     }
 }
 
@@ -691,29 +631,35 @@ void prepare_tiles(h2_matrix_s *A, int tpt, cudaStream_t s) {
     h2_tree_s *t = A->tree;
     const int nn = t->nnodes;
     if (A->far_tile_tpt != tpt) {
+        A->far_tile_tpt = 0;  // set again only once the tiles exist
         std::vector<int32_t> kh = read_vec(A->k.p, nn, s);
         std::vector<int64_t> fp = read_vec(t->far_ptr.p, nn + 1, s);
         build_tiles(kh, fp, 32 * tpt, A->far_tiles, s);
         A->far_tile_tpt = tpt;
     }
     if (t->near_tile_tpt != tpt) {
+        t->near_tile_tpt = 0;
         std::vector<int32_t> b = read_vec(t->begin.p, nn, s), e = read_vec(t->end.p, nn, s),
                              nc = read_vec(t->nchild.p, nn, s);
         std::vector<int64_t> np = read_vec(t->near_ptr.p, nn + 1, s);
         std::vector<int32_t> cnt(nn);
         for (int i = 0; i < nn; i++) cnt[i] = nc[i] == 0 ? e[i] - b[i] : 0;
-        build_tiles(cnt, np, 32 * tpt, t->near_tiles, s);
-        t->near_tile_tpt = tpt;
-        if (!t->leaf_start.p) {  // int64 starts of every node's points (nearfield point sets)
+        if (!t->leaf_start.p || !t->leaf_count.p) {  // int64 starts of every node's points (nearfield point sets)
             std::vector<int64_t> st(b.begin(), b.end());
             std::vector<int32_t> ct(nn);
             for (int i = 0; i < nn; i++) ct[i] = e[i] - b[i];
-            t->leaf_start.alloc(nn, s);
-            t->leaf_count.alloc(nn, s);
-            H2_CUDA(cudaMemcpyAsync(t->leaf_start.p, st.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-            H2_CUDA(cudaMemcpyAsync(t->leaf_count.p, ct.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            DevBuf<int64_t> ls;
+            DevBuf<int32_t> lc;
+            ls.alloc(nn, s);
+            lc.alloc(nn, s);
+            H2_CUDA(cudaMemcpyAsync(ls.p, st.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            H2_CUDA(cudaMemcpyAsync(lc.p, ct.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice, s));
             H2_CUDA(cudaStreamSynchronize(s));
+            t->leaf_start = std::move(ls);
+            t->leaf_count = std::move(lc);
         }
+        build_tiles(cnt, np, 32 * tpt, t->near_tiles, s);
+        t->near_tile_tpt = tpt;  // last: a failure above leaves the tiles to be rebuilt
     }
 }
 
@@ -737,14 +683,17 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
     prepare_tiles(A, 1, s);
     // one right-hand side: each unordered block pair is evaluated once
     const bool sym = R == 1;
-    if (sym && !t->near_first.p) {
+    if (sym && (!t->near_first.p || !t->far_first.p)) {
         const int nn = t->nnodes;
-        t->near_first.alloc(nn, s);
-        t->far_first.alloc(nn, s);
-        k_list_first<<<blocks_for(nn, 256), 256, 0, s>>>(t->near_ptr.p, t->near_idx.p, nn, t->near_first.p);
-        k_list_first<<<blocks_for(nn, 256), 256, 0, s>>>(t->far_ptr.p, t->far_idx.p, nn, t->far_first.p);
+        DevBuf<int64_t> nf, ff;  // both exist before either is kept
+        nf.alloc(nn, s);
+        ff.alloc(nn, s);
+        k_list_first<<<blocks_for(nn, 256), 256, 0, s>>>(t->near_ptr.p, t->near_idx.p, nn, nf.p);
+        k_list_first<<<blocks_for(nn, 256), 256, 0, s>>>(t->far_ptr.p, t->far_idx.p, nn, ff.p);
         note_launches(1);  // (two launches above)
         H2_LAUNCH("k_list_first");
+        t->near_first = std::move(nf);
+        t->far_first = std::move(ff);
     }
     const int64_t kt = std::max<int64_t>(A->ktotal, 1);
     DevBuf<double> xm, ym, xh, zh;
@@ -812,8 +761,17 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
         H2_CUDA(cudaMemsetAsync(czero.p, 0, t->nnodes * sizeof(float2), s));
         CF[0] = CF[1] = CF[2] = czero.p;
     }
-    // coupling over far pairs: B_ij = K(Xhat_i, Xhat_j) on the fly
-    {
+    // coupling over far pairs: B_ij = K(Xhat_i, Xhat_j), stored or on the fly
+    const bool st = sym && A->stored;
+    if (st) {
+        ProfScope ps(KT_COUPLING_ST, s);
+        if (f64)
+            stored_product<double>(A->far_tiles, A->sk_off.p, A->k.p, A->far_blk.p, A->far_boff.p, xh.p, zh.p,
+                                   t->far_ptr.p, t->far_first.p, t->far_idx.p, s);
+        else
+            stored_product<float>(A->far_tiles, A->sk_off.p, A->k.p, A->far_blk.p, A->far_boff.p, xhf.p, zh.p,
+                                  t->far_ptr.p, t->far_first.p, t->far_idx.p, s);
+    } else {
         ProfScope ps(KT_COUPLING, s);
         if (sym && f64)
             nbody_sym<double>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skc[0].p, A->skc[1].p, A->skc[2].p,
@@ -851,8 +809,16 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
         }
         H2_LAUNCH("k_downward");
     }
-    // nearfield over near leaf pairs: K(X_i, X_j) on the fly
-    {
+    // nearfield over near leaf pairs: K(X_i, X_j), stored or on the fly
+    if (st) {
+        ProfScope ps(KT_NEAR_ST, s);
+        if (f64)
+            stored_product<double>(t->near_tiles, t->leaf_start.p, t->leaf_count.p, A->near_blk.p, A->near_boff.p,
+                                   xm.p, ym.p, t->near_ptr.p, t->near_first.p, t->near_idx.p, s);
+        else
+            stored_product<float>(t->near_tiles, t->leaf_start.p, t->leaf_count.p, A->near_blk.p, A->near_boff.p,
+                                  xmf.p, ym.p, t->near_ptr.p, t->near_first.p, t->near_idx.p, s);
+    } else {
         ProfScope ps(KT_NEAR, s);
         if (sym && f64)
             nbody_sym<double>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xs[0].p, t->xs[1].p,

@@ -25,7 +25,27 @@ void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
     fail(e == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA, buf);
 }
 
+// Allocation-failure injection (h2_debug_fail_alloc): device allocations are
+// counted from the last arming; the one numbered g_fail_at fails as if the
+// stream-ordered allocator had run out of memory.  0 = never.
+static std::atomic<int64_t> g_alloc_count{0};
+static std::atomic<int64_t> g_fail_at{0};
+
+int64_t debug_fail_alloc(int64_t k) {
+    const int64_t made = g_alloc_count.exchange(0);
+    g_fail_at.store(k);
+    return made;
+}
+
 void *dmalloc_bytes(size_t bytes, cudaStream_t s) {
+    const int64_t k = ++g_alloc_count;
+    const int64_t f = g_fail_at.load();
+    if (f > 0 && k == f) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "device allocation of %zu bytes failed: injected failure of allocation %lld",
+                 bytes, (long long)k);
+        fail(H2_ERR_OOM, buf);
+    }
     void *p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
@@ -43,7 +63,8 @@ void dfree_bytes(void *p, cudaStream_t s) {
 
 // -------------------------------------------------------------- profiling
 const char *const kernel_kind_names[KT_COUNT] = {"datareduct", "keval", "cpqr", "id_solve", "upward", "coupling",
-                                                 "downward", "near", "exact_rows", "radix_sort", "lists"};
+                                                 "downward", "near", "exact_rows", "radix_sort", "lists",
+                                                 "fill_blocks", "coupling_stored", "near_stored"};
 namespace {
 struct Pending {
     int kind;

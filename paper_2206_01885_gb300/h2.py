@@ -49,7 +49,10 @@ class _Params(C.Structure):
 
 
 class _ConstructOpts(C.Structure):
-    _fields_ = [("g_bound", C.c_double)]
+    _fields_ = [("g_bound", C.c_double), ("mem_mode", C.c_int), ("mem_fraction", C.c_double)]
+
+
+MEM_MODES = {"on_the_fly": 0, "store": 1, "auto": 2}  # H2_MEM_*
 
 
 def lib():
@@ -81,6 +84,7 @@ def lib():
             "h2_profile": [i32, i32],
             "h2_exact_rows_noalloc": [vp, i32, vp, vp, vp, i64, vp, vp],
             "h2_construct_batched": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
+            "h2_debug_fail_alloc": [i64, C.POINTER(i64)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -214,9 +218,14 @@ class H2Matrix(_Handle):
     """h2_construct: nested bases (Algorithm 2); .matvec applies K~."""
 
     def __init__(self, tree: Tree, hidr: Hidr, kernel, kparams=(), id_tol: float = 1e-6, precision="fp64",
-                 stream=None, g_bound: float = 0.0, _handle=None):
+                 stream=None, g_bound: float = 0.0, mem_mode: str = "on_the_fly", mem_fraction: float = 0.0,
+                 _handle=None):
         """g_bound = f > 1 bounds ||G||_max by f through exchanges after the
-        QR (h2_construct_ex); 0 is the plain column-pivoted ID."""
+        QR (h2_construct_ex); 0 is the plain column-pivoted ID.  mem_mode:
+        "on_the_fly" (coupling and nearfield blocks evaluated in every
+        product), "store" (evaluated once and kept; single-vector products
+        read them) or "auto" (stored when they fit in the float64 form);
+        mem_fraction: the share of free device memory they may take (0: 0.5)."""
         if _handle is not None:  # built by construct_batched
             self._h = _handle
             self.tree = tree
@@ -224,7 +233,7 @@ class H2Matrix(_Handle):
         h = C.c_void_p()
         kp = _kparams(kparams)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        opts = _ConstructOpts(float(g_bound))
+        opts = _ConstructOpts(float(g_bound), MEM_MODES[mem_mode], float(mem_fraction))
         _check("h2_construct_ex", lib().h2_construct_ex(tree.handle, hidr.handle, _kid(kernel), kp, float(id_tol),
                                                          prec, C.byref(opts), _stream(stream), C.byref(h)))
         self._h = h.value
@@ -440,6 +449,14 @@ def kernel_times() -> dict:
     st = _global_stats()
     st.pop("launches_total", None)
     return st
+
+
+def debug_fail_alloc(k: int) -> int:
+    """Arm the library's k-th device allocation from now on to fail with
+    H2_ERR_OOM (0 disarms); returns the allocations made since the last call."""
+    made = C.c_int64(0)
+    _check("h2_debug_fail_alloc", lib().h2_debug_fail_alloc(int(k), C.byref(made)))
+    return made.value
 
 
 def launches_total() -> int:

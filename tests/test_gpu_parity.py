@@ -15,6 +15,7 @@ import pytest
 
 from oracle import h2_oracle as O
 from paper_2206_01885_gb300 import inputs as I
+from rowcheck import assert_rows_close
 
 pytestmark = pytest.mark.gpu
 
@@ -143,7 +144,7 @@ def test_surface_reduction_builds_accurate_h2(H2):
     y = A.matvec(dev(z)).cpu().numpy()
     o = O.tree_build(pts, q)
     yo = O.H2(o, O.Hidr(o, g, g, method="surface"), "coulomb", (), eps).matvec(z)
-    assert np.linalg.norm(y - yo) <= 1e-12 * np.linalg.norm(yo)
+    assert_rows_close(y, yo, 1e-12, "surface H2 vs oracle")
     yd = O.dense_matvec(pts, "coulomb", (), z)
     assert np.linalg.norm(y - yd) <= 10 * eps * np.linalg.norm(yd)
 
@@ -202,7 +203,7 @@ def test_construct_and_matvec_fp64(H2, name, d, n, q, kern, kp, eps, g):
     assert abs(max(1.0, st["g_max"]) - umax) <= 1e-6 * umax
     y = A.matvec(dev(z)).cpu().numpy()
     yo = OH.matvec(z)
-    assert np.linalg.norm(y - yo) <= 1e-12 * np.linalg.norm(yo)
+    assert_rows_close(y, yo, 1e-12, f"{name} float64 H2 vs oracle")
     yd = O.dense_matvec(pts, kern, kp, z)
     assert np.linalg.norm(y - yd) / np.linalg.norm(yd) <= 10 * eps
     # host-pointer matvec is the same product
@@ -293,7 +294,7 @@ def test_construct_and_matvec_mixed(H2, name, d, n, q, kern, kp, eps, g):
     assert np.linalg.norm(y - yd) / np.linalg.norm(yd) <= 10 * eps
     o, oh, OH = O.build_h2(pts, kern, kp, q, eps, g, g)
     yo = OH.matvec(z)
-    assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps
+    assert_rows_close(y, yo, 10 * eps, f"{name} mixed H2 vs oracle float64 H2")
     # structure: sorted skeletons inside the candidates, identity rows of U
     ranks, nc = A.get("rank"), A.get("ncand")
     skel, U = A.get("skel"), A.get("U")
@@ -348,7 +349,7 @@ def test_matvec_multi_rhs(H2, name, d, n, q, kern, kp, eps, g, prec):
     for j in [0, 20]:
         yo = OH.matvec(Z[:, j])
         lim = 1e-12 if prec == "fp64" else 10 * eps
-        assert np.linalg.norm(Y[:, j] - yo) <= lim * np.linalg.norm(yo), j
+        assert_rows_close(Y[:, j], yo, lim, f"{name} column {j} vs oracle")
         yd = O.dense_matvec(pts, kern, kp, Z[:, j])
         assert np.linalg.norm(Y[:, j] - yd) <= 10 * eps * np.linalg.norm(yd), j
     # float32 vectors in and out

@@ -12,6 +12,7 @@ import pytest
 
 from oracle import h2_oracle as O
 from paper_2206_01885_gb300 import inputs as I
+from rowcheck import assert_rows_close
 
 from test_gpu_parity import HIDR_CASES, SURFACE_CASES, _hidr_points, dev
 
@@ -70,9 +71,6 @@ def test_il_reduce_h2_matvec(H2, prec, eps, g):
     y = A.matvec(dev(z)).cpu().numpy()
     o = O.tree_build(pts, q)
     yo = O.H2(o, O.Hidr(o, g, g, il_reduce=True), "coulomb", (), eps).matvec(z)
-    if prec == "fp64":
-        assert np.linalg.norm(y - yo) <= 1e-12 * np.linalg.norm(yo)
-    else:
-        assert np.linalg.norm(y - yo) <= 10 * eps * np.linalg.norm(yo)
+    assert_rows_close(y, yo, 1e-12 if prec == "fp64" else 10 * eps, f"{prec} H2 with IL reduction vs oracle")
     yd = O.dense_matvec(pts, "coulomb", (), z)
     assert np.linalg.norm(y - yd) <= 10 * eps * np.linalg.norm(yd)

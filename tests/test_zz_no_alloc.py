@@ -67,3 +67,28 @@ def test_noalloc_rejects_trees_above_its_limit(H2):
     assert _noalloc(H2, t, "coulomb", (), z, rows, out) == 1  # H2_ERR_INVALID_ARG
     assert b"1048576" in H2.lib().h2_last_error()
     t.free()
+
+
+def test_noalloc_refuses_host_pointers_without_launching(H2):
+    n = 5000
+    pts = I.uniform_cube(n, 3, seed=521)
+    dev = torch.device("cuda")
+    t = H2.Tree(torch.from_numpy(pts).to(dev), 128)
+    z_d = torch.from_numpy(I.standard_normal(n, seed=522)).to(dev)
+    rows_d = torch.from_numpy(I.sample_rows(n, 16, seed=523)).to(dev)
+    out_d = torch.zeros(16, dtype=torch.float64, device=dev)
+    z_h = torch.from_numpy(I.standard_normal(n, seed=522))          # pageable host memory
+    out_h = torch.zeros(16, dtype=torch.float64).pin_memory()       # pinned host memory
+    torch.cuda.synchronize()
+    before = H2.launches_total()
+    assert _noalloc(H2, t, "coulomb", (), z_h, rows_d, out_d) == 1  # H2_ERR_INVALID_ARG
+    assert b"z" in H2.lib().h2_last_error()
+    assert _noalloc(H2, t, "coulomb", (), z_d, rows_d, out_h) == 1
+    assert b"out" in H2.lib().h2_last_error()
+    assert H2.launches_total() == before  # refused before any kernel launch
+    # the context is still usable: a valid call right after succeeds
+    assert _noalloc(H2, t, "coulomb", (), z_d, rows_d, out_d) == 0, H2.lib().h2_last_error()
+    torch.cuda.synchronize()
+    want = H2.exact_rows(t, "coulomb", (), z_d, rows_d).cpu().numpy()
+    assert np.allclose(out_d.cpu().numpy(), want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    t.free()

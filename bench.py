@@ -78,9 +78,11 @@ WORKLOADS = {
     "gmix2m_mixed": dict(n=1 << 21, d=2, kernel="gaussian", kparams=(0.2,), q=128, eps=1e-6, prec="mixed", seed=3,
                          rows=1000, points="gmix2d", g=20),
     # 8,388,608 points on the unit sphere, 16 float32 right-hand sides (the
-    # sampled error is taken on the first column)
+    # sampled error is taken on the first column); tau = 1/2 with the
+    # interaction-list reduction, g = 6: within 10 eps (Algorithm 1 as printed
+    # at tau = 7/10 gives 1.6e-4 here)
     "sphere8m_mixed16": dict(n=1 << 23, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-6, prec="mixed", seed=5,
-                             rows=2000, points="sphere", g=8, rhs=16),
+                             rows=2000, points="sphere", g=6, rhs=16, tau=(1, 2), il_reduce=True),
 }
 
 
@@ -120,11 +122,12 @@ def workload_rhs(wl, n, seed):
 MIN_SQ = {3: 8, 2: 5}
 
 # Peaks: HBM and bf16 are the measured copy / cuBLAS figures of this GPU pool;
-# the float64 and float32 ALU peaks are derived from 152 SMs at 2070 MHz:
-# float64 1.25 TFLOP/s (the GB300 nominal dense rate), float32 152 x 128 lanes
-# x 2 flops x 2.07 GHz = 80.5 TFLOP/s.
-PEAK_FP64_TFLOPS = 1.25
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# the float64 and float32 ALU peaks are measured once per run by the library's
+# fused multiply-add probe (h2_fma_peak), with the nominal figures beside them:
+# float64 1.25 TFLOP/s (the GB300 dense rate), float32 152 SMs x 128 lanes x 2
+# flops x 2.07 GHz = 80.5 TFLOP/s.
+NOMINAL_FP64_TFLOPS = 1.25
+NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOPS_PER_PAIR = 11  # 3 sub, 3 mul/add for r^2 (5 flops), 1 rsqrt, 1 fma accumulate (2 flops)
 # DRAM bytes per algorithmic unit (ncu dram__bytes_read.sum + dram__bytes_write.sum
 # over the timed step of the 262,144-point workloads): float64 CPQR bytes per QR
@@ -218,7 +221,19 @@ def aggregate_value(n_per_rank: int, world: int, ms_per_step: float) -> float:
 
 
 # ----------------------------------------------------------- GPU arm
-def measure_form(args, wl, rank, world, dev, with_e2e):
+def alu_peaks(h2, dev):
+    """float64 / float32 multiply-add throughput measured on this GPU (best of
+    ten probe runs, clocks sampled meanwhile), with the nominal figures."""
+    sampler = ClockSampler(dev)
+    sampler.start()
+    runs = [h2.fma_peak() for _ in range(10)]
+    clocks = sampler.stop()
+    return {"fp64_tflops": max(r[0] for r in runs), "fp32_tflops": max(r[1] for r in runs),
+            "fp64_nominal_tflops": NOMINAL_FP64_TFLOPS, "fp32_nominal_tflops": NOMINAL_FP32_TFLOPS,
+            "clocks": clocks, "probe": "h2_fma_peak: 8 independent FMA chains per thread, 8 CTAs x 256 per SM"}
+
+
+def measure_form(args, wl, rank, world, dev, with_e2e, alu=None):
     """W warm-up and K timed steps of one form (precision + tolerance) on this
     rank's problem; returns the per-form measurements."""
     import torch
@@ -330,14 +345,29 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
     # DataReduct: the bytes it must read at least once (every entry of its input
     # sets T_i: a 4-byte label and d float64 coordinates), against HBM.
     fp64 = wl["prec"] == "fp64"
-    alu_peak = PEAK_FP64_TFLOPS if fp64 else PEAK_FP32_TFLOPS
+    if alu is None:
+        alu_peak, alu_src = (NOMINAL_FP64_TFLOPS, "nominal GB300 float64 1.25 TFLOP/s") if fp64 else \
+            (NOMINAL_FP32_TFLOPS, "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz")
+    elif fp64:
+        alu_peak, alu_src = alu["fp64_tflops"], "measured float64 FMA throughput (h2_fma_peak)"
+    else:
+        alu_peak, alu_src = alu["fp32_tflops"], "measured float32 FMA throughput (h2_fma_peak)"
     peaks, peak_kind = measured_peaks()
+    # the U passes read U once (u_entries elements) and the vectors they map:
+    # upward reads the children's or leaves' entries and writes xh; downward
+    # reads zh and read-modify-writes the children's zh or y (float64 vectors)
+    esz = 8 if fp64 else 4
+    kt, ut = mat_i["k_total"], mat_i["u_entries"]
     work = {  # kernel -> (bound, algorithmic units per step)
         "cpqr": ("alu", qr_flops),
         "coupling": ("alu", coupling_pairs * FLOPS_PER_PAIR),
         "near": ("alu", near_pairs * FLOPS_PER_PAIR),
         "keval": ("alu", block_evals * FLOPS_PER_PAIR),
         "datareduct": ("hbm", hidr_i["t_total"] * (4 + 8 * d)),
+        "upward": ("hbm", ut * esz + 8 * (n + 2 * kt)),
+        "downward": ("hbm", ut * esz + 8 * (2 * n + 3 * kt)),
+        "coupling_stored": ("hbm", mat_i.get("stored_far_bytes", 0)),
+        "near_stored": ("hbm", mat_i.get("stored_near_bytes", 0)),
     }
     per_kernel = {}
     for k, v in ktimes.items():
@@ -370,13 +400,12 @@ def measure_form(args, wl, rank, world, dev, with_e2e):
                 "peak_source": f"{peak_kind} (copy bandwidth)",
                 "work_per_launch": work[dom][1] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
     elif dom in work:
-        peak_src = "derived: GB300 nominal float64 1.25 TFLOP/s" if fp64 else \
-            "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+        peak_src = alu_src
         achieved = work[dom][1] / launches_per_step / (dom_ms_per_launch * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak,
                 "traffic": traffic_ratio * work[dom][1] / launches_per_step if traffic_ratio else None,
-                "peak_source": peak_src,
+                "peak_source": peak_src, "peak_nominal": NOMINAL_FP64_TFLOPS if fp64 else NOMINAL_FP32_TFLOPS,
                 "work_per_launch": work[dom][1] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "TFLOP/s", "frac": None,
@@ -501,8 +530,10 @@ def gpu_arm(args, wl, rank, world, dev):
 
     from paper_2206_01885_gb300 import build as B
     B.build()
+    from paper_2206_01885_gb300 import h2
     torch.cuda.set_device(dev)
-    prim = measure_form(args, wl, rank, world, dev, with_e2e=True)
+    alu = alu_peaks(h2, dev)  # once, outside the timed steps
+    prim = measure_form(args, wl, rank, world, dev, with_e2e=True, alu=alu)
     R = wl.get("rhs", 1)
     result = {
         "metric": METRIC, "value": prim["value"], "unit": "points/s", "n_gpus": world, "steps": args.steps,
@@ -512,9 +543,10 @@ def gpu_arm(args, wl, rank, world, dev):
                 + ("standard-normal right-hand side)" if R == 1 else f"{R} float32 standard-normal right-hand sides)"),
     }
     result.update({k: v for k, v in prim.items() if k not in ("value", "ms_per_step")})
+    result["alu_peaks"] = alu
     other = wl.get("compare")
     if other and not args.no_compare:
-        sec = measure_form(args, dict(WORKLOADS[other], name=other), rank, world, dev, with_e2e=False)
+        sec = measure_form(args, dict(WORKLOADS[other], name=other), rank, world, dev, with_e2e=False, alu=alu)
         result["compare"] = {"form": other, "value": sec["value"], "ms_per_step": sec["ms_per_step"],
                              "matvec_repeat": sec["matvec_repeat"],
                              "rel_err": sec["rel_err"], "config": sec["config"], "phases_ms": sec["phases_ms"],
@@ -604,7 +636,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube1m_fp64", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-sample", type=int, default=131072)
+    ap.add_argument("--cpu-sample", type=int, default=65536)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the second (mixed) form")
     args = ap.parse_args()

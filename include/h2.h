@@ -426,6 +426,14 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap);
  * Off by default. */
 h2_status h2_profile(int enable, int reset);
 
+/* Measured arithmetic peaks of the current device, the denominators of the
+ * roofline fractions of ALU-bound kernels (the paper has no counterpart): a
+ * kernel of 8 independent fused multiply-add chains per thread, 8 CTAs of
+ * 256 threads per SM, timed with CUDA events after a warm-up launch; a
+ * multiply-add counts as 2 flops.  Either output may be NULL (not both).
+ * Synchronises `stream`.  Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
+h2_status h2_fma_peak(double *fp64_tflops, double *fp32_tflops, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -759,6 +759,13 @@ h2_status h2_profile(int enable, int reset) {
     return guard([&] { profile_set(enable != 0, reset != 0); });
 }
 
+h2_status h2_fma_peak(double *fp64_tflops, double *fp32_tflops, void *stream) {
+    return guard([&] {
+        H2_REQUIRE(fp64_tflops || fp32_tflops, "NULL argument");
+        fma_peaks(fp64_tflops, fp32_tflops, static_cast<cudaStream_t>(stream));
+    });
+}
+
 h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
     return guard([&] {
         H2_REQUIRE(json && cap > 0, "NULL argument");

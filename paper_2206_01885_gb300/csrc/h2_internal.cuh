@@ -38,7 +38,9 @@ long long launches_total();
 // ----------------------------------------------------------- device memory
 void *dmalloc_bytes(size_t bytes, cudaStream_t s);
 void dfree_bytes(void *p, cudaStream_t s);
-int64_t debug_fail_alloc(int64_t k);  // arm the k-th allocation to fail; returns the count since the last arming
+int64_t debug_fail_alloc(int64_t k);
+// measured float64 / float32 fused multiply-add throughput of this device (TFLOP/s)
+void fma_peaks(double *fp64_tflops, double *fp32_tflops, cudaStream_t s);  // arm the k-th allocation to fail; returns the count since the last arming
 
 // Owning device array, released on the stream it was allocated on.
 template <class T>

@@ -313,3 +313,59 @@ void radix_sort(uint64_t *keys, int32_t *vals, int64_t n, int nbits, cudaStream_
 }
 
 }  // namespace h2
+
+// ------------------------------------------------------- ALU peak probe
+namespace h2 {
+namespace {
+// Each thread runs FP_CHAINS independent multiply-add chains (enough
+// instruction-level parallelism to cover the pipe latency); the results are
+// stored so that nothing is optimised away.
+constexpr int FP_CHAINS = 8;
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, T a, T b, T *sink) {
+    T x[FP_CHAINS];
+#pragma unroll
+    for (int c = 0; c < FP_CHAINS; c++) x[c] = (T)(threadIdx.x + c);
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int c = 0; c < FP_CHAINS; c++) x[c] = fma(x[c], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < FP_CHAINS; c++) s += x[c];
+    sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <class T>
+double probe_tflops(int sms, int iters, cudaStream_t s) {
+    const int ctas = sms * 8, threads = 256;
+    DevBuf<T> sink;
+    sink.alloc((size_t)ctas * threads, s);
+    cudaEvent_t e0, e1;
+    H2_CUDA(cudaEventCreate(&e0));
+    H2_CUDA(cudaEventCreate(&e1));
+    // a: slightly below one, b: small, so the chains stay finite
+    k_fma_probe<T><<<ctas, threads, 0, s>>>(iters / 10, (T)0.999999, (T)1e-7, sink.p);  // warm-up
+    H2_LAUNCH("k_fma_probe");
+    H2_CUDA(cudaEventRecord(e0, s));
+    k_fma_probe<T><<<ctas, threads, 0, s>>>(iters, (T)0.999999, (T)1e-7, sink.p);
+    H2_LAUNCH("k_fma_probe");
+    H2_CUDA(cudaEventRecord(e1, s));
+    H2_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double flops = 2.0 * FP_CHAINS * (double)iters * ctas * threads;
+    return flops / (ms * 1e-3) / 1e12;
+}
+}  // namespace
+
+void fma_peaks(double *fp64_tflops, double *fp32_tflops, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    H2_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (fp64_tflops) *fp64_tflops = probe_tflops<double>(sms, 4096, s);
+    if (fp32_tflops) *fp32_tflops = probe_tflops<float>(sms, 65536, s);
+}
+}  // namespace h2

@@ -85,6 +85,7 @@ def lib():
             "h2_exact_rows_noalloc": [vp, i32, vp, vp, vp, i64, vp, vp],
             "h2_construct_batched": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
             "h2_debug_fail_alloc": [i64, C.POINTER(i64)],
+            "h2_fma_peak": [C.POINTER(dbl), C.POINTER(dbl), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -457,6 +458,13 @@ def debug_fail_alloc(k: int) -> int:
     made = C.c_int64(0)
     _check("h2_debug_fail_alloc", lib().h2_debug_fail_alloc(int(k), C.byref(made)))
     return made.value
+
+
+def fma_peak(stream=None):
+    """(float64, float32) fused multiply-add throughput of this GPU, TFLOP/s."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    _check("h2_fma_peak", lib().h2_fma_peak(C.byref(a), C.byref(b), _stream(stream)))
+    return a.value, b.value
 
 
 def launches_total() -> int:

@@ -33,4 +33,4 @@ def test_generators_small():
 
 def test_fixed_g_skips_the_calibration():
     assert bench.oracle_g(bench.WORKLOADS["gmix2m_fp64"]) == 20
-    assert bench.oracle_g(bench.WORKLOADS["sphere8m_mixed16"]) == 8
+    assert bench.oracle_g(bench.WORKLOADS["sphere8m_mixed16"]) == 6

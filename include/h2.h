@@ -241,6 +241,15 @@ typedef struct {
                             construction) the stored blocks may take, in (0, 1];
                             0 means 0.5.  STORE above it fails with H2_ERR_OOM;
                             AUTO above it stays on the fly                      */
+    int fp64_products;   /* float64 form, 3D Coulomb, one right-hand side: 0 (default)
+                            evaluates the on-the-fly coupling and nearfield
+                            products in float-float arithmetic on the float32
+                            units (values hi + lo of two float32, relative error
+                            of an evaluation below 2^-43, offsets from the cell
+                            centres carried to ~2^-48 of a cell width); 1 keeps
+                            them in float64 arithmetic.  The construction, the
+                            stored blocks and every other product are float64
+                            either way                                          */
 } h2_construct_opts;
 
 /* h2_construct with options (opts may be NULL: exactly h2_construct).

@@ -1129,6 +1129,7 @@ void matrix_rebind(h2_matrix_s *A, cudaStream_t s) {
     A->near_blk.rebind(s);
     A->far_boff.rebind(s);
     A->near_boff.rebind(s);
+    for (int k = 0; k < 3; k++) A->skdf[k].rebind(s);
 }
 
 }  // namespace h2

@@ -175,6 +175,13 @@ struct h2_tree_s {
     h2::DevBuf<int64_t> near_first, far_first;  // first list entry of each node with index >= its own
     h2::DevBuf<int64_t> leaf_start;  // begin of every node as int64 (nearfield point sets)
     h2::DevBuf<int32_t> leaf_count;  // end - begin of every node
+    // coordinates of the float64 form's float-float Coulomb products (3D, built
+    // on first use): integer doubled cell centres A of the nodes (centre =
+    // lo + A u, u = side / 2^(B+1)), and every point as integer cells K and a
+    // float-pair residual in units of a power of two u' (three float4 a point)
+    bool df_ready = false;
+    h2::DevBuf<int32_t> cellA[3];
+    h2::DevBuf<float4> xcell;
 };
 
 struct h2_hidr_s {
@@ -231,6 +238,12 @@ struct h2_matrix_s {
     h2::DevBuf<int64_t> far_boff, near_boff;
     int64_t stored_far_bytes = 0, stored_near_bytes = 0, stored_bytes_plan = 0;
     double ms_blocks = 0;
+    // float64 form: Coulomb products in float-float arithmetic unless
+    // fp64_products is set (then plain float64); skeleton offsets from their
+    // node's centre as hi + lo, built on first use
+    bool fp64_products = false;
+    bool df_ready = false;
+    h2::DevBuf<float2> skdf[3];
 };
 
 // a matvec recorded as a CUDA graph (h2_matvec_graph_create)
@@ -264,6 +277,13 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x_dev, void *y_dev, int nrhs,
                        cudaStream_t s);
 void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z_dev, const int64_t *rows_dev,
                      int64_t nrows, double *out_dev, cudaStream_t s);
+// float-float Coulomb products of the float64 form (3D)
+void ensure_df_tree(h2_tree_s *t, cudaStream_t s);
+void ensure_df_matrix(h2_matrix_s *A, cudaStream_t s);
+void split_vector(const double *v, int64_t n, float2 *out, cudaStream_t s);
+void nbody_sym_df(const h2_tree_s *t, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count,
+                  const DevBuf<float2> *X, const float2 *w, double *out, const int64_t *lptr, const int64_t *lfirst,
+                  const int32_t *lidx, cudaStream_t s);
 // evaluate and keep the coupling and nearfield blocks (mode H2_MEM_STORE:
 // H2_ERR_OOM above `fraction` of the free memory; H2_MEM_AUTO: keep them
 // only when they fit)

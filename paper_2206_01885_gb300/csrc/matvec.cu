@@ -732,6 +732,17 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
         }
         H2_LAUNCH("k_upward");
     }
+    // float-pair copies of the weights for the float64 form's float-float
+    // Coulomb products (3D, one right-hand side, blocks not stored)
+    const bool df = f64 && sym && !A->stored && !A->fp64_products && A->kid == H2_K_COULOMB && d == 3;
+    DevBuf<float2> xm2, xh2;
+    if (df) {
+        ensure_df_matrix(A, s);
+        xm2.alloc(n, s);
+        xh2.alloc(kt, s);
+        split_vector(xm.p, n, xm2.p, s);
+        split_vector(xh.p, kt, xh2.p, s);
+    }
     // float32 copies of the weights for the float32 N-body kernels
     DevBuf<float> xmf, xhf;
     if (!f64) {
@@ -773,7 +784,10 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
                                   t->far_ptr.p, t->far_first.p, t->far_idx.p, s);
     } else {
         ProfScope ps(KT_COUPLING, s);
-        if (sym && f64)
+        if (df)
+            nbody_sym_df(t, A->far_tiles, A->sk_off.p, A->k.p, A->skdf, xh2.p, zh.p, t->far_ptr.p, t->far_first.p,
+                         t->far_idx.p, s);
+        else if (sym && f64)
             nbody_sym<double>(A->kid, A->far_tiles, A->sk_off.p, A->k.p, A->skc[0].p, A->skc[1].p, A->skc[2].p,
                               nullptr, nullptr, nullptr, xh.p, zh.p, t->far_ptr.p, t->far_first.p, t->far_idx.p, d,
                               A->kp[0], s);
@@ -820,7 +834,10 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
                                   xmf.p, ym.p, t->near_ptr.p, t->near_first.p, t->near_idx.p, s);
     } else {
         ProfScope ps(KT_NEAR, s);
-        if (sym && f64)
+        if (df)
+            nbody_sym_df(t, t->near_tiles, t->leaf_start.p, t->leaf_count.p, nullptr, xm2.p, ym.p, t->near_ptr.p,
+                         t->near_first.p, t->near_idx.p, s);
+        else if (sym && f64)
             nbody_sym<double>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xs[0].p, t->xs[1].p,
                               t->xs[2].p, nullptr, nullptr, nullptr, xm.p, ym.p, t->near_ptr.p, t->near_first.p,
                               t->near_idx.p, d, A->kp[0], s);

@@ -66,6 +66,13 @@ WORKLOADS = {
                                 compare="cube128k_mixed_store"),
     "cube128k_mixed_store": dict(n=1 << 17, d=3, kernel="coulomb", kparams=(), q=256, eps=3e-6, prec="mixed",
                                  seed=2, rows=1000, tau=(1, 2), il_reduce=True, g=6, mem_mode="store", mv_reps=20),
+    # 64 independent problems of uneven sizes (n log-uniform in [2e4, 5e5],
+    # uniform cube or unit sphere, Coulomb / Gaussian h = 0.5 / multiquadric),
+    # mixed form at eps = 1e-5, leaf size per point set and kernel from the
+    # autotuner, all constructions in one batched call
+    "batched64_mixed": dict(kind="batched", count=64, nmin=20000, nmax=500000, n=None, d=3, kernel="mixed set",
+                            kparams=(), q=None, eps=1e-5, prec="mixed", seed=4, rows=100, tau=(1, 2),
+                            il_reduce=True, g=6),
     # the paper's second dataset: three unit spheres on a unit equilateral triangle
     "spheres3_1m_fp64": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-8, prec="fp64", seed=6,
                              rows=1000, points="spheres3", compare="spheres3_1m_mixed"),
@@ -83,6 +90,14 @@ WORKLOADS = {
     # at tau = 7/10 gives 1.6e-4 here)
     "sphere8m_mixed16": dict(n=1 << 23, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-6, prec="mixed", seed=5,
                              rows=2000, points="sphere", g=6, rhs=16, tau=(1, 2), il_reduce=True),
+    # 1,048,576 sphere points, 16 right-hand sides: the nearfield on the CUDA
+    # cores (default) and on the tensor cores (tcgen05, 3 x tf32 split)
+    "sphere1m_mixed16": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-6, prec="mixed", seed=5,
+                             rows=1000, points="sphere", g=6, rhs=16, tau=(1, 2), il_reduce=True,
+                             compare="sphere1m_mixed16_tc"),
+    "sphere1m_mixed16_tc": dict(n=1 << 20, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-6, prec="mixed",
+                                seed=5, rows=1000, points="sphere", g=6, rhs=16, tau=(1, 2), il_reduce=True,
+                                tensor_core_products=True),
 }
 
 
@@ -280,7 +295,8 @@ def measure_form(args, wl, rank, world, dev, with_e2e, alu=None):
             ex = h2.exact_rows(t, wl["kernel"], wl["kparams"], z_in, rows_in, stream=side)
         hd = h2.Hidr(t, g, g, il_reduce=wl.get("il_reduce", False))
         A = h2.H2Matrix(t, hd, wl["kernel"], wl["kparams"], wl["eps"], wl["prec"],
-                        mem_mode=wl.get("mem_mode", "on_the_fly"))
+                        mem_mode=wl.get("mem_mode", "on_the_fly"),
+                        tensor_core_products=wl.get("tensor_core_products", False))
         y = A.matvec(zm_in)
         stream.wait_stream(side)
         ex.record_stream(stream)
@@ -434,7 +450,8 @@ def measure_form(args, wl, rank, world, dev, with_e2e, alu=None):
             job.start()
             hd2 = h2.Hidr(t2, g, g, il_reduce=wl.get("il_reduce", False))
             A2 = h2.H2Matrix(t2, hd2, wl["kernel"], wl["kparams"], wl["eps"], wl["prec"],
-                             mem_mode=wl.get("mem_mode", "on_the_fly"))
+                             mem_mode=wl.get("mem_mode", "on_the_fly"),
+                             tensor_core_products=wl.get("tensor_core_products", False))
             y_h = A2.matvec(zm_h.numpy())
             job.join()
             err_h = h2.sampled_error(ex_box["ex"], y_h if R == 1 else np.ascontiguousarray(y_h[:, 0], np.float64),
@@ -470,6 +487,7 @@ def measure_form(args, wl, rank, world, dev, with_e2e, alu=None):
                    "kernel": wl["kernel"], "leaf_size": wl["q"], "id_tol": wl["eps"], "precision": wl["prec"],
                    "g": g, "r1": g ** d, "r2": g ** d, "tau": "%d/%d" % wl.get("tau", (7, 10)),
                    "il_reduce": bool(wl.get("il_reduce", False)),
+                   "tensor_core_products": bool(wl.get("tensor_core_products", False)),
                    "sampled_rows": len(rows), "rhs": R,
                    "l2": "flushed (256 MB write) between timed steps, outside the timed interval",
                    "parallelism": f"{world} independent problem(s), one per GPU"},
@@ -525,6 +543,133 @@ def repeated_products(wl, h2, t, hd, A, x, stream, peaks):
     return out
 
 
+BATCH_KERNELS = [("coulomb", ()), ("gaussian", (0.5,)), ("multiquadric", ())]
+
+
+def measure_batched(args, wl, rank, world, dev, alu):
+    """The batched configuration: W warm-up and K timed steps, a step being
+    every problem's tree and HiDR, one h2_construct_batched over all of them,
+    and one product per problem.  Outside the timed steps: the leaf sizes (the
+    autotuner on a 200,000-point sample of each point set and kernel), the
+    one-by-one construction time for comparison, and the sampled error of
+    every problem against exact float64 sums."""
+    import torch
+
+    from paper_2206_01885_gb300 import h2
+    probs = I.batched_problems(wl["count"], wl["nmin"], wl["nmax"], seed=problem_seed(wl["seed"], rank))
+    tau, g, eps, ilr = wl["tau"], wl["g"], wl["eps"], wl["il_reduce"]
+    t0 = time.perf_counter()
+    qsel = {}
+    for kind in ("cube", "sphere"):
+        sample = I.uniform_cube(200000, 3, seed=11) if kind == "cube" else I.sphere_surface(200000, seed=11)
+        for ki, (kern, kp) in enumerate(BATCH_KERNELS):
+            q, _ = h2.autotune_leaf(sample, (64, 128, 256), g=g, kernel=kern, kparams=kp, id_tol=eps,
+                                    precision=wl["prec"], reps=1)
+            qsel[(kind, ki)] = q
+    tune_ms = (time.perf_counter() - t0) * 1e3
+    pts_d, z_d = [], []
+    for n, kind, ki, ps in probs:
+        pts = I.uniform_cube(n, 3, seed=ps) if kind == "cube" else I.sphere_surface(n, seed=ps)
+        pts_d.append(torch.from_numpy(pts).to(dev))
+        z_d.append(torch.from_numpy(I.standard_normal(n, seed=ps + 7)).to(dev))
+    ntot = sum(p[0] for p in probs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        ts = [h2.Tree(pts_d[a], qsel[(kind, ki)], tau=tau) for a, (n, kind, ki, ps) in enumerate(probs)]
+        hs = [h2.Hidr(t, g, g, il_reduce=ilr) for t in ts]
+        mats = h2.construct_batched([(ts[a], hs[a], BATCH_KERNELS[ki][0], BATCH_KERNELS[ki][1], eps, wl["prec"])
+                                     for a, (n, kind, ki, ps) in enumerate(probs)])
+        ys = [mats[a].matvec(z_d[a]) for a in range(len(probs))]
+        return ts, hs, mats, ys
+
+    def free(out):
+        ts, hs, mats, ys = out
+        for o in mats + hs + ts:
+            o.free()
+
+    for _ in range(args.warmup):
+        free(step())
+    torch.cuda.synchronize()
+    h2.profile(True, True)
+    launches0 = h2.launches_total()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    step_ms, last = [], None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = step()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if last is not None:
+            free(last)
+        last = out
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = h2.launches_total() - launches0
+    ktimes = h2.kernel_times()
+    h2.profile(False, False)
+    ts, hs, mats, ys = last
+    # batched against one-by-one construction (device time from the matrices' own events)
+    batched_ms = sum(json.loads(m.stats())["ms_construct"] for m in mats)
+    torch.cuda.synchronize()
+    c0 = time.perf_counter()
+    one = [h2.H2Matrix(ts[a], hs[a], BATCH_KERNELS[ki][0], BATCH_KERNELS[ki][1], eps, wl["prec"])
+           for a, (n, kind, ki, ps) in enumerate(probs)]
+    torch.cuda.synchronize()
+    one_by_one_ms = (time.perf_counter() - c0) * 1e3
+    for m in one:
+        m.free()
+    c0 = time.perf_counter()
+    again = h2.construct_batched([(ts[a], hs[a], BATCH_KERNELS[ki][0], BATCH_KERNELS[ki][1], eps, wl["prec"])
+                                  for a, (n, kind, ki, ps) in enumerate(probs)])
+    torch.cuda.synchronize()
+    batched_wall_ms = (time.perf_counter() - c0) * 1e3
+    for m in again:
+        m.free()
+    # sampled error of every problem against exact float64 sums
+    errs = []
+    for a, (n, kind, ki, ps) in enumerate(probs):
+        rows = torch.from_numpy(I.sample_rows(n, wl["rows"], seed=ps + 9)).to(dev)
+        ex = h2.exact_rows(ts[a], BATCH_KERNELS[ki][0], BATCH_KERNELS[ki][1], z_d[a], rows)
+        errs.append(float(h2.sampled_error(ex, ys[a], rows).item()))
+    qr_flops = sum(json.loads(m.stats())["qr_flops"] for m in mats)
+    free(last)
+    ms_per_step = max_over_ranks(sum(step_ms), world, dev) / args.steps
+    dom = max((k for k in ktimes if ktimes[k]["ms"] > 0), key=lambda k: ktimes[k]["ms"])
+    per_kernel = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+                  for k, v in ktimes.items() if v["launches"]}
+    roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "ms_per_launch": ktimes[dom]["ms"] / max(1, ktimes[dom]["launches"])}
+    if dom == "cpqr":
+        ach = qr_flops * args.steps / (ktimes[dom]["ms"] * 1e-3) / 1e12
+        roof.update({"bound": "alu", "achieved": ach, "peak": alu["fp32_tflops"], "unit": "TFLOP/s",
+                     "frac": ach / alu["fp32_tflops"], "peak_source": "measured float32 FMA throughput"})
+    return {
+        "value": world * ntot / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
+        "config": {"workload": args.workload, "problems": len(probs), "n_total": ntot,
+                   "n_range": [min(p[0] for p in probs), max(p[0] for p in probs)],
+                   "point_sets": {"cube": sum(p[1] == "cube" for p in probs),
+                                  "sphere": sum(p[1] == "sphere" for p in probs)},
+                   "kernels": {BATCH_KERNELS[i][0]: sum(p[2] == i for p in probs) for i in range(3)},
+                   "leaf_sizes": {f"{k[0]}/{BATCH_KERNELS[k[1]][0]}": v for k, v in qsel.items()},
+                   "id_tol": eps, "precision": wl["prec"], "g": g, "tau": "%d/%d" % tau, "il_reduce": ilr,
+                   "sampled_rows_per_problem": wl["rows"],
+                   "timed": "every problem's tree, HiDR and product plus one batched construction per step; "
+                            "exact rows outside the timed steps",
+                   "l2": "flushed (256 MB write) between timed steps, outside the timed interval",
+                   "parallelism": f"{world} GPU(s), the problems of each rank in one batched construction"},
+        "rel_err": max(errs), "rel_err_median": statistics.median(errs),
+        "phases_ms": {"autotune_ms": tune_ms, "construct_batched_ms": batched_wall_ms,
+                      "construct_one_by_one_ms": one_by_one_ms, "construct_events_sum_ms": batched_ms},
+        "kernels": per_kernel, "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+        "counts": {"qr_flops": qr_flops}, "calibration": None, "e2e": None, "matvec_repeat": None,
+    }
+
+
 def gpu_arm(args, wl, rank, world, dev):
     import torch
 
@@ -533,13 +678,17 @@ def gpu_arm(args, wl, rank, world, dev):
     from paper_2206_01885_gb300 import h2
     torch.cuda.set_device(dev)
     alu = alu_peaks(h2, dev)  # once, outside the timed steps
-    prim = measure_form(args, wl, rank, world, dev, with_e2e=True, alu=alu)
+    if wl.get("kind") == "batched":
+        prim = measure_batched(args, wl, rank, world, dev, alu)
+    else:
+        prim = measure_form(args, wl, rank, world, dev, with_e2e=True, alu=alu)
     R = wl.get("rhs", 1)
     result = {
         "metric": METRIC, "value": prim["value"], "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": prim["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if wl["prec"] == "fp64" else "f32+f64",
-        "data": f"synthetic (seeded {points_name(wl)}, "
+        "data": "synthetic (seeded cube and sphere point sets, standard-normal right-hand sides)"
+                if wl.get("kind") == "batched" else f"synthetic (seeded {points_name(wl)}, "
                 + ("standard-normal right-hand side)" if R == 1 else f"{R} float32 standard-normal right-hand sides)"),
     }
     result.update({k: v for k, v in prim.items() if k not in ("value", "ms_per_step")})
@@ -653,7 +802,7 @@ def main():
         dist.init_process_group("nccl")
     res = gpu_arm(args, wl, rank, world, local)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and wl.get("kind") != "batched":
             res["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample)
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -250,6 +250,16 @@ typedef struct {
                             them in float64 arithmetic.  The construction, the
                             stored blocks and every other product are float64
                             either way                                          */
+    int tensor_core_products; /* mixed form, several right-hand sides: 1 runs the
+                            nearfield 16 columns at a time on the tensor cores
+                            (kernel values and weights split as tf32 hi + lo,
+                            three tcgen05 products per 32-source chunk, float32
+                            accumulation folded per chunk, error per term ~2^-21
+                            relative); 0 (default) keeps every column on the CUDA
+                            cores, which measure faster (the kernel values, not
+                            the products, bound this step).  A tensor-core wait
+                            that gives up (never expected) makes a synchronising
+                            h2_matvec return H2_ERR_TIMEOUT                    */
 } h2_construct_opts;
 
 /* h2_construct with options (opts may be NULL: exactly h2_construct).

@@ -308,6 +308,7 @@ h2_status h2_construct_ex(h2_tree th, h2_hidr hh, int kernel, const double *kpar
         A->mem_mode = mm;
         A->mem_fraction = mf > 0.0 ? mf : 0.5;
         A->fp64_products = opts && opts->fp64_products != 0;
+        A->tensor_core_products = opts && opts->tensor_core_products != 0;
         try {
             kparams_check(kernel, kparams, A->kp);
             construct_impl(A, h);
@@ -542,6 +543,11 @@ h2_status h2_matvec(h2_matrix ah, const void *x, void *y, int nrhs, int dtype, i
             matvec_multi_impl(A, xd.p, yd.p, nrhs, dtype, n, s);
         H2_CUDA(cudaMemcpy2DAsync(y, ld * es, yd.p, n * es, n * es, nrhs, cudaMemcpyDeviceToHost, s));
         H2_CUDA(cudaStreamSynchronize(s));
+        if (A->tree->tc_status.p) {  // a tensor-core wait that gave up (the call synchronised)
+            int st = 0;
+            H2_CUDA(cudaMemcpy(&st, A->tree->tc_status.p, sizeof st, cudaMemcpyDeviceToHost));
+            if (st) fail(H2_ERR_TIMEOUT, "a tensor-core wait of the nearfield gave up; the product is incomplete");
+        }
     });
 }
 

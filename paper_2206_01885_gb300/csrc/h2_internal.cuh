@@ -182,6 +182,11 @@ struct h2_tree_s {
     bool df_ready = false;
     h2::DevBuf<int32_t> cellA[3];
     h2::DevBuf<float4> xcell;
+    // tiles of 128 targets of the tensor-core nearfield (several right-hand
+    // sides, mixed form), built on first use; the kernel's timeout flag
+    h2::DevBuf<int2> near_tiles_tc;
+    bool near_tiles_tc_ready = false;
+    h2::DevBuf<int> tc_status;
 };
 
 struct h2_hidr_s {
@@ -242,6 +247,7 @@ struct h2_matrix_s {
     // fp64_products is set (then plain float64); skeleton offsets from their
     // node's centre as hi + lo, built on first use
     bool fp64_products = false;
+    bool tensor_core_products = false;  // mixed form: the 16-column nearfield on the tensor cores
     bool df_ready = false;
     h2::DevBuf<float2> skdf[3];
 };
@@ -284,6 +290,11 @@ void split_vector(const double *v, int64_t n, float2 *out, cudaStream_t s);
 void nbody_sym_df(const h2_tree_s *t, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count,
                   const DevBuf<float2> *X, const float2 *w, double *out, const int64_t *lptr, const int64_t *lfirst,
                   const int32_t *lidx, cudaStream_t s);
+// the mixed form's nearfield for 16 right-hand sides on the tensor cores
+void nbody_tc16(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const float *X0,
+                const float *X1, const float *X2, const float2 *F0, const float2 *F1, const float2 *F2,
+                const float *w, int ws, double *out, int os, const int64_t *lptr, const int32_t *lidx, int d,
+                double kp0, int *status, cudaStream_t s);
 // evaluate and keep the coupling and nearfield blocks (mode H2_MEM_STORE:
 // H2_ERR_OOM above `fraction` of the free memory; H2_MEM_AUTO: keep them
 // only when they fit)

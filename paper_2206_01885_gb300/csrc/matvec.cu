@@ -585,9 +585,10 @@ void nbody_kid(int kid, const DevBuf<int2> &tiles, const int64_t *start, const i
 template <class Real>
 void nbody(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count, const Real *X0,
            const Real *X1, const Real *X2, const float2 *F0, const float2 *F1, const float2 *F2, const Real *w,
-           double *out, int nrhs, const int64_t *lptr, const int32_t *lidx, int d, double kp0, cudaStream_t s) {
+           double *out, int nrhs, const int64_t *lptr, const int32_t *lidx, int d, double kp0, cudaStream_t s,
+           int cbegin = 0) {
     if (tiles.n == 0) return;
-    for (int c0 = 0; c0 < nrhs;) {
+    for (int c0 = cbegin; c0 < nrhs;) {
         const int left = nrhs - c0;
         const Real *wc = w + c0;
         double *oc = out + c0;
@@ -613,6 +614,24 @@ void nbody(int kid, const DevBuf<int2> &tiles, const int64_t *start, const int32
             c0 += 1;
         }
     }
+}
+
+// tiles of 128 targets of every leaf with a near list (the tensor-core
+// nearfield), and its timeout flag, built on first use
+void prepare_tc_tiles(h2_tree_s *t, cudaStream_t s) {
+    if (t->near_tiles_tc_ready) return;
+    const int nn = t->nnodes;
+    std::vector<int32_t> b = read_vec(t->begin.p, nn, s), e = read_vec(t->end.p, nn, s),
+                         nc = read_vec(t->nchild.p, nn, s);
+    std::vector<int64_t> np = read_vec(t->near_ptr.p, nn + 1, s);
+    std::vector<int32_t> cnt(nn);
+    for (int i = 0; i < nn; i++) cnt[i] = nc[i] == 0 ? e[i] - b[i] : 0;
+    DevBuf<int> st;
+    st.alloc(1, s);
+    H2_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), s));
+    build_tiles(cnt, np, 128, t->near_tiles_tc, s);
+    t->tc_status = std::move(st);
+    t->near_tiles_tc_ready = true;
 }
 
 // the upward/downward kernels' shared-memory opt-in, once per process
@@ -848,9 +867,19 @@ void matvec_multi_impl(h2_matrix_s *A, const void *x, void *y, int R, int dtype,
             nbody<double>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, t->xs[0].p, t->xs[1].p,
                           t->xs[2].p, nullptr, nullptr, nullptr, xm.p, ym.p, R, t->near_ptr.p, t->near_idx.p, d,
                           A->kp[0], s);
-        else
+        else {
+            // 16 columns at a time on the tensor cores, the rest on the CUDA cores
+            const int rtc = A->tensor_core_products ? R / 16 * 16 : 0;
+            if (rtc > 0) {
+                prepare_tc_tiles(t, s);
+                for (int c0 = 0; c0 < rtc; c0 += 16)
+                    nbody_tc16(A->kid, t->near_tiles_tc, t->leaf_start.p, t->leaf_count.p, PX[0], PX[1], PX[2],
+                               CF[0], CF[1], CF[2], xmf.p + c0, R, ym.p + c0, R, t->near_ptr.p, t->near_idx.p, d,
+                               A->kp[0], t->tc_status.p, s);
+            }
             nbody<float>(A->kid, t->near_tiles, t->leaf_start.p, t->leaf_count.p, PX[0], PX[1], PX[2], CF[0], CF[1],
-                         CF[2], xmf.p, ym.p, R, t->near_ptr.p, t->near_idx.p, d, A->kp[0], s);
+                         CF[2], xmf.p, ym.p, R, t->near_ptr.p, t->near_idx.p, d, A->kp[0], s, rtc);
+        }
     }
     if (dtype == H2_DTYPE_F64)
         k_perm_out_multi<double><<<blocks_for(nr, 256), 256, 0, s>>>(ym.p, t->perm.p, n, R, static_cast<double *>(y),

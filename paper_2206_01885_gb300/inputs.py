@@ -125,3 +125,17 @@ def workload(name: str):
     if name == "sphere8m":
         return sphere_surface(1 << 23, seed=5), "coulomb", (), 256, 1e-6
     raise KeyError(name)
+
+
+def batched_problems(count: int, nmin: int, nmax: int, seed: int = 4):
+    """Independent problems of uneven sizes (the batched configuration): for
+    each, n log-uniform in [nmin, nmax], the point set ("cube" or "sphere",
+    50/50) and a kernel index in {0, 1, 2}, each drawn uniformly.  Returns a
+    list of (n, kind, kernel_index, point_seed)."""
+    rng = _rng(seed)
+    out = []
+    for a in range(count):
+        n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
+        kind = "cube" if rng.random() < 0.5 else "sphere"
+        out.append((n, kind, int(rng.integers(0, 3)), seed * 1000 + a))
+    return out

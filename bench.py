@@ -576,8 +576,8 @@ def measure_batched(args, wl, rank, world, dev, alu):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
-        ts = [h2.Tree(pts_d[a], qsel[(kind, ki)], tau=tau) for a, (n, kind, ki, ps) in enumerate(probs)]
-        hs = [h2.Hidr(t, g, g, il_reduce=ilr) for t in ts]
+        ts = h2.tree_build_batched(pts_d, [qsel[(kind, ki)] for (n, kind, ki, ps) in probs], tau=tau)
+        hs = h2.hidr_reduce_batched(ts, g, g, il_reduce=ilr)
         mats = h2.construct_batched([(ts[a], hs[a], BATCH_KERNELS[ki][0], BATCH_KERNELS[ki][1], eps, wl["prec"])
                                      for a, (n, kind, ki, ps) in enumerate(probs)])
         ys = [mats[a].matvec(z_d[a]) for a in range(len(probs))]
@@ -658,8 +658,8 @@ def measure_batched(args, wl, rank, world, dev, alu):
                    "leaf_sizes": {f"{k[0]}/{BATCH_KERNELS[k[1]][0]}": v for k, v in qsel.items()},
                    "id_tol": eps, "precision": wl["prec"], "g": g, "tau": "%d/%d" % tau, "il_reduce": ilr,
                    "sampled_rows_per_problem": wl["rows"],
-                   "timed": "every problem's tree, HiDR and product plus one batched construction per step; "
-                            "exact rows outside the timed steps",
+                   "timed": "one batched tree build, one batched HiDR and one batched construction over all "
+                            "problems and every problem's product per step; exact rows outside the timed steps",
                    "l2": "flushed (256 MB write) between timed steps, outside the timed interval",
                    "parallelism": f"{world} GPU(s), the problems of each rank in one batched construction"},
         "rel_err": max(errs), "rel_err_median": statistics.median(errs),

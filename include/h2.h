@@ -109,6 +109,19 @@ typedef struct {
 h2_status h2_tree_build(const double *pts, int64_t n, int dim, int pts_on_device,
                         const h2_tree_params *params, void *stream, h2_tree *out);
 
+/* Trees of nprob independent point sets (the batched configuration; no
+ * counterpart in the paper beyond its independent problems): tree p is exactly
+ * what h2_tree_build(pts[p], ns[p], dim, pts_on_device, &params[p]) returns,
+ * but the builds run concurrently, each on one of up to eight internal
+ * streams driven by host threads.  The work starts after the work already
+ * queued on `stream`; on return `stream` is ordered after every build and
+ * every tree belongs to it.  pts: nprob pointers to n x dim float64 arrays
+ * (all device or all host, as pts_on_device says); ns, params: nprob entries.
+ * Errors: as h2_tree_build; on any error no tree is returned (out[] all NULL)
+ * and the message names the first failing problem. */
+h2_status h2_tree_build_batched(int nprob, const double *const *pts, const int64_t *ns, int dim, int pts_on_device,
+                                const h2_tree_params *params, void *stream, h2_tree *out);
+
 /* what for h2_tree_get (element type, length):
  *   H2_TREE_PERM      int64 [n]          Morton position -> original index
  *   H2_TREE_KEYS      uint64 [n]         sorted Morton keys
@@ -195,6 +208,14 @@ typedef enum {
  * Errors: as h2_hidr_reduce; H2_ERR_INVALID_ARG for an unknown method or flag,
  * or for H2_HIDR_IL_REDUCE with g2^dim > 4096. */
 h2_status h2_hidr_reduce_ex(h2_tree t, int g1, int g2, int method, void *stream, h2_hidr *out);
+
+/* HiDR of nprob trees at once (the batched configuration): hidr p is exactly
+ * h2_hidr_reduce_ex(trees[p], g1[p], g2[p], methods[p]) (methods may be NULL:
+ * H2_DR_VOLUME for all), the reductions running concurrently on up to eight
+ * internal streams driven by host threads.  Stream and error conventions as
+ * h2_tree_build_batched.  A tree may appear more than once. */
+h2_status h2_hidr_reduce_batched(int nprob, const h2_tree *trees, const int *g1, const int *g2, const int *methods,
+                                 void *stream, h2_hidr *out);
 
 /* which: 0 = X_i*, 1 = Y_i*.  Fills counts (int32 [nnodes], may be NULL) and,
  * if data is not NULL, the concatenation over nodes in node order of the

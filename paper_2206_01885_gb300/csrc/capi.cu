@@ -118,63 +118,195 @@ h2_matrix_s *as_matrix(void *h) {
 
 using namespace h2;
 
+namespace {
+// release every buffer of a tree / hidr on s from now on (s ordered after the
+// work that built it), and make s the handle's stream
+void tree_rebind(h2_tree_s *t, cudaStream_t s) {
+    t->stream = s;
+    for (int k = 0; k < 3; k++) {
+        t->xs[k].rebind(s); t->cen[k].rebind(s); t->xr[k].rebind(s); t->cenf[k].rebind(s);
+        t->cellA[k].rebind(s);
+    }
+    t->key.rebind(s); t->perm.rebind(s); t->iperm.rebind(s);
+    t->level.rebind(s); t->parent.rebind(s); t->fchild.rebind(s); t->nchild.rebind(s);
+    t->begin.rebind(s); t->end.rebind(s); t->prefix.rebind(s);
+    t->near_ptr.rebind(s); t->far_ptr.rebind(s); t->near_idx.rebind(s); t->far_idx.rebind(s);
+    t->xq.rebind(s); t->near_tiles.rebind(s); t->near_first.rebind(s); t->far_first.rebind(s);
+    t->leaf_start.rebind(s); t->leaf_count.rebind(s); t->xcell.rebind(s);
+    t->near_tiles_tc.rebind(s); t->tc_status.rebind(s);
+}
+void hidr_rebind(h2_hidr_s *h, cudaStream_t s) {
+    h->stream = s;
+    h->xcnt.rebind(s); h->ycnt.rebind(s); h->xptr.rebind(s); h->yptr.rebind(s);
+    h->xbox.rebind(s); h->ybox.rebind(s);
+    for (auto &b : h->xbufs) b.rebind(s);
+    for (auto &b : h->ybufs) b.rebind(s);
+}
+
+// Runs work(p, stream) for p = 0..nprob-1 on up to eight internal streams
+// driven by host threads, after the work queued on s; on return s is ordered
+// after all of it.  Per-problem errors are collected (st, msg), not thrown.
+template <class F>
+void run_concurrently(int nprob, cudaStream_t s, std::vector<h2_status> &st, std::vector<std::string> &msg,
+                      F &&work) {
+    st.assign(nprob, H2_OK);
+    msg.assign(nprob, std::string());
+    int dev = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    const int nw = std::min(nprob, 8);
+    std::vector<cudaStream_t> ws(nw, nullptr);
+    std::vector<cudaEvent_t> done(nw, nullptr);
+    cudaEvent_t ready = nullptr;
+    auto cleanup = [&] {
+        for (int w = 0; w < nw; w++) {
+            if (done[w]) cudaEventDestroy(done[w]);
+            if (ws[w]) cudaStreamDestroy(ws[w]);
+        }
+        if (ready) cudaEventDestroy(ready);
+    };
+    try {
+        H2_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        H2_CUDA(cudaEventRecord(ready, s));
+        for (int w = 0; w < nw; w++) {
+            H2_CUDA(cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking));
+            H2_CUDA(cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming));
+            H2_CUDA(cudaStreamWaitEvent(ws[w], ready, 0));
+        }
+        std::atomic<int> next{0};
+        auto worker = [&](int w) {
+            if (cudaSetDevice(dev) != cudaSuccess) return;
+            for (int p = next++; p < nprob; p = next++) {
+                try {
+                    work(p, ws[w]);
+                } catch (const Error &e) {
+                    st[p] = e.st;
+                    msg[p] = e.msg;
+                } catch (const std::bad_alloc &) {
+                    st[p] = H2_ERR_OOM;
+                    msg[p] = "host allocation failed";
+                } catch (...) {
+                    st[p] = H2_ERR_CUDA;
+                    msg[p] = "unknown error";
+                }
+            }
+        };
+        std::vector<std::thread> th;
+        try {
+            for (int w = 0; w < nw; w++) th.emplace_back(worker, w);
+        } catch (...) {
+            next = nprob;
+            for (auto &x : th) x.join();
+            throw;
+        }
+        for (auto &x : th) x.join();
+        for (int w = 0; w < nw; w++) {
+            H2_CUDA(cudaEventRecord(done[w], ws[w]));
+            H2_CUDA(cudaStreamWaitEvent(s, done[w], 0));
+        }
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+}  // namespace
+
+namespace {
+// one tree: arguments checked, built on stream s; throws on failure (nothing leaks)
+h2_tree_s *tree_build_one(const double *pts, int64_t n, int dim, int pts_on_device, const h2_tree_params *params,
+                          cudaStream_t s) {
+    H2_REQUIRE(pts != nullptr, "pts is NULL");
+    H2_REQUIRE(params != nullptr, "params is NULL");
+    H2_REQUIRE(n >= 1 && n < (int64_t)INT32_MAX, "n must be in [1, 2^31 - 1)");
+    H2_REQUIRE(dim == 2 || dim == 3, "dim must be 2 or 3");
+    H2_REQUIRE(params->leaf_size >= 1, "leaf_size must be >= 1");
+    H2_REQUIRE(params->tau_num >= 0 && params->tau_den >= 1, "tau must be tau_num/tau_den with tau_den >= 1");
+    pool_keep_memory();
+    auto *t = new h2_tree_s();
+    try {
+        t->stream = s;
+        t->n = n;
+        t->d = dim;
+        t->B = dim == 3 ? 21 : 31;
+        t->q = params->leaf_size;
+        t->tau_num = params->tau_num;
+        t->tau_den = params->tau_den;
+        DevBuf<double> tmp;
+        const double *pd = pts;
+        if (!pts_on_device) {
+            tmp.alloc((size_t)n * dim, s);
+            H2_CUDA(cudaMemcpyAsync(tmp.p, pts, (size_t)n * dim * sizeof(double), cudaMemcpyHostToDevice, s));
+            pd = tmp.p;
+        }
+        cudaEvent_t e0, e1, e2;
+        H2_CUDA(cudaEventCreate(&e0));
+        H2_CUDA(cudaEventCreate(&e1));
+        H2_CUDA(cudaEventCreate(&e2));
+        H2_CUDA(cudaEventRecord(e0, s));
+        tree_build_impl(t, pd);
+        H2_CUDA(cudaEventRecord(e1, s));
+        lists_build_impl(t);
+        H2_CUDA(cudaEventRecord(e2, s));
+        H2_CUDA(cudaEventSynchronize(e2));
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, e0, e1);
+        cudaEventElapsedTime(&b, e1, e2);
+        t->ms_tree = a;
+        t->ms_lists = b;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+    } catch (...) {
+        t->tag = TAG_DEAD;
+        delete t;
+        throw;
+    }
+    return t;
+}
+}  // namespace
+
+namespace {
+h2_hidr_s *hidr_one(h2_tree_s *t, int g1, int g2, int method, cudaStream_t s) {
+    const bool il = (method & H2_HIDR_IL_REDUCE) != 0;
+    method &= ~H2_HIDR_IL_REDUCE;
+    H2_REQUIRE(method == H2_DR_VOLUME || method == H2_DR_SURFACE || method == H2_DR_FPS,
+               "unknown DataReduct method or flag");
+    H2_REQUIRE(g1 >= 1 && g2 >= 1, "g1 and g2 must be >= 1");
+    if (il) {
+        int64_t G = 1;
+        for (int k = 0; k < t->d; k++) G = std::min<int64_t>(G * g2, 1 << 20);
+        H2_REQUIRE(G <= 4096, "the interaction-list reduction needs g2^dim <= 4096");
+    }
+    auto *h = new h2_hidr_s();
+    h->tree = t;
+    h->stream = s;
+    h->g1 = g1;
+    h->g2 = g2;
+    h->method = method;
+    h->il_reduce = il;
+    try {
+        hidr_impl(h);
+    } catch (...) {
+        h->tag = TAG_DEAD;
+        delete h;
+        throw;
+    }
+    return h;
+}
+}  // namespace
+
 extern "C" {
 
 const char *h2_last_error(void) { return g_last_error.c_str(); }
+
+
 
 h2_status h2_tree_build(const double *pts, int64_t n, int dim, int pts_on_device, const h2_tree_params *params,
                         void *stream, h2_tree *out) {
     return guard([&] {
         H2_REQUIRE(out != nullptr, "out is NULL");
         *out = nullptr;
-        H2_REQUIRE(pts != nullptr, "pts is NULL");
-        H2_REQUIRE(params != nullptr, "params is NULL");
-        H2_REQUIRE(n >= 1 && n < (int64_t)INT32_MAX, "n must be in [1, 2^31 - 1)");
-        H2_REQUIRE(dim == 2 || dim == 3, "dim must be 2 or 3");
-        H2_REQUIRE(params->leaf_size >= 1, "leaf_size must be >= 1");
-        H2_REQUIRE(params->tau_num >= 0 && params->tau_den >= 1, "tau must be tau_num/tau_den with tau_den >= 1");
-        pool_keep_memory();
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
-        auto *t = new h2_tree_s();
-        try {
-            t->stream = s;
-            t->n = n;
-            t->d = dim;
-            t->B = dim == 3 ? 21 : 31;
-            t->q = params->leaf_size;
-            t->tau_num = params->tau_num;
-            t->tau_den = params->tau_den;
-            DevBuf<double> tmp;
-            const double *pd = pts;
-            if (!pts_on_device) {
-                tmp.alloc((size_t)n * dim, s);
-                H2_CUDA(cudaMemcpyAsync(tmp.p, pts, (size_t)n * dim * sizeof(double), cudaMemcpyHostToDevice, s));
-                pd = tmp.p;
-            }
-            cudaEvent_t e0, e1, e2;
-            H2_CUDA(cudaEventCreate(&e0));
-            H2_CUDA(cudaEventCreate(&e1));
-            H2_CUDA(cudaEventCreate(&e2));
-            H2_CUDA(cudaEventRecord(e0, s));
-            tree_build_impl(t, pd);
-            H2_CUDA(cudaEventRecord(e1, s));
-            lists_build_impl(t);
-            H2_CUDA(cudaEventRecord(e2, s));
-            H2_CUDA(cudaEventSynchronize(e2));
-            float a = 0, b = 0;
-            cudaEventElapsedTime(&a, e0, e1);
-            cudaEventElapsedTime(&b, e1, e2);
-            t->ms_tree = a;
-            t->ms_lists = b;
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            cudaEventDestroy(e2);
-        } catch (...) {
-            t->tag = TAG_DEAD;
-            delete t;
-            throw;
-        }
-        *out = t;
+        *out = tree_build_one(pts, n, dim, pts_on_device, params, static_cast<cudaStream_t>(stream));
     });
 }
 
@@ -217,37 +349,96 @@ h2_status h2_hidr_reduce(h2_tree th, int g1, int g2, void *stream, h2_hidr *out)
     return h2_hidr_reduce_ex(th, g1, g2, H2_DR_VOLUME, stream, out);
 }
 
+
 h2_status h2_hidr_reduce_ex(h2_tree th, int g1, int g2, int method, void *stream, h2_hidr *out) {
     return guard([&] {
         H2_REQUIRE(out != nullptr, "out is NULL");
         *out = nullptr;
-        const bool il = (method & H2_HIDR_IL_REDUCE) != 0;
-        method &= ~H2_HIDR_IL_REDUCE;
-        H2_REQUIRE(method == H2_DR_VOLUME || method == H2_DR_SURFACE || method == H2_DR_FPS,
-                   "unknown DataReduct method or flag");
+        const int m = method & ~H2_HIDR_IL_REDUCE;  // (the method and flags are checked before the handle)
+        H2_REQUIRE(m == H2_DR_VOLUME || m == H2_DR_SURFACE || m == H2_DR_FPS, "unknown DataReduct method or flag");
         h2_tree_s *t = as_tree(th);
-        H2_REQUIRE(g1 >= 1 && g2 >= 1, "g1 and g2 must be >= 1");
-        if (il) {
-            int64_t G = 1;
-            for (int k = 0; k < t->d; k++) G = std::min<int64_t>(G * g2, 1 << 20);
-            H2_REQUIRE(G <= 4096, "the interaction-list reduction needs g2^dim <= 4096");
-        }
-        auto *h = new h2_hidr_s();
-        h->tree = t;
-        h->stream = static_cast<cudaStream_t>(stream);
-        h->g1 = g1;
-        h->g2 = g2;
-        h->method = method;
-        h->il_reduce = il;
-        try {
-            hidr_impl(h);
-        } catch (...) {
-            h->tag = TAG_DEAD;
-            delete h;
-            throw;
-        }
+        h2_hidr_s *h = hidr_one(t, g1, g2, method, static_cast<cudaStream_t>(stream));
         t->refs++;
         *out = h;
+    });
+}
+
+h2_status h2_tree_build_batched(int nprob, const double *const *pts, const int64_t *ns, int dim, int pts_on_device,
+                                const h2_tree_params *params, void *stream, h2_tree *out) {
+    return guard([&] {
+        H2_REQUIRE(nprob >= 0, "nprob must be >= 0");
+        if (nprob == 0) return;
+        H2_REQUIRE(pts && ns && params && out, "NULL argument");
+        for (int p = 0; p < nprob; p++) out[p] = nullptr;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        std::vector<h2_tree_s *> trees(nprob, nullptr);
+        std::vector<h2_status> st;
+        std::vector<std::string> msg;
+        auto drop = [&] {
+            for (auto *t : trees)
+                if (t) { tree_rebind(t, s); t->tag = TAG_DEAD; delete t; }
+        };
+        try {
+            run_concurrently(nprob, s, st, msg, [&](int p, cudaStream_t ws) {
+                trees[p] = tree_build_one(pts[p], ns[p], dim, pts_on_device, params + p, ws);
+            });
+            for (auto *t : trees)
+                if (t) tree_rebind(t, s);
+        } catch (...) {
+            drop();
+            throw;
+        }
+        for (int p = 0; p < nprob; p++)
+            if (st[p] != H2_OK) {
+                drop();
+                fail(st[p], "problem " + std::to_string(p) + ": " + msg[p]);
+            }
+        for (int p = 0; p < nprob; p++) out[p] = trees[p];
+    });
+}
+
+h2_status h2_hidr_reduce_batched(int nprob, const h2_tree *trees, const int *g1, const int *g2, const int *methods,
+                                 void *stream, h2_hidr *out) {
+    return guard([&] {
+        H2_REQUIRE(nprob >= 0, "nprob must be >= 0");
+        if (nprob == 0) return;
+        H2_REQUIRE(trees && g1 && g2 && out, "NULL argument");
+        for (int p = 0; p < nprob; p++) out[p] = nullptr;
+        std::vector<h2_tree_s *> ts(nprob);
+        for (int p = 0; p < nprob; p++) {
+            try {
+                ts[p] = as_tree(trees[p]);
+            } catch (const Error &e) {
+                fail(e.st, "problem " + std::to_string(p) + ": " + e.msg);
+            }
+        }
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        std::vector<h2_hidr_s *> hs(nprob, nullptr);
+        std::vector<h2_status> st;
+        std::vector<std::string> msg;
+        auto drop = [&] {
+            for (auto *h : hs)
+                if (h) { hidr_rebind(h, s); h->tag = TAG_DEAD; delete h; }
+        };
+        try {
+            run_concurrently(nprob, s, st, msg, [&](int p, cudaStream_t ws) {
+                hs[p] = hidr_one(ts[p], g1[p], g2[p], methods ? methods[p] : H2_DR_VOLUME, ws);
+            });
+            for (auto *h : hs)
+                if (h) hidr_rebind(h, s);
+        } catch (...) {
+            drop();
+            throw;
+        }
+        for (int p = 0; p < nprob; p++)
+            if (st[p] != H2_OK) {
+                drop();
+                fail(st[p], "problem " + std::to_string(p) + ": " + msg[p]);
+            }
+        for (int p = 0; p < nprob; p++) {
+            ts[p]->refs++;
+            out[p] = hs[p];
+        }
     });
 }
 

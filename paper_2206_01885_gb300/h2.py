@@ -87,6 +87,8 @@ def lib():
             "h2_construct_batched": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
             "h2_debug_fail_alloc": [i64, C.POINTER(i64)],
             "h2_fma_peak": [C.POINTER(dbl), C.POINTER(dbl), vp],
+            "h2_tree_build_batched": [i32, vp, vp, i32, i32, vp, vp, vp],
+            "h2_hidr_reduce_batched": [i32, vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -166,6 +168,14 @@ class _Handle:
 class Tree(_Handle):
     """h2_tree_build: Morton cluster tree and near/far interaction lists."""
 
+    @classmethod
+    def _wrap(cls, handle):
+        t = cls.__new__(cls)
+        t._h = handle
+        info = t.get("info")
+        t.n, t.d, t.B, t.nnodes, t.nlevels, t.nnear, t.nfar, t.q = (int(v) for v in info)
+        return t
+
     def __init__(self, points, leaf_size: int, tau=(7, 10), stream=None):
         if not _is_cuda(points):
             points = np.ascontiguousarray(points, dtype=np.float64)
@@ -190,6 +200,13 @@ class Tree(_Handle):
 
 class Hidr(_Handle):
     """h2_hidr_reduce: X_i*, Y_i* of Algorithm 1."""
+
+    @classmethod
+    def _wrap(cls, handle, tree):
+        h = cls.__new__(cls)
+        h._h = handle
+        h.tree = tree
+        return h
 
     def __init__(self, tree: Tree, g1: int, g2: int, stream=None, method: str = "volume", il_reduce: bool = False):
         """method: the DataReduct of section 3.3, "volume", "surface" or "fps".
@@ -330,6 +347,47 @@ def hidr_reduce(tree, g1, g2, stream=None) -> Hidr:
 
 def construct(tree, hidr, kernel, kparams=(), id_tol=1e-6, precision="fp64", stream=None) -> H2Matrix:
     return H2Matrix(tree, hidr, kernel, kparams, id_tol, precision, stream)
+
+
+def tree_build_batched(points_list, leaf_sizes, tau=(7, 10), stream=None):
+    """h2_tree_build_batched: one tree per point set (CUDA tensors, or host
+    arrays; not mixed), leaf_sizes per set (or one for all), built
+    concurrently on the GPU."""
+    n = len(points_list)
+    if n == 0:
+        return []
+    on_dev = _is_cuda(points_list[0])
+    if any(_is_cuda(p) != on_dev for p in points_list):
+        raise TypeError("point sets must be all CUDA tensors or all host arrays")
+    keep = [p.contiguous() if on_dev else np.ascontiguousarray(p, dtype=np.float64) for p in points_list]
+    d = keep[0].shape[1]
+    if any(p.shape[1] != d for p in keep):
+        raise ValueError("every point set needs the same dimension")
+    ptrs = (C.c_void_p * n)(*[p.data_ptr() if on_dev else p.ctypes.data for p in keep])
+    ns = (C.c_int64 * n)(*[p.shape[0] for p in keep])
+    qs = [leaf_sizes] * n if isinstance(leaf_sizes, int) else list(leaf_sizes)
+    prm = (_Params * n)(*[_Params(int(q), int(tau[0]), int(tau[1])) for q in qs])
+    outs = (C.c_void_p * n)()
+    _check("h2_tree_build_batched", lib().h2_tree_build_batched(n, ptrs, ns, d, int(on_dev), prm, _stream(stream),
+                                                                 outs))
+    return [Tree._wrap(outs[i]) for i in range(n)]
+
+
+def hidr_reduce_batched(trees, g1s, g2s, il_reduce=False, method="volume", stream=None):
+    """h2_hidr_reduce_batched: one Hidr per tree (g1, g2 per tree or one for
+    all), reduced concurrently on the GPU."""
+    n = len(trees)
+    if n == 0:
+        return []
+    g1 = [g1s] * n if isinstance(g1s, int) else list(g1s)
+    g2 = [g2s] * n if isinstance(g2s, int) else list(g2s)
+    flags = DR_METHODS[method] | (HIDR_IL_REDUCE if il_reduce else 0)
+    th = (C.c_void_p * n)(*[t.handle for t in trees])
+    outs = (C.c_void_p * n)()
+    _check("h2_hidr_reduce_batched", lib().h2_hidr_reduce_batched(n, th, (C.c_int * n)(*g1), (C.c_int * n)(*g2),
+                                                                   (C.c_int * n)(*([flags] * n)), _stream(stream),
+                                                                   outs))
+    return [Hidr._wrap(outs[i], trees[i]) for i in range(n)]
 
 
 def construct_batched(problems, stream=None):

@@ -502,3 +502,47 @@ def test_matvec_graph(H2, prec, dtype):
     assert e.value.status == 7  # H2_ERR_STATE
     G.free()
     A.free()
+
+
+def test_tree_and_hidr_batched_equal_one_by_one(H2):
+    """h2_tree_build_batched and h2_hidr_reduce_batched: independent problems
+    of uneven sizes (cube and sphere, several leaf sizes and grids, with and
+    without the interaction-list reduction) give exactly the trees and HiDR
+    sets of one-by-one calls; a bad problem fails the whole call and names it."""
+    rng = np.random.default_rng(93)
+    pts, qs, gs = [], [], []
+    for a in range(10):
+        n = int(np.exp(rng.uniform(np.log(1500), np.log(25000))))
+        pts.append(I.uniform_cube(n, 3, seed=200 + a) if a % 2 == 0 else I.sphere_surface(n, seed=200 + a))
+        qs.append([64, 128, 256][a % 3])
+        gs.append([4, 5, 6][a % 3])
+    trees = H2.tree_build_batched([dev(p) for p in pts], qs, tau=(1, 2))
+    for a, t in enumerate(trees):
+        o = H2.Tree(dev(pts[a]), qs[a], tau=(1, 2))
+        for f in ["perm", "near_ptr", "near_idx", "far_ptr", "far_idx", "lptr"]:
+            assert np.array_equal(t.get(f), o.get(f)), (a, f)
+        o.free()
+    for ilr in (False, True):
+        hs = H2.hidr_reduce_batched(trees, gs, gs, il_reduce=ilr)
+        for a, (t, h) in enumerate(zip(trees, hs)):
+            o = H2.Hidr(t, gs[a], gs[a], il_reduce=ilr)
+            for which in ("x", "y"):
+                (c1, d1), (c2, d2) = h.get(which), o.get(which)
+                assert np.array_equal(c1, c2) and np.array_equal(d1, d2), (a, which, ilr)
+            o.free()
+        for h in hs:
+            h.free()
+    # host point sets through the same call
+    th = H2.tree_build_batched(pts[:3], 64)
+    for a, t in enumerate(th):
+        assert np.array_equal(t.get("perm"), H2.Tree(pts[a], 64).get("perm"))
+        t.free()
+    # a bad leaf size in problem 2: no tree is returned and the message names it
+    with pytest.raises(H2.H2Error) as e:
+        H2.tree_build_batched([dev(p) for p in pts[:4]], [64, 64, 0, 64])
+    assert e.value.status == 1 and "problem 2" in str(e.value)
+    with pytest.raises(H2.H2Error) as e:
+        H2.hidr_reduce_batched(trees[:3], [4, 4, 4], [4, 0, 4])
+    assert e.value.status == 1 and "problem 1" in str(e.value)
+    for t in trees:
+        t.free()

@@ -281,6 +281,15 @@ typedef struct {
                             the products, bound this step).  A tensor-core wait
                             that gives up (never expected) makes a synchronising
                             h2_matvec return H2_ERR_TIMEOUT                    */
+    int fp64_qr;         /* float64 form: 0 (default) runs the column-pivoted QR's
+                            reflectors and trailing updates in float-float
+                            arithmetic on the float32 units (the block held as
+                            float pairs of ~48 bits; norms, downdates, pivots,
+                            the stop test and the reflector's scalars stay
+                            float64; R is returned to float64 for the solve);
+                            1 keeps the QR in float64 arithmetic throughout.
+                            The kernel blocks and the solve are float64 either
+                            way                                                 */
 } h2_construct_opts;
 
 /* h2_construct with options (opts may be NULL: exactly h2_construct).

@@ -500,6 +500,7 @@ h2_status h2_construct_ex(h2_tree th, h2_hidr hh, int kernel, const double *kpar
         A->mem_fraction = mf > 0.0 ? mf : 0.5;
         A->fp64_products = opts && opts->fp64_products != 0;
         A->tensor_core_products = opts && opts->tensor_core_products != 0;
+        A->fp64_qr = opts && opts->fp64_qr != 0;
         try {
             kparams_check(kernel, kparams, A->kp);
             construct_impl(A, h);
@@ -999,13 +1000,13 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
                      "\"qr_flops\": %.6e, \"block_evals\": %.6e, \"g_max\": %.6e, \"g_bound\": %.6e, "
                      "\"exchanges\": %lld, \"precision\": \"%s\", \"mem_mode\": \"%s\", "
                      "\"stored_bytes\": %lld, \"stored_far_bytes\": %lld, \"stored_near_bytes\": %lld, "
-                     "\"planned_bytes\": %lld, \"ms_blocks\": %.4f, \"fp64_products\": %s}",
+                     "\"planned_bytes\": %lld, \"ms_blocks\": %.4f, \"fp64_products\": %s, \"fp64_qr\": %s}",
                      (long long)A->ktotal, (long long)A->utotal, A->kmax, A->ms_construct, A->flops_qr,
                      A->evals_block, A->g_max, A->g_bound, (long long)A->exchanges,
                      A->prec == H2_PREC_FP64 ? "fp64" : "mixed", A->stored ? "stored" : "on_the_fly",
                      (long long)(A->stored_far_bytes + A->stored_near_bytes), (long long)A->stored_far_bytes,
                      (long long)A->stored_near_bytes, (long long)A->stored_bytes_plan, A->ms_blocks,
-                     A->fp64_products ? "true" : "false");
+                     A->fp64_products ? "true" : "false", A->fp64_qr ? "true" : "false");
         } else {
             fail(H2_ERR_INVALID_ARG, "not a live h2 handle");
         }

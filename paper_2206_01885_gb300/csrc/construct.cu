@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "h2_internal.cuh"
+#include "df.cuh"
 
 namespace h2 {
 namespace {
@@ -424,6 +425,187 @@ __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr(int lb, const int32_t *y
     if (threadIdx.x == 0) kout[node] = k;
 }
 
+// Float64 form, float-float arithmetic: the same column-pivoted Householder
+// QR as k_cpqr<double, 0> (right-looking, one warp per trailing column, the
+// same pivots, downdates, recomputation and stop test in float64), with the
+// block held as float pairs hi + lo (about 48 bits) and the reflector, its
+// products with the trailing columns and their rank-1 updates computed in
+// float-float arithmetic on the float32 units (float64 runs at 1/74 of the
+// float32 rate on this GPU).  The float64 block is converted in place on
+// entry (each element keeps its 8 bytes); on exit rows 0..k-1 of every column
+// -- R, what the solve reads -- are converted back to float64 in place.  The
+// reflector's scalars (one square root, two divisions) and the column norms
+// stay float64.
+__global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr_df(int lb, const int32_t *ycnt, const int32_t *cc,
+                                                         const int64_t *aoff, double *Abase, double tol,
+                                                         int32_t *kout, const int64_t *coff, int32_t *pivbase) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int a = blockIdx.x, node = lb + a;
+    const int m = ycnt[node], c = cc[node];
+    if (m == 0 || c == 0) {
+        if (threadIdx.x == 0) kout[node] = 0;
+        return;
+    }
+    double *nrm = reinterpret_cast<double *>(smem_raw);
+    double *nrm0 = nrm + c;
+    double *rowj = nrm0 + c;                            // row j of the updated trailing columns
+    float2 *v = reinterpret_cast<float2 *>(rowj + c);  // the reflector, rows j..m-1
+    int32_t *pv = reinterpret_cast<int32_t *>(v + m);
+    unsigned char *flag = reinterpret_cast<unsigned char *>(pv + c);
+    __shared__ double red[QR_WARPS];
+    __shared__ long long bkey[QR_WARPS];
+    __shared__ int bidx[QR_WARPS];
+    __shared__ int s_p, s_stop;
+    __shared__ float2 s_tau, s_beta, s_sc;
+    __shared__ int s_has;
+    double *Ad = Abase + aoff[a];
+    float2 *A = reinterpret_cast<float2 *>(Ad);  // the same 8 bytes per element
+    int32_t *piv = pivbase + coff[a];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const double tol3z = sqrt(ldexp(1.0, -53));
+    const int64_t mc = (int64_t)m * c;
+    for (int64_t e = threadIdx.x; e < mc; e += blockDim.x) A[e] = df::from_double(Ad[e]);
+    for (int l = threadIdx.x; l < c; l += blockDim.x) pv[l] = l;
+    __syncthreads();
+    for (int l = warp; l < c; l += nwarps) {
+        const float2 *col = A + (int64_t)l * m;
+        float sh = 0.f, sl = 0.f;
+        for (int r = lane; r < m; r += 32) df::mac(sh, sl, col[r], col[r]);
+        const double s = df::to_double(df::warp_sum(sh, sl));
+        if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
+    }
+    __syncthreads();
+    const int kmax = min(m, c);
+    int k = 0;
+    double r11 = 0.0;
+    for (int j = 0; j < kmax; j++) {
+        // pivot: largest downdated norm among columns j..c-1
+        long long bk = -1;
+        int bi = INT_MAX;
+        for (int l = j + threadIdx.x; l < c; l += blockDim.x) argmax_key(bk, bi, __double_as_longlong(nrm[l]), l);
+        for (int o = 16; o > 0; o >>= 1) {
+            long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+            int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            argmax_key(bk, bi, k2, i2);
+        }
+        if (lane == 0) { bkey[warp] = bk; bidx[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long kk2 = bkey[0];
+            int ii = bidx[0];
+            for (int w = 1; w < nwarps; w++) argmax_key(kk2, ii, bkey[w], bidx[w]);
+            const double vv = __longlong_as_double(kk2);
+            if (j == 0) r11 = vv;
+            s_p = ii;
+            s_stop = (!(vv > tol * r11) || vv == 0.0) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const int p = s_p;
+        if (p != j) {
+            float2 *cj = A + (int64_t)j * m, *cp = A + (int64_t)p * m;
+            for (int r = threadIdx.x; r < m; r += blockDim.x) {
+                float2 t = cj[r]; cj[r] = cp[r]; cp[r] = t;
+            }
+            if (threadIdx.x == 0) {
+                double t = nrm[j]; nrm[j] = nrm[p]; nrm[p] = t;
+                t = nrm0[j]; nrm0[j] = nrm0[p]; nrm0[p] = t;
+                int ti = pv[j]; pv[j] = pv[p]; pv[p] = ti;
+            }
+        }
+        __syncthreads();
+        // Householder reflector for A[j:m, j]: sum of squares in float-float,
+        // the warps' sums added in float64 by thread 0, which forms the
+        // scalars in float64 and broadcasts them as float pairs
+        float2 *aj = A + (int64_t)j * m;
+        {
+            float sh = 0.f, sl = 0.f;
+            for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) df::mac(sh, sl, aj[r], aj[r]);
+            const float2 ws = df::warp_sum(sh, sl);
+            if (lane == 0) red[warp] = df::to_double(ws);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sigma = 0;
+            for (int w = 0; w < nwarps; w++) sigma += red[w];
+            const double alpha = df::to_double(aj[j]);
+            double tau = 0, beta = alpha, sc = 0;
+            if (sigma != 0.0) {
+                const double xn = sqrt(alpha * alpha + sigma);
+                beta = alpha >= 0.0 ? -xn : xn;
+                tau = (beta - alpha) / beta;
+                sc = 1.0 / (alpha - beta);
+            }
+            s_tau = df::from_double(tau);
+            s_beta = df::from_double(beta);
+            s_sc = df::from_double(sc);
+            s_has = tau != 0.0;
+            s_stop = (alpha == 0.0 && sigma == 0.0) ? 1 : 0;  // exactly zero pivot column
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const bool has_tau = s_has != 0;
+        const float2 scD = s_sc, tauD = s_tau;
+        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) v[r] = df::mul(aj[r], scD);
+        __syncthreads();
+        if (threadIdx.x == 0) aj[j] = s_beta;
+        // apply to the trailing columns, one warp per column: w = tau (v^T a),
+        // a -= w v, all in float-float; row j of the result (float64) feeds the
+        // norm downdate
+        for (int l = j + 1 + warp; l < c; l += nwarps) {
+            float2 *al = A + (int64_t)l * m;
+            float2 ajl = al[j];
+            if (has_tau) {
+                float sh = 0.f, sl = 0.f;
+                for (int r = j + 1 + lane; r < m; r += 32) df::mac(sh, sl, v[r], al[r]);
+                float2 w = df::add(df::warp_sum(sh, sl), ajl);
+                w = df::mul(w, tauD);
+                for (int r = j + 1 + lane; r < m; r += 32) al[r] = df::fms(al[r], w, v[r]);
+                ajl = df::sub(ajl, w);
+                if (lane == 0) al[j] = ajl;
+            }
+            if (lane == 0) rowj[l] = df::to_double(ajl);
+        }
+        __syncthreads();
+        // downdate the norms (float64, LAPACK's rule), one thread per column;
+        // flag the ones that have lost about half their digits
+        for (int l = j + 1 + threadIdx.x; l < c; l += blockDim.x) {
+            double nl = nrm[l];
+            flag[l] = 0;
+            if (nl != 0.0) {
+                const double rj = rowj[l];
+                double tt = fabs(rj) / nl;
+                tt = 1.0 - tt * tt;
+                if (tt < 0.0) tt = 0.0;
+                double t2 = nl / nrm0[l];
+                t2 = tt * t2 * t2;
+                if (t2 <= tol3z) flag[l] = 1;
+                else nrm[l] = nl * sqrt(tt);
+            }
+        }
+        __syncthreads();
+        for (int l = j + 1 + warp; l < c; l += nwarps) {
+            if (!flag[l]) continue;
+            const float2 *al = A + (int64_t)l * m;
+            float sh = 0.f, sl = 0.f;
+            for (int r = j + 1 + lane; r < m; r += 32) df::mac(sh, sl, al[r], al[r]);
+            const double s = df::to_double(df::warp_sum(sh, sl));
+            if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
+        }
+        __syncthreads();
+        k = j + 1;
+    }
+    // R (rows 0..k-1 of every column) back to float64, in place
+    __syncthreads();
+    for (int l = warp; l < c; l += nwarps)
+        for (int r = lane; r < k; r += 32) {
+            const int64_t e = r + (int64_t)l * m;
+            Ad[e] = df::to_double(A[e]);
+        }
+    for (int l = threadIdx.x; l < c; l += blockDim.x) piv[l] = pv[l];
+    if (threadIdx.x == 0) kout[node] = k;
+}
+
 // shared memory of the loop-form solve for ranks up to kmax: the reciprocals
 // of R11's diagonal and the skeleton sort (a power of two >= kmax)
 size_t loop_solve_smem(int kmax) {
@@ -830,6 +1012,7 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     std::call_once(attr, [] {
         set_qr_attrs<double>();
         set_qr_attrs<float>();
+        H2_CUDA(cudaFuncSetAttribute(k_cpqr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_LIMIT));
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -890,7 +1073,11 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         A->evals_block += (double)atot;
         {
             ProfScope ps(KT_CPQR, s);
-            if (f64)
+            if (f64 && !A->fp64_qr)
+                k_cpqr_df<<<nl, qr_threads(cmax), qr_smem(cmax, mmax, esize), s>>>(
+                    lb, h->ycnt.p, A->c.p, aoff.p, reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p,
+                    piv.p);
+            else if (f64)
                 launch_cpqr<double>(nl, qr_smem(cmax, mmax, esize), mmax, lb, h->ycnt.p, A->c.p, aoff.p,
                                     reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p, piv.p, s, cmax);
             else

@@ -247,6 +247,7 @@ struct h2_matrix_s {
     // fp64_products is set (then plain float64); skeleton offsets from their
     // node's centre as hi + lo, built on first use
     bool fp64_products = false;
+    bool fp64_qr = false;  // float64 form: the QR's trailing updates in float64 (else float-float)
     bool tensor_core_products = false;  // mixed form: the 16-column nearfield on the tensor cores
     bool df_ready = false;
     h2::DevBuf<float2> skdf[3];

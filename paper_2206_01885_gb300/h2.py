@@ -50,7 +50,7 @@ class _Params(C.Structure):
 
 class _ConstructOpts(C.Structure):
     _fields_ = [("g_bound", C.c_double), ("mem_mode", C.c_int), ("mem_fraction", C.c_double),
-                ("fp64_products", C.c_int), ("tensor_core_products", C.c_int)]
+                ("fp64_products", C.c_int), ("tensor_core_products", C.c_int), ("fp64_qr", C.c_int)]
 
 
 MEM_MODES = {"on_the_fly": 0, "store": 1, "auto": 2}  # H2_MEM_*
@@ -238,7 +238,8 @@ class H2Matrix(_Handle):
 
     def __init__(self, tree: Tree, hidr: Hidr, kernel, kparams=(), id_tol: float = 1e-6, precision="fp64",
                  stream=None, g_bound: float = 0.0, mem_mode: str = "on_the_fly", mem_fraction: float = 0.0,
-                 fp64_products: bool = False, tensor_core_products: bool = False, _handle=None):
+                 fp64_products: bool = False, tensor_core_products: bool = False, fp64_qr: bool = False,
+                 _handle=None):
         """g_bound = f > 1 bounds ||G||_max by f through exchanges after the
         QR (h2_construct_ex); 0 is the plain column-pivoted ID.  mem_mode:
         "on_the_fly" (coupling and nearfield blocks evaluated in every
@@ -248,7 +249,8 @@ class H2Matrix(_Handle):
         fp64_products: in the float64 form, evaluate the 3D Coulomb products
         in float64 arithmetic instead of float-float.  tensor_core_products: in
         the mixed form, run the several-right-hand-side nearfield 16 columns at
-        a time on the tensor cores."""
+        a time on the tensor cores.  fp64_qr: in the float64 form, keep the
+        QR's trailing updates in float64 arithmetic instead of float-float."""
         if _handle is not None:  # built by construct_batched
             self._h = _handle
             self.tree = tree
@@ -257,7 +259,7 @@ class H2Matrix(_Handle):
         kp = _kparams(kparams)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opts = _ConstructOpts(float(g_bound), MEM_MODES[mem_mode], float(mem_fraction), int(bool(fp64_products)),
-                              int(bool(tensor_core_products)))
+                              int(bool(tensor_core_products)), int(bool(fp64_qr)))
         _check("h2_construct_ex", lib().h2_construct_ex(tree.handle, hidr.handle, _kid(kernel), kp, float(id_tol),
                                                          prec, C.byref(opts), _stream(stream), C.byref(h)))
         self._h = h.value

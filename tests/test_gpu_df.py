@@ -91,3 +91,36 @@ def test_float_float_small_trees_equal_the_dense_product(H2, n, q):
     assert_rows_close(y, O.dense_matvec(pts, "coulomb", (), z), 1e-10, "dense")
     for h in (A, B, hd, t):
         h.free()
+
+
+@pytest.mark.parametrize("kern,kp,eps", [("coulomb", (), 1e-9), ("gaussian", (0.3,), 1e-8), ("multiquadric", (), 1e-8)])
+def test_float_float_qr_equals_float64_qr(H2, kern, kp, eps):
+    """The float64 form's QR in float-float arithmetic (the default) and in
+    float64 arithmetic (fp64_qr): equal ranks and skeletons, U within
+    64 u' c / eps with u' = 2^-46 (the float pairs' rounding in place of
+    float64's), and the oracle's H^2 product within 1e-12 row by row."""
+    n, q, g = 8000, 64, 6
+    pts = I.uniform_cube(n, 3, seed=48)
+    z = I.standard_normal(n, seed=49)
+    t = H2.Tree(dev(pts), q, tau=(1, 2))
+    hd = H2.Hidr(t, g, g, il_reduce=True)
+    A = H2.H2Matrix(t, hd, kern, kp, eps, "fp64")
+    B = H2.H2Matrix(t, hd, kern, kp, eps, "fp64", fp64_qr=True)
+    assert json.loads(A.stats())["fp64_qr"] is False and json.loads(B.stats())["fp64_qr"] is True
+    ka, kb = A.get("rank"), B.get("rank")
+    assert np.array_equal(ka, kb)
+    assert np.array_equal(A.get("skel"), B.get("skel"))
+    nc = A.get("ncand")
+    Ua, Ub = A.get("U"), B.get("U")
+    off = np.concatenate([[0], np.cumsum(ka.astype(np.int64) * nc)])
+    for i in range(t.nnodes):
+        if ka[i] == 0:
+            continue
+        ua, ub = Ua[off[i]:off[i + 1]], Ub[off[i]:off[i + 1]]
+        tol = 64 * 2.0 ** -46 * nc[i] / eps
+        assert np.max(np.abs(ua - ub)) <= tol * max(1.0, np.abs(ub).max()), i
+    o = O.tree_build(pts, q, (1, 2))
+    yo = O.H2(o, O.Hidr(o, g, g, il_reduce=True), kern, kp, eps).matvec(z)
+    assert_rows_close(A.matvec(dev(z)).cpu().numpy(), yo, 1e-12, f"{kern}: float-float QR vs the oracle")
+    for h in (A, B, hd, t):
+        h.free()

@@ -203,8 +203,14 @@ typedef enum {
  * their samples.  Requires g2^dim <= 4096. */
 #define H2_HIDR_IL_REDUCE 0x100
 
+/* Flag ORed into h2_hidr_reduce_ex's method: the top-down sets T_i are copied
+ * into one array each and binned entry by entry, instead of the default volume
+ * search that reads the X_j* in place (with chunk and member boxes).  Both
+ * give the same X_i*, Y_i*; this form is slower and serves comparisons. */
+#define H2_HIDR_COPY_SETS 0x200
+
 /* h2_hidr_reduce with the DataReduct variant `method` (h2_datareduct),
- * optionally ORed with H2_HIDR_IL_REDUCE.
+ * optionally ORed with H2_HIDR_IL_REDUCE and H2_HIDR_COPY_SETS.
  * Errors: as h2_hidr_reduce; H2_ERR_INVALID_ARG for an unknown method or flag,
  * or for H2_HIDR_IL_REDUCE with g2^dim > 4096. */
 h2_status h2_hidr_reduce_ex(h2_tree t, int g1, int g2, int method, void *stream, h2_hidr *out);

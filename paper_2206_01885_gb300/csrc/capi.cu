@@ -267,8 +267,8 @@ h2_tree_s *tree_build_one(const double *pts, int64_t n, int dim, int pts_on_devi
 
 namespace {
 h2_hidr_s *hidr_one(h2_tree_s *t, int g1, int g2, int method, cudaStream_t s) {
-    const bool il = (method & H2_HIDR_IL_REDUCE) != 0;
-    method &= ~H2_HIDR_IL_REDUCE;
+    const bool il = (method & H2_HIDR_IL_REDUCE) != 0, copy = (method & H2_HIDR_COPY_SETS) != 0;
+    method &= ~(H2_HIDR_IL_REDUCE | H2_HIDR_COPY_SETS);
     H2_REQUIRE(method == H2_DR_VOLUME || method == H2_DR_SURFACE || method == H2_DR_FPS,
                "unknown DataReduct method or flag");
     H2_REQUIRE(g1 >= 1 && g2 >= 1, "g1 and g2 must be >= 1");
@@ -284,6 +284,7 @@ h2_hidr_s *hidr_one(h2_tree_s *t, int g1, int g2, int method, cudaStream_t s) {
     h->g2 = g2;
     h->method = method;
     h->il_reduce = il;
+    h->copy_sets = copy;
     try {
         hidr_impl(h);
     } catch (...) {
@@ -354,7 +355,7 @@ h2_status h2_hidr_reduce_ex(h2_tree th, int g1, int g2, int method, void *stream
     return guard([&] {
         H2_REQUIRE(out != nullptr, "out is NULL");
         *out = nullptr;
-        const int m = method & ~H2_HIDR_IL_REDUCE;  // (the method and flags are checked before the handle)
+        const int m = method & ~(H2_HIDR_IL_REDUCE | H2_HIDR_COPY_SETS);  // (checked before the handle)
         H2_REQUIRE(m == H2_DR_VOLUME || m == H2_DR_SURFACE || m == H2_DR_FPS, "unknown DataReduct method or flag");
         h2_tree_s *t = as_tree(th);
         h2_hidr_s *h = hidr_one(t, g1, g2, method, static_cast<cudaStream_t>(stream));
@@ -987,10 +988,10 @@ h2_status h2_get_stats(const void *handle, char *json, int64_t cap) {
             auto *h = static_cast<const h2_hidr_s *>(handle);
             snprintf(buf, sizeof buf,
                      "{\"g1\": %d, \"g2\": %d, \"x_total\": %lld, \"y_total\": %lld, \"t_max_level\": %lld, "
-                     "\"t_total\": %lld, \"ms_up\": %.4f, \"ms_down\": %.4f, \"method\": \"%s\", "
-                     "\"il_reduce\": %s}",
+                     "\"t_total\": %lld, \"t_il_total\": %lld, \"ms_up\": %.4f, \"ms_down\": %.4f, "
+                     "\"method\": \"%s\", \"il_reduce\": %s}",
                      h->g1, h->g2, (long long)h->xtotal, (long long)h->ytotal, (long long)h->tmax,
-                     (long long)h->ttotal, h->ms_up, h->ms_down,
+                     (long long)h->ttotal, (long long)h->iltotal, h->ms_up, h->ms_down,
                      h->method == H2_DR_SURFACE ? "surface" : (h->method == H2_DR_FPS ? "fps" : "volume"),
                      h->il_reduce ? "true" : "false");
         } else if (tag == TAG_MATRIX) {

@@ -197,6 +197,7 @@ struct h2_hidr_s {
     int g1 = 0, g2 = 0;
     int method = 0;  // DataReduct: 0 volume-based, 1 surface-based, 2 farthest point sampling
     bool il_reduce = false;  // Y_i* also takes the reduction of its interaction-list part alone
+    bool copy_sets = false;  // top-down sets copied out and binned entry by entry (H2_HIDR_COPY_SETS)
     // per node: count and device pointer into one of the per-level buffers
     h2::DevBuf<int32_t> xcnt, ycnt;
     h2::DevBuf<int32_t *> xptr, yptr;
@@ -204,7 +205,9 @@ struct h2_hidr_s {
     h2::DevBuf<long long> xbox, ybox;  // per node: bounding box of X_i*, Y_i* (6 integer keys)
     std::vector<int> xmax_level, ymax_level;  // host: largest set per level
     int64_t xtotal = 0, ytotal = 0, tmax = 0, ttotal = 0;
+    int64_t iltotal = 0;  // entries of the interaction-list parts (interaction-list reduction only)
     double ms_up = 0, ms_down = 0;
+    int members_levels = 0;  // top-down levels reduced by the search over members (hidr.cu)
 };
 
 struct h2_matrix_s {

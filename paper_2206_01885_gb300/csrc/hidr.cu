@@ -41,9 +41,10 @@ __global__ void k_size_up(int lb, int nl, const int32_t *nchild, const int32_t *
 // |T_i| = |Y_p*| + sum over j in IL(i) of |X_j*|; one warp per node.  With
 // szl (the interaction-list reduction), szl[a] = the interaction-list part's
 // size, capl[a] its reduced set's capacity, and cap[a] holds both reductions.
+// psz[a] (when given) = |Y_p*|.
 __global__ void k_size_down(int lb, int nl, const int32_t *parent, const int64_t *far_ptr, const int32_t *far_idx,
                             const int32_t *xcnt, const int32_t *ycnt, int g, int d, int64_t *sz, int64_t *cap,
-                            int64_t *szl, int64_t *capl) {
+                            int64_t *szl, int64_t *capl, int64_t *psz) {
     int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (a >= nl) return;
@@ -54,6 +55,7 @@ __global__ void k_size_down(int lb, int nl, const int32_t *parent, const int64_t
     if (lane == 0) {
         const int64_t sl = s;
         s += ycnt[parent[i]];
+        if (psz) psz[a] = ycnt[parent[i]];
         int64_t G = 1;
         for (int k = 0; k < d; k++) G *= g;
         sz[a] = s;
@@ -465,9 +467,10 @@ __device__ __forceinline__ float dr_cell_lb(int packed, int d, const int *cid, c
 
 // Float32 top-two over the points of the cells the lanes selected (lane c's
 // cell `bin` when ok), walked as one flat range across the warp: lane c's cell
-// is [cs, cs + cn) at offset exc of the warp's prefix sum of the counts.
+// is [cs, cs + cn) at offset exc of the warp's prefix sum of the counts.  l1 is
+// the label of the lane's smallest.
 __device__ __forceinline__ void dr_scan_top2(bool ok, int bin, const int *bstart, const float4 *pq, const float *qf,
-                                             float &b1, float &b2, int &p1, int lane) {
+                                             float &b1, float &b2, int32_t &l1, int lane) {
     if (__ballot_sync(0xffffffffu, ok) == 0u) return;
     int cs = 0, cn = 0;
     if (ok) {
@@ -508,7 +511,7 @@ __device__ __forceinline__ void dr_scan_top2(bool ok, int bin, const int *bstart
                 if (d32 < b1) {
                     b2 = b1;
                     b1 = d32;
-                    p1 = p;
+                    l1 = __float_as_int(e.w);
                 } else {
                     b2 = d32;
                 }
@@ -741,7 +744,7 @@ __global__ void __launch_bounds__(DR_THREADS, 5) k_datareduct(const int64_t *tof
                 }
             }
             float b1 = INFINITY, b2 = INFINITY;  // this lane's two smallest float32 distances
-            int p1 = -1;                         // bin-order position of its smallest
+            int32_t l1 = INT_MAX;                // the label of its smallest
             float lim = INFINITY;                // the warp's smallest distance + M
             // rings 0 and 1 with the stop test; a search still open after ring 1
             // (sparse or empty surroundings) scans the non-empty cells instead
@@ -758,7 +761,7 @@ __global__ void __launch_bounds__(DR_THREADS, 5) k_datareduct(const int64_t *tof
                     float lb = 0.f;
                     bool ok = e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, flat, hf, qf, delf, bin, lb);
                     ok = ok && lb <= lim;
-                    dr_scan_top2(ok, bin, bstart, pq, qf, b1, b2, p1, lane);
+                    dr_scan_top2(ok, bin, bstart, pq, qf, b1, b2, l1, lane);
                     lim = warp_minf(b1) + M;
                 }
                 // (r + 1/2) h_min - delta and its square rounded down in float32
@@ -786,7 +789,7 @@ __global__ void __launch_bounds__(DR_THREADS, 5) k_datareduct(const int64_t *tof
                 const float mlb = warp_minf(blb);
                 const int b0 = __shfl_sync(0xffffffffu, bbin, __ffs(__ballot_sync(0xffffffffu, blb == mlb)) - 1);
                 if (b0 >= 0 && mlb <= lim) {
-                    dr_scan_top2(lane == 0, b0, bstart, pq, qf, b1, b2, p1, lane);
+                    dr_scan_top2(lane == 0, b0, bstart, pq, qf, b1, b2, l1, lane);
                     lim = warp_minf(b1) + M;
                 }
                 for (int e0 = 0; e0 < nne; e0 += 32) {
@@ -799,7 +802,7 @@ __global__ void __launch_bounds__(DR_THREADS, 5) k_datareduct(const int64_t *tof
                         const float lb = dr_cell_lb(pk, d, cid, flat, hf, qf, delf, cheb);
                         ok = cheb >= 2 && lb <= lim && bin != b0;
                     }
-                    dr_scan_top2(ok, bin, bstart, pq, qf, b1, b2, p1, lane);
+                    dr_scan_top2(ok, bin, bstart, pq, qf, b1, b2, l1, lane);
                     lim = warp_minf(b1) + M;
                 }
             }
@@ -809,7 +812,7 @@ __global__ void __launch_bounds__(DR_THREADS, 5) k_datareduct(const int64_t *tof
             const float limx = m1 + M;
             int32_t winner;
             if (sec > limx) {
-                winner = __float_as_int(pq[__shfl_sync(0xffffffffu, p1, w)].w);
+                winner = __shfl_sync(0xffffffffu, l1, w);
             } else {
                 // near tie: every point within M of the smallest in float64, over
                 // the cells the search visited
@@ -978,6 +981,720 @@ __global__ void __launch_bounds__(DR_THREADS, 5) k_datareduct(const int64_t *tof
     block_bitonic_sort(win, P);
     int m = block_unique_write(win, P, out, scratch);
     if (threadIdx.x == 0) outcnt[node] = m;
+}
+
+// ------------------------------------- DataReduct over a union of reduced sets
+// A top-down set is a union, S = Y_p* (when given) u X_j* over j in IL(i).
+// The X_j* are many (hundreds per node at tau = 1/2) and each one recurs in
+// the sets of many nodes of its level, so copying S out and binning every
+// entry dominated HiDR.  This form reads the X_j* in place.  Each X_j*
+// (sorted labels, so Morton-coherent) is cut into chunks of DM_CHUNK
+// consecutive labels; the box of every chunk and of every member is computed
+// once per build, in the hi parts of the float32 root-relative split
+// (xh = fl32(fl64(x - corner)), monotone in x, so these boxes bound the hi
+// parts exactly).  Per node the members are entered in every cell of the
+// reference grid their box overlaps (mode A) or, when the member-cell pairs
+// exceed the list's capacity, in the cell of their box centre only, with every
+// cell bound and the stopping radius widened by the largest half extent E
+// (mode B).  A grid point's search walks the cells as the binned search of
+// k_datareduct does; in each cell it scans Y_p*'s points (binned point by
+// point, as there) and, for every member this warp has not yet visited whose
+// box bound passes, the chunks whose box bound passes, lane k taking entry k
+// of a chunk.  The float32 top-two, the stopping rule and the float64
+// decision of near ties are the binned search's, so the result is the same
+// set: for every grid point the float64-nearest point of S, ties to the
+// smaller label.
+//
+// Offsets in a node's frame: a point's offset f = (xh - lh) + (xl - ll) has
+// |fl32(xl - ll)| <= 2u R (1 + u) (u = 2^-24, R the root extent), so xh in
+// [a, b] puts f in [fl32(a - lh) - cR, fl32(b - lh) + cR] for cR = 2.5 u R;
+// the boxes are moved to the frame with cw = 2e-7 R + delf per side, delf
+// being the binned search's widening (it absorbs the rounding of the bound
+// itself).
+constexpr int DM_CHUNK = 32;
+constexpr int DM_MAX_MEMBERS = 16384;  // longest interaction list the member search takes
+
+__global__ void k_chunk_counts(int nn, const int32_t *xcnt, int64_t *nch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nn) nch[i] = (xcnt[i] + DM_CHUNK - 1) / DM_CHUNK;
+}
+
+// chunk boxes cbox[2 (choff[i] + c)], [.. + 1] (low, high corner of the hi
+// parts) and member boxes mbox[2 i], [2 i + 1] of X_i* for nodes [n0, nn);
+// one warp a node
+__global__ void k_member_boxes(int n0, int nn, int32_t *const *xptr, const int32_t *xcnt, const int64_t *choff,
+                               const float4 *xq, float4 *cbox, float4 *mbox) {
+    const int i = n0 + (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= nn) return;
+    const int cnt = xcnt[i];
+    const int32_t *lab = xptr[i];
+    float mlo[3] = {INFINITY, INFINITY, INFINITY}, mhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int c = 0; c * DM_CHUNK < cnt; c++) {
+        const int r = c * DM_CHUNK + lane;
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        if (r < cnt) {
+            const float4 qa = xq[2 * (int64_t)lab[r]];
+            lo[0] = hi[0] = qa.x;
+            lo[1] = hi[1] = qa.y;
+            lo[2] = hi[2] = qa.z;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+                hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            }
+        if (lane == 0) {
+            const int64_t cc = choff[i] + c;
+            cbox[2 * cc] = make_float4(lo[0], lo[1], lo[2], 0.f);
+            cbox[2 * cc + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            mlo[k] = fminf(mlo[k], lo[k]);
+            mhi[k] = fmaxf(mhi[k], hi[k]);
+        }
+    }
+    if (lane == 0) {
+        mbox[2 * (int64_t)i] = make_float4(mlo[0], mlo[1], mlo[2], 0.f);
+        mbox[2 * (int64_t)i + 1] = make_float4(mhi[0], mhi[1], mhi[2], 0.f);
+    }
+}
+
+// Lower bound of the float32 squared distance from the grid point (offset qf)
+// to any point whose hi parts lie in the box (lo, hi), in this node's frame
+// (corner hi parts lh) with cw added per side; flat coordinates add nothing.
+__device__ __forceinline__ float dm_box_lb(float4 lo, float4 hi, const float *lh, const float *qf,
+                                           const bool *flat, float cw, int d) {
+    const float l3[3] = {lo.x, lo.y, lo.z}, h3[3] = {hi.x, hi.y, hi.z};
+    float lb = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (k >= d) break;
+        if (flat[k]) continue;
+        const float a = (l3[k] - lh[k]) - cw, b = (h3[k] - lh[k]) + cw;
+        const float gap = fmaxf(0.f, fmaxf(a - qf[k], qf[k] - b));
+        lb = fmaf(gap, gap, lb);
+    }
+    return lb;
+}
+
+struct DMArgs {
+    int lb;        // first node of the level; node lb + a is CTA a's
+    int outlb;     // the result of CTA a goes to outptr / outcnt / outbox [outlb + a]
+    int g, d;
+    int mcap;      // capacity of the member-cell list (entries)
+    int vwords;    // 32-bit words of a warp's visited-member bitmask
+    const int64_t *toff;   // |S| of CTA a's set = toff[a + 1] - toff[a]
+    const int32_t *parent;  // null: the set has no Y_p* part
+    int32_t *const *yptr;
+    const int32_t *ycnt;
+    const long long *ybox;
+    const int64_t *poff;    // staging of CTA a's Y_p* part: pbin / pq [poff[a] ..)
+    int2 *pbin;
+    float4 *pq;
+    const int64_t *far_ptr;
+    const int32_t *far_idx;
+    int32_t *const *xptr;
+    const int32_t *xcnt;
+    const long long *xbox;
+    const int64_t *choff;
+    const float4 *cbox, *mbox;
+    int32_t *const *outptr;
+    int32_t *outcnt;
+    long long *outbox;
+};
+
+// the grid point's frame, shared by the scans of one warp
+struct DMFrame {
+    const float4 *xq;
+    const double *x0, *x1, *x2;
+    float lh[3], ll[3], qf[3];
+    double q[3];
+    bool flat[3];
+    float cw, M;
+    int d;
+};
+
+__device__ __forceinline__ float dm_point_d32(const DMFrame &F, int32_t sid) {
+    const float4 qa = F.xq[2 * (int64_t)sid], qb = F.xq[2 * (int64_t)sid + 1];
+    const float e0 = ((qa.x - F.lh[0]) + (qa.w - F.ll[0])) - F.qf[0];
+    const float e1 = F.d > 1 ? ((qa.y - F.lh[1]) + (qb.x - F.ll[1])) - F.qf[1] : 0.f;
+    const float e2 = F.d > 2 ? ((qa.z - F.lh[2]) + (qb.y - F.ll[2])) - F.qf[2] : 0.f;
+    return fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
+}
+
+// The chunks of member j whose box bound is at most lim, in order: float32
+// top-two of the lane (entry k of a chunk on lane k, l1 the label of its
+// smallest), lim = the warp's smallest + M after each chunk.
+__device__ __forceinline__ void dm_scan_member(const DMArgs &A, const DMFrame &F, int j, float &b1, float &b2,
+                                               int32_t &l1, float &lim, int lane) {
+    const int cnt = A.xcnt[j];
+    const int32_t *lab = A.xptr[j];
+    const float4 *cb = A.cbox + 2 * A.choff[j];
+    const int nc = (cnt + DM_CHUNK - 1) / DM_CHUNK;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+        float lbc = INFINITY;
+        bool cand = false;
+        if (c0 + lane < nc) {
+            lbc = dm_box_lb(cb[2 * (c0 + lane)], cb[2 * (c0 + lane) + 1], F.lh, F.qf, F.flat, F.cw, F.d);
+            cand = lbc <= lim;
+        }
+        unsigned pc = __ballot_sync(0xffffffffu, cand);
+        while (pc) {
+            const int s = __ffs(pc) - 1;
+            pc &= pc - 1;
+            if (__shfl_sync(0xffffffffu, lbc, s) > lim) continue;  // lim fell since the test
+            const int r = (c0 + s) * DM_CHUNK + lane;
+            if (r < cnt) {
+                const int32_t sid = lab[r];
+                const float d32 = dm_point_d32(F, sid);
+                if (d32 < b2) {
+                    if (d32 < b1) {
+                        b2 = b1;
+                        b1 = d32;
+                        l1 = sid;
+                    } else {
+                        b2 = d32;
+                    }
+                }
+            }
+            lim = warp_minf(b1) + F.M;
+        }
+    }
+}
+
+// Near ties over member j: every point of its chunks whose float32 distance is
+// at most limx, compared in float64 (the lane's best key bk and label bl; the
+// caller reduces over the warp).
+__device__ __forceinline__ void dm_exact_member(const DMArgs &A, const DMFrame &F, int j, float limx,
+                                                long long &bk, int32_t &bl, int lane) {
+    const int cnt = A.xcnt[j];
+    const int32_t *lab = A.xptr[j];
+    const float4 *cb = A.cbox + 2 * A.choff[j];
+    const int nc = (cnt + DM_CHUNK - 1) / DM_CHUNK;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+        bool pass = false;
+        if (c0 + lane < nc)
+            pass = dm_box_lb(cb[2 * (c0 + lane)], cb[2 * (c0 + lane) + 1], F.lh, F.qf, F.flat, F.cw, F.d) <= limx;
+        unsigned pc = __ballot_sync(0xffffffffu, pass);
+        while (pc) {
+            const int s = __ffs(pc) - 1;
+            pc &= pc - 1;
+            const int r = (c0 + s) * DM_CHUNK + lane;
+            if (r < cnt) {
+                const int32_t sid = lab[r];
+                if (dm_point_d32(F, sid) <= limx) {
+                    const long long kk = __double_as_longlong(h2_dist2(F.d, F.x0[sid], F.d > 1 ? F.x1[sid] : 0.0,
+                                                                       F.d > 2 ? F.x2[sid] : 0.0, F.q[0], F.q[1],
+                                                                       F.q[2]));
+                    if (kk < bk || (kk == bk && sid < bl)) {
+                        bk = kk;
+                        bl = sid;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// The members listed in the cells the lanes selected (lane c's cell `bin`
+// when ok), walked as one flat range across the warp as dr_scan_top2 walks
+// points.  A member not yet in the warp's visited bitmask whose box bound is
+// at most lim (limx, exact) is marked and scanned.
+template <bool EXACT>
+__device__ __forceinline__ void dm_visit(bool ok, int bin, const int *mstart, const uint16_t *mlist, uint32_t *vis,
+                                         int64_t f0, const DMArgs &A, const DMFrame &F, float &b1, float &b2,
+                                         int32_t &l1, float &lim, long long &bk, int32_t &bl, int lane) {
+    if (__ballot_sync(0xffffffffu, ok) == 0u) return;
+    int cs = 0, cn = 0;
+    if (ok) {
+        cs = mstart[bin];
+        cn = mstart[bin + 1] - cs;
+    }
+    int inc = cn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    const int exc = inc - cn;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        const int f = t0 + lane;
+        int src = 0;  // last lane whose range starts at or before f
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int ex = __shfl_sync(0xffffffffu, exc, src + st);
+            if (ex <= f) src += st;
+        }
+        const int pos = __shfl_sync(0xffffffffu, cs, src) + f - __shfl_sync(0xffffffffu, exc, src);
+        int e = -1;
+        float lbm = INFINITY;
+        bool cand = false;  // (explicit: lim starts infinite, and INF <= INF)
+        if (f < total) {
+            e = mlist[pos];
+            if (!((vis[e >> 5] >> (e & 31)) & 1u)) {
+                const int j = A.far_idx[f0 + e];
+                lbm = dm_box_lb(A.mbox[2 * (int64_t)j], A.mbox[2 * (int64_t)j + 1], F.lh, F.qf, F.flat, F.cw, F.d);
+                cand = lbm <= lim;
+            }
+        }
+        unsigned pm = __ballot_sync(0xffffffffu, cand);
+        while (pm) {
+            const int s = __ffs(pm) - 1;
+            pm &= pm - 1;
+            const int es = __shfl_sync(0xffffffffu, e, s);
+            const float lbs = __shfl_sync(0xffffffffu, lbm, s);
+            const uint32_t bit = 1u << (es & 31);
+            uint32_t was = 0u;  // mark it; lane 0's test decides for the warp
+            if (lane == 0) was = atomicOr(&vis[es >> 5], bit);
+            if (__shfl_sync(0xffffffffu, was, 0) & bit) continue;  // listed twice among these cells
+            if (lbs > lim) continue;
+            const int j = A.far_idx[f0 + es];
+            if (EXACT) dm_exact_member(A, F, j, lim, bk, bl, lane);
+            else dm_scan_member(A, F, j, b1, b2, l1, lim, lane);
+        }
+    }
+}
+
+// dynamic shared memory of k_dr_members (G <= DR_BIN_MAX): k_datareduct's
+// binned layout (winners, Y_p*'s bin starts, the non-empty cells, the
+// grid-point table), then the member cells' starts (G + 2 ints), the warps'
+// visited bitmasks (vwords words each) and the member-cell list (mcap 16-bit
+// member indices)
+__host__ __device__ inline size_t dm_mstart_offset(int G) { return (dr_smem_bytes(G) + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t dm_vis_offset(int G) {
+    return (dm_mstart_offset(G) + (size_t)(G + 2) * 4 + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t dm_mlist_offset(int G, int vwords) {
+    return dm_vis_offset(G) + (size_t)(DR_THREADS / 32) * vwords * 4;
+}
+__host__ __device__ inline size_t dm_smem_bytes(int G, int vwords, int mcap) {
+    return dm_mlist_offset(G, vwords) + (size_t)mcap * 2;
+}
+
+// cell range [c0, c1] per coordinate of a member box (hi parts lo, hi) moved
+// to this node's frame and widened by cw; flat coordinates take cell 0
+__device__ __forceinline__ void dm_cell_range(float4 lo4, float4 hi4, const float *lh, const bool *flat,
+                                              const float *ihf, float cw, int d, int g, int *c0, int *c1,
+                                              float &ext) {
+    const float l3[3] = {lo4.x, lo4.y, lo4.z}, h3[3] = {hi4.x, hi4.y, hi4.z};
+    ext = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        c0[k] = c1[k] = 0;
+        if (k >= d || flat[k]) continue;
+        const float a = (l3[k] - lh[k]) - cw, b = (h3[k] - lh[k]) + cw;
+        c0[k] = min(max((int)(a * ihf[k]), 0), g - 1);
+        c1[k] = min(max((int)(b * ihf[k]), 0), g - 1);
+        ext = fmaxf(ext, b - a);
+    }
+}
+
+// bin of the cell holding the centre of a member box (as dm_cell_range moves it)
+__device__ __forceinline__ int dm_centre_bin(float4 lo4, float4 hi4, const float *lh, const bool *flat,
+                                             const float *ihf, float cw, int d, int g) {
+    const float l3[3] = {lo4.x, lo4.y, lo4.z}, h3[3] = {hi4.x, hi4.y, hi4.z};
+    int bin = 0, stride = 1;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (k >= d) break;
+        int c = 0;
+        if (!flat[k]) {
+            const float a = (l3[k] - lh[k]) - cw, b = (h3[k] - lh[k]) + cw;
+            c = min(max((int)(0.5f * (a + b) * ihf[k]), 0), g - 1);
+        }
+        bin += c * stride;
+        stride *= g;
+    }
+    return bin;
+}
+
+// One CTA per node: DataReduct(S, g^d) for S = Y_p* (when A.parent) u X_j*
+// over j in IL(i), read in place.  Result as k_datareduct's: the distinct
+// winners sorted to outptr[outlb + a], their number and box.
+__global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints PT) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int scratch[33];
+    __shared__ long long s_box[6];
+    __shared__ int s_cnt, s_nne;
+    __shared__ unsigned s_ext;
+    const int a = blockIdx.x, i = A.lb + a;
+    const int d = A.d, g = A.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int G = 1;
+    for (int k = 0; k < d; k++) G *= g;
+    const int64_t nt = A.toff[a + 1] - A.toff[a];
+    const int64_t f0 = A.far_ptr[i];
+    const int m = (int)(A.far_ptr[i + 1] - f0);
+    const int p = A.parent ? A.parent[i] : -1;
+    const int np = p >= 0 ? A.ycnt[p] : 0;
+    const int32_t *Yp = np > 0 ? A.yptr[p] : nullptr;
+    int32_t *out = A.outptr[A.outlb + a];
+    int32_t *win = reinterpret_cast<int32_t *>(smem_raw);
+    {  // the box of S: the union of its parts' boxes
+        long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+        for (int e = threadIdx.x; e < m; e += blockDim.x) box_merge(lo, hi, A.xbox + 6 * (int64_t)A.far_idx[f0 + e]);
+        if (threadIdx.x == 0 && np > 0) box_merge(lo, hi, A.ybox + 6 * (int64_t)p);
+        block_box_write(lo, hi, s_box);
+        __syncthreads();
+    }
+    if (nt <= G) {  // DataReduct returns S itself
+        int P = 1;
+        while (P < nt) P <<= 1;
+        for (int r = threadIdx.x; r < P; r += blockDim.x) win[r] = r < np ? Yp[r] : INT_MAX;
+        if (threadIdx.x == 0) s_cnt = np;
+        __syncthreads();
+        for (int e = warp; e < m; e += nw) {
+            const int j = A.far_idx[f0 + e];
+            const int c = A.xcnt[j];
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&s_cnt, c);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int32_t *src = A.xptr[j];
+            for (int r = lane; r < c; r += 32) win[base + r] = src[r];
+        }
+        __syncthreads();
+        block_bitonic_sort(win, P);
+        for (int r = threadIdx.x; r < nt; r += blockDim.x) out[r] = win[r];
+        if (threadIdx.x < 6) A.outbox[6 * (int64_t)(A.outlb + a) + threadIdx.x] = s_box[threadIdx.x];
+        if (threadIdx.x == 0) A.outcnt[A.outlb + a] = (int32_t)nt;
+        return;
+    }
+    DMFrame F;
+    F.xq = PT.xq;
+    F.x0 = PT.x[0];
+    F.x1 = PT.x[1];
+    F.x2 = PT.x[2];
+    F.d = d;
+    double l[3] = {0.0, 0.0, 0.0}, h[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (k >= d) break;
+        l[k] = dkey_inv(s_box[k]);
+        h[k] = __ddiv_rn(__dsub_rn(dkey_inv(s_box[3 + k]), l[k]), (double)g);
+    }
+    double W = 0.0, hmin = INFINITY;
+    float ihf[3] = {0.f, 0.f, 0.f}, hf[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        F.flat[k] = true;
+        F.lh[k] = F.ll[k] = F.qf[k] = 0.f;
+        F.q[k] = 0.0;
+        if (k >= d) continue;
+        W = dmax_(W, __dmul_rn(h[k], (double)g));
+        F.flat[k] = !(h[k] > 0.0);
+        if (!F.flat[k]) {
+            hmin = dmin_(hmin, h[k]);
+            ihf[k] = (float)(1.0 / h[k]);
+            hf[k] = (float)h[k];
+        }
+        const double Lk = l[k] - PT.ref[k];
+        F.lh[k] = (float)Lk;
+        F.ll[k] = (float)(Lk - (double)F.lh[k]);
+    }
+    // M and delf as in k_datareduct; cw widens the member and chunk boxes
+    F.M = (float)(8e-6 * W * W + 1e-12 * W * PT.R);
+    const float delf = (float)(1e-5 * W + 1e-12 * PT.R);
+    F.cw = (float)(2e-7 * PT.R) + delf;
+    const float hminf = (float)hmin;
+    int *bstart = reinterpret_cast<int *>(smem_raw + dr_bins_offset(G));
+    int *mstart = reinterpret_cast<int *>(smem_raw + dm_mstart_offset(G));
+    uint32_t *vis = reinterpret_cast<uint32_t *>(smem_raw + dm_vis_offset(G)) + warp * A.vwords;
+    uint16_t *mlist = reinterpret_cast<uint16_t *>(smem_raw + dm_mlist_offset(G, A.vwords));
+    for (int b = threadIdx.x; b <= G; b += blockDim.x) bstart[b] = 0;
+    for (int b = threadIdx.x; b < G + 2; b += blockDim.x) mstart[b] = 0;
+    if (threadIdx.x == 0) {
+        s_cnt = 0;
+        s_ext = 0u;
+    }
+    __syncthreads();
+    // Y_p*: counting sort into the cells, as k_datareduct bins its set
+    int2 *bidx = A.pbin + (np > 0 ? A.poff[a] : 0);
+    float4 *pq = A.pq + (np > 0 ? A.poff[a] : 0);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int p0 = warp * 32; p0 < np; p0 += blockDim.x) {
+        const int pp = p0 + lane;
+        int bi = -1;
+        if (pp < np) {
+            const int32_t sid = Yp[pp];
+            int stride = 1;
+            bi = 0;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k >= d) break;
+                int cidx = 0;
+                if (!F.flat[k]) {
+                    const float f = dr_offset(PT.xq, sid, k, F.lh[k], F.ll[k]);
+                    cidx = min(max((int)(f * ihf[k]), 0), g - 1);
+                }
+                bi += cidx * stride;
+                stride *= g;
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, bi);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (bi >= 0 && lane == leader) base = atomicAdd(&bstart[bi + 1], __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (bi >= 0) bidx[pp] = make_int2(bi, base + __popc(peers & lt));
+    }
+    // members: count the member-cell pairs (mode A)
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+        const int j = A.far_idx[f0 + e];
+        int c0[3], c1[3];
+        float ext;
+        dm_cell_range(A.mbox[2 * (int64_t)j], A.mbox[2 * (int64_t)j + 1], F.lh, F.flat, ihf, F.cw, d, g, c0, c1, ext);
+        atomicAdd(&s_cnt, (c1[0] - c0[0] + 1) * (c1[1] - c0[1] + 1) * (c1[2] - c0[2] + 1));
+        for (int z = c0[2]; z <= c1[2]; z++)
+            for (int y = c0[1]; y <= c1[1]; y++)
+                for (int x = c0[0]; x <= c1[0]; x++) atomicAdd(&mstart[x + g * (y + g * z) + 2], 1);
+    }
+    __syncthreads();
+    const bool modeB = s_cnt > A.mcap;
+    if (modeB) {  // too many pairs: each member in the cell of its box centre
+        for (int b = threadIdx.x; b < G + 2; b += blockDim.x) mstart[b] = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < m; e += blockDim.x) {
+            const int j = A.far_idx[f0 + e];
+            int c0[3], c1[3];
+            float ext;
+            const float4 lo4 = A.mbox[2 * (int64_t)j], hi4 = A.mbox[2 * (int64_t)j + 1];
+            dm_cell_range(lo4, hi4, F.lh, F.flat, ihf, F.cw, d, g, c0, c1, ext);
+            atomicMax(&s_ext, __float_as_uint(ext));  // non-negative floats order as their bits
+            atomicAdd(&mstart[dm_centre_bin(lo4, hi4, F.lh, F.flat, ihf, F.cw, d, g) + 2], 1);
+        }
+    }
+    __syncthreads();
+    block_scan_inclusive(bstart, G + 1, scratch);  // bstart[b]: first position of bin b
+    block_scan_inclusive(mstart, G + 2, scratch);  // mstart[b + 1]: first position of bin b
+    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+        const int2 bo = bidx[pp];
+        const int pos = bstart[bo.x] + bo.y;
+        const int32_t sid = Yp[pp];
+        const float4 qa = PT.xq[2 * (int64_t)sid], qb = PT.xq[2 * (int64_t)sid + 1];
+        const float p0f = (qa.x - F.lh[0]) + (qa.w - F.ll[0]);
+        const float p1f = d > 1 ? (qa.y - F.lh[1]) + (qb.x - F.ll[1]) : 0.f;
+        const float p2f = d > 2 ? (qa.z - F.lh[2]) + (qb.y - F.ll[2]) : 0.f;
+        pq[pos] = make_float4(p0f, p1f, p2f, __int_as_float(sid));
+    }
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {  // the member-cell list, bin by bin
+        const int j = A.far_idx[f0 + e];
+        const float4 lo4 = A.mbox[2 * (int64_t)j], hi4 = A.mbox[2 * (int64_t)j + 1];
+        if (modeB) {
+            mlist[atomicAdd(&mstart[dm_centre_bin(lo4, hi4, F.lh, F.flat, ihf, F.cw, d, g) + 1], 1)] = (uint16_t)e;
+        } else {
+            int c0[3], c1[3];
+            float ext;
+            dm_cell_range(lo4, hi4, F.lh, F.flat, ihf, F.cw, d, g, c0, c1, ext);
+            for (int z = c0[2]; z <= c1[2]; z++)
+                for (int y = c0[1]; y <= c1[1]; y++)
+                    for (int x = c0[0]; x <= c1[0]; x++)
+                        mlist[atomicAdd(&mstart[x + g * (y + g * z) + 1], 1)] = (uint16_t)e;
+        }
+    }
+    // grid points: float64 q and its float32 offset qf, computed once each
+    double *qtab = reinterpret_cast<double *>(smem_raw + dr_qtab_offset(G));
+    float *qftab = reinterpret_cast<float *>(qtab + 3 * G);
+    const bool table = G <= DR_QTAB;
+    if (table)
+        for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
+            int rem = gi;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k >= d) break;
+                const int idx = rem % g;
+                rem /= g;
+                const double qk = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
+                qtab[3 * gi + k] = qk;
+                qftab[3 * gi + k] = (float)__dsub_rn(qk, l[k]);
+            }
+        }
+    __syncthreads();  // mstart[b] is now the first position of bin b
+    int *nel = bstart + G + 1;
+    if (threadIdx.x == 0) s_nne = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < G; b += blockDim.x)
+        if (bstart[b + 1] > bstart[b] || mstart[b + 1] > mstart[b]) nel[atomicAdd(&s_nne, 1)] = dr_pack_cell(b, d, g);
+    __syncthreads();
+    const int nne = s_nne;
+    // mode B widens every cell bound and the stopping radius by the largest
+    // half extent of a member box (plus its rounding)
+    const float delc = modeB ? delf + fmaf(0.5f, __uint_as_float(s_ext), 1e-6f * __uint_as_float(s_ext)) + delf : delf;
+    for (int gi = warp; gi < G; gi += nw) {
+        int cid[3] = {0, 0, 0};
+        int rmax = 0;
+        {
+            int rem = gi;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k >= d) break;
+                const int idx = rem % g;
+                rem /= g;
+                if (table) {
+                    F.q[k] = qtab[3 * gi + k];
+                    F.qf[k] = qftab[3 * gi + k];
+                } else {
+                    F.q[k] = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
+                    F.qf[k] = (float)__dsub_rn(F.q[k], l[k]);
+                }
+                cid[k] = F.flat[k] ? 0 : idx;
+                if (!F.flat[k]) rmax = max(rmax, max(cid[k], g - 1 - cid[k]));
+            }
+        }
+        for (int w = lane; w < A.vwords; w += 32) vis[w] = 0u;
+        __syncwarp();
+        float b1 = INFINITY, b2 = INFINITY;  // this lane's two smallest float32 distances
+        int32_t l1 = INT_MAX;                // the label of its smallest
+        float lim = INFINITY;                // the warp's smallest distance + M
+        long long bk = LLONG_MAX;            // (near ties) the best float64 key and its label
+        int32_t bl = INT_MAX;
+        // rings 0 and 1 with the stop test; a search still open after ring 1
+        // scans the non-empty cells instead
+        const int rA = min(rmax, 1);
+        int stage = 2;  // 0 or 1: stopped after that ring; 2: the non-empty cells were scanned
+        for (int r = 0; r <= rA; r++) {
+            const int side = 2 * r + 1;
+            int total = 1;
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (k < d) total *= F.flat[k] ? 1 : side;
+            for (int e0 = 0; e0 < total; e0 += 32) {
+                int bin = 0;
+                float lb = 0.f;
+                bool ok = e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, F.flat, hf, F.qf, delc, bin, lb);
+                ok = ok && lb <= lim;
+                dr_scan_top2(ok, bin, bstart, pq, F.qf, b1, b2, l1, lane);
+                lim = warp_minf(b1) + F.M;
+                dm_visit<false>(ok, bin, mstart, mlist, vis, f0, A, F, b1, b2, l1, lim, bk, bl, lane);
+            }
+            // (r + 1/2) h_min - delta and its square rounded down in float32
+            const float rr = ((float)r + 0.5f) * hminf * 0.9999996f - delc;
+            if (rr > 0.f && lim < rr * rr * 0.9999996f) {
+                stage = r;
+                break;
+            }
+        }
+        if (stage == 2 && rmax <= 1) stage = rA;  // rings 0..rmax held every cell
+        if (stage == 2) {
+            // the non-empty cell with the smallest bound first, then the
+            // others whose bound passes
+            float blb = INFINITY;
+            int bbin = -1;
+            for (int e0 = lane; e0 < nne; e0 += 32) {
+                const int pk = nel[e0];
+                int cheb;
+                const float lb = dr_cell_lb(pk, d, cid, F.flat, hf, F.qf, delc, cheb);
+                if (cheb >= 2 && lb < blb) {
+                    blb = lb;
+                    bbin = pk & 4095;
+                }
+            }
+            const float mlb = warp_minf(blb);
+            const int b0 = __shfl_sync(0xffffffffu, bbin, __ffs(__ballot_sync(0xffffffffu, blb == mlb)) - 1);
+            if (b0 >= 0 && mlb <= lim) {
+                dr_scan_top2(lane == 0, b0, bstart, pq, F.qf, b1, b2, l1, lane);
+                lim = warp_minf(b1) + F.M;
+                dm_visit<false>(lane == 0, b0, mstart, mlist, vis, f0, A, F, b1, b2, l1, lim, bk, bl, lane);
+            }
+            for (int e0 = 0; e0 < nne; e0 += 32) {
+                bool ok = false;
+                int bin = 0;
+                if (e0 + lane < nne) {
+                    const int pk = nel[e0 + lane];
+                    bin = pk & 4095;
+                    int cheb;
+                    const float lb = dr_cell_lb(pk, d, cid, F.flat, hf, F.qf, delc, cheb);
+                    ok = cheb >= 2 && lb <= lim && bin != b0;
+                }
+                dr_scan_top2(ok, bin, bstart, pq, F.qf, b1, b2, l1, lane);
+                lim = warp_minf(b1) + F.M;
+                dm_visit<false>(ok, bin, mstart, mlist, vis, f0, A, F, b1, b2, l1, lim, bk, bl, lane);
+            }
+        }
+        const float m1 = warp_minf(b1);
+        const int w = __ffs(__ballot_sync(0xffffffffu, b1 == m1)) - 1;
+        const float sec = warp_minf(lane == w ? b2 : b1);
+        float limx = m1 + F.M;
+        int32_t winner;
+        if (sec > limx) {
+            winner = __shfl_sync(0xffffffffu, l1, w);
+        } else {
+            // near tie: every point within M of the smallest in float64, over
+            // the cells the search visited
+            for (int v = lane; v < A.vwords; v += 32) vis[v] = 0u;
+            __syncwarp();
+            const int rB = stage == 2 ? rA : stage;
+            for (int r = 0; r <= rB; r++) {
+                const int side = 2 * r + 1;
+                int total = 1;
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    if (k < d) total *= F.flat[k] ? 1 : side;
+                for (int e0 = 0; e0 < total; e0 += 32) {
+                    int bin = 0;
+                    float lb = 0.f;
+                    bool ok =
+                        e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, F.flat, hf, F.qf, delc, bin, lb);
+                    ok = ok && lb <= limx;
+                    dr_scan_exact(ok && bstart[bin + 1] > bstart[bin], bin, bstart, pq, F.qf, limx, d, F.x0, F.x1,
+                                  F.x2, F.q, bk, bl, lane);
+                    dm_visit<true>(ok, bin, mstart, mlist, vis, f0, A, F, b1, b2, l1, limx, bk, bl, lane);
+                }
+            }
+            if (stage == 2)
+                for (int e0 = 0; e0 < nne; e0 += 32) {
+                    bool ok = false;
+                    int bin = 0;
+                    if (e0 + lane < nne) {
+                        const int pk = nel[e0 + lane];
+                        bin = pk & 4095;
+                        int cheb;
+                        const float lb = dr_cell_lb(pk, d, cid, F.flat, hf, F.qf, delc, cheb);
+                        ok = cheb >= 2 && lb <= limx;
+                    }
+                    dr_scan_exact(ok && bstart[bin + 1] > bstart[bin], bin, bstart, pq, F.qf, limx, d, F.x0, F.x1,
+                                  F.x2, F.q, bk, bl, lane);
+                    dm_visit<true>(ok, bin, mstart, mlist, vis, f0, A, F, b1, b2, l1, limx, bk, bl, lane);
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long kk = __shfl_xor_sync(0xffffffffu, bk, o);
+                const int32_t kl = __shfl_xor_sync(0xffffffffu, bl, o);
+                if (kk < bk || (kk == bk && kl < bl)) {
+                    bk = kk;
+                    bl = kl;
+                }
+            }
+            winner = bl;
+        }
+        if (lane == 0) win[gi] = winner;
+    }
+    __syncthreads();
+    {  // bounding box of the winners
+        long long blo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, bhi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+        for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
+            const int32_t sid = win[gi];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k >= d) break;
+                const long long kv = dkey((k == 0 ? F.x0 : (k == 1 ? F.x1 : F.x2))[sid]);
+                blo[k] = min(blo[k], kv);
+                bhi[k] = max(bhi[k], kv);
+            }
+        }
+        block_box_write(blo, bhi, A.outbox + 6 * (int64_t)(A.outlb + a));
+    }
+    int P = 1;
+    while (P < G) P <<= 1;
+    for (int r = G + threadIdx.x; r < P; r += blockDim.x) win[r] = INT_MAX;
+    __syncthreads();
+    block_bitonic_sort(win, P);
+    const int mm = block_unique_write(win, P, out, scratch);
+    if (threadIdx.x == 0) A.outcnt[A.outlb + a] = mm;
 }
 
 // Surface-based DataReduct (section 3.3): the reference set is ne points on
@@ -1364,6 +2081,28 @@ void launch_datareduct(const int64_t *toff, const int32_t *tdata, int64_t ttot, 
     H2_LAUNCH("k_datareduct");
 }
 
+constexpr int DM_MCAP_MAX = 32768;         // member-cell list entries at most
+constexpr size_t DM_SMEM_MAX = 200 * 1024;  // dynamic shared memory of k_dr_members at most
+
+// DataReduct of the nl sets A describes by the search over members; ilmax is
+// the longest interaction list among them
+void launch_members(DMArgs A, const DRPoints &pts, int nl, int G, int ilmax, cudaStream_t s) {
+    if (nl <= 0) return;
+    A.vwords = std::max(1, (ilmax + 31) / 32);
+    // about six cells a member (boxes near a cell's size overlap two cells per
+    // coordinate at most); a node needing more takes mode B
+    A.mcap = std::max(ilmax, std::min(6 * ilmax + G, DM_MCAP_MAX));
+    const size_t sm = dm_smem_bytes(G, A.vwords, A.mcap);
+    H2_REQUIRE(sm <= DM_SMEM_MAX, "DataReduct over members: shared memory");
+    static std::once_flag attr;
+    std::call_once(attr, [] {
+        H2_CUDA(cudaFuncSetAttribute(k_dr_members, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DM_SMEM_MAX));
+    });
+    ProfScope ps(KT_DATAREDUCT, s);
+    k_dr_members<<<nl, DR_THREADS, sm, s>>>(A, pts);
+    H2_LAUNCH("k_dr_members");
+}
+
 }  // namespace
 
 void hidr_impl(h2_hidr_s *h) {
@@ -1428,6 +2167,35 @@ void hidr_impl(h2_hidr_s *h) {
     // top-down: Y_i* = DataReduct(Y_p* u X_j* (j in IL(i)), g2^d), level 1 first;
     // with the interaction-list reduction, u DataReduct(X_j* (j in IL(i)), g2^d)
     const bool il = h->il_reduce;
+    const int G2 = (int)gridsize(h->g2, d);
+    // The volume method on a grid binned in shared memory reads the X_j* in
+    // place (k_dr_members) on levels whose interaction lists are at most
+    // DM_MAX_MEMBERS long; other levels and methods copy each set out first.
+    const bool members = h->method == 0 && G2 <= DR_BIN_MAX && !h->copy_sets;
+    std::vector<int> ilmax(t->nlevels, 0);
+    DevBuf<int64_t> nch, choff, psz, poff;
+    DevBuf<float4> cbox, mbox;
+    DevBuf<int2> pbin;
+    DevBuf<float4> ppq;
+    if (members) {
+        const std::vector<int64_t> fp = read_vec(t->far_ptr.p, (size_t)nn + 1, s);
+        for (int l = 1; l < t->nlevels; l++)
+            for (int i = t->lptr[l]; i < t->lptr[l + 1]; i++)
+                ilmax[l] = std::max(ilmax[l], (int)std::min<int64_t>(fp[i + 1] - fp[i], INT_MAX));
+        nch.alloc(nn, s);
+        choff.alloc(nn + 1, s);
+        k_chunk_counts<<<blocks_for(nn, 256), 256, 0, s>>>(nn, h->xcnt.p, nch.p);
+        H2_LAUNCH("k_chunk_counts");
+        scan_exclusive(nch.p, choff.p, nn, s);
+        const int64_t nchunks = read_scalar(choff.p + nn, s);
+        cbox.alloc((size_t)std::max<int64_t>(2 * nchunks, 2), s);
+        mbox.alloc((size_t)2 * nn, s);
+        if (nn > 1) {
+            k_member_boxes<<<blocks_for((int64_t)(nn - 1) * 32, 256), 256, 0, s>>>(1, nn, h->xptr.p, h->xcnt.p,
+                                                                                   choff.p, t->xq.p, cbox.p, mbox.p);
+            H2_LAUNCH("k_member_boxes");
+        }
+    }
     DevBuf<int64_t> szl, capl, loff, lcoff;
     DevBuf<int32_t> tl, lbuf, lcnt;
     DevBuf<int32_t *> lptr;
@@ -1439,48 +2207,97 @@ void hidr_impl(h2_hidr_s *h) {
         merge_smem = (size_t)P * sizeof(int32_t);
         H2_REQUIRE(merge_smem <= 48 * 1024, "the interaction-list reduction needs g2^dim <= 4096");
     }
+    h->members_levels = 0;
     for (int l = 1; l < t->nlevels; l++) {
         int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
+        const bool mem_l = members && ilmax[l] <= DM_MAX_MEMBERS;
         sz.alloc(nl, s); cap.alloc(nl, s); toff.alloc(nl + 1, s); coff.alloc(nl + 1, s);
         if (il) { szl.alloc(nl, s); capl.alloc(nl, s); loff.alloc(nl + 1, s); lcoff.alloc(nl + 1, s); }
+        if (mem_l) { psz.alloc(nl, s); poff.alloc(nl + 1, s); }
         k_size_down<<<blocks_for((int64_t)nl * 32, 256), 256, 0, s>>>(lb, nl, t->parent.p, t->far_ptr.p,
                                                                        t->far_idx.p, h->xcnt.p, h->ycnt.p, h->g2, d,
                                                                        sz.p, cap.p, il ? szl.p : nullptr,
-                                                                       il ? capl.p : nullptr);
+                                                                       il ? capl.p : nullptr, mem_l ? psz.p : nullptr);
         H2_LAUNCH("k_size_down");
         scan_exclusive(sz.p, toff.p, nl, s);
         scan_exclusive(cap.p, coff.p, nl, s);
         int64_t ttot = read_scalar(toff.p + nl, s), ctot = read_scalar(coff.p + nl, s);
         h->tmax = std::max(h->tmax, ttot);
         h->ttotal += ttot;
-        tdata.alloc(ttot > 0 ? ttot : 1, s);
         h->ybufs[l].alloc(ctot > 0 ? ctot : 1, s);
         k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(lb, nl, h->ybufs[l].p, coff.p, h->yptr.p);
         H2_LAUNCH("k_set_ptrs");
-        tbox.alloc((size_t)nl * 6, s);
-        k_gather_down<<<nl, GD_THREADS, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->xptr.p, h->xcnt.p,
-                                         h->yptr.p, h->ycnt.p, toff.p, tdata.p, h->xbox.p, h->ybox.p, tbox.p);
-        H2_LAUNCH("k_gather_down");
-        launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, pts, h->yptr.p, h->ycnt.p, lb, tbox.p, h->ybox.p, s,
-                          h->method);
+        DMArgs A{};
+        if (mem_l) {
+            h->members_levels++;
+            scan_exclusive(psz.p, poff.p, nl, s);
+            const int64_t ptot = read_scalar(poff.p + nl, s);
+            pbin.alloc((size_t)std::max<int64_t>(ptot, 1), s);
+            ppq.alloc((size_t)std::max<int64_t>(ptot, 1), s);
+            A.lb = lb;
+            A.outlb = lb;
+            A.g = h->g2;
+            A.d = d;
+            A.toff = toff.p;
+            A.parent = t->parent.p;
+            A.yptr = h->yptr.p;
+            A.ycnt = h->ycnt.p;
+            A.ybox = h->ybox.p;
+            A.poff = poff.p;
+            A.pbin = pbin.p;
+            A.pq = ppq.p;
+            A.far_ptr = t->far_ptr.p;
+            A.far_idx = t->far_idx.p;
+            A.xptr = h->xptr.p;
+            A.xcnt = h->xcnt.p;
+            A.xbox = h->xbox.p;
+            A.choff = choff.p;
+            A.cbox = cbox.p;
+            A.mbox = mbox.p;
+            A.outptr = h->yptr.p;
+            A.outcnt = h->ycnt.p;
+            A.outbox = h->ybox.p;
+            launch_members(A, pts, nl, G2, ilmax[l], s);
+        } else {
+            tdata.alloc(ttot > 0 ? ttot : 1, s);
+            tbox.alloc((size_t)nl * 6, s);
+            k_gather_down<<<nl, GD_THREADS, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->xptr.p,
+                                                    h->xcnt.p, h->yptr.p, h->ycnt.p, toff.p, tdata.p, h->xbox.p,
+                                                    h->ybox.p, tbox.p);
+            H2_LAUNCH("k_gather_down");
+            launch_datareduct(toff.p, tdata.p, ttot, nl, h->g2, d, pts, h->yptr.p, h->ycnt.p, lb, tbox.p,
+                              h->ybox.p, s, h->method);
+        }
         if (il) {
             scan_exclusive(szl.p, loff.p, nl, s);
             scan_exclusive(capl.p, lcoff.p, nl, s);
             const int64_t ltot = read_scalar(loff.p + nl, s), lctot = read_scalar(lcoff.p + nl, s);
-            tl.alloc(ltot > 0 ? ltot : 1, s);
+            h->iltotal += ltot;
             lbuf.alloc(lctot > 0 ? lctot : 1, s);
             lptr.alloc(nl, s);
             lcnt.alloc(nl, s);
-            lbox.alloc((size_t)nl * 6, s);
             lobox.alloc((size_t)nl * 6, s);
             k_set_ptrs<<<blocks_for(nl, 128), 128, 0, s>>>(0, nl, lbuf.p, lcoff.p, lptr.p);
             H2_LAUNCH("k_set_ptrs");
-            k_gather_il<<<nl, 256, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->ycnt.p, toff.p, tdata.p,
-                                           loff.p, tl.p, h->xbox.p, lbox.p);
-            H2_LAUNCH("k_gather_il");
             // outputs indexed from 0: lptr, lcnt and lobox hold this level's nodes only
-            launch_datareduct(loff.p, tl.p, ltot, nl, h->g2, d, pts, lptr.p, lcnt.p, 0, lbox.p, lobox.p, s,
-                              h->method);
+            if (mem_l) {
+                DMArgs B = A;
+                B.outlb = 0;
+                B.toff = loff.p;
+                B.parent = nullptr;
+                B.outptr = lptr.p;
+                B.outcnt = lcnt.p;
+                B.outbox = lobox.p;
+                launch_members(B, pts, nl, G2, ilmax[l], s);
+            } else {
+                tl.alloc(ltot > 0 ? ltot : 1, s);
+                lbox.alloc((size_t)nl * 6, s);
+                k_gather_il<<<nl, 256, 0, s>>>(lb, t->parent.p, t->far_ptr.p, t->far_idx.p, h->ycnt.p, toff.p,
+                                               tdata.p, loff.p, tl.p, h->xbox.p, lbox.p);
+                H2_LAUNCH("k_gather_il");
+                launch_datareduct(loff.p, tl.p, ltot, nl, h->g2, d, pts, lptr.p, lcnt.p, 0, lbox.p, lobox.p, s,
+                                  h->method);
+            }
             k_merge_il<<<nl, 256, merge_smem, s>>>(lb, h->yptr.p, h->ycnt.p, h->ybox.p, lptr.p, lcnt.p, lobox.p);
             H2_LAUNCH("k_merge_il");
         }

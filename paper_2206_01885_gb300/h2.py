@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libh2gb300.so")
 
 DR_METHODS = {"volume": 0, "surface": 1, "fps": 2}
 HIDR_IL_REDUCE = 0x100  # H2_HIDR_IL_REDUCE, ORed into the method
+HIDR_COPY_SETS = 0x200  # H2_HIDR_COPY_SETS
 KERNELS = {"coulomb": 1, "gaussian": 2, "exponential": 3, "multiquadric": 4, "bump": 5, "power": 6,
            "cosdot": 7}
 PRECISIONS = {"fp64": 0, "mixed": 1}
@@ -208,12 +209,15 @@ class Hidr(_Handle):
         h.tree = tree
         return h
 
-    def __init__(self, tree: Tree, g1: int, g2: int, stream=None, method: str = "volume", il_reduce: bool = False):
+    def __init__(self, tree: Tree, g1: int, g2: int, stream=None, method: str = "volume", il_reduce: bool = False,
+                 copy_sets: bool = False):
         """method: the DataReduct of section 3.3, "volume", "surface" or "fps".
         il_reduce: each Y_i* also takes the reduction of its interaction-list
-        part alone, on that part's own box (H2_HIDR_IL_REDUCE)."""
+        part alone, on that part's own box (H2_HIDR_IL_REDUCE).  copy_sets:
+        the top-down sets are copied out and binned entry by entry
+        (H2_HIDR_COPY_SETS; same result)."""
         h = C.c_void_p()
-        flags = DR_METHODS[method] | (HIDR_IL_REDUCE if il_reduce else 0)
+        flags = DR_METHODS[method] | (HIDR_IL_REDUCE if il_reduce else 0) | (HIDR_COPY_SETS if copy_sets else 0)
         _check("h2_hidr_reduce_ex", lib().h2_hidr_reduce_ex(tree.handle, int(g1), int(g2), flags,
                                                              _stream(stream), C.byref(h)))
         self._h = h.value

@@ -49,7 +49,7 @@ def test_invalid_arguments_are_rejected_without_device_work(L):
     bogus = (C.c_uint32 * 4)(1, 2, 3, 4)
     assert L.h2_free(bogus) == 1
     assert L.h2_hidr_reduce(bogus, 3, 3, None, C.byref(out)) == 1
-    assert L.h2_hidr_reduce_ex(bogus, 3, 3, 0x200, None, C.byref(out)) == 1  # unknown flag
+    assert L.h2_hidr_reduce_ex(bogus, 3, 3, 0x400, None, C.byref(out)) == 1  # unknown flag
     assert b"flag" in L.h2_last_error()
     assert L.h2_hidr_reduce_ex(bogus, 3, 3, 3 | h2.HIDR_IL_REDUCE, None, C.byref(out)) == 1  # unknown method
     assert L.h2_hidr_reduce_ex(bogus, 3, 3, h2.HIDR_IL_REDUCE, None, C.byref(out)) == 1  # bogus tree

@@ -391,8 +391,10 @@ __device__ __forceinline__ bool dr_ring_cell(int e, int r, int d, int g, const i
         if (k >= d) break;
         int o = 0;
         if (!flat[k]) {
-            o = rem % side - r;
-            rem /= side;
+            // rem / side: rings 0 and 1 (side 1, 3; rem < 27) by multiply-shift
+            const int qd = side == 1 ? rem : (side == 3 && rem < 32 ? (rem * 11) >> 5 : rem / side);
+            o = rem - qd * side - r;
+            rem = qd;
         }
         const int ck = cid[k] + o;
         ok = ok && ck >= 0 && ck < g;
@@ -1126,9 +1128,29 @@ __device__ __forceinline__ float dm_point_d32(const DMFrame &F, int32_t sid) {
     return fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
 }
 
-// The chunks of member j whose box bound is at most lim, in order: float32
-// top-two of the lane (entry k of a chunk on lane k, l1 the label of its
-// smallest), lim = the warp's smallest + M after each chunk.
+// The first lane still a candidate, or -1; its candidacy is cleared.
+__device__ __forceinline__ int dm_next_any(bool &cand, int lane) {
+    const unsigned cm = __ballot_sync(0xffffffffu, cand);
+    if (cm == 0u) return -1;
+    const int s = __ffs(cm) - 1;
+    if (lane == s) cand = false;
+    return s;
+}
+
+// The lane holding the smallest bound among the candidates (cand), or -1
+// when there is none or that bound exceeds lim; its candidacy is cleared.
+__device__ __forceinline__ int dm_next_nearest(bool &cand, float bound, float lim, int lane) {
+    if (__ballot_sync(0xffffffffu, cand) == 0u) return -1;
+    const float mb = warp_minf(cand ? bound : INFINITY);
+    if (mb > lim) return -1;
+    const int s = __ffs(__ballot_sync(0xffffffffu, cand && bound == mb)) - 1;
+    if (lane == s) cand = false;
+    return s;
+}
+
+// The chunks of member j whose box bound is at most lim, nearest bound first:
+// float32 top-two of the lane (entry k of a chunk on lane k, l1 the label of
+// its smallest), lim = the warp's smallest + M after each chunk.
 __device__ __forceinline__ void dm_scan_member(const DMArgs &A, const DMFrame &F, int j, float &b1, float &b2,
                                                int32_t &l1, float &lim, int lane) {
     const int cnt = A.xcnt[j];
@@ -1142,11 +1164,7 @@ __device__ __forceinline__ void dm_scan_member(const DMArgs &A, const DMFrame &F
             lbc = dm_box_lb(cb[2 * (c0 + lane)], cb[2 * (c0 + lane) + 1], F.lh, F.qf, F.flat, F.cw, F.d);
             cand = lbc <= lim;
         }
-        unsigned pc = __ballot_sync(0xffffffffu, cand);
-        while (pc) {
-            const int s = __ffs(pc) - 1;
-            pc &= pc - 1;
-            if (__shfl_sync(0xffffffffu, lbc, s) > lim) continue;  // lim fell since the test
+        for (int s; (s = dm_next_nearest(cand, lbc, lim, lane)) >= 0;) {
             const int r = (c0 + s) * DM_CHUNK + lane;
             if (r < cnt) {
                 const int32_t sid = lab[r];
@@ -1203,7 +1221,7 @@ __device__ __forceinline__ void dm_exact_member(const DMArgs &A, const DMFrame &
 // The members listed in the cells the lanes selected (lane c's cell `bin`
 // when ok), walked as one flat range across the warp as dr_scan_top2 walks
 // points.  A member not yet in the warp's visited bitmask whose box bound is
-// at most lim (limx, exact) is marked and scanned.
+// at most lim (limx, exact) is marked and scanned, nearest bound first.
 template <bool EXACT>
 __device__ __forceinline__ void dm_visit(bool ok, int bin, const int *mstart, const uint16_t *mlist, uint32_t *vis,
                                          int64_t f0, const DMArgs &A, const DMFrame &F, float &b1, float &b2,
@@ -1242,17 +1260,13 @@ __device__ __forceinline__ void dm_visit(bool ok, int bin, const int *mstart, co
                 cand = lbm <= lim;
             }
         }
-        unsigned pm = __ballot_sync(0xffffffffu, cand);
-        while (pm) {
-            const int s = __ffs(pm) - 1;
-            pm &= pm - 1;
+        // nearest bound first (the exact pass takes them in any order)
+        for (int s; (s = EXACT ? dm_next_any(cand, lane) : dm_next_nearest(cand, lbm, lim, lane)) >= 0;) {
             const int es = __shfl_sync(0xffffffffu, e, s);
-            const float lbs = __shfl_sync(0xffffffffu, lbm, s);
             const uint32_t bit = 1u << (es & 31);
             uint32_t was = 0u;  // mark it; lane 0's test decides for the warp
             if (lane == 0) was = atomicOr(&vis[es >> 5], bit);
             if (__shfl_sync(0xffffffffu, was, 0) & bit) continue;  // listed twice among these cells
-            if (lbs > lim) continue;
             const int j = A.far_idx[f0 + es];
             if (EXACT) dm_exact_member(A, F, j, lim, bk, bl, lane);
             else dm_scan_member(A, F, j, b1, b2, l1, lim, lane);
@@ -1524,6 +1538,10 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
     // mode B widens every cell bound and the stopping radius by the largest
     // half extent of a member box (plus its rounding)
     const float delc = modeB ? delf + fmaf(0.5f, __uint_as_float(s_ext), 1e-6f * __uint_as_float(s_ext)) + delf : delf;
+    const bool havep = np > 0;  // a Y_p* part to scan
+    // gi / g through a float reciprocal: (gi + 1/2) / g lies at least 1 / (2 g)
+    // from an integer, far above the product's rounding for gi < 2^21
+    const float invg = 1.0f / (float)g;
     for (int gi = warp; gi < G; gi += nw) {
         int cid[3] = {0, 0, 0};
         int rmax = 0;
@@ -1532,8 +1550,9 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 if (k >= d) break;
-                const int idx = rem % g;
-                rem /= g;
+                const int qd = (int)(((float)rem + 0.5f) * invg);
+                const int idx = rem - qd * g;
+                rem = qd;
                 if (table) {
                     F.q[k] = qtab[3 * gi + k];
                     F.qf[k] = qftab[3 * gi + k];
@@ -1567,7 +1586,7 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
                 float lb = 0.f;
                 bool ok = e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, F.flat, hf, F.qf, delc, bin, lb);
                 ok = ok && lb <= lim;
-                dr_scan_top2(ok, bin, bstart, pq, F.qf, b1, b2, l1, lane);
+                dr_scan_top2(havep && ok, bin, bstart, pq, F.qf, b1, b2, l1, lane);
                 lim = warp_minf(b1) + F.M;
                 dm_visit<false>(ok, bin, mstart, mlist, vis, f0, A, F, b1, b2, l1, lim, bk, bl, lane);
             }
@@ -1596,7 +1615,7 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
             const float mlb = warp_minf(blb);
             const int b0 = __shfl_sync(0xffffffffu, bbin, __ffs(__ballot_sync(0xffffffffu, blb == mlb)) - 1);
             if (b0 >= 0 && mlb <= lim) {
-                dr_scan_top2(lane == 0, b0, bstart, pq, F.qf, b1, b2, l1, lane);
+                dr_scan_top2(havep && lane == 0, b0, bstart, pq, F.qf, b1, b2, l1, lane);
                 lim = warp_minf(b1) + F.M;
                 dm_visit<false>(lane == 0, b0, mstart, mlist, vis, f0, A, F, b1, b2, l1, lim, bk, bl, lane);
             }
@@ -1610,7 +1629,7 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
                     const float lb = dr_cell_lb(pk, d, cid, F.flat, hf, F.qf, delc, cheb);
                     ok = cheb >= 2 && lb <= lim && bin != b0;
                 }
-                dr_scan_top2(ok, bin, bstart, pq, F.qf, b1, b2, l1, lane);
+                dr_scan_top2(havep && ok, bin, bstart, pq, F.qf, b1, b2, l1, lane);
                 lim = warp_minf(b1) + F.M;
                 dm_visit<false>(ok, bin, mstart, mlist, vis, f0, A, F, b1, b2, l1, lim, bk, bl, lane);
             }
@@ -1640,7 +1659,7 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
                     bool ok =
                         e0 + lane < total && dr_ring_cell(e0 + lane, r, d, g, cid, F.flat, hf, F.qf, delc, bin, lb);
                     ok = ok && lb <= limx;
-                    dr_scan_exact(ok && bstart[bin + 1] > bstart[bin], bin, bstart, pq, F.qf, limx, d, F.x0, F.x1,
+                    dr_scan_exact(havep && ok && bstart[bin + 1] > bstart[bin], bin, bstart, pq, F.qf, limx, d, F.x0, F.x1,
                                   F.x2, F.q, bk, bl, lane);
                     dm_visit<true>(ok, bin, mstart, mlist, vis, f0, A, F, b1, b2, l1, limx, bk, bl, lane);
                 }
@@ -1656,7 +1675,7 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
                         const float lb = dr_cell_lb(pk, d, cid, F.flat, hf, F.qf, delc, cheb);
                         ok = cheb >= 2 && lb <= limx;
                     }
-                    dr_scan_exact(ok && bstart[bin + 1] > bstart[bin], bin, bstart, pq, F.qf, limx, d, F.x0, F.x1,
+                    dr_scan_exact(havep && ok && bstart[bin + 1] > bstart[bin], bin, bstart, pq, F.qf, limx, d, F.x0, F.x1,
                                   F.x2, F.q, bk, bl, lane);
                     dm_visit<true>(ok, bin, mstart, mlist, vis, f0, A, F, b1, b2, l1, limx, bk, bl, lane);
                 }

@@ -1022,10 +1022,12 @@ __global__ void k_chunk_counts(int nn, const int32_t *xcnt, int64_t *nch) {
 }
 
 // chunk boxes cbox[2 (choff[i] + c)], [.. + 1] (low, high corner of the hi
-// parts) and member boxes mbox[2 i], [2 i + 1] of X_i* for nodes [n0, nn);
-// one warp a node
+// parts) and member boxes mbox[2 i], [2 i + 1] of X_i* for nodes [n0, nn),
+// and the packed coordinates of X_i*'s entry r copied to xqm[2 (32 choff[i] +
+// r)], [.. + 1] (xq's two float4, the label in the second's .z as int bits),
+// so that a chunk is read with one coalesced load; one warp a node
 __global__ void k_member_boxes(int n0, int nn, int32_t *const *xptr, const int32_t *xcnt, const int64_t *choff,
-                               const float4 *xq, float4 *cbox, float4 *mbox) {
+                               const float4 *xq, float4 *cbox, float4 *mbox, float4 *xqm) {
     const int i = n0 + (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= nn) return;
@@ -1036,7 +1038,11 @@ __global__ void k_member_boxes(int n0, int nn, int32_t *const *xptr, const int32
         const int r = c * DM_CHUNK + lane;
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
         if (r < cnt) {
-            const float4 qa = xq[2 * (int64_t)lab[r]];
+            const int32_t sid = lab[r];
+            const float4 qa = xq[2 * (int64_t)sid], qb = xq[2 * (int64_t)sid + 1];
+            const int64_t o = 2 * (DM_CHUNK * choff[i] + r);
+            xqm[o] = qa;
+            xqm[o + 1] = make_float4(qb.x, qb.y, __int_as_float(sid), 0.f);
             lo[0] = hi[0] = qa.x;
             lo[1] = hi[1] = qa.y;
             lo[2] = hi[2] = qa.z;
@@ -1103,7 +1109,7 @@ struct DMArgs {
     const int32_t *xcnt;
     const long long *xbox;
     const int64_t *choff;
-    const float4 *cbox, *mbox;
+    const float4 *cbox, *mbox, *xqm;
     int32_t *const *outptr;
     int32_t *outcnt;
     long long *outbox;
@@ -1111,7 +1117,7 @@ struct DMArgs {
 
 // the grid point's frame, shared by the scans of one warp
 struct DMFrame {
-    const float4 *xq;
+    const float4 *xq, *xqm;
     const double *x0, *x1, *x2;
     float lh[3], ll[3], qf[3];
     double q[3];
@@ -1120,8 +1126,7 @@ struct DMFrame {
     int d;
 };
 
-__device__ __forceinline__ float dm_point_d32(const DMFrame &F, int32_t sid) {
-    const float4 qa = F.xq[2 * (int64_t)sid], qb = F.xq[2 * (int64_t)sid + 1];
+__device__ __forceinline__ float dm_entry_d32(const DMFrame &F, float4 qa, float4 qb) {
     const float e0 = ((qa.x - F.lh[0]) + (qa.w - F.ll[0])) - F.qf[0];
     const float e1 = F.d > 1 ? ((qa.y - F.lh[1]) + (qb.x - F.ll[1])) - F.qf[1] : 0.f;
     const float e2 = F.d > 2 ? ((qa.z - F.lh[2]) + (qb.y - F.ll[2])) - F.qf[2] : 0.f;
@@ -1154,8 +1159,8 @@ __device__ __forceinline__ int dm_next_nearest(bool &cand, float bound, float li
 __device__ __forceinline__ void dm_scan_member(const DMArgs &A, const DMFrame &F, int j, float &b1, float &b2,
                                                int32_t &l1, float &lim, int lane) {
     const int cnt = A.xcnt[j];
-    const int32_t *lab = A.xptr[j];
-    const float4 *cb = A.cbox + 2 * A.choff[j];
+    const int64_t ch = A.choff[j];
+    const float4 *cb = A.cbox + 2 * ch, *xm = F.xqm + 2 * DM_CHUNK * ch;
     const int nc = (cnt + DM_CHUNK - 1) / DM_CHUNK;
     for (int c0 = 0; c0 < nc; c0 += 32) {
         float lbc = INFINITY;
@@ -1167,8 +1172,9 @@ __device__ __forceinline__ void dm_scan_member(const DMArgs &A, const DMFrame &F
         for (int s; (s = dm_next_nearest(cand, lbc, lim, lane)) >= 0;) {
             const int r = (c0 + s) * DM_CHUNK + lane;
             if (r < cnt) {
-                const int32_t sid = lab[r];
-                const float d32 = dm_point_d32(F, sid);
+                const float4 qa = xm[2 * r], qb = xm[2 * r + 1];
+                const int32_t sid = __float_as_int(qb.z);
+                const float d32 = dm_entry_d32(F, qa, qb);
                 if (d32 < b2) {
                     if (d32 < b1) {
                         b2 = b1;
@@ -1190,8 +1196,8 @@ __device__ __forceinline__ void dm_scan_member(const DMArgs &A, const DMFrame &F
 __device__ __forceinline__ void dm_exact_member(const DMArgs &A, const DMFrame &F, int j, float limx,
                                                 long long &bk, int32_t &bl, int lane) {
     const int cnt = A.xcnt[j];
-    const int32_t *lab = A.xptr[j];
-    const float4 *cb = A.cbox + 2 * A.choff[j];
+    const int64_t ch = A.choff[j];
+    const float4 *cb = A.cbox + 2 * ch, *xm = F.xqm + 2 * DM_CHUNK * ch;
     const int nc = (cnt + DM_CHUNK - 1) / DM_CHUNK;
     for (int c0 = 0; c0 < nc; c0 += 32) {
         bool pass = false;
@@ -1203,8 +1209,9 @@ __device__ __forceinline__ void dm_exact_member(const DMArgs &A, const DMFrame &
             pc &= pc - 1;
             const int r = (c0 + s) * DM_CHUNK + lane;
             if (r < cnt) {
-                const int32_t sid = lab[r];
-                if (dm_point_d32(F, sid) <= limx) {
+                const float4 qa = xm[2 * r], qb = xm[2 * r + 1];
+                const int32_t sid = __float_as_int(qb.z);
+                if (dm_entry_d32(F, qa, qb) <= limx) {
                     const long long kk = __double_as_longlong(h2_dist2(F.d, F.x0[sid], F.d > 1 ? F.x1[sid] : 0.0,
                                                                        F.d > 2 ? F.x2[sid] : 0.0, F.q[0], F.q[1],
                                                                        F.q[2]));
@@ -1274,12 +1281,15 @@ __device__ __forceinline__ void dm_visit(bool ok, int bin, const int *mstart, co
     }
 }
 
-// dynamic shared memory of k_dr_members (G <= DR_BIN_MAX): k_datareduct's
-// binned layout (winners, Y_p*'s bin starts, the non-empty cells, the
-// grid-point table), then the member cells' starts (G + 2 ints), the warps'
-// visited bitmasks (vwords words each) and the member-cell list (mcap 16-bit
-// member indices)
-__host__ __device__ inline size_t dm_mstart_offset(int G) { return (dr_smem_bytes(G) + 15) & ~(size_t)15; }
+// dynamic shared memory of k_dr_members (G <= DR_BIN_MAX): the winners,
+// Y_p*'s bin starts and the non-empty cells as k_datareduct lays them out,
+// the grid points' float32 offsets (3 G floats), then the member cells' starts
+// (G + 2 ints), the warps' visited bitmasks (vwords words each) and the
+// member-cell list (mcap 16-bit member indices)
+__host__ __device__ inline size_t dm_qf_offset(int G) {
+    return (dr_bins_offset(G) + (size_t)(2 * G + 1) * 4 + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t dm_mstart_offset(int G) { return dm_qf_offset(G) + (size_t)G * 12; }
 __host__ __device__ inline size_t dm_vis_offset(int G) {
     return (dm_mstart_offset(G) + (size_t)(G + 2) * 4 + 15) & ~(size_t)15;
 }
@@ -1330,7 +1340,7 @@ __device__ __forceinline__ int dm_centre_bin(float4 lo4, float4 hi4, const float
 // One CTA per node: DataReduct(S, g^d) for S = Y_p* (when A.parent) u X_j*
 // over j in IL(i), read in place.  Result as k_datareduct's: the distinct
 // winners sorted to outptr[outlb + a], their number and box.
-__global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints PT) {
+__global__ void __launch_bounds__(DR_THREADS, 5) k_dr_members(DMArgs A, DRPoints PT) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int scratch[33];
     __shared__ long long s_box[6];
@@ -1380,6 +1390,7 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
     }
     DMFrame F;
     F.xq = PT.xq;
+    F.xqm = A.xqm;
     F.x0 = PT.x[0];
     F.x1 = PT.x[1];
     F.x2 = PT.x[2];
@@ -1510,23 +1521,20 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
                         mlist[atomicAdd(&mstart[x + g * (y + g * z) + 1], 1)] = (uint16_t)e;
         }
     }
-    // grid points: float64 q and its float32 offset qf, computed once each
-    double *qtab = reinterpret_cast<double *>(smem_raw + dr_qtab_offset(G));
-    float *qftab = reinterpret_cast<float *>(qtab + 3 * G);
-    const bool table = G <= DR_QTAB;
-    if (table)
-        for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
-            int rem = gi;
+    // grid points' float32 offsets qf, computed once each (the float64 point
+    // itself is formed again only for a near tie)
+    float *qftab = reinterpret_cast<float *>(smem_raw + dm_qf_offset(G));
+    for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
+        int rem = gi;
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                if (k >= d) break;
-                const int idx = rem % g;
-                rem /= g;
-                const double qk = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
-                qtab[3 * gi + k] = qk;
-                qftab[3 * gi + k] = (float)__dsub_rn(qk, l[k]);
-            }
+        for (int k = 0; k < 3; k++) {
+            if (k >= d) break;
+            const int idx = rem % g;
+            rem /= g;
+            qftab[3 * gi + k] =
+                (float)__dsub_rn(__dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k])), l[k]);
         }
+    }
     __syncthreads();  // mstart[b] is now the first position of bin b
     int *nel = bstart + G + 1;
     if (threadIdx.x == 0) s_nne = 0;
@@ -1543,7 +1551,7 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
     // from an integer, far above the product's rounding for gi < 2^21
     const float invg = 1.0f / (float)g;
     for (int gi = warp; gi < G; gi += nw) {
-        int cid[3] = {0, 0, 0};
+        int cid[3] = {0, 0, 0}, gidx[3] = {0, 0, 0};
         int rmax = 0;
         {
             int rem = gi;
@@ -1553,13 +1561,8 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
                 const int qd = (int)(((float)rem + 0.5f) * invg);
                 const int idx = rem - qd * g;
                 rem = qd;
-                if (table) {
-                    F.q[k] = qtab[3 * gi + k];
-                    F.qf[k] = qftab[3 * gi + k];
-                } else {
-                    F.q[k] = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)idx, 0.5), h[k]));
-                    F.qf[k] = (float)__dsub_rn(F.q[k], l[k]);
-                }
+                gidx[k] = idx;
+                F.qf[k] = qftab[3 * gi + k];
                 cid[k] = F.flat[k] ? 0 : idx;
                 if (!F.flat[k]) rmax = max(rmax, max(cid[k], g - 1 - cid[k]));
             }
@@ -1644,6 +1647,9 @@ __global__ void __launch_bounds__(DR_THREADS, 4) k_dr_members(DMArgs A, DRPoints
         } else {
             // near tie: every point within M of the smallest in float64, over
             // the cells the search visited
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (k < d) F.q[k] = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)gidx[k], 0.5), h[k]));
             for (int v = lane; v < A.vwords; v += 32) vis[v] = 0u;
             __syncwarp();
             const int rB = stage == 2 ? rA : stage;
@@ -2108,9 +2114,9 @@ constexpr size_t DM_SMEM_MAX = 200 * 1024;  // dynamic shared memory of k_dr_mem
 void launch_members(DMArgs A, const DRPoints &pts, int nl, int G, int ilmax, cudaStream_t s) {
     if (nl <= 0) return;
     A.vwords = std::max(1, (ilmax + 31) / 32);
-    // about six cells a member (boxes near a cell's size overlap two cells per
+    // about five cells a member (boxes near a cell's size overlap two cells per
     // coordinate at most); a node needing more takes mode B
-    A.mcap = std::max(ilmax, std::min(6 * ilmax + G, DM_MCAP_MAX));
+    A.mcap = std::max(ilmax, std::min(5 * ilmax + G, DM_MCAP_MAX));
     const size_t sm = dm_smem_bytes(G, A.vwords, A.mcap);
     H2_REQUIRE(sm <= DM_SMEM_MAX, "DataReduct over members: shared memory");
     static std::once_flag attr;
@@ -2193,7 +2199,7 @@ void hidr_impl(h2_hidr_s *h) {
     const bool members = h->method == 0 && G2 <= DR_BIN_MAX && !h->copy_sets;
     std::vector<int> ilmax(t->nlevels, 0);
     DevBuf<int64_t> nch, choff, psz, poff;
-    DevBuf<float4> cbox, mbox;
+    DevBuf<float4> cbox, mbox, xqm;
     DevBuf<int2> pbin;
     DevBuf<float4> ppq;
     if (members) {
@@ -2209,9 +2215,10 @@ void hidr_impl(h2_hidr_s *h) {
         const int64_t nchunks = read_scalar(choff.p + nn, s);
         cbox.alloc((size_t)std::max<int64_t>(2 * nchunks, 2), s);
         mbox.alloc((size_t)2 * nn, s);
+        xqm.alloc((size_t)std::max<int64_t>(2 * DM_CHUNK * nchunks, 2), s);
         if (nn > 1) {
             k_member_boxes<<<blocks_for((int64_t)(nn - 1) * 32, 256), 256, 0, s>>>(1, nn, h->xptr.p, h->xcnt.p,
-                                                                                   choff.p, t->xq.p, cbox.p, mbox.p);
+                                                                                   choff.p, t->xq.p, cbox.p, mbox.p, xqm.p);
             H2_LAUNCH("k_member_boxes");
         }
     }
@@ -2273,6 +2280,7 @@ void hidr_impl(h2_hidr_s *h) {
             A.choff = choff.p;
             A.cbox = cbox.p;
             A.mbox = mbox.p;
+            A.xqm = xqm.p;
             A.outptr = h->yptr.p;
             A.outcnt = h->ycnt.p;
             A.outbox = h->ybox.p;

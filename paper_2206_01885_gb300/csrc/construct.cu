@@ -556,11 +556,47 @@ __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr_df(int lb, const int32_t
             float2 *al = A + (int64_t)l * m;
             float2 ajl = al[j];
             if (has_tau) {
-                float sh = 0.f, sl = 0.f;
-                for (int r = j + 1 + lane; r < m; r += 32) df::mac(sh, sl, v[r], al[r]);
-                float2 w = df::add(df::warp_sum(sh, sl), ajl);
+                // eight (then four) rows a lane in flight, two accumulators (the
+                // loads are independent; the float-float sums chain)
+                float sh = 0.f, sl = 0.f, th = 0.f, tl = 0.f;
+                int r = j + 1 + lane;
+                for (; r + 224 < m; r += 256) {
+                    float2 a[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) a[u] = al[r + 32 * u];
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        df::mac(sh, sl, v[r + 32 * u], a[u]);
+                        df::mac(th, tl, v[r + 32 * u + 32], a[u + 1]);
+                    }
+                }
+                for (; r + 96 < m; r += 128) {
+                    const float2 a0 = al[r], a1 = al[r + 32], a2 = al[r + 64], a3 = al[r + 96];
+                    df::mac(sh, sl, v[r], a0);
+                    df::mac(th, tl, v[r + 32], a1);
+                    df::mac(sh, sl, v[r + 64], a2);
+                    df::mac(th, tl, v[r + 96], a3);
+                }
+                for (; r < m; r += 32) df::mac(sh, sl, v[r], al[r]);
+                const float2 s2 = df::add(df::norm(sh, sl), df::norm(th, tl));
+                float2 w = df::add(df::warp_sum(s2.x, s2.y), ajl);
                 w = df::mul(w, tauD);
-                for (int r = j + 1 + lane; r < m; r += 32) al[r] = df::fms(al[r], w, v[r]);
+                r = j + 1 + lane;
+                for (; r + 224 < m; r += 256) {
+                    float2 a[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) a[u] = al[r + 32 * u];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) al[r + 32 * u] = df::fms(a[u], w, v[r + 32 * u]);
+                }
+                for (; r + 96 < m; r += 128) {
+                    const float2 a0 = al[r], a1 = al[r + 32], a2 = al[r + 64], a3 = al[r + 96];
+                    al[r] = df::fms(a0, w, v[r]);
+                    al[r + 32] = df::fms(a1, w, v[r + 32]);
+                    al[r + 64] = df::fms(a2, w, v[r + 64]);
+                    al[r + 96] = df::fms(a3, w, v[r + 96]);
+                }
+                for (; r < m; r += 32) al[r] = df::fms(al[r], w, v[r]);
                 ajl = df::sub(ajl, w);
                 if (lane == 0) al[j] = ajl;
             }

@@ -431,14 +431,15 @@ __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr(int lb, const int32_t *y
 // block held as float pairs hi + lo (about 48 bits) and the reflector, its
 // products with the trailing columns and their rank-1 updates computed in
 // float-float arithmetic on the float32 units (float64 runs at 1/74 of the
-// float32 rate on this GPU).  The float64 block is converted in place on
-// entry (each element keeps its 8 bytes); on exit rows 0..k-1 of every column
-// -- R, what the solve reads -- are converted back to float64 in place.  The
-// reflector's scalars (one square root, two divisions) and the column norms
-// stay float64.
+// float32 rate on this GPU).  A float64 block is converted in place on entry
+// (each element keeps its 8 bytes; split = 1: the block already holds float
+// pairs); on exit rows 0..k-1 of every column -- R, what the solve reads --
+// are converted back to float64 in place.  The reflector's scalars (one
+// square root, two divisions) and the column norms stay float64.
 __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr_df(int lb, const int32_t *ycnt, const int32_t *cc,
                                                          const int64_t *aoff, double *Abase, double tol,
-                                                         int32_t *kout, const int64_t *coff, int32_t *pivbase) {
+                                                         int32_t *kout, const int64_t *coff, int32_t *pivbase,
+                                                         int split) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int a = blockIdx.x, node = lb + a;
     const int m = ycnt[node], c = cc[node];
@@ -464,7 +465,8 @@ __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr_df(int lb, const int32_t
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const double tol3z = sqrt(ldexp(1.0, -53));
     const int64_t mc = (int64_t)m * c;
-    for (int64_t e = threadIdx.x; e < mc; e += blockDim.x) A[e] = df::from_double(Ad[e]);
+    if (!split)
+        for (int64_t e = threadIdx.x; e < mc; e += blockDim.x) A[e] = df::from_double(Ad[e]);
     for (int l = threadIdx.x; l < c; l += blockDim.x) pv[l] = l;
     __syncthreads();
     for (int l = warp; l < c; l += nwarps) {
@@ -1026,6 +1028,9 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     const int nn = t->nnodes, d = t->d;
     const bool f64 = A->prec == H2_PREC_FP64;
     const size_t esize = f64 ? sizeof(double) : sizeof(float);
+    // float64 form, 3D Coulomb, float-float QR: the blocks are evaluated in
+    // float-float arithmetic too and handed to the QR as float pairs
+    const bool dfblocks = f64 && !A->fp64_qr && A->kid == H2_K_COULOMB && d == 3;
     A->k.alloc(nn, s);
     A->c.alloc(nn, s);
     DevBuf<unsigned long long> gmax, nexd;  // largest |G| entry over all nodes (float64 bits); exchanges
@@ -1093,7 +1098,11 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         dim3 kg(nl, std::max(1, std::min(16, (int)((int64_t)cmax * mmax / (256 * 64)))));
         {
             ProfScope ps(KT_KEVAL, s);
-            if (f64) {
+            if (dfblocks) {
+                ensure_df_tree(t, s);
+                keval_df(t, nl, (int)kg.y, lb, h->ycnt.p, A->c.p, h->yptr.p, cand.p, coff.p, aoff.p,
+                         reinterpret_cast<float2 *>(Ablk.p), s);
+            } else if (f64) {
                 k_keval_f64<<<kg, 256, 0, s>>>(lb, h->ycnt.p, A->c.p, h->yptr.p, cand.p, coff.p, aoff.p, t->xs[0].p,
                                                t->xs[1].p, t->xs[2].p, d, A->kid, A->kp[0],
                                                reinterpret_cast<double *>(Ablk.p));
@@ -1112,7 +1121,7 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
             if (f64 && !A->fp64_qr)
                 k_cpqr_df<<<nl, qr_threads(cmax), qr_smem(cmax, mmax, esize), s>>>(
                     lb, h->ycnt.p, A->c.p, aoff.p, reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p,
-                    piv.p);
+                    piv.p, dfblocks ? 1 : 0);
             else if (f64)
                 launch_cpqr<double>(nl, qr_smem(cmax, mmax, esize), mmax, lb, h->ycnt.p, A->c.p, aoff.p,
                                     reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p, piv.p, s, cmax);

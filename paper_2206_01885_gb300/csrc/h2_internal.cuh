@@ -289,6 +289,11 @@ void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z_de
                      int64_t nrows, double *out_dev, cudaStream_t s);
 // float-float Coulomb products of the float64 form (3D)
 void ensure_df_tree(h2_tree_s *t, cudaStream_t s);
+// float64 form, 3D Coulomb: kernel blocks of a level in float-float
+// arithmetic, each entry a float pair hi + lo in its 8 bytes (nbody_df.cu)
+void keval_df(const h2_tree_s *t, int nl, int ysplit, int lb, const int32_t *ycnt, const int32_t *cc,
+              int32_t *const *yptr, const int32_t *cand, const int64_t *coff, const int64_t *aoff, float2 *A,
+              cudaStream_t s);
 void ensure_df_matrix(h2_matrix_s *A, cudaStream_t s);
 void split_vector(const double *v, int64_t n, float2 *out, cudaStream_t s);
 void nbody_sym_df(const h2_tree_s *t, const DevBuf<int2> &tiles, const int64_t *start, const int32_t *count,

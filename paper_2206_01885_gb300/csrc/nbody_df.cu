@@ -24,6 +24,8 @@
 // side / 2^B; x - y = (K_x - K_y) + (r_x - r_y) has an exact integer part, so
 // its error is ~2^-48 of |x - y| itself, as in float64; the sums are scaled by
 // 1/u' (exact) when they are folded into float64.
+#include <mutex>
+
 #include "h2_internal.cuh"
 
 namespace h2 {
@@ -371,11 +373,56 @@ double df_cell(const h2_tree_s *t) {
     return ldexp(1.0, ex - 1);
 }
 
+// The float64 form's Coulomb kernel blocks A_i = K(Y_i*, Xbar_i) (Algorithm 2)
+// in float-float arithmetic: each entry 1/|y - x| from the points' integer
+// cells and residuals (exact integer part, so full relative accuracy at any
+// distance), scaled by the power of two 1/u' (exact) and stored as the float
+// pair hi + lo in the entry's 8 bytes, the layout the float-float QR works
+// in.  Columns split over the node's CTAs, rows over the threads, as
+// k_keval_f64.
+__global__ void k_keval_df(int lb, const int32_t *ycnt, const int32_t *cc, int32_t *const *yptr,
+                           const int32_t *cand, const int64_t *coff, const int64_t *aoff, const float4 *P,
+                           float scale, float2 *Abase) {
+    const int a = blockIdx.x, i = lb + a;
+    const int m = ycnt[i], c = cc[i];
+    if (m == 0 || c == 0) return;
+    const int32_t *Y = yptr[i];
+    const int32_t *X = cand + coff[a];
+    float2 *A = Abase + aoff[a];
+    for (int l = blockIdx.y; l < c; l += gridDim.y) {
+        const int32_t x = X[l];
+        const float4 sk = P[3 * (int64_t)x], sh = P[3 * (int64_t)x + 1], sl = P[3 * (int64_t)x + 2];
+        float2 *Acol = A + (int64_t)l * m;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+            const int64_t y = Y[r];
+            const float4 tk = P[3 * y], th = P[3 * y + 1], tl = P[3 * y + 2];
+            const float t[3][3] = {{tk.x, th.x, tl.x}, {tk.y, th.y, tl.y}, {tk.z, th.z, tl.z}};
+            float kh, kl;
+            df_coulomb_int<true>(t, sk, sh, sl, kh, kl);
+            Acol[r] = make_float2(__fmul_rn(kh, scale), __fmul_rn(kl, scale));
+        }
+    }
+}
+
 }  // namespace
 
+void keval_df(const h2_tree_s *t, int nl, int ysplit, int lb, const int32_t *ycnt, const int32_t *cc,
+              int32_t *const *yptr, const int32_t *cand, const int64_t *coff, const int64_t *aoff, float2 *A,
+              cudaStream_t s) {
+    if (nl <= 0) return;
+    k_keval_df<<<dim3(nl, ysplit), 256, 0, s>>>(lb, ycnt, cc, yptr, cand, coff, aoff, t->xcell.p,
+                                                (float)(1.0 / df_cell(t)), A);
+    H2_LAUNCH("k_keval_df");
+}
+
 // the tree's float-pair point coordinates and integer cell centres, built on
-// first use (3D trees)
+// first use (3D trees).  Several host threads may construct on one tree at
+// once (h2_construct_batched): the first builds under a lock and waits for
+// its stream before publishing, so no other stream reads a half-built buffer.
+static std::mutex df_tree_mutex;
+
 void ensure_df_tree(h2_tree_s *t, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(df_tree_mutex);
     if (t->df_ready) return;
     const int nn = t->nnodes;
     const int64_t n = t->n;
@@ -388,7 +435,14 @@ void ensure_df_tree(h2_tree_s *t, cudaStream_t s) {
     k_df_cells<<<blocks_for(n, 256), 256, 0, s>>>(t->xs[0].p, t->xs[1].p, t->xs[2].p, n, t->geom.lo[0],
                                                    t->geom.lo[1], t->geom.lo[2], 1.0 / df_cell(t), P.p);
     H2_LAUNCH("k_df_cells");
-    for (int k = 0; k < 3; k++) t->cellA[k] = std::move(A[k]);
+    H2_CUDA(cudaStreamSynchronize(s));
+    // the tree frees them on its own stream (s may be a batched call's
+    // internal stream, gone when the tree is freed)
+    for (int k = 0; k < 3; k++) {
+        A[k].rebind(t->stream);
+        t->cellA[k] = std::move(A[k]);
+    }
+    P.rebind(t->stream);
     t->xcell = std::move(P);
     t->df_ready = true;
 }

@@ -293,9 +293,12 @@ typedef struct {
                             float pairs of ~48 bits; norms, downdates, pivots,
                             the stop test and the reflector's scalars stay
                             float64; R is returned to float64 for the solve);
-                            1 keeps the QR in float64 arithmetic throughout.
-                            The kernel blocks and the solve are float64 either
-                            way                                                 */
+                            with it, for 3D Coulomb, the kernel blocks are
+                            evaluated in float-float arithmetic as well and
+                            handed to the QR as float pairs.  1 keeps the
+                            blocks and the QR in float64 arithmetic throughout
+                            (blocks bit-identical to a plain float64
+                            evaluation).  The solve is float64 either way     */
 } h2_construct_opts;
 
 /* h2_construct with options (opts may be NULL: exactly h2_construct).

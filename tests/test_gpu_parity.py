@@ -1,8 +1,9 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
 
 Bit-exact: permutation, keys, node arrays, near/far lists, X_i*, Y_i*.
-Float64 construction: ranks and skeletons equal (the kernel blocks are
-bit-identical for Coulomb; pivot near-ties are reported, none occur here), U
+Float64 construction: ranks and skeletons equal (3D Coulomb blocks and QR
+run in float-float arithmetic, within ~2^-43 of float64, and the other
+kernels' blocks are float64; pivot near-ties are reported, none occur here), U
 within 64 u c / eps of the oracle's (u = 2^-53, the conditioning bound of
 R11^{-1} R12 after truncation at eps), the H^2 matvec within 1e-12 of the oracle's
 H^2 matvec and within 10 eps of the dense product; exact rows within 1e-12.

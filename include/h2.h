@@ -393,7 +393,10 @@ h2_status h2_matvec_graph_launch(h2_graph g, void *stream);
 /* ---------------------------------------------------------- exact rows --- */
 /* The reference of the section 6 error ||K z - K~ z|| / ||K z||: for each
  * row s in rows (original indices), out[s'] = sum_j kappa(x_s, x_j) z_j over
- * all n points, in float64 (kappa(x, x) = 0 for Coulomb).  z: n float64,
+ * all n points, by direct summation (kappa(x, x) = 0 for Coulomb): in float64,
+ * and for 3D Coulomb in float-float arithmetic (each term within about 2^-43
+ * of exact, float-pair sums, a float64 result), which frees the float64 units
+ * for the path it runs beside.  z: n float64,
  * rows: nrows int64, out: nrows float64; all device if on_device, else host
  * (then the call synchronises).  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
 h2_status h2_exact_rows(h2_tree t, int kernel, const double *kparams, const double *z,

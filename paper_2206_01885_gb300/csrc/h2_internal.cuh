@@ -289,6 +289,10 @@ void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z_de
                      int64_t nrows, double *out_dev, cudaStream_t s);
 // float-float Coulomb products of the float64 form (3D)
 void ensure_df_tree(h2_tree_s *t, cudaStream_t s);
+// exact rows of a 3D Coulomb tree in float-float arithmetic: part[r * nch + c]
+// = the sum over chunk c (chunk points) of row r (nbody_df.cu)
+void exact_rows_df_parts(h2_tree_s *t, const double *zm, const int64_t *rows, int64_t nrows, int64_t chunk,
+                         int nch, double *part, cudaStream_t s);
 // float64 form, 3D Coulomb: kernel blocks of a level in float-float
 // arithmetic, each entry a float pair hi + lo in its 8 bytes (nbody_df.cu)
 void keval_df(const h2_tree_s *t, int nl, int ysplit, int lb, const int32_t *ycnt, const int32_t *cc,

@@ -897,7 +897,20 @@ void exact_rows_impl(h2_tree_s *t, int kid, const double *kp, const double *z, c
     zm.alloc(n, s);
     k_perm_in<<<blocks_for(n, 256), 256, 0, s>>>(z, t->perm.p, n, zm.p);
     H2_LAUNCH("k_perm_in");
-    if (nrows > 0) {
+    if (nrows > 0 && kid == H2_K_COULOMB && t->d == 3) {
+        // 3D Coulomb: float-float terms and sums (nbody_df.cu), eight rows a CTA
+        const int nch = (int)((n + ER_CHUNK - 1) / ER_CHUNK);
+        const int64_t rb = std::min<int64_t>(nrows, 65536);
+        DevBuf<double> part;
+        part.alloc((size_t)rb * nch, s);
+        ProfScope ps(KT_EXACT, s);
+        for (int64_t r0 = 0; r0 < nrows; r0 += rb) {
+            const int64_t nr = std::min<int64_t>(rb, nrows - r0);
+            exact_rows_df_parts(t, zm.p, rows + r0, nr, ER_CHUNK, nch, part.p, s);
+            k_exact_sum<<<blocks_for(nr, 256), 256, 0, s>>>(part.p, nr, nch, out + r0);
+            H2_LAUNCH("k_exact_sum");
+        }
+    } else if (nrows > 0) {
         const int nch = (int)((n + ER_CHUNK - 1) / ER_CHUNK);
         const int64_t rb = std::min<int64_t>(nrows, 65535);  // rows per launch (grid y limit)
         DevBuf<double> part;

@@ -404,7 +404,98 @@ __global__ void k_keval_df(int lb, const int32_t *ycnt, const int32_t *cc, int32
     }
 }
 
+// The exact sampled-row sums of the section 6 metric, (K z)_s = sum_q
+// 1/|x_s - x_q| z_q, for 3D Coulomb in float-float arithmetic: every term from
+// the points' integer cells and residuals (full relative accuracy at any
+// distance, ~2^-43 a term), z as float pairs, float-pair accumulators.  CTA
+// (chunk c, group of XD_ROWS rows) sums chunk c (ER_CHUNK points) for its
+// rows, each point's coordinates and weight loaded once for all of them; the
+// row's sum is reduced in a fixed order and written in float64 (scaled by
+// 1/u', a power of two) to part[r * nch + c].  A row index outside [0, n)
+// gives NaN, as in the float64 kernels.  p = iperm[row] is its tree position.
+constexpr int XD_ROWS = 8;
+constexpr int XD_THREADS = 256;
+
+__global__ void __launch_bounds__(XD_THREADS)
+    k_exact_part_df(const int64_t *rows, int64_t nrows, const int32_t *iperm, const float4 *P, const float2 *zf,
+                    int64_t n, int64_t chunk, int nch, double inv_u, double *part) {
+    __shared__ float2 red[XD_ROWS][XD_THREADS / 32];
+    const int64_t r0 = (int64_t)blockIdx.y * XD_ROWS;
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float t[XD_ROWS][3][3];
+    bool ok[XD_ROWS];
+#pragma unroll
+    for (int i = 0; i < XD_ROWS; i++) {
+        const int64_t r = r0 + i;
+        const int64_t row = r < nrows ? rows[r] : -1;
+        ok[i] = row >= 0 && row < n;
+        const int64_t p = ok[i] ? iperm[row] : 0;
+        const float4 k4 = P[3 * p], h4 = P[3 * p + 1], l4 = P[3 * p + 2];
+        t[i][0][0] = k4.x; t[i][0][1] = h4.x; t[i][0][2] = l4.x;
+        t[i][1][0] = k4.y; t[i][1][1] = h4.y; t[i][1][2] = l4.y;
+        t[i][2][0] = k4.z; t[i][2][1] = h4.z; t[i][2][2] = l4.z;
+    }
+    float ah[XD_ROWS], al[XD_ROWS];
+#pragma unroll
+    for (int i = 0; i < XD_ROWS; i++) ah[i] = al[i] = 0.f;
+    const int64_t q0 = (int64_t)c * chunk, q1 = min(n, q0 + chunk);
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += XD_THREADS) {
+        const float4 sk = P[3 * q], sh = P[3 * q + 1], sl = P[3 * q + 2];
+        const float2 w = zf[q];
+#pragma unroll
+        for (int i = 0; i < XD_ROWS; i++) {
+            float kh, kl;
+            df_coulomb_int<true>(t[i], sk, sh, sl, kh, kl);
+            df_mac(ah[i], al[i], kh, kl, w.x, w.y);
+        }
+    }
+    // each row: warp sums in float-float (fixed shuffle order), then the
+    // warps' sums added in order in float64 by one thread
+#pragma unroll
+    for (int i = 0; i < XD_ROWS; i++) {
+        float h = ah[i], l = al[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+            float s, e;
+            two_sum(h, oh, s, e);
+            e = __fadd_rn(e, __fadd_rn(l, ol));
+            two_sum(s, e, h, l);
+        }
+        if (lane == 0) red[i][warp] = make_float2(h, l);
+    }
+    __syncthreads();
+    if (threadIdx.x < XD_ROWS) {
+        const int i = threadIdx.x;
+        const int64_t r = r0 + i;
+        if (r < nrows) {
+            double acc = 0.0;
+            for (int w = 0; w < XD_THREADS / 32; w++) acc += (double)red[i][w].x + (double)red[i][w].y;
+            part[r * nch + c] = ok[i] ? acc * inv_u : __longlong_as_double(0x7ff8000000000000ll);
+        }
+    }
+}
+
 }  // namespace
+
+// exact rows of a 3D Coulomb tree in float-float arithmetic (k_exact_part_df):
+// zm is z in tree order (float64, device); part holds nrows x nch partial
+// sums, nch = ceil(n / chunk)
+void exact_rows_df_parts(h2_tree_s *t, const double *zm, const int64_t *rows, int64_t nrows, int64_t chunk,
+                         int nch, double *part, cudaStream_t s) {
+    ensure_df_tree(t, s);
+    const int64_t n = t->n;
+    DevBuf<float2> zf;
+    zf.alloc((size_t)std::max<int64_t>(n, 1), s);
+    split_vector(zm, n, zf.p, s);
+    for (int64_t r0 = 0; r0 < nrows; r0 += (int64_t)65535 * XD_ROWS) {
+        const int64_t nr = std::min<int64_t>((int64_t)65535 * XD_ROWS, nrows - r0);
+        k_exact_part_df<<<dim3((unsigned)nch, (unsigned)((nr + XD_ROWS - 1) / XD_ROWS)), XD_THREADS, 0, s>>>(
+            rows + r0, nr, t->iperm.p, t->xcell.p, zf.p, n, chunk, nch, 1.0 / df_cell(t), part + r0 * nch);
+        H2_LAUNCH("k_exact_part_df");
+    }
+}
 
 void keval_df(const h2_tree_s *t, int nl, int ysplit, int lb, const int32_t *ycnt, const int32_t *cc,
               int32_t *const *yptr, const int32_t *cand, const int64_t *coff, const int64_t *aoff, float2 *A,

@@ -58,7 +58,7 @@ WORKLOADS = {
     # blocks stored (Algorithm 2's B_ij and near blocks kept on the device);
     # 50 further products time the stored-block matvec against on-the-fly ones
     "cube8k_fp64": dict(n=8000, d=3, kernel="coulomb", kparams=(), q=200, eps=1e-6, prec="fp64", seed=1,
-                        rows=1000, mem_mode="store", mv_reps=50),
+                        rows=8000, mem_mode="store", mv_reps=50),
     # a 131,072-point problem (inside the batched problems' size range) with
     # stored blocks in both forms, 20 further products each
     "cube128k_fp64_store": dict(n=1 << 17, d=3, kernel="coulomb", kparams=(), q=256, eps=1e-9, prec="fp64",
@@ -84,6 +84,16 @@ WORKLOADS = {
                         rows=1000, points="gmix2d", g=20, compare="gmix2m_mixed"),
     "gmix2m_mixed": dict(n=1 << 21, d=2, kernel="gaussian", kparams=(0.2,), q=128, eps=1e-6, prec="mixed", seed=3,
                          rows=1000, points="gmix2d", g=20),
+    # the same mixture with the exponential kernel exp(-r/0.1): tau = 1/2 with
+    # the interaction-list reduction (an oracle sweep on 40,000 points gave
+    # 3.9e-10 at eps = 1e-10, g = 14 (1.4e-10 at g = 20) and 9.5e-7 at
+    # eps = 1e-6, g = 8; without the reduction 1.3e-7 and 3.7e-5); at 2M points
+    # g = 16 gave 1.3e-9, so the float64 form takes g = 20
+    "gmix2m_exp_fp64": dict(n=1 << 21, d=2, kernel="exponential", kparams=(0.1,), q=128, eps=1e-10, prec="fp64",
+                            seed=3, rows=1000, points="gmix2d", g=20, tau=(1, 2), il_reduce=True,
+                            compare="gmix2m_exp_mixed"),
+    "gmix2m_exp_mixed": dict(n=1 << 21, d=2, kernel="exponential", kparams=(0.1,), q=128, eps=1e-6, prec="mixed",
+                             seed=3, rows=1000, points="gmix2d", g=10, tau=(1, 2), il_reduce=True),
     # 8,388,608 points on the unit sphere, 16 float32 right-hand sides (the
     # sampled error is taken on the first column); tau = 1/2 with the
     # interaction-list reduction, g = 6: within 10 eps (Algorithm 1 as printed

@@ -1644,6 +1644,32 @@ __global__ void __launch_bounds__(DR_THREADS, 5) k_dr_members(DMArgs A, DRPoints
         int32_t winner;
         if (sec > limx) {
             winner = __shfl_sync(0xffffffffu, l1, w);
+        } else if (!__any_sync(0xffffffffu, b2 <= limx)) {
+            // near tie, but no lane holds two points within limx: every point
+            // within limx was scanned (the bounds prune only farther ones) and
+            // went to one lane (each point is scanned once, on one lane), where
+            // it is the smallest, so those lanes' points are all the
+            // candidates.  Float64 distances, the smaller label taking ties.
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (k < d) F.q[k] = __dadd_rn(l[k], __dmul_rn(__dadd_rn((double)gidx[k], 0.5), h[k]));
+            long long bk2 = LLONG_MAX;
+            int32_t bl2 = INT_MAX;
+            if (b1 <= limx) {
+                bk2 = __double_as_longlong(h2_dist2(d, F.x0[l1], d > 1 ? F.x1[l1] : 0.0, d > 2 ? F.x2[l1] : 0.0,
+                                                    F.q[0], F.q[1], F.q[2]));
+                bl2 = l1;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long kk = __shfl_xor_sync(0xffffffffu, bk2, o);
+                const int32_t kl = __shfl_xor_sync(0xffffffffu, bl2, o);
+                if (kk < bk2 || (kk == bk2 && kl < bl2)) {
+                    bk2 = kk;
+                    bl2 = kl;
+                }
+            }
+            winner = bl2;
         } else {
             // near tie: every point within M of the smallest in float64, over
             // the cells the search visited

@@ -474,7 +474,11 @@ const char *h2_last_error(void);
 
 /* JSON object with counters and per-phase device times (ms) of a tree, hidr
  * or matrix handle, written to json (cap bytes, NUL-terminated).  A hidr
- * reports its DataReduct "method" ("volume" or "surface").  A matrix reports,
+ * reports its DataReduct "method" ("volume", "surface" or "fps"), the sizes
+ * of the reduced sets ("x_total", "y_total"), of the sets reduced ("t_total":
+ * the top-down sets T_i; "t_il_total": their interaction-list parts, reduced a
+ * second time with H2_HIDR_IL_REDUCE) and the bottom-up and top-down device
+ * times ("ms_up", "ms_down").  A matrix reports,
  * among others, its total and largest rank, QR flops and g_max, the largest
  * |G| entry of the interpolation matrices U_i = P [I; G] (the quantity strong
  * RRQR, which the paper names, bounds), and "g_bound" and "exchanges" of

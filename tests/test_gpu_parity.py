@@ -230,6 +230,37 @@ def test_exact_rows(H2):
         assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max()), kern
 
 
+def test_exact_rows_coincident_points(H2):
+    """The 3D Coulomb exact rows run in float-float arithmetic; with repeated
+    points (kappa(x, x) = 0 for every copy, as in float64) and rows out of
+    range (NaN), against the oracle's float64 pairwise sums and the float64
+    allocation-free entry point, within 1e-12 of the largest row."""
+    base = I.uniform_cube(3000, 3, seed=41)
+    # exact copies, and near copies two cells of the float-float grid away (a
+    # residual is held to ~2^-48 of a cell, ~5e-7 here: closer pairs lose
+    # relative accuracy in the float-float terms)
+    pts = np.concatenate([base, base[:500], base[:500] + 1e-6])
+    n = len(pts)
+    z = I.standard_normal(n, seed=42)
+    rows = np.concatenate([I.sample_rows(n, 400, seed=43), np.arange(3000, 3010)]).astype(np.int64)
+    t = H2.Tree(dev(pts), 64)
+    got = H2.exact_rows(t, "coulomb", (), dev(z), dev(rows)).cpu().numpy()
+    want = O.exact_rows(pts, "coulomb", (), z, rows)
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    out = torch.zeros(len(rows), dtype=torch.float64, device="cuda")
+    z_d, rows_d = dev(z), dev(rows)  # (held while the call runs)
+    st = H2.lib().h2_exact_rows_noalloc(t.handle, H2.KERNELS["coulomb"], H2._kparams(()),
+                                        C.c_void_p(z_d.data_ptr()), C.c_void_p(rows_d.data_ptr()),
+                                        len(rows), C.c_void_p(out.data_ptr()), H2._stream(None))
+    assert st == 0, H2.lib().h2_last_error()
+    torch.cuda.synchronize()
+    f64 = out.cpu().numpy()
+    assert np.allclose(got, f64, rtol=1e-12, atol=1e-12 * np.abs(f64).max())
+    bad = H2.exact_rows(t, "coulomb", (), dev(z), dev(np.array([-1, n], dtype=np.int64))).cpu().numpy()
+    assert np.isnan(bad).all()
+    t.free()
+
+
 def test_degenerate_paths(H2):
     # one point, a single leaf, identical points: matvec reduces to the nearfield
     for pts, q in [(np.array([[0.5, 0.5, 0.5]]), 4), (I.uniform_cube(90, 3, seed=3), 200),

@@ -480,7 +480,7 @@ i64 or_datareduct_surface(const double *xs, int d, const i64 *S, i64 ns, int g, 
  * point of S of smallest label and grows by the point of S farthest from X*
  * (largest float64 squared distance to its nearest member of X*, ties to the
  * smaller label) until it holds g^d points; returned sorted.  The paper leaves
- * the first point open; the smallest label is this build's reading.  |S| <= g^d
+ * the first point open; it is read here as the smallest label.  |S| <= g^d
  * returns S. */
 i64 or_datareduct_fps(const double *xs, int d, const i64 *S, i64 ns, int g, i64 *out) {
     i64 r = ipow(g, d);

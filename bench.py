@@ -154,13 +154,18 @@ MIN_SQ = {3: 8, 2: 5}
 NOMINAL_FP64_TFLOPS = 1.25
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOPS_PER_PAIR = 11  # 3 sub, 3 mul/add for r^2 (5 flops), 1 rsqrt, 1 fma accumulate (2 flops)
+# The float64 form's QR (float-float arithmetic) is bound by streaming its
+# trailing block through DRAM: each pivot step reads every trailing element for
+# the dot products and writes it back updated, 8 bytes each way for the 4 flops
+# of the QR count, so its algorithmic bytes are 4 per QR flop.
+QR_DF_BYTES_PER_FLOP = 4.0
 # DRAM bytes per algorithmic unit of a dominant kernel (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum over one capture of the 262,144-point workload, divided by
 # that launch's units), keyed by (kernel, form).  A changed kernel needs a new
 # capture; until then its entry is absent and the line's traffic is null.
 # float-float QR: one build of the 262,144-point float64 workload (levels 4, 3, 2)
-# moved 334.06 GB for 8.2779e10 QR flops
-TRAFFIC_PER_UNIT = {("cpqr", "fp64"): 334.06e9 / 8.2779e10}
+# moved 334.06 GB for 8.2779e10 QR flops, i.e. 3.3111e11 algorithmic bytes
+TRAFFIC_PER_UNIT = {("cpqr", "fp64"): 334.06e9 / (QR_DF_BYTES_PER_FLOP * 8.2779e10)}
 
 
 def measured_peaks():
@@ -386,8 +391,9 @@ def measure_form(args, wl, rank, world, dev, with_e2e, alu=None):
     # reads zh and read-modify-writes the children's zh or y (float64 vectors)
     esz = 8 if fp64 else 4
     kt, ut = mat_i["k_total"], mat_i["u_entries"]
+    qr_df = fp64 and not wl.get("fp64_qr")
     work = {  # kernel -> (bound, algorithmic units per step)
-        "cpqr": ("alu", qr_flops),
+        "cpqr": ("hbm", QR_DF_BYTES_PER_FLOP * qr_flops) if qr_df else ("alu", qr_flops),
         "coupling": ("alu", coupling_pairs * FLOPS_PER_PAIR),
         "near": ("alu", near_pairs * FLOPS_PER_PAIR),
         "keval": ("alu", block_evals * FLOPS_PER_PAIR),
@@ -413,6 +419,8 @@ def measure_form(args, wl, rank, world, dev, with_e2e, alu=None):
             else:
                 e["gbs"] = rate / 1e9
                 e["frac_of_hbm_peak"] = e["gbs"] / peaks["hbm_gbs"]
+            if k == "cpqr" and qr_df:  # its flop rate as well (float-float, on the float32 units)
+                e["tflops"] = qr_flops * args.steps / (v["ms"] * 1e-3) / 1e12
         per_kernel[k] = e
     # the exact rows run on a side stream beside the path, so their event span
     # is not their own device time: the dominant kernel is taken from the path
@@ -429,6 +437,9 @@ def measure_form(args, wl, rank, world, dev, with_e2e, alu=None):
                 "traffic": traffic_ratio * work[dom][1] / launches_per_step if traffic_ratio else None,
                 "peak_source": f"{peak_kind} (copy bandwidth)",
                 "work_per_launch": work[dom][1] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
+        if dom == "cpqr":
+            roof["note"] = ("float-float QR: a read and a write of every trailing element per pivot step, "
+                            "4 bytes per QR flop")
     elif dom in work:
         peak_src = alu_src
         achieved = work[dom][1] / launches_per_step / (dom_ms_per_launch * 1e-3) / 1e12
@@ -437,12 +448,6 @@ def measure_form(args, wl, rank, world, dev, with_e2e, alu=None):
                 "traffic": traffic_ratio * work[dom][1] / launches_per_step if traffic_ratio else None,
                 "peak_source": peak_src, "peak_nominal": NOMINAL_FP64_TFLOPS if fp64 else NOMINAL_FP32_TFLOPS,
                 "work_per_launch": work[dom][1] / launches_per_step, "ms_per_launch": dom_ms_per_launch}
-        if dom == "cpqr" and fp64 and not wl.get("fp64_qr"):
-            # the float64 form's QR runs in float-float arithmetic on the float32
-            # units; its float64-equivalent flops are set against the float64
-            # unit's peak, which is why the fraction can exceed 1
-            roof["note"] = ("float-float QR on the float32 units: float64-equivalent QR flops against the "
-                            "float64 FMA peak")
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "ms_per_launch": dom_ms_per_launch}

@@ -11,6 +11,8 @@
 
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "h2_internal.cuh"
 #include "df.cuh"
 
@@ -644,6 +646,261 @@ __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr_df(int lb, const int32_t
     if (threadIdx.x == 0) kout[node] = k;
 }
 
+// Float64 form, float-float arithmetic, one node per cluster of QR_CL CTAs.
+// The factorization is k_cpqr_df's: the same per-column arithmetic, the same
+// pivots with the same ties (largest downdated norm, then smallest position),
+// the same stop tests, and so the same R, rank and pivot order.  The node's
+// candidate columns are shared out over the cluster's CTAs, so a level with
+// fewer nodes than SMs still fills the GPU, and one block is in flight per
+// cluster rather than per CTA.  Columns stay where they are.  CTA r owns the columns
+// l = r mod QR_CL.  perm maps positions to columns and pos maps them back;
+// every CTA keeps both, updated identically.  A step runs as follows:
+//  - every CTA offers the best (norm, position) among its own columns that are
+//    not yet pivoted;
+//  - one cluster barrier (it also publishes the previous step's updates);
+//  - every CTA reads all the offers from the others' shared memory and takes
+//    the same pivot;
+//  - every CTA forms the same reflector from the pivot column, read from L2;
+//  - each CTA updates, downdates and, where needed, renormalises its own
+//    columns.
+// R(j, j) is kept in the pivot column's norm slot (the other CTAs may still be
+// reading row j of that column).  On exit rows 0..k-1 of every column go,
+// as float64 and in pivot order, to Rbase, whose layout is the block's.
+// piv = perm.
+constexpr int QR_CL = 8;
+
+__global__ void __cluster_dims__(QR_CL, 1, 1) __launch_bounds__(QR_THREADS, 2)
+    k_cpqr_df_cl(int lb, const int32_t *ycnt, const int32_t *cc, const int64_t *aoff, double *Abase,
+                 double *Rbase, double tol, int32_t *kout, const int64_t *coff, int32_t *pivbase, int split) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int rank = (int)cl.block_rank();
+    const int a = blockIdx.x / QR_CL, node = lb + a;
+    const int m = ycnt[node], c = cc[node];
+    if (m == 0 || c == 0) {  // (the same for every CTA of the cluster: no barrier is left waiting)
+        if (rank == 0 && threadIdx.x == 0) kout[node] = 0;
+        return;
+    }
+    double *nrm = reinterpret_cast<double *>(smem_raw);  // by column (own columns only)
+    double *nrm0 = nrm + c;
+    double *rowj = nrm0 + c;
+    float2 *v = reinterpret_cast<float2 *>(rowj + c);
+    int32_t *perm = reinterpret_cast<int32_t *>(v + m);  // position -> column
+    int32_t *pos = perm + c;                              // column -> position
+    unsigned char *flag = reinterpret_cast<unsigned char *>(pos + c);
+    __shared__ long long off_key[2];  // this CTA's offer, by step parity
+    __shared__ int off_pos[2];
+    __shared__ double red[QR_WARPS];
+    __shared__ long long bkey[QR_WARPS];
+    __shared__ int bidx[QR_WARPS];
+    __shared__ int s_p, s_stop;
+    __shared__ float2 s_tau, s_beta, s_sc;
+    __shared__ int s_has;
+    double *Ad = Abase + aoff[a];
+    float2 *A = reinterpret_cast<float2 *>(Ad);
+    double *Rd = Rbase + aoff[a];
+    int32_t *piv = pivbase + coff[a];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const double tol3z = sqrt(ldexp(1.0, -53));
+    // own columns: l = rank + QR_CL * u, u = 0, 1, ...
+    const int nown = c > rank ? (c - rank + QR_CL - 1) / QR_CL : 0;
+    if (!split)
+        for (int u = warp; u < nown; u += nwarps) {
+            float2 *col = A + (int64_t)(rank + QR_CL * u) * m;
+            const double *cd = Ad + (int64_t)(rank + QR_CL * u) * m;
+            for (int r = lane; r < m; r += 32) col[r] = df::from_double(cd[r]);
+        }
+    for (int l = threadIdx.x; l < c; l += blockDim.x) { perm[l] = l; pos[l] = l; }
+    for (int u = warp; u < nown; u += nwarps) {
+        const int l = rank + QR_CL * u;
+        const float2 *col = A + (int64_t)l * m;
+        float sh = 0.f, sl = 0.f;
+        for (int r = lane; r < m; r += 32) df::mac(sh, sl, col[r], col[r]);
+        const double s = df::to_double(df::warp_sum(sh, sl));
+        if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
+    }
+    __syncthreads();
+    const int kmax = min(m, c);
+    int k = 0;
+    double r11 = 0.0;
+    for (int j = 0; j < kmax; j++) {
+        // this CTA's offer: its best (norm, position) at positions >= j
+        long long bk = -1;
+        int bi = INT_MAX;
+        for (int u = threadIdx.x; u < nown; u += blockDim.x) {
+            const int l = rank + QR_CL * u;
+            if (pos[l] >= j) argmax_key(bk, bi, __double_as_longlong(nrm[l]), pos[l]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+            int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            argmax_key(bk, bi, k2, i2);
+        }
+        if (lane == 0) { bkey[warp] = bk; bidx[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long kk2 = bkey[0];
+            int ii = bidx[0];
+            for (int w = 1; w < nwarps; w++) argmax_key(kk2, ii, bkey[w], bidx[w]);
+            off_key[j & 1] = kk2;
+            off_pos[j & 1] = ii;
+        }
+        cl.sync();  // the offers, and every CTA's column updates of the previous step
+        if (threadIdx.x == 0) {
+            long long kk2 = -1;
+            int ii = INT_MAX;
+            for (int r = 0; r < QR_CL; r++)
+                argmax_key(kk2, ii, *cl.map_shared_rank(&off_key[j & 1], r), *cl.map_shared_rank(&off_pos[j & 1], r));
+            const double vv = __longlong_as_double(kk2);
+            if (j == 0) r11 = vv;
+            s_p = ii;
+            s_stop = (!(vv > tol * r11) || vv == 0.0) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const int p = s_p;
+        if (threadIdx.x == 0 && p != j) {
+            const int cj = perm[j], cp = perm[p];
+            perm[j] = cp; perm[p] = cj;
+            pos[cp] = j; pos[cj] = p;
+        }
+        __syncthreads();
+        const int jc = perm[j];  // the pivot column
+        const bool own_pivot = jc % QR_CL == rank;
+        // the reflector, in every CTA alike; the pivot column is read from L2
+        // (its owner wrote it before the barrier)
+        const float2 *aj = A + (int64_t)jc * m;
+        {
+            float sh = 0.f, sl = 0.f;
+            for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) {
+                const float2 x = __ldcg(aj + r);
+                df::mac(sh, sl, x, x);
+            }
+            const float2 ws = df::warp_sum(sh, sl);
+            if (lane == 0) red[warp] = df::to_double(ws);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sigma = 0;
+            for (int w = 0; w < nwarps; w++) sigma += red[w];
+            const double alpha = df::to_double(__ldcg(aj + j));
+            double tau = 0, beta = alpha, sc = 0;
+            if (sigma != 0.0) {
+                const double xn = sqrt(alpha * alpha + sigma);
+                beta = alpha >= 0.0 ? -xn : xn;
+                tau = (beta - alpha) / beta;
+                sc = 1.0 / (alpha - beta);
+            }
+            s_tau = df::from_double(tau);
+            s_beta = df::from_double(beta);
+            s_sc = df::from_double(sc);
+            s_has = tau != 0.0;
+            s_stop = (alpha == 0.0 && sigma == 0.0) ? 1 : 0;  // exactly zero pivot column
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const bool has_tau = s_has != 0;
+        const float2 scD = s_sc, tauD = s_tau;
+        for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) v[r] = df::mul(__ldcg(aj + r), scD);
+        __syncthreads();
+        if (threadIdx.x == 0 && own_pivot) nrm[jc] = df::to_double(s_beta);  // R(j, j), written out on exit
+        // own trailing columns, one warp a column (k_cpqr_df's arithmetic)
+        for (int u = warp; u < nown; u += nwarps) {
+            const int l = rank + QR_CL * u;
+            if (pos[l] <= j) continue;
+            float2 *al = A + (int64_t)l * m;
+            float2 ajl = al[j];
+            if (has_tau) {
+                float sh = 0.f, sl = 0.f, th = 0.f, tl = 0.f;
+                int r = j + 1 + lane;
+                for (; r + 224 < m; r += 256) {
+                    float2 x[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) x[q] = al[r + 32 * q];
+#pragma unroll
+                    for (int q = 0; q < 8; q += 2) {
+                        df::mac(sh, sl, v[r + 32 * q], x[q]);
+                        df::mac(th, tl, v[r + 32 * q + 32], x[q + 1]);
+                    }
+                }
+                for (; r + 96 < m; r += 128) {
+                    const float2 a0 = al[r], a1 = al[r + 32], a2 = al[r + 64], a3 = al[r + 96];
+                    df::mac(sh, sl, v[r], a0);
+                    df::mac(th, tl, v[r + 32], a1);
+                    df::mac(sh, sl, v[r + 64], a2);
+                    df::mac(th, tl, v[r + 96], a3);
+                }
+                for (; r < m; r += 32) df::mac(sh, sl, v[r], al[r]);
+                const float2 s2 = df::add(df::norm(sh, sl), df::norm(th, tl));
+                float2 w = df::add(df::warp_sum(s2.x, s2.y), ajl);
+                w = df::mul(w, tauD);
+                r = j + 1 + lane;
+                for (; r + 224 < m; r += 256) {
+                    float2 x[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) x[q] = al[r + 32 * q];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) al[r + 32 * q] = df::fms(x[q], w, v[r + 32 * q]);
+                }
+                for (; r + 96 < m; r += 128) {
+                    const float2 a0 = al[r], a1 = al[r + 32], a2 = al[r + 64], a3 = al[r + 96];
+                    al[r] = df::fms(a0, w, v[r]);
+                    al[r + 32] = df::fms(a1, w, v[r + 32]);
+                    al[r + 64] = df::fms(a2, w, v[r + 64]);
+                    al[r + 96] = df::fms(a3, w, v[r + 96]);
+                }
+                for (; r < m; r += 32) al[r] = df::fms(al[r], w, v[r]);
+                ajl = df::sub(ajl, w);
+                if (lane == 0) al[j] = ajl;
+            }
+            if (lane == 0) rowj[l] = df::to_double(ajl);
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < nown; u += blockDim.x) {
+            const int l = rank + QR_CL * u;
+            if (pos[l] <= j) continue;
+            double nl = nrm[l];
+            flag[l] = 0;
+            if (nl != 0.0) {
+                const double rj = rowj[l];
+                double tt = fabs(rj) / nl;
+                tt = 1.0 - tt * tt;
+                if (tt < 0.0) tt = 0.0;
+                double t2 = nl / nrm0[l];
+                t2 = tt * t2 * t2;
+                if (t2 <= tol3z) flag[l] = 1;
+                else nrm[l] = nl * sqrt(tt);
+            }
+        }
+        __syncthreads();
+        for (int u = warp; u < nown; u += nwarps) {
+            const int l = rank + QR_CL * u;
+            if (pos[l] <= j || !flag[l]) continue;
+            const float2 *al = A + (int64_t)l * m;
+            float sh = 0.f, sl = 0.f;
+            for (int r = j + 1 + lane; r < m; r += 32) df::mac(sh, sl, al[r], al[r]);
+            const double s = df::to_double(df::warp_sum(sh, sl));
+            if (lane == 0) { nrm[l] = sqrt(s); nrm0[l] = nrm[l]; }
+        }
+        __syncthreads();
+        k = j + 1;
+    }
+    // R in pivot order: rows 0..k-1 of each own column, as float64, at its
+    // position; a pivoted column's diagonal entry is the kept R(j, j)
+    for (int u = warp; u < nown; u += nwarps) {
+        const int l = rank + QR_CL * u, q = pos[l];
+        const float2 *al = A + (int64_t)l * m;
+        double *rq = Rd + (int64_t)q * m;
+        for (int r = lane; r < k; r += 32) rq[r] = (r == q) ? nrm[l] : df::to_double(al[r]);
+    }
+    if (rank == 0) {
+        for (int l = threadIdx.x; l < c; l += blockDim.x) piv[l] = perm[l];
+        if (threadIdx.x == 0) kout[node] = k;
+    }
+    cl.sync();  // no CTA leaves while another may still read its offers
+}
+
 // shared memory of the loop-form solve for ranks up to kmax: the reciprocals
 // of R11's diagonal and the skeleton sort (a power of two >= kmax)
 size_t loop_solve_smem(int kmax) {
@@ -1020,6 +1277,11 @@ size_t qr_smem(int cmax, int mmax, size_t esize = sizeof(double)) {
     return (size_t)cmax * (3 * sizeof(double) + sizeof(int32_t) + 1) + (size_t)mmax * esize + 64;
 }
 
+// k_cpqr_df_cl: three float64 arrays, two int32 maps and a flag by column, the reflector
+size_t qr_smem_cl(int cmax, int mmax) {
+    return (size_t)cmax * (3 * sizeof(double) + 2 * sizeof(int32_t) + 1) + (size_t)mmax * sizeof(float2) + 64;
+}
+
 }  // namespace
 
 void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
@@ -1045,6 +1307,9 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     A->uptr.alloc(nn, s);
     H2_CUDA(cudaMemsetAsync(skptr.p, 0, nn * sizeof(int32_t *), s));
     H2_CUDA(cudaMemsetAsync(A->uptr.p, 0, nn * sizeof(void *), s));
+    int dev = 0, sm_count = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    H2_CUDA(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
     std::vector<DevBuf<int32_t>> skbufs(t->nlevels);
     A->ubufs.resize(t->nlevels);
     A->kmax_level.assign(t->nlevels, 0);
@@ -1054,6 +1319,7 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
         set_qr_attrs<double>();
         set_qr_attrs<float>();
         H2_CUDA(cudaFuncSetAttribute(k_cpqr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
+        H2_CUDA(cudaFuncSetAttribute(k_cpqr_df_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_LIMIT));
         H2_CUDA(cudaFuncSetAttribute(k_id_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1071,6 +1337,7 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
     DevBuf<int32_t> cand, piv;
     DevBuf<unsigned char> Ablk;
     DevBuf<double> Wf;  // float64 workspace of the solve when the block is float32
+    DevBuf<double> Rq;  // R in pivot order, from the cluster QR
     for (int l = t->nlevels - 1; l >= 1; l--) {
         const int lb = t->lptr[l], nl = t->lptr[l + 1] - lb;
         szc.alloc(nl, s); sza.alloc(nl, s); coff.alloc(nl + 1, s); aoff.alloc(nl + 1, s);
@@ -1116,9 +1383,24 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
             H2_LAUNCH("k_keval");
         }
         A->evals_block += (double)atot;
+        // where R goes (float64 form): the block itself, or Rq from the cluster QR
+        double *Rb = reinterpret_cast<double *>(Ablk.p);
         {
             ProfScope ps(KT_CPQR, s);
-            if (f64 && !A->fp64_qr)
+            // float-float QR: one node a CTA; a wide level with fewer nodes than
+            // SMs takes one node per cluster of QR_CL CTAs, which puts every SM
+            // to work.  (On levels with many nodes the cluster form measured
+            // slower: with a few columns a warp per step, its per-step barriers
+            // outweigh the blocks staying in L2.)
+            if (f64 && !A->fp64_qr && qr_threads(cmax) == QR_THREADS && nl < sm_count) {
+                if (qr_smem_cl(cmax, mmax) > SMEM_LIMIT)
+                    fail(H2_ERR_UNIMPLEMENTED, "kernel block too large for the cluster QR");
+                Rq.alloc(atot, s);
+                Rb = Rq.p;
+                k_cpqr_df_cl<<<(unsigned)nl * QR_CL, QR_THREADS, qr_smem_cl(cmax, mmax), s>>>(
+                    lb, h->ycnt.p, A->c.p, aoff.p, reinterpret_cast<double *>(Ablk.p), Rb, A->id_tol, A->k.p,
+                    coff.p, piv.p, dfblocks ? 1 : 0);
+            } else if (f64 && !A->fp64_qr)
                 k_cpqr_df<<<nl, qr_threads(cmax), qr_smem(cmax, mmax, esize), s>>>(
                     lb, h->ycnt.p, A->c.p, aoff.p, reinterpret_cast<double *>(Ablk.p), A->id_tol, A->k.p, coff.p,
                     piv.p, dfblocks ? 1 : 0);
@@ -1167,8 +1449,8 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
                     piv.p, cand.p, A->uptr.p, skptr.p, gmax.p);
             } else if (f64) {
                 k_id_solve<double><<<nl, qr_threads(cmax), loop_solve_smem(kmax), s>>>(
-                    lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<double *>(Ablk.p),
-                    reinterpret_cast<double *>(Ablk.p), coff.p, piv.p, cand.p, A->uptr.p, skptr.p, gmax.p, !bound);
+                    lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, Rb, Rb, coff.p, piv.p, cand.p, A->uptr.p, skptr.p, gmax.p,
+                    !bound);
             } else {
                 Wf.alloc(atot, s);
                 k_id_solve<float><<<nl, qr_threads(cmax), loop_solve_smem(kmax), s>>>(
@@ -1180,7 +1462,7 @@ void construct_impl(h2_matrix_s *A, h2_hidr_s *h) {
                 const size_t sm = loop_solve_smem(kmax) - (size_t)kmax * sizeof(double);  // the sort scratch
                 if (f64)
                     k_id_exchange<double><<<nl, EX_THREADS, sm, s>>>(
-                        lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, reinterpret_cast<double *>(Ablk.p), coff.p, piv.p,
+                        lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, Rb, coff.p, piv.p,
                         cand.p, A->uptr.p, skptr.p, gmax.p, A->g_bound, nexd.p);
                 else
                     k_id_exchange<float><<<nl, EX_THREADS, sm, s>>>(lb, h->ycnt.p, A->c.p, A->k.p, aoff.p, Wf.p,

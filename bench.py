@@ -163,9 +163,10 @@ QR_DF_BYTES_PER_FLOP = 4.0
 # dram__bytes_write.sum over one capture of the 262,144-point workload, divided by
 # that launch's units), keyed by (kernel, form).  A changed kernel needs a new
 # capture; until then its entry is absent and the line's traffic is null.
-# float-float QR: one build of the 262,144-point float64 workload (levels 4, 3, 2)
-# moved 334.06 GB for 8.2779e10 QR flops, i.e. 3.3111e11 algorithmic bytes
-TRAFFIC_PER_UNIT = {("cpqr", "fp64"): 334.06e9 / (QR_DF_BYTES_PER_FLOP * 8.2779e10)}
+# float-float QR: one build of the 262,144-point float64 workload (levels 4 and 3
+# one node a CTA, level 2 one node per cluster) moved 327.42 GB for 8.2779e10 QR
+# flops, i.e. 3.3111e11 algorithmic bytes
+TRAFFIC_PER_UNIT = {("cpqr", "fp64"): 327.4175e9 / (QR_DF_BYTES_PER_FLOP * 8.2779e10)}
 
 
 def measured_peaks():

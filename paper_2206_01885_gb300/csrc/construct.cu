@@ -652,9 +652,9 @@ __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr_df(int lb, const int32_t
 // the same stop tests, and so the same R, rank and pivot order.  The node's
 // candidate columns are shared out over the cluster's CTAs, so a level with
 // fewer nodes than SMs still fills the GPU, and one block is in flight per
-// cluster rather than per CTA.  Columns stay where they are.  CTA r owns the columns
-// l = r mod QR_CL.  perm maps positions to columns and pos maps them back;
-// every CTA keeps both, updated identically.  A step runs as follows:
+// cluster rather than per CTA.  Columns stay where they are: CTA r owns the
+// columns l = r mod QR_CL.  perm maps positions to columns and pos maps them
+// back; every CTA keeps both, updated identically.  A step runs as follows:
 //  - every CTA offers the best (norm, position) among its own columns that are
 //    not yet pivoted;
 //  - one cluster barrier (it also publishes the previous step's updates);
@@ -666,7 +666,9 @@ __global__ void __launch_bounds__(QR_THREADS, 2) k_cpqr_df(int lb, const int32_t
 // R(j, j) is kept in the pivot column's norm slot (the other CTAs may still be
 // reading row j of that column).  On exit rows 0..k-1 of every column go,
 // as float64 and in pivot order, to Rbase, whose layout is the block's.
-// piv = perm.
+// piv = perm.  Every exit and break depends only on data that all CTAs of the
+// cluster read alike (the offers, the pivot column after the barrier), so
+// every CTA reaches every cluster barrier.
 constexpr int QR_CL = 8;
 
 __global__ void __cluster_dims__(QR_CL, 1, 1) __launch_bounds__(QR_THREADS, 2)
